@@ -1,0 +1,402 @@
+/*
+ * lsnif.h -- C ABI of a GB300-native (sm_103a) implementation of the LSNIF
+ * neural ray-intersection query.
+ *
+ * LSNIF (Fujieda, Kao, Harada, "LSNIF: Locally-Subdivided Neural Intersection
+ * Function", PACMCGIT 8(1), 2025) replaces the bottom-level BVH of one object
+ * with a small per-object model (Sec. 3, Fig. 2): the ray is clipped to the
+ * object's AABB, a 3D-DDA walks a binary V^3 occupancy grid, the ray's entry
+ * and exit points of occupied voxels are encoded by a multiresolution sparse
+ * hash grid, the concatenated features go through an MLP, and the MLP returns
+ * occlusion, hit distance, shading normal, albedo and material index.
+ * Objects are trained offline, stored, and loaded at run time (Sec. 3.3);
+ * many objects are served by one dispatch grouped by object (Sec. 4).
+ *
+ * Conventions for every entry point:
+ *  - The return value is a status code: LSNIF_OK (0) on success,
+ *    LSNIF_PENDING (1) for "still running", a negative LSNIF_ERR_* code on
+ *    failure. No C++ exception crosses this boundary. On failure,
+ *    lsnif_last_error() returns a message for the calling thread and no
+ *    output buffer is guaranteed to have been written.
+ *  - "device pointer" means memory of the context's CUDA device
+ *    (cudaMalloc, or a PyTorch CUDA tensor's data pointer); "host pointer"
+ *    means ordinary process memory. Buffers passed in are owned by the
+ *    caller and are not retained after the call returns, except for the
+ *    serving calls (lsnif_submit), whose buffers must stay valid until
+ *    lsnif_poll reports completion.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream). Calls
+ *    that take a stream enqueue their kernels on it and return without
+ *    waiting unless stated otherwise; outputs are ready when the stream
+ *    reaches that point.
+ *  - A context is used by one host thread at a time (it is not internally
+ *    locked); separate contexts are independent.
+ *  - Rays are structure-of-arrays FP32 in the object's space (the mesh's
+ *    coordinate frame): origin, direction (need not be unit), tmin, tmax.
+ *    n = 0 is a no-op returning LSNIF_OK. A ray with a NaN component or an
+ *    all-zero direction is reported as a miss, not an error.
+ */
+#ifndef LSNIF_H
+#define LSNIF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LSNIF_API_VERSION 1
+
+#if defined(__GNUC__)
+#define LSNIF_API __attribute__((visibility("default")))
+#else
+#define LSNIF_API
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define LSNIF_OK 0
+#define LSNIF_PENDING 1
+#define LSNIF_ERR_INVALID_ARG (-1)   /* a pointer, size or config field is invalid */
+#define LSNIF_ERR_BAD_HANDLE (-2)    /* unknown object handle or ticket */
+#define LSNIF_ERR_OUT_OF_MEMORY (-3) /* a device or host allocation failed */
+#define LSNIF_ERR_OVER_BUDGET (-4)   /* the context's device-memory budget is exhausted */
+#define LSNIF_ERR_CORRUPT (-5)       /* a serialized object failed validation */
+#define LSNIF_ERR_TIMEOUT (-6)       /* lsnif_poll reached its time limit */
+#define LSNIF_ERR_CUDA (-7)          /* a CUDA runtime call failed */
+#define LSNIF_ERR_DEVICE_CHECK (-8)  /* a kernel reported a failed internal check or wait */
+#define LSNIF_ERR_BUSY (-9)          /* the request queue is full */
+#define LSNIF_ERR_UNSUPPORTED (-10)  /* configuration not supported by the requested path */
+
+typedef struct lsnif_ctx lsnif_ctx; /* opaque; owns every object and all scratch memory */
+typedef uint32_t lsnif_obj;         /* object handle; 0 is never a valid handle */
+
+/* Arithmetic of the query. FP32_PLAIN: FP32 tables, FP32 SIMT network, one
+ * kernel per stage with global intermediates. BF16_FUSED: FP16 table copies,
+ * FP32 interpolation, BF16 tcgen05 tensor-core MLP with FP32 accumulation,
+ * gather + every layer + decode in one kernel (Sec. 5: half precision,
+ * fused layers). Traversal is FP32 in both. */
+enum lsnif_precision { LSNIF_FP32_PLAIN = 0, LSNIF_BF16_FUSED = 1 };
+
+/* Hidden-layer activation: ReLU, or leaky ReLU with slope 0.01 (Sec. 5.1). */
+enum lsnif_activation { LSNIF_RELU = 0, LSNIF_LEAKY_RELU = 1 };
+
+#define LSNIF_MAX_LEVELS 32
+#define LSNIF_MAX_HIDDEN 8
+
+/* Hyper-parameters of one object (Sec. 3.1, 3.2, 5.1). */
+typedef struct lsnif_config {
+    int32_t V;          /* voxels per axis of the occupancy grid (2..1024) */
+    int32_t H;          /* cap on boundary points per ray, even (2..64); H/2 voxels */
+    int32_t L;          /* hash-grid levels (1..LSNIF_MAX_LEVELS) */
+    int32_t F;          /* features per level: 1, 2 or 4 */
+    int32_t log2_T;     /* table entries per level = 2^log2_T (4..24) */
+    int32_t N_min;      /* coarsest lattice resolution */
+    int32_t N_max;      /* finest lattice resolution (>= N_min) */
+    int32_t n_hidden;   /* hidden layers (1..LSNIF_MAX_HIDDEN) */
+    int32_t width;      /* neurons per hidden layer (16..256, multiple of 16) */
+    int32_t n_mat;      /* materials; the network has 8 + n_mat outputs (1..56) */
+    int32_t activation; /* enum lsnif_activation */
+    float table_init;   /* features start U(-table_init, table_init) (paper: 1e-4) */
+    uint64_t seed;      /* seed of the built-in initialisation */
+} lsnif_config;
+
+/* A triangle mesh (host pointers, read during the call only). */
+typedef struct lsnif_mesh {
+    const float *verts;      /* nv x 3 positions */
+    const int32_t *tris;     /* nt x 3 vertex indices */
+    const float *vnormals;   /* nv x 3 unit shading normals, or NULL (training labels need them) */
+    const int32_t *tri_mat;  /* nt material indices in [0, n_mat), or NULL (all 0) */
+    const float *mat_albedo; /* n_mat x 3 RGB, or NULL (0.5 grey) */
+    int64_t nv, nt;
+} lsnif_mesh;
+
+/* How lsnif_load_object builds an object. Exactly one source of geometry:
+ * a serialized blob, or a mesh (voxelized on load, Sec. 3.1). Parameters
+ * come from the blob, from `tables`/`mlp` when given, or from the built-in
+ * seeded initialisation (tables uniform, weights Xavier-uniform, biases 0). */
+typedef struct lsnif_object_desc {
+    lsnif_config cfg;        /* ignored when blob != NULL */
+    lsnif_mesh mesh;         /* used when blob == NULL */
+    const float *tables;     /* host, L x 2^log2_T x F FP32, or NULL */
+    const float *mlp;        /* host, packed FP32 [W0 (out x in, row-major), b0, W1, b1, ...], or NULL */
+    int32_t keep_mesh;       /* nonzero: keep the mesh on the device for training labels */
+    const void *blob;        /* host, from lsnif_save_object, or NULL */
+    size_t blob_len;
+} lsnif_object_desc;
+
+/* Read-only facts about a loaded object. */
+typedef struct lsnif_object_info {
+    lsnif_config cfg;
+    float bmin[3], bmax[3];              /* AABB (object space) */
+    int32_t res[LSNIF_MAX_LEVELS];       /* lattice resolution per level */
+    int64_t n_occupied;                  /* occupied voxels */
+    int64_t n_params_mlp;                /* weights + biases */
+    size_t device_bytes;                 /* device memory charged to the budget */
+    size_t footprint_fp16_bytes;         /* paper's storage model: bits + FP16 tables + FP16 network */
+} lsnif_object_info;
+
+/* Rays, structure of arrays, DEVICE pointers (host pointers for
+ * lsnif_query_rays_host). obj: per-ray handle (NULL: every ray uses
+ * single_obj). */
+typedef struct lsnif_rays {
+    const float *ox, *oy, *oz;
+    const float *dx, *dy, *dz;
+    const float *tmin, *tmax;
+    const uint32_t *obj;
+    lsnif_obj single_obj;
+    int64_t n;
+} lsnif_rays;
+
+/* Per-ray results; every pointer may be NULL (not written). For rays that
+ * meet no occupied voxel: hit 0, t +inf, normal 0, material -1, albedo 0,
+ * logits NaN. Otherwise the decoded network outputs (Sec. 5.3): hit =
+ * (occlusion logit > 0) and tmin <= t <= tmax; t = t0 + sigmoid(z1)(t1-t0)
+ * over the ray's clipped AABB interval [t0, t1]; normal = z2..4 normalised;
+ * albedo = sigmoid(z5..7); material = argmax z8.. (lowest index on ties).
+ * logits: n x (8 + n_mat) raw network outputs, row-major. */
+typedef struct lsnif_hits {
+    uint8_t *hit;
+    float *t;
+    float *nx, *ny, *nz;
+    int32_t *mat;
+    float *ar, *ag, *ab;
+    float *logits;
+} lsnif_hits;
+
+/* ---- context ------------------------------------------------------------ */
+
+/* Create a context on CUDA device `device`. mem_budget_bytes caps the device
+ * memory the context may hold (objects + scratch); 0 means no cap.
+ * Errors: INVALID_ARG (out == NULL or bad device), CUDA, OUT_OF_MEMORY. */
+LSNIF_API int lsnif_create(lsnif_ctx **out, int device, size_t mem_budget_bytes);
+
+/* Destroy a context: waits for its queued work, frees every object and all
+ * scratch memory. NULL is accepted. */
+LSNIF_API int lsnif_destroy(lsnif_ctx *ctx);
+
+/* Message of the most recent failing call on this thread ("" if none). The
+ * string is owned by the library and valid until the next call. */
+LSNIF_API const char *lsnif_last_error(void);
+
+/* API version compiled into the library (LSNIF_API_VERSION). */
+LSNIF_API int lsnif_version(void);
+
+/* Wait for `stream` and report kernel-side failures since the last check:
+ * DEVICE_CHECK when a kernel flagged an unknown object handle, a failed
+ * internal bound check or a bounded wait that gave up (the flag is then
+ * cleared); CUDA when the stream itself failed. Kernels never trap. */
+LSNIF_API int lsnif_check(lsnif_ctx *ctx, void *stream);
+
+/* ---- objects (Sec. 3.3: voxels, grid and weights stored, loaded at run time) */
+
+/* Build an object from a mesh (FP64 separating-axis voxelization of the
+ * mesh's AABB, Sec. 3.1) or from a serialized blob, upload it and return its
+ * handle in *out. All desc pointers are host pointers read during the call.
+ * Errors: INVALID_ARG (bad config or mesh), CORRUPT (bad blob),
+ * OVER_BUDGET, OUT_OF_MEMORY, CUDA. */
+LSNIF_API int lsnif_load_object(lsnif_ctx *ctx, const lsnif_object_desc *desc, lsnif_obj *out);
+
+/* Serialize an object (config, AABB, occupancy, FP32 tables and network)
+ * into buf. With buf == NULL or *inout_len too small, sets *inout_len to
+ * the size needed and returns INVALID_ARG (buf != NULL) or OK (buf == NULL).
+ * The blob round-trips bit-exactly through lsnif_load_object. */
+LSNIF_API int lsnif_save_object(lsnif_ctx *ctx, lsnif_obj obj, void *buf, size_t *inout_len);
+
+/* Free an object's device memory. Errors: BAD_HANDLE. */
+LSNIF_API int lsnif_unload_object(lsnif_ctx *ctx, lsnif_obj obj);
+
+/* Fill *out with facts about the object. Errors: BAD_HANDLE. */
+LSNIF_API int lsnif_get_object_info(lsnif_ctx *ctx, lsnif_obj obj, lsnif_object_info *out);
+
+/* Which array lsnif_read_params / lsnif_write_params move. */
+enum lsnif_param {
+    LSNIF_PARAM_OCCUPANCY = 0, /* ceil(V^3/32) uint32 words, bit i of word i>>5 = voxel i */
+    LSNIF_PARAM_TABLES = 1,    /* L x T x F FP32 (master copy) */
+    LSNIF_PARAM_MLP = 2,       /* packed FP32 network, layout of lsnif_object_desc.mlp */
+    LSNIF_PARAM_GRAD_TABLES = 3, /* gradients of the last lsnif_train_step, FP32 */
+    LSNIF_PARAM_GRAD_MLP = 4
+};
+
+/* Copy an object array to host memory (synchronous). bytes must equal the
+ * array's size. Errors: BAD_HANDLE, INVALID_ARG (size), CUDA. */
+LSNIF_API int lsnif_read_params(lsnif_ctx *ctx, lsnif_obj obj, int which, void *host_dst, size_t bytes);
+
+/* Replace the tables or network (LSNIF_PARAM_TABLES / _MLP) from host
+ * memory; refreshes the reduced-precision copies and resets the optimiser. */
+LSNIF_API int lsnif_write_params(lsnif_ctx *ctx, lsnif_obj obj, int which, const void *host_src, size_t bytes);
+
+/* ---- the query (Fig. 2; Sec. 3.1-3.3; Sec. 4 single dispatch grouped by object) */
+
+/* Intersect rays with objects: AABB clip, 3D-DDA over the occupancy grid,
+ * entry/exit points of the first H/2 occupied voxels, hash-grid encoding,
+ * MLP, decode. Device pointers for rays and hits. With rays->obj, rays of
+ * many objects go through one launch sequence grouped by object. Uses
+ * context-owned scratch memory (grown on demand and charged to the budget).
+ * Results do not depend on which other rays share the call.
+ * Errors: INVALID_ARG, BAD_HANDLE (a ray names an unknown object: checked
+ * on the device, reported as DEVICE_CHECK), UNSUPPORTED (BF16 path with a
+ * config it does not cover), OVER_BUDGET, CUDA. */
+LSNIF_API int lsnif_query_rays(lsnif_ctx *ctx, const lsnif_rays *rays, lsnif_hits *hits, int precision,
+                     void *stream);
+
+/* lsnif_query_rays with HOST ray and hit buffers: copies the rays to the
+ * device, runs the query and copies the results back, returning when they
+ * are in host memory. Page-locked host buffers make the copies faster. */
+LSNIF_API int lsnif_query_rays_host(lsnif_ctx *ctx, const lsnif_rays *rays, lsnif_hits *hits, int precision,
+                          void *stream);
+
+/* Stage outputs of the traversal (a1-a5 of the query) for one object, all
+ * DEVICE pointers, any may be NULL: k[n] kept occupied voxels (<= H/2);
+ * t01[2n] the clipped AABB interval (NaN on a miss); pts[n*H*3] boundary
+ * points in unit-cube coordinates of the AABB, entry then exit per voxel,
+ * the crossed coordinate exactly face/V, slots past 2k untouched;
+ * vox[n*H/2] voxel ids (z*V+y)*V+x, -1 past k. */
+typedef struct lsnif_trace_out {
+    int32_t *k;
+    float *t01;
+    float *pts;
+    int32_t *vox;
+} lsnif_trace_out;
+
+/* Run only the traversal kernel (Sec. 3.1) for rays->single_obj. */
+LSNIF_API int lsnif_trace(lsnif_ctx *ctx, const lsnif_rays *rays, lsnif_trace_out *out, void *stream);
+
+/* Hash-grid encoding of n unit-cube points (Sec. 3.2): pts DEVICE n x 3 FP32
+ * -> feats DEVICE n x L x F FP32. precision FP32_PLAIN reads the FP32
+ * tables; BF16_FUSED reads the FP16 copies (interpolation in FP32 either
+ * way). Zero-weight corners are skipped. */
+LSNIF_API int lsnif_encode(lsnif_ctx *ctx, lsnif_obj obj, const float *pts, int64_t n, float *feats,
+                 int precision, void *stream);
+
+/* Table index of each of the 8 cell corners per point and level: DEVICE
+ * out n x L x 8 uint32, corner order dx + 2 dy + 4 dz. The cell is the floor
+ * of the exact product p * N_l of the FP32 point and the level resolution
+ * (computed with an error-free FMA split, identical to an FP64 evaluation). */
+LSNIF_API int lsnif_corner_indices(lsnif_ctx *ctx, lsnif_obj obj, const float *pts, int64_t n, uint32_t *out,
+                         void *stream);
+
+/* The object's network alone (Sec. 5.1) on n given input rows: X DEVICE
+ * n x (H*L*F) FP32 -> Z DEVICE n x (8+n_mat) FP32 logits. BF16_FUSED runs
+ * the tcgen05 tensor-core layers (inputs rounded to BF16). */
+LSNIF_API int lsnif_mlp(lsnif_ctx *ctx, lsnif_obj obj, const float *X, int64_t n, float *Z, int precision,
+              void *stream);
+
+/* ---- training (Sec. 5.2, 5.3) ------------------------------------------ */
+
+/* Number of uniforms per training ray that lsnif_make_training_rays reads. */
+#define LSNIF_TRAIN_UNIFORMS 40
+
+/* Balanced training rays (Sec. 5.2) for an object loaded with keep_mesh:
+ * rays [0, n_outside) start uniformly on the sphere of radius 1.05 x half
+ * the AABB diagonal about its centre (u0, u1) with cosine-weighted
+ * directions about the inward direction (u2, u3); rays [n_outside, n) cast
+ * up to 8 such rays (u[4+4a .. 8+4a]) until one hits the mesh and start at
+ * the hit, offset 1e-4 x diagonal along the geometric normal facing the
+ * incoming ray, with a cosine-weighted direction about it (u36, u37); if no
+ * attempt hits they keep the outside ray of u0..u3. u: DEVICE n x 40 FP32
+ * uniforms in [0,1) (the caller draws them). rays_out: DEVICE 8 x n FP32
+ * (ox,oy,oz,dx,dy,dz,tmin=0,tmax=inf rows). surface: DEVICE n bytes, 1 for
+ * rays that start on the surface; may be NULL. */
+LSNIF_API int lsnif_make_training_rays(lsnif_ctx *ctx, lsnif_obj obj, const float *u, int64_t n,
+                             int64_t n_outside, float *rays_out, uint8_t *surface, void *stream);
+
+/* Ground-truth labels by ray casting against the kept mesh (Sec. 5.2),
+ * DEVICE outputs, any may be NULL: occ (0/1), t_local = (t_hit-t0)/(t1-t0)
+ * over the clipped AABB interval (0 on a miss), normal (3n, barycentric
+ * shading normal, not flipped), albedo (3n), mat, t_hit (+inf on a miss),
+ * tri (-1 on a miss), k (kept occupied voxels of the traversal, so callers
+ * can drop rays that never reach the network). */
+typedef struct lsnif_labels {
+    float *occ;
+    float *t_local;
+    float *normal;
+    float *albedo;
+    int32_t *mat;
+    float *t_hit;
+    int32_t *tri;
+    int32_t *k;
+} lsnif_labels;
+
+LSNIF_API int lsnif_label_rays(lsnif_ctx *ctx, const lsnif_rays *rays, lsnif_labels *out, void *stream);
+
+typedef struct lsnif_train_opts {
+    float lr;            /* Adam learning rate (paper: 0.01) */
+    float beta1, beta2;  /* Adam moments (0.9, 0.999) */
+    float eps;           /* Adam epsilon (1e-8) */
+    int32_t apply_update;/* 0: only compute the loss and gradients (kept for lsnif_read_params) */
+} lsnif_train_opts;
+
+typedef struct lsnif_train_stats {
+    float total, occ, t, normal, albedo, mat; /* batch-mean loss terms (Sec. 5.3) */
+    int64_t step;                              /* optimiser steps taken so far */
+} lsnif_train_stats;
+
+/* One optimisation step of the whole object (network and tables jointly,
+ * Sec. 5.2) on a batch: forward with saved activations, multi-head loss
+ * (BCE; masked MAE, cosine, relative L2, cross-entropy; Sec. 5.3), backward
+ * (network, then trilinear scatter of feature gradients into the tables),
+ * Adam. rays: DEVICE batch (single object); labels: DEVICE occ, t_local,
+ * normal, albedo, mat as produced by lsnif_label_rays. Rays that meet no
+ * occupied voxel contribute nothing. stats (host, may be NULL) are written
+ * after a stream synchronisation. The FP16/BF16 copies used by the fused
+ * query are refreshed after each update. */
+LSNIF_API int lsnif_train_step(lsnif_ctx *ctx, const lsnif_rays *rays, const lsnif_labels *labels,
+                     const lsnif_train_opts *opts, lsnif_train_stats *stats, void *stream);
+
+/* ---- serving: continuous batching (Sec. 4 dispatch, served as requests) -- */
+
+typedef struct lsnif_req_stats {
+    double submit_us, start_us, done_us; /* host clock, microseconds */
+    double gpu_ms;                        /* device time of the request's work */
+    int64_t n_rays;
+} lsnif_req_stats;
+
+/* Queue a query. rays/hits are DEVICE buffers that must stay valid until
+ * lsnif_poll returns OK or an error for the ticket. A request is admitted
+ * to the device when one of the context's streams is free and its scratch
+ * fits the memory budget; admitted requests run concurrently with those
+ * already on the device. Errors: INVALID_ARG, BUSY (queue full),
+ * OVER_BUDGET (the request alone can never fit the budget). */
+LSNIF_API int lsnif_submit(lsnif_ctx *ctx, const lsnif_rays *rays, lsnif_hits *hits, int precision,
+                 uint64_t *ticket);
+
+/* Advance the queue and report a request: OK (done; *st filled if not
+ * NULL), PENDING (not done and timeout_us == 0), TIMEOUT (not done within
+ * timeout_us microseconds), BAD_HANDLE, or the request's own error. Never
+ * blocks longer than timeout_us (plus one admission step). */
+LSNIF_API int lsnif_poll(lsnif_ctx *ctx, uint64_t ticket, int64_t timeout_us, lsnif_req_stats *st);
+
+/* Number of submitted requests not yet reported done by lsnif_poll. */
+LSNIF_API int64_t lsnif_pending(lsnif_ctx *ctx);
+
+/* ---- measurement ------------------------------------------------------- */
+
+typedef struct lsnif_profile {
+    float ms_trace;      /* traversal + compaction kernels */
+    float ms_group;      /* grouping of live rays by object and point count */
+    float ms_encode;     /* FP32 path: gather kernel */
+    float ms_mlp;        /* FP32 path: network kernel; BF16 path: fused gather+network kernel */
+    float ms_total;
+    int64_t n_rays, n_live, n_points; /* rays, rays reaching the network, boundary points */
+    int32_t launches;    /* kernels launched by the last query */
+} lsnif_profile;
+
+/* Turn per-stage CUDA-event timing of queries on (1) or off (0). */
+LSNIF_API int lsnif_set_profiling(lsnif_ctx *ctx, int on);
+
+/* Stage times and counts of the last query run with profiling on
+ * (synchronises the stream it ran on). */
+LSNIF_API int lsnif_last_profile(lsnif_ctx *ctx, lsnif_profile *out);
+
+/* Device memory the context currently holds (objects + scratch). */
+LSNIF_API size_t lsnif_device_bytes(lsnif_ctx *ctx);
+
+/* Host-side fault injection for tests: after `n` further successful device
+ * allocations the next one fails as if cudaMalloc had (n < 0 disables). */
+LSNIF_API int lsnif_debug_fail_alloc_after(lsnif_ctx *ctx, int64_t n);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LSNIF_H */

@@ -474,29 +474,6 @@ ORC_API void orc_encode_backward(const double *pts, int64_t npts, const int32_t 
     }
 }
 
-/*
- * Lattice cells and corner indices with the floor decision taken in FP32,
- * the precision of the CUDA kernels: x = fl32(p * N_l), c = floor(x).
- * For identical FP32 points both sides must then agree bit for bit.
- * out_idx: (npts, L, 8) in corner order dx + 2 dy + 4 dz.
- */
-ORC_API void orc_corner_indices_f32(const float *pts, int64_t npts, const int32_t *res, int L,
-                                    int log2T, uint32_t *out_idx)
-{
-    for (int64_t i = 0; i < npts; ++i)
-        for (int l = 0; l < L; ++l) {
-            int64_t c[3];
-            for (int a = 0; a < 3; ++a) {
-                volatile float x = pts[3 * i + a] * (float)res[l];
-                c[a] = (int64_t)floorf(x);
-            }
-            for (int corner = 0; corner < 8; ++corner)
-                out_idx[(i * L + l) * 8 + corner] =
-                    orc_hash(c[0] + (corner & 1), c[1] + ((corner >> 1) & 1), c[2] + ((corner >> 2) & 1),
-                             log2T);
-        }
-}
-
 /* ------------------------------------------------------------------------
  * Geometric judge: nearest Moller-Trumbore hit over all triangles.
  * rays: n x 8 floats (object space). Accepts tmin <= t <= tmax, u >= 0,

@@ -61,7 +61,6 @@ def lib():
         L.orc_hash.restype = ctypes.c_uint32
         L.orc_encode.argtypes = [P, i64, P, i32, i32, i32, P, P, P, P]
         L.orc_encode_backward.argtypes = [P, i64, P, i32, i32, i32, P, P]
-        L.orc_corner_indices_f32.argtypes = [P, i64, P, i32, i32, P]
         L.orc_judge.argtypes = [P, i64, P, P, i64, P, P, P, P]
         _lib = L
     return _lib
@@ -207,15 +206,6 @@ def encode_backward(pts: np.ndarray, res, F: int, log2_T: int, dout: np.ndarray,
     d = _c(dout, np.float64)
     assert grad_tables.dtype == np.float64 and grad_tables.flags["C_CONTIGUOUS"]
     lib().orc_encode_backward(_p(p), p.shape[0], _p(res), res.size, F, log2_T, _p(d), _p(grad_tables))
-
-
-def corner_indices_f32(pts_f32: np.ndarray, res, log2_T: int) -> np.ndarray:
-    """Corner table indices with the cell decision in FP32 (the kernels' precision)."""
-    p = _c(pts_f32, np.float32).reshape(-1, 3)
-    res = _c(res, np.int32)
-    out = np.zeros((p.shape[0], res.size, 8), np.uint32)
-    lib().orc_corner_indices_f32(_p(p), p.shape[0], _p(res), res.size, log2_T, _p(out))
-    return out
 
 
 def features(obj: OracleObject, seg: Segments, tables: np.ndarray | None = None) -> np.ndarray:
@@ -512,8 +502,11 @@ REL_L2_EPS = 0.01
 NORMAL_EPS = 1e-12
 
 
-def loss_terms(Z: np.ndarray, lab: Labels):
-    """Per-ray loss terms and dLoss/dZ (for the batch MEAN of the total).
+def loss_terms(Z: np.ndarray, lab: Labels, live: np.ndarray | None = None):
+    """Per-ray loss terms and dLoss/dZ for the batch mean of the total over
+    the rays that reach the network (`live`; all rays when None): a ray that
+    meets no occupied voxel is answered without the network, so it takes no
+    part in training.
 
     BCE on the occlusion logit (stable form); for rays whose reference is
     occluded also: MAE of sigmoid(z1) against the local hit distance, 1 -
@@ -547,10 +540,12 @@ def loss_terms(Z: np.ndarray, lab: Labels):
     sm[np.arange(n), lab.mat] -= 1.0
     g[:, 8:] = sm
     g[:, 1:] *= y[:, None]
+    w = np.ones(n) if live is None else live.astype(np.float64)
+    m = max(w.sum(), 1.0)
     per_ray = l_occ + y * (l_t + l_n + l_a + l_m)
-    terms = dict(occ=l_occ.mean(), t=(y * l_t).mean(), normal=(y * l_n).mean(),
-                 albedo=(y * l_a).mean(), mat=(y * l_m).mean(), total=per_ray.mean())
-    return terms, g / n
+    terms = dict(occ=(w * l_occ).sum() / m, t=(w * y * l_t).sum() / m, normal=(w * y * l_n).sum() / m,
+                 albedo=(w * y * l_a).sum() / m, mat=(w * y * l_m).sum() / m, total=(w * per_ray).sum() / m)
+    return terms, g * (w / m)[:, None]
 
 
 # --------------------------------------------------------------------------
@@ -558,13 +553,14 @@ def loss_terms(Z: np.ndarray, lab: Labels):
 # --------------------------------------------------------------------------
 
 def forward_backward(obj: OracleObject, rays: np.ndarray, lab: Labels, seg: Segments | None = None):
-    """Loss terms and gradients of the batch-mean loss with respect to every
-    network weight/bias and every hash-table entry."""
+    """Loss terms and gradients of the batch-mean loss (over rays that reach
+    the network) with respect to every network weight/bias and every
+    hash-table entry."""
     cfg = obj.cfg
     seg = ray_segments(obj, rays) if seg is None else seg
     X = features(obj, seg)
     Z, cache = mlp_forward(X, obj.weights, cfg.activation, keep=True)
-    terms, dZ = loss_terms(Z, lab)
+    terms, dZ = loss_terms(Z, lab, live=seg.k > 0)
     grads = []
     d = dZ
     for i in range(len(obj.weights) - 1, -1, -1):

@@ -1,0 +1,184 @@
+// Hash-grid corner gather and trilinear interpolation of one point at one
+// level (Sec. 3.2), for FP32 or FP16 tables of F features per entry.
+//
+// The gather is bound by the number of L2 requests, not bytes: the two
+// x-neighbours of a corner pair hash to indices that differ only in their
+// low bits (the x multiplier is 1), so both usually fall in the same aligned
+// 16-byte group of entries and one 16-byte load serves the pair.
+#pragma once
+
+#include "device.cuh"
+
+namespace lsnif {
+
+struct Cell {
+  uint32_t cx, cy, cz;
+  float wx, wy, wz;
+};
+
+// Lattice cell of a unit-cube point at resolution N (vertices 0..N, no
+// offset): c = floor(p * N), w = p * N - c, from the EXACT product. The FP32
+// product x = fl(p * N) is split with an FMA into x + e == p * N exactly
+// (the error-free product of Ogita, Rump and Oishi, "Accurate Sum and Dot
+// Product", 2005), so the cell is the floor of the exact value: for a
+// non-integer x, |e| <= ulp(x)/2 cannot cross an integer; for an integer x
+// the cell drops by one when e < 0. The weight keeps e. The decision thus
+// equals the one an FP64 evaluation of p * N makes for the same FP32 p.
+__device__ __forceinline__ void exact_cell(float p, float N, uint32_t &c, float &w) {
+  const float x = p * N;
+  const float e = fmaf(p, N, -x);
+  float f = floorf(x);
+  if (x == f && e < 0.f) f -= 1.f;
+  c = (uint32_t)(int)f;
+  w = (x - f) + e;
+}
+
+__device__ __forceinline__ Cell lattice_cell(const float3 &p, float N) {
+  Cell c;
+  exact_cell(p.x, N, c.cx, c.wx);
+  exact_cell(p.y, N, c.cy, c.wy);
+  exact_cell(p.z, N, c.cz, c.wz);
+  return c;
+}
+
+template <typename T, int F>
+struct Entry {
+  static constexpr int kBytes = F * (int)sizeof(T);
+  static constexpr int kGroup = 16 / kBytes;  // entries per 16-byte group
+};
+
+template <typename T, int F>
+__device__ __forceinline__ void unpack_entry(const uint4 &g, uint32_t j, float (&v)[F]);
+
+template <>
+__device__ __forceinline__ void unpack_entry<float, 1>(const uint4 &g, uint32_t j, float (&v)[1]) {
+  v[0] = __uint_as_float(pick4(g, j));
+}
+template <>
+__device__ __forceinline__ void unpack_entry<float, 2>(const uint4 &g, uint32_t j, float (&v)[2]) {
+  v[0] = __uint_as_float(j ? g.z : g.x);
+  v[1] = __uint_as_float(j ? g.w : g.y);
+}
+template <>
+__device__ __forceinline__ void unpack_entry<float, 4>(const uint4 &g, uint32_t, float (&v)[4]) {
+  v[0] = __uint_as_float(g.x);
+  v[1] = __uint_as_float(g.y);
+  v[2] = __uint_as_float(g.z);
+  v[3] = __uint_as_float(g.w);
+}
+template <>
+__device__ __forceinline__ void unpack_entry<__half, 1>(const uint4 &g, uint32_t j, float (&v)[1]) {
+  uint32_t w = pick4(g, j >> 1);
+  v[0] = __half2float(__ushort_as_half((unsigned short)((j & 1) ? (w >> 16) : (w & 0xFFFFu))));
+}
+template <>
+__device__ __forceinline__ void unpack_entry<__half, 2>(const uint4 &g, uint32_t j, float (&v)[2]) {
+  uint32_t w = pick4(g, j);
+  float2 f = __half22float2(*reinterpret_cast<const __half2 *>(&w));
+  v[0] = f.x;
+  v[1] = f.y;
+}
+template <>
+__device__ __forceinline__ void unpack_entry<__half, 4>(const uint4 &g, uint32_t j, float (&v)[4]) {
+  uint32_t w0 = j ? g.z : g.x, w1 = j ? g.w : g.y;
+  float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&w0));
+  float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&w1));
+  v[0] = a.x;
+  v[1] = a.y;
+  v[2] = b.x;
+  v[3] = b.y;
+}
+
+// Load one entry on its own (bytes = F * sizeof(T)).
+template <typename T, int F>
+__device__ __forceinline__ void load_entry(const T *tab, uint32_t i, float (&v)[F]) {
+  constexpr int B = Entry<T, F>::kBytes;
+  const uint8_t *p = reinterpret_cast<const uint8_t *>(tab) + (size_t)i * B;
+  uint4 g;
+  if constexpr (B == 16) {
+    g = ldg16(p);
+    unpack_entry<T, F>(g, 0, v);
+  } else if constexpr (B == 8) {
+    uint2 u = ldg8(p);
+    g = make_uint4(u.x, u.y, 0, 0);
+    unpack_entry<T, F>(g, 0, v);
+  } else if constexpr (B == 4) {
+    g = make_uint4(ldg4(p), 0, 0, 0);
+    unpack_entry<T, F>(g, 0, v);
+  } else {  // 2 bytes
+    uint32_t w = ldg4(reinterpret_cast<const uint8_t *>(tab) + (size_t)(i & ~1u) * 2);
+    g = make_uint4(w, 0, 0, 0);
+    unpack_entry<T, F>(g, i & 1u, v);
+  }
+}
+
+// Entries i0 (always) and i1 (when need1): one 16-byte load when both sit
+// in the same aligned group, otherwise a group load plus one entry load.
+template <typename T, int F>
+__device__ __forceinline__ void load_pair(const T *tab, uint32_t i0, uint32_t i1, bool need1, float (&v0)[F],
+                                          float (&v1)[F]) {
+  constexpr int G = Entry<T, F>::kGroup;
+  constexpr int B = Entry<T, F>::kBytes;
+  const uint8_t *base = reinterpret_cast<const uint8_t *>(tab);
+  uint4 g = ldg16(base + (size_t)(i0 & ~(uint32_t)(G - 1)) * B);
+  unpack_entry<T, F>(g, i0 & (G - 1), v0);
+  if (need1) {
+    if ((i0 ^ i1) < (uint32_t)G) unpack_entry<T, F>(g, i1 & (G - 1), v1);
+    else load_entry<T, F>(tab, i1, v1);
+  } else {
+#pragma unroll
+    for (int f = 0; f < F; ++f) v1[f] = 0.f;
+  }
+}
+
+// Trilinear feature of point p at one level: sum over the 8 cell corners of
+// prod_axis(d ? w : 1-w) * table[hash(c + d) & mask]. Corners whose weight is
+// exactly zero (a coordinate on a lattice plane) are not fetched.
+template <typename T, int F>
+__device__ __forceinline__ void encode_level(const T *__restrict__ tab, uint32_t mask, const float3 &p, float N,
+                                             float (&out)[F]) {
+  Cell c = lattice_cell(p, N);
+#pragma unroll
+  for (int f = 0; f < F; ++f) out[f] = 0.f;
+  const bool nx = c.wx != 0.f, ny = c.wy != 0.f, nz = c.wz != 0.f;
+  const uint32_t hy0 = c.cy * kPi2, hy1 = (c.cy + 1u) * kPi2;
+  const uint32_t hz0 = c.cz * kPi3, hz1 = (c.cz + 1u) * kPi3;
+  float v0[4][F], v1[4][F];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int dy = q & 1, dz = q >> 1;
+    const bool need = (dy == 0 || ny) && (dz == 0 || nz);
+    const uint32_t b = (dy ? hy1 : hy0) ^ (dz ? hz1 : hz0);
+    const uint32_t i0 = (c.cx ^ b) & mask, i1 = ((c.cx + 1u) ^ b) & mask;
+    if (need) {
+      load_pair<T, F>(tab, i0, i1, nx, v0[q], v1[q]);
+    } else {
+#pragma unroll
+      for (int f = 0; f < F; ++f) { v0[q][f] = 0.f; v1[q][f] = 0.f; }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int dy = q & 1, dz = q >> 1;
+    const float wyz = (dy ? c.wy : 1.f - c.wy) * (dz ? c.wz : 1.f - c.wz);
+#pragma unroll
+    for (int f = 0; f < F; ++f) out[f] = fmaf(wyz, fmaf(c.wx, v1[q][f] - v0[q][f], v0[q][f]), out[f]);
+  }
+}
+
+// Scatter of a feature gradient into the level's table (backward of
+// encode_level): table[idx] += weight * g, every non-zero corner.
+__device__ __forceinline__ void encode_level_backward(float *__restrict__ gtab, uint32_t mask, const float3 &p,
+                                                      float N, const float *g, int F) {
+  Cell c = lattice_cell(p, N);
+#pragma unroll
+  for (int corner = 0; corner < 8; ++corner) {
+    const int dx = corner & 1, dy = (corner >> 1) & 1, dz = corner >> 2;
+    const float w = (dx ? c.wx : 1.f - c.wx) * (dy ? c.wy : 1.f - c.wy) * (dz ? c.wz : 1.f - c.wz);
+    if (w == 0.f) continue;
+    const uint32_t idx = hash3(c.cx + dx, c.cy + dy, c.cz + dz) & mask;
+    for (int f = 0; f < F; ++f) atomicAdd(gtab + (size_t)idx * F + f, w * g[f]);
+  }
+}
+
+}  // namespace lsnif

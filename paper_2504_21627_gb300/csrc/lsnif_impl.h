@@ -1,0 +1,161 @@
+// Internal declarations of the LSNIF library: the device-side object record,
+// kernel argument blocks and the launchers each .cu file exports to api.cpp.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+
+#include "lsnif.h"
+
+namespace lsnif {
+
+// spatial-hash multipliers (instant-NGP, the encoding LSNIF's sparse grid uses)
+constexpr uint32_t kPi2 = 2654435761u;
+constexpr uint32_t kPi3 = 805459861u;
+
+constexpr int kMaxCap = 32;          // H/2 <= 32
+constexpr int kBuckets = kMaxCap + 1;  // per object: k = 0..32
+constexpr int kTileM = 128;          // rays per tensor-core tile (tcgen05 M)
+
+// error word bits written by kernels (never trap, never hang)
+enum DeviceError : int {
+  kErrBadHandle = 1,
+  kErrWaitTimeout = 2,
+  kErrCheck = 4,
+};
+
+// Everything a kernel needs to know about one object. Plain data, copied to
+// a device array indexed by object slot.
+struct DevObject {
+  float bmin[3];
+  float inv_ext[3];
+  int32_t V;
+  int32_t log2V;
+  float invV;
+  const uint32_t *occ;  // ceil(V^3/32) words
+
+  int32_t L, F, log2T;
+  uint32_t mask;
+  int32_t res[LSNIF_MAX_LEVELS];
+  const float *tab32;   // L x T x F
+  const uint16_t *tab16;  // FP16 copy, same layout
+
+  int32_t H, n_in, n_hidden, width, n_out, n_out_pad, n_mat, act;
+  const float *mlp32;   // packed FP32 [W0 b0 W1 b1 ...]
+  const uint8_t *umma;  // BF16 weights in tcgen05 core-matrix layout + FP32 biases
+  uint32_t umma_bytes;  // total bytes of the umma blob
+  uint32_t umma_bias_off;  // byte offset of the FP32 biases inside it
+  const float *plain_out;  // FP32 output layer padded to n_out_pad rows, then its bias
+
+  // kept mesh (training labels): per-voxel triangle lists in CSR form
+  const float *verts;
+  const int32_t *tris;
+  const float *vnormals;
+  const int32_t *tri_mat;
+  const float *albedo;
+  const int32_t *vox_start;  // V^3 + 1
+  const int32_t *vox_tris;
+  int64_t nt;
+
+  uint32_t handle;  // handle the slot currently holds (0 = free)
+  int32_t valid;
+};
+
+// Rays as the kernels see them (SoA device pointers).
+struct RaysArg {
+  const float *ox, *oy, *oz, *dx, *dy, *dz, *tmin, *tmax;
+  const uint32_t *obj;
+  uint32_t single_handle;
+  int64_t n;
+};
+
+struct HitsArg {
+  uint8_t *hit;
+  float *t, *nx, *ny, *nz;
+  int32_t *mat;
+  float *ar, *ag, *ab;
+  float *logits;
+};
+
+// Scratch a query uses (device pointers into the context's workspace).
+struct QueryScratch {
+  float *pts;        // n x H x 3
+  float *t01;        // n x 2
+  uint8_t *k;        // n
+  int16_t *slot;     // n object slot per ray (-1 invalid)
+  int32_t *order;    // n ray indices grouped by (object, k desc)
+  int32_t *counts;   // n_slots x kBuckets
+  int32_t *offsets;  // n_slots x kBuckets
+  int32_t *cursor;   // n_slots x kBuckets
+  int32_t *tiles;    // max_tiles x 3 (slot, start, count)
+  int32_t *meta;     // [0] n_live, [1] n_tiles, [2] n_points, [3] tile cursor
+  float *X;          // FP32 path: chunk of tiles x kTileM rows x ldx features
+  int32_t max_tiles; // upper bound on tiles (n / kTileM + n_slots)
+  int32_t wmax;      // FP32 path: widest layer (hidden width or padded output)
+};
+
+struct QueryLaunch {
+  const DevObject *objs;  // device array [n_slots]
+  int32_t n_slots;
+  int32_t H_max;
+  RaysArg rays;
+  HitsArg hits;
+  QueryScratch s;
+  int *err;               // device error word
+  cudaStream_t stream;
+};
+
+// ---- launchers (query.cu) ----
+// Traversal + histogram; returns kernels launched (adds to *launches).
+cudaError_t launch_trace(const QueryLaunch &q, int *launches);
+cudaError_t launch_group(const QueryLaunch &q, int *launches);
+cudaError_t launch_plain_tail(const QueryLaunch &q, int ldx, int chunk_tiles, int *launches);
+cudaError_t launch_trace_only(const DevObject *dobj, const RaysArg &rays, int32_t *k, float *t01,
+                              float *pts, int32_t *vox, int *err, cudaStream_t st);
+cudaError_t launch_encode(const DevObject *dobj, const DevObject &host_obj, const float *pts, int64_t n,
+                          float *feats, int precision, cudaStream_t st);
+cudaError_t launch_corners(const DevObject *dobj, const DevObject &host_obj, const float *pts,
+                           int64_t n, uint32_t *out, cudaStream_t st);
+cudaError_t launch_mlp_plain(const DevObject *dobj, const DevObject &host_obj, const float *X,
+                             int64_t n, float *Z, cudaStream_t st);
+cudaError_t launch_build_umma(const DevObject &host_obj, uint8_t *dst, cudaStream_t st);
+cudaError_t launch_tables_to_half(const float *src, uint16_t *dst, int64_t n, cudaStream_t st);
+
+// ---- fused tensor-core path (fused.cu) ----
+// Returns cudaErrorNotSupported when the object's shape is outside the
+// fused kernel's instantiations.
+bool fused_supported(const DevObject &host_obj);
+size_t fused_smem_bytes(const DevObject &host_obj);
+cudaError_t launch_fused(const QueryLaunch &q, const DevObject &host_obj, int *launches);
+cudaError_t launch_mlp_fused(const DevObject *dobj, const DevObject &host_obj, const float *X,
+                             int64_t n, float *Z, int *err, cudaStream_t st);
+
+// ---- training (train.cu) ----
+struct TrainBuffers {
+  float *feats;     // B x n_in (FP32)
+  float *acts;      // B x width x n_hidden (post-activation)
+  float *pre;       // B x width x n_hidden (pre-activation)
+  float *Z;         // B x n_out
+  float *dZ;        // B x n_out
+  float *dA;        // B x max(width, n_in) scratch
+  float *dB;        // B x max(width, n_in) scratch
+  float *pts;       // B x H x 3
+  float *t01;       // B x 2
+  int32_t *k;       // B
+  float *loss;      // 8 accumulators
+  float *grad_mlp;  // n_params_mlp
+  float *grad_tab;  // L x T x F
+  float *m_mlp, *v_mlp, *m_tab, *v_tab;
+};
+
+cudaError_t launch_make_training_rays(const DevObject *dobj, const DevObject &h, const float *u, int64_t n,
+                                      int64_t n_outside, float *rays_out, uint8_t *surface,
+                                      cudaStream_t st);
+cudaError_t launch_label_rays(const DevObject *dobj, const DevObject &h, const RaysArg &rays,
+                              const lsnif_labels &out, cudaStream_t st);
+cudaError_t launch_train_step(const DevObject *dobj, const DevObject &h, const RaysArg &rays,
+                              const lsnif_labels &lab, const lsnif_train_opts &opts, int64_t step,
+                              TrainBuffers &tb, int64_t n_params_mlp, cudaStream_t st);
+
+}  // namespace lsnif

@@ -1,0 +1,574 @@
+// Query kernels shared by both precisions (traversal, grouping) and the plain
+// FP32 path (gather kernel, SIMT network + decode kernel), plus the stage
+// kernels behind lsnif_trace / lsnif_encode / lsnif_corner_indices /
+// lsnif_mlp.
+#include <cstdio>
+
+#include "device.cuh"
+#include "encode.cuh"
+
+namespace lsnif {
+
+// ---------------------------------------------------------------------------
+// a1-a5: transform, slab test, 3D-DDA over occupied voxels, boundary points.
+// One thread per ray; also histograms live rays by (object slot, k).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) trace_kernel(QueryLaunch q, int smem_hist) {
+  extern __shared__ int sh_hist[];
+  const int nb = q.n_slots * kBuckets;
+  if (smem_hist) {
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) sh_hist[i] = 0;
+    __syncthreads();
+  }
+  const int64_t n = q.rays.n;
+  const int Hs = q.H_max;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t h = q.rays.obj ? q.rays.obj[i] : q.rays.single_handle;
+    int s = slot_of(q.objs, q.n_slots, h);
+    int k = 0;
+    float t0 = CUDART_NAN_F, t1 = CUDART_NAN_F;
+    if (s < 0) {
+      atomicOr(q.err, kErrBadHandle);
+      q.s.slot[i] = -1;
+      q.s.k[i] = 0;
+      miss_store(q.hits, i, 0);
+      continue;
+    }
+    const DevObject &ob = q.objs[s];
+    float3 o, d;
+    int ea;
+    float tmin = q.rays.tmin[i];
+    bool live = to_unit(ob, q.rays.ox[i], q.rays.oy[i], q.rays.oz[i], q.rays.dx[i], q.rays.dy[i], q.rays.dz[i], o,
+                        d) &&
+                unit_slab(o, d, tmin, t0, t1, ea);
+    if (live) {
+      float *P = q.s.pts + (size_t)i * Hs * 3;
+      const int cap = ob.H >> 1;
+      const uint32_t *occ = ob.occ;
+      dda_walk(
+          ob, o, d, t0, t1, ea, [&](uint32_t vid) { return occupied(occ, vid); },
+          [&](const Seg &sg) {
+            float3 a = seg_point(o, d, sg.tin, sg.ain, sg.fin);
+            float3 b = seg_point(o, d, sg.tout, sg.aout, sg.fout);
+            float *w = P + 6 * k;
+            reinterpret_cast<float2 *>(w)[0] = make_float2(a.x, a.y);
+            reinterpret_cast<float2 *>(w)[1] = make_float2(a.z, b.x);
+            reinterpret_cast<float2 *>(w)[2] = make_float2(b.y, b.z);
+            ++k;
+            return k < cap;
+          });
+    } else {
+      t0 = t1 = CUDART_NAN_F;
+    }
+    q.s.k[i] = (uint8_t)k;
+    q.s.slot[i] = (int16_t)s;
+    reinterpret_cast<float2 *>(q.s.t01)[i] = make_float2(t0, t1);
+    if (k == 0) miss_store(q.hits, i, ob.n_out);
+    if (k > 0) {
+      if (smem_hist) atomicAdd(&sh_hist[s * kBuckets + k], 1);
+      else atomicAdd(&q.s.counts[s * kBuckets + k], 1);
+    }
+  }
+  if (smem_hist) {
+    __syncthreads();
+    for (int b = threadIdx.x; b < nb; b += blockDim.x)
+      if (sh_hist[b]) atomicAdd(&q.s.counts[b], sh_hist[b]);
+  }
+}
+
+// Single block: bucket offsets (object ascending, k descending), tiles of
+// kTileM rays that never straddle objects, totals, cursors reset.
+__global__ void __launch_bounds__(1024) scan_kernel(QueryLaunch q) {
+  __shared__ int tile_off[1025];
+  __shared__ int obj_live[1024];
+  const int ns = q.n_slots;
+  if (threadIdx.x == 0) {
+    int run = 0, tiles = 0, pts = 0;
+    for (int s = 0; s < ns; ++s) {
+      int start = run;
+      for (int k = kMaxCap; k >= 1; --k) {
+        int c = q.s.counts[s * kBuckets + k];
+        q.s.offsets[s * kBuckets + k] = run;
+        q.s.cursor[s * kBuckets + k] = 0;
+        run += c;
+        pts += 2 * k * c;
+      }
+      int live = run - start;
+      if (s < 1024) {
+        obj_live[s] = start;  // start of the object's range
+        tile_off[s] = tiles;
+      }
+      tiles += (live + kTileM - 1) / kTileM;
+    }
+    if (ns <= 1024) tile_off[ns] = tiles;
+    if (tiles > q.s.max_tiles) {
+      atomicOr(q.err, kErrCheck);
+      tiles = q.s.max_tiles;
+    }
+    q.s.meta[0] = run;
+    q.s.meta[1] = tiles;
+    q.s.meta[2] = pts;
+    q.s.meta[3] = 0;
+  }
+  __syncthreads();
+  const int tiles = q.s.meta[1];
+  for (int t = threadIdx.x; t < tiles; t += blockDim.x) {
+    // object of tile t: last s with tile_off[s] <= t
+    int lo = 0, hi = ns - 1;
+    while (lo < hi) {
+      int mid = (lo + hi + 1) >> 1;
+      if (tile_off[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    int s = lo;
+    int first = obj_live[s];
+    int obj_end = first;
+    for (int k = 1; k <= kMaxCap; ++k) obj_end += q.s.counts[s * kBuckets + k];
+    int start = first + (t - tile_off[s]) * kTileM;
+    int cnt = min(kTileM, obj_end - start);
+    q.s.tiles[3 * t + 0] = s;
+    q.s.tiles[3 * t + 1] = start;
+    q.s.tiles[3 * t + 2] = cnt;
+  }
+}
+
+// Scatter live rays into their bucket ranges; warp-aggregated atomics keep
+// rays of one warp contiguous (spatially coherent rays stay together).
+__global__ void __launch_bounds__(256) scatter_kernel(QueryLaunch q) {
+  const int64_t n = q.rays.n;
+  const int lane = threadIdx.x & 31;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
+    int64_t i = base + threadIdx.x;
+    int bucket = -1;
+    if (i < n) {
+      int k = q.s.k[i];
+      int s = q.s.slot[i];
+      if (k > 0 && s >= 0) bucket = s * kBuckets + k;
+    }
+    unsigned active = __ballot_sync(0xffffffffu, bucket >= 0);
+    if (bucket >= 0) {
+      unsigned peers = __match_any_sync(active, bucket);
+      int leader = __ffs(peers) - 1;
+      int rank = __popc(peers & ((1u << lane) - 1u));
+      int basep = 0;
+      if (lane == leader) basep = atomicAdd(&q.s.cursor[bucket], __popc(peers));
+      basep = __shfl_sync(peers, basep, leader);
+      q.s.order[q.s.offsets[bucket] + basep + rank] = (int32_t)i;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// FP32 path: gather into X, one chunk of tiles at a time. Row (t, r) of the
+// chunk is ray r of tile t; the row stride is the largest input width.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void encode_level_any(const DevObject &ob, const float *tab, const float3 &p, int l,
+                                                 float *out) {
+  const float *tl = tab + (size_t)l * (ob.mask + 1) * ob.F;
+  const float N = (float)ob.res[l];
+  if (ob.F == 2) {
+    float f[2];
+    encode_level<float, 2>(tl, ob.mask, p, N, f);
+    out[0] = f[0]; out[1] = f[1];
+  } else if (ob.F == 4) {
+    float f[4];
+    encode_level<float, 4>(tl, ob.mask, p, N, f);
+    out[0] = f[0]; out[1] = f[1]; out[2] = f[2]; out[3] = f[3];
+  } else {
+    float f[1];
+    encode_level<float, 1>(tl, ob.mask, p, N, f);
+    out[0] = f[0];
+  }
+}
+
+__global__ void __launch_bounds__(256) gather_fp32_kernel(QueryLaunch q, int tile0, int ntile, int ldx) {
+  const int Hs = q.H_max;
+  const int64_t tot = (int64_t)ntile * kTileM * Hs;
+  const int n_tiles = q.s.meta[1];
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int h = (int)(e % Hs);
+    const int64_t rr = e / Hs;
+    const int r = (int)(rr % kTileM);
+    const int t = tile0 + (int)(rr / kTileM);
+    if (t >= n_tiles) continue;
+    const int slot = q.s.tiles[3 * t], start = q.s.tiles[3 * t + 1], cnt = q.s.tiles[3 * t + 2];
+    if (r >= cnt) continue;
+    const DevObject &ob = q.objs[slot];
+    if (h >= ob.H) continue;
+    const int32_t ray = q.s.order[start + r];
+    const int k = q.s.k[ray];
+    const int LF = ob.L * ob.F;
+    float *xo = q.s.X + ((int64_t)(t - tile0) * kTileM + r) * ldx + (size_t)h * LF;
+    if (h >= 2 * k) {
+      for (int j = 0; j < LF; ++j) xo[j] = 0.f;
+      continue;
+    }
+    const float *P = q.s.pts + ((size_t)ray * Hs + h) * 3;
+    const float3 p = make_float3(P[0], P[1], P[2]);
+    for (int l = 0; l < ob.L; ++l) encode_level_any(ob, ob.tab32, p, l, xo + l * ob.F);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// FP32 SIMT network: 128-row tiles, activations stay in shared memory
+// between layers; decode in the epilogue.
+// ---------------------------------------------------------------------------
+constexpr int kMT = kTileM;  // rows per tile
+constexpr int kKC = 32;      // K chunk
+
+// out[N][kMT] = act(W[N][K] . in + b); in is global rows (Xg, stride ldx,
+// rows_valid valid) or shared [K][kMT].
+template <int CPT>
+__device__ __forceinline__ void simt_layer(const float *__restrict__ Ain, const float *__restrict__ Xg, int64_t ldx,
+                                           int rows_valid, int K, int N, const float *__restrict__ W,
+                                           const float *__restrict__ bias, int act, bool apply_act, float *As,
+                                           float *Ws, float *Aout) {
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;  // 16 column groups x 16 row groups of 8
+  float acc[8][CPT];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < CPT; ++j) acc[i][j] = 0.f;
+  for (int kc = 0; kc < K; kc += kKC) {
+    const int kn = min(kKC, K - kc);
+    __syncthreads();
+    if (Xg) {
+      for (int e = tid; e < kMT * kKC; e += blockDim.x) {
+        const int r = e / kKC, kk = e % kKC;
+        As[kk * kMT + r] = (r < rows_valid && kk < kn) ? Xg[(int64_t)r * ldx + kc + kk] : 0.f;
+      }
+    }
+    for (int e = tid; e < kKC * N; e += blockDim.x) {
+      const int nn = e / kKC, kk = e % kKC;
+      Ws[kk * N + nn] = kk < kn ? W[(int64_t)nn * K + kc + kk] : 0.f;
+    }
+    __syncthreads();
+    const float *A = Xg ? As : (Ain + (size_t)kc * kMT);
+    for (int kk = 0; kk < kn; ++kk) {
+      float a[8], b[CPT];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) a[i] = A[kk * kMT + ty * 8 + i];
+#pragma unroll
+      for (int j = 0; j < CPT; ++j) b[j] = Ws[kk * N + tx * CPT + j];
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < CPT; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < CPT; ++j) {
+    const int col = tx * CPT + j;
+    const float bj = bias[col];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const float v = acc[i][j] + bj;
+      Aout[col * kMT + ty * 8 + i] = apply_act ? act_fn(v, act) : v;
+    }
+  }
+  __syncthreads();
+}
+
+__device__ void simt_dispatch(int N, const float *Ain, const float *Xg, int64_t ldx, int rows_valid, int K,
+                              const float *W, const float *bias, int act, bool apply_act, float *As, float *Ws,
+                              float *Aout) {
+  switch (N / 16) {
+    case 1: simt_layer<1>(Ain, Xg, ldx, rows_valid, K, N, W, bias, act, apply_act, As, Ws, Aout); break;
+    case 2: simt_layer<2>(Ain, Xg, ldx, rows_valid, K, N, W, bias, act, apply_act, As, Ws, Aout); break;
+    case 3: simt_layer<3>(Ain, Xg, ldx, rows_valid, K, N, W, bias, act, apply_act, As, Ws, Aout); break;
+    case 4: simt_layer<4>(Ain, Xg, ldx, rows_valid, K, N, W, bias, act, apply_act, As, Ws, Aout); break;
+    case 8: simt_layer<8>(Ain, Xg, ldx, rows_valid, K, N, W, bias, act, apply_act, As, Ws, Aout); break;
+    case 16: simt_layer<16>(Ain, Xg, ldx, rows_valid, K, N, W, bias, act, apply_act, As, Ws, Aout); break;
+    default: {
+      // other multiples of 16: generic path, 1 column group at a time
+      for (int n0 = 0; n0 < N; n0 += 16)
+        simt_layer<1>(Ain, Xg, ldx, rows_valid, K, 16, W + (int64_t)n0 * K, bias + n0, act, apply_act, As, Ws,
+                      Aout + (size_t)n0 * kMT);
+    }
+  }
+}
+
+// One tile's network from its input rows X (stride ldx, `rows` valid) into
+// logits out[n_out_pad][kMT] (a shared buffer); returns that buffer.
+__device__ float *simt_network(const DevObject &ob, const float *X, int64_t ldx, int rows, float *As, float *Ws,
+                               float *act0, float *act1) {
+  const int W = ob.width;
+  const float *p = ob.mlp32;
+  simt_dispatch(W, nullptr, X, ldx, rows, ob.n_in, p, p + (size_t)W * ob.n_in, ob.act, true, As, Ws, act0);
+  p += (size_t)W * ob.n_in + W;
+  float *cur = act0, *nxt = act1;
+  for (int l = 1; l < ob.n_hidden; ++l) {
+    simt_dispatch(W, cur, nullptr, 0, kMT, W, p, p + (size_t)W * W, ob.act, true, As, Ws, nxt);
+    p += (size_t)W * W + W;
+    float *tmp = cur; cur = nxt; nxt = tmp;
+  }
+  // output layer, padded to n_out_pad rows (zero weights) by the launcher's copy
+  const float *Wo = ob.plain_out, *bo = ob.plain_out + (size_t)ob.n_out_pad * W;
+  simt_dispatch(ob.n_out_pad, cur, nullptr, 0, kMT, W, Wo, bo, ob.act, false, As, Ws, nxt);
+  return nxt;
+}
+
+__global__ void __launch_bounds__(256) mlp_fp32_kernel(QueryLaunch q, int tile0, int ntile, int ldx) {
+  extern __shared__ __align__(16) float sm[];
+  const int wmax = q.s.wmax;
+  float *As = sm;
+  float *Ws = As + kKC * kMT;
+  float *act0 = Ws + kKC * wmax;
+  float *act1 = act0 + (size_t)wmax * kMT;
+  const int n_tiles = q.s.meta[1];
+  for (int tt = blockIdx.x; tt < ntile; tt += gridDim.x) {
+    const int t = tile0 + tt;
+    if (t >= n_tiles) break;
+    const int slot = q.s.tiles[3 * t], start = q.s.tiles[3 * t + 1], cnt = q.s.tiles[3 * t + 2];
+    const DevObject &ob = q.objs[slot];
+    float *Z = simt_network(ob, q.s.X + (int64_t)tt * kMT * ldx, ldx, cnt, As, Ws, act0, act1);
+    if (threadIdx.x < cnt) {
+      const int r = threadIdx.x;
+      float z[64];
+      for (int j = 0; j < ob.n_out; ++j) z[j] = Z[j * kMT + r];
+      const int32_t ray = q.s.order[start + r];
+      const float2 tt01 = reinterpret_cast<const float2 *>(q.s.t01)[ray];
+      decode_store(q.hits, ray, z, ob.n_out, ob.n_mat, tt01.x, tt01.y, q.rays.tmin[ray], q.rays.tmax[ray]);
+    }
+    __syncthreads();
+  }
+}
+
+// lsnif_mlp, FP32: X rows in, logits out.
+__global__ void __launch_bounds__(256) mlp_fp32_rows_kernel(const DevObject *dobj, const float *X, int64_t n,
+                                                            float *Zout, int wmax) {
+  extern __shared__ __align__(16) float sm[];
+  const DevObject &ob = *dobj;
+  float *As = sm;
+  float *Ws = As + kKC * kMT;
+  float *act0 = Ws + kKC * wmax;
+  float *act1 = act0 + (size_t)wmax * kMT;
+  for (int64_t t0 = (int64_t)blockIdx.x * kMT; t0 < n; t0 += (int64_t)gridDim.x * kMT) {
+    const int rv = (int)min((int64_t)kMT, n - t0);
+    float *Z = simt_network(ob, X + t0 * ob.n_in, ob.n_in, rv, As, Ws, act0, act1);
+    if (threadIdx.x < rv)
+      for (int j = 0; j < ob.n_out; ++j) Zout[(t0 + threadIdx.x) * ob.n_out + j] = Z[j * kMT + threadIdx.x];
+    __syncthreads();
+  }
+}
+
+static size_t mlp_fp32_smem(int wmax) {
+  return sizeof(float) * ((size_t)kKC * kMT + (size_t)kKC * wmax + 2 * (size_t)wmax * kMT);
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+static int grid_for(int64_t n, int threads, int cap) {
+  int64_t g = (n + threads - 1) / threads;
+  if (g < 1) g = 1;
+  if (g > cap) g = cap;
+  return (int)g;
+}
+
+cudaError_t launch_trace(const QueryLaunch &q, int *launches) {
+  cudaMemsetAsync(q.s.counts, 0, sizeof(int32_t) * q.n_slots * kBuckets, q.stream);
+  const int nb = q.n_slots * kBuckets;
+  const int smem_hist = nb <= 12288;
+  const size_t smem = smem_hist ? nb * sizeof(int) : 0;
+  const int grid = grid_for(q.rays.n, 256, 152 * 16);
+  trace_kernel<<<grid, 256, smem, q.stream>>>(q, smem_hist);
+  *launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_group(const QueryLaunch &q, int *launches) {
+  scan_kernel<<<1, 1024, 0, q.stream>>>(q);
+  const int grid = grid_for(q.rays.n, 256, 152 * 16);
+  scatter_kernel<<<grid, 256, 0, q.stream>>>(q);
+  *launches += 2;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_plain_tail(const QueryLaunch &q, int ldx, int chunk_tiles, int *launches) {
+  const size_t smem = mlp_fp32_smem(q.s.wmax);
+  cudaError_t e = cudaFuncSetAttribute(mlp_fp32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  for (int t0 = 0; t0 < q.s.max_tiles; t0 += chunk_tiles) {
+    const int nt = min(chunk_tiles, q.s.max_tiles - t0);
+    const int64_t items = (int64_t)nt * kTileM * q.H_max;
+    gather_fp32_kernel<<<grid_for(items, 256, 152 * 32), 256, 0, q.stream>>>(q, t0, nt, ldx);
+    mlp_fp32_kernel<<<min(nt, 152 * 4), 256, smem, q.stream>>>(q, t0, nt, ldx);
+    *launches += 2;
+  }
+  return cudaGetLastError();
+}
+
+// ---- stage entry points ----------------------------------------------------
+
+__global__ void trace_only_kernel(const DevObject *dobj, RaysArg r, int32_t *kout, float *t01, float *pts,
+                                  int32_t *vox, int *err) {
+  const DevObject &ob = *dobj;
+  const int H = ob.H, cap = H >> 1;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < r.n; i += (int64_t)gridDim.x * blockDim.x) {
+    float3 o, d;
+    int ea;
+    float t0 = CUDART_NAN_F, t1 = CUDART_NAN_F;
+    int k = 0;
+    bool live = to_unit(ob, r.ox[i], r.oy[i], r.oz[i], r.dx[i], r.dy[i], r.dz[i], o, d) &&
+                unit_slab(o, d, r.tmin[i], t0, t1, ea);
+    if (live) {
+      dda_walk(
+          ob, o, d, t0, t1, ea, [&](uint32_t vid) { return occupied(ob.occ, vid); },
+          [&](const Seg &sg) {
+            float3 a = seg_point(o, d, sg.tin, sg.ain, sg.fin);
+            float3 b = seg_point(o, d, sg.tout, sg.aout, sg.fout);
+            if (pts) {
+              float *w = pts + ((size_t)i * H + 2 * k) * 3;
+              w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = b.x; w[4] = b.y; w[5] = b.z;
+            }
+            if (vox) vox[(size_t)i * cap + k] = (int32_t)sg.vid;
+            ++k;
+            return k < cap;
+          });
+    } else {
+      t0 = t1 = CUDART_NAN_F;
+    }
+    if (vox)
+      for (int j = k; j < cap; ++j) vox[(size_t)i * cap + j] = -1;
+    if (kout) kout[i] = k;
+    if (t01) { t01[2 * i] = t0; t01[2 * i + 1] = t1; }
+  }
+}
+
+cudaError_t launch_trace_only(const DevObject *dobj, const RaysArg &rays, int32_t *k, float *t01, float *pts,
+                              int32_t *vox, int *err, cudaStream_t st) {
+  int grid = grid_for(rays.n, 256, 152 * 16);
+  trace_only_kernel<<<grid, 256, 0, st>>>(dobj, rays, k, t01, pts, vox, err);
+  return cudaGetLastError();
+}
+
+template <typename T, int F>
+__global__ void encode_kernel(DevObject hob, const T *tab, const float *pts, int64_t n, float *feats) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    float3 p = make_float3(pts[3 * i], pts[3 * i + 1], pts[3 * i + 2]);
+    for (int l = 0; l < hob.L; ++l) {
+      float f[F];
+      encode_level<T, F>(tab + (size_t)l * (hob.mask + 1) * F, hob.mask, p, (float)hob.res[l], f);
+      for (int j = 0; j < F; ++j) feats[(i * hob.L + l) * F + j] = f[j];
+    }
+  }
+}
+
+cudaError_t launch_encode(const DevObject *dobj, const DevObject &h, const float *pts, int64_t n, float *feats,
+                          int precision, cudaStream_t st) {
+  (void)dobj;
+  int grid = grid_for(n, 256, 152 * 32);
+  if (precision == LSNIF_FP32_PLAIN) {
+    if (h.F == 2) encode_kernel<float, 2><<<grid, 256, 0, st>>>(h, h.tab32, pts, n, feats);
+    else if (h.F == 4) encode_kernel<float, 4><<<grid, 256, 0, st>>>(h, h.tab32, pts, n, feats);
+    else encode_kernel<float, 1><<<grid, 256, 0, st>>>(h, h.tab32, pts, n, feats);
+  } else {
+    const __half *t16 = reinterpret_cast<const __half *>(h.tab16);
+    if (h.F == 2) encode_kernel<__half, 2><<<grid, 256, 0, st>>>(h, t16, pts, n, feats);
+    else if (h.F == 4) encode_kernel<__half, 4><<<grid, 256, 0, st>>>(h, t16, pts, n, feats);
+    else encode_kernel<__half, 1><<<grid, 256, 0, st>>>(h, t16, pts, n, feats);
+  }
+  return cudaGetLastError();
+}
+
+__global__ void corners_kernel(DevObject hob, const float *pts, int64_t n, uint32_t *out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    float3 p = make_float3(pts[3 * i], pts[3 * i + 1], pts[3 * i + 2]);
+    for (int l = 0; l < hob.L; ++l) {
+      Cell c = lattice_cell(p, (float)hob.res[l]);
+      for (int corner = 0; corner < 8; ++corner) {
+        uint32_t x = c.cx + (corner & 1), y = c.cy + ((corner >> 1) & 1), z = c.cz + ((corner >> 2) & 1);
+        out[(i * hob.L + l) * 8 + corner] = hash3(x, y, z) & hob.mask;
+      }
+    }
+  }
+}
+
+cudaError_t launch_corners(const DevObject *dobj, const DevObject &h, const float *pts, int64_t n, uint32_t *out,
+                           cudaStream_t st) {
+  (void)dobj;
+  int grid = grid_for(n, 256, 152 * 32);
+  corners_kernel<<<grid, 256, 0, st>>>(h, pts, n, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_plain(const DevObject *dobj, const DevObject &h, const float *X, int64_t n, float *Z,
+                             cudaStream_t st) {
+  const int wmax = max(h.width, h.n_out_pad);
+  const size_t smem = mlp_fp32_smem(wmax);
+  cudaError_t e = cudaFuncSetAttribute(mlp_fp32_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  mlp_fp32_rows_kernel<<<grid_for(n, kMT, 152 * 4), 256, smem, st>>>(dobj, X, n, Z, wmax);
+  return cudaGetLastError();
+}
+
+// ---- object preparation -----------------------------------------------------
+
+__global__ void to_half_kernel(const float *src, __half *dst, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = __float2half_rn(src[i]);
+}
+
+cudaError_t launch_tables_to_half(const float *src, uint16_t *dst, int64_t n, cudaStream_t st) {
+  to_half_kernel<<<grid_for(n, 256, 152 * 32), 256, 0, st>>>(src, reinterpret_cast<__half *>(dst), n);
+  return cudaGetLastError();
+}
+
+// BF16 weights in the tcgen05 no-swizzle K-major core-matrix layout:
+// element (n, k) of a layer with K inputs sits at byte
+//   ((n/8)*(K/8) + k/8)*128 + (n%8)*16 + (k%8)*2
+// Rows past the real output count are zero. Biases follow as FP32.
+__global__ void build_umma_kernel(DevObject h, uint8_t *dst) {
+  const float *p = h.mlp32;
+  uint32_t off = 0;
+  int n_layers = h.n_hidden + 1;
+  for (int l = 0; l < n_layers; ++l) {
+    int K = l == 0 ? h.n_in : h.width;
+    int Nr = l < h.n_hidden ? h.width : h.n_out;
+    int Np = l < h.n_hidden ? h.width : h.n_out_pad;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)Np * K;
+         e += (int64_t)gridDim.x * blockDim.x) {
+      int nn = (int)(e / K), kk = (int)(e % K);
+      float v = nn < Nr ? p[(int64_t)nn * K + kk] : 0.f;
+      size_t o = off + ((size_t)(nn / 8) * (K / 8) + kk / 8) * 128 + (nn % 8) * 16 + (kk % 8) * 2;
+      *reinterpret_cast<__nv_bfloat16 *>(dst + o) = __float2bfloat16_rn(v);
+    }
+    const float *b = p + (size_t)Nr * K;
+    float *bd = reinterpret_cast<float *>(dst + h.umma_bias_off) + (size_t)l * h.width;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < Np; j += gridDim.x * blockDim.x)
+      bd[j] = j < Nr ? b[j] : 0.f;
+    off += (uint32_t)Np * K * 2;
+    p += (size_t)Nr * K + Nr;
+  }
+}
+
+// FP32 output layer padded with zero rows to n_out_pad (plain SIMT path).
+__global__ void build_plain_out_kernel(DevObject h, float *dst) {
+  const float *p = h.mlp32;
+  int fan_in = h.n_in;
+  for (int l = 0; l < h.n_hidden; ++l) {
+    p += (size_t)h.width * fan_in + h.width;
+    fan_in = h.width;
+  }
+  const float *b = p + (size_t)h.n_out * h.width;
+  const int tot = h.n_out_pad * h.width;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < tot + h.n_out_pad; i += gridDim.x * blockDim.x) {
+    if (i < tot) {
+      const int r = i / h.width;
+      dst[i] = r < h.n_out ? p[i] : 0.f;
+    } else {
+      const int j = i - tot;
+      dst[i] = j < h.n_out ? b[j] : 0.f;
+    }
+  }
+}
+
+cudaError_t launch_build_umma(const DevObject &h, uint8_t *dst, cudaStream_t st) {
+  build_umma_kernel<<<152, 256, 0, st>>>(h, dst);
+  build_plain_out_kernel<<<16, 256, 0, st>>>(h, const_cast<float *>(h.plain_out));
+  return cudaGetLastError();
+}
+
+}  // namespace lsnif

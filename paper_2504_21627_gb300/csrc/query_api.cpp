@@ -1,0 +1,343 @@
+// Query orchestration behind lsnif_query_rays: scratch workspaces, the
+// launch sequence of either precision, host-buffer queries, the stage entry
+// points used to check each kernel on its own, and profiling.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+
+#include "lsnif_impl.h"
+#include "runtime.h"
+
+using namespace lsnif;
+
+namespace {
+
+constexpr int kChunkTiles = 1024;  // FP32 path: tiles whose features are materialised at once
+
+size_t al(size_t b) { return (b + 255) & ~size_t(255); }
+
+struct Carve {
+  uint8_t *p;
+  template <class T>
+  T *take(size_t bytes) {
+    T *r = reinterpret_cast<T *>(p);
+    p += al(bytes);
+    return r;
+  }
+};
+
+int max_tiles_for(int64_t n, int n_slots) { return (int)(n / kTileM + n_slots + 1); }
+
+}  // namespace
+
+size_t lsnif::workspace_bytes(int64_t n, int H, int n_slots, int n_in) {
+  const int mt = max_tiles_for(n, n_slots);
+  size_t b = al((size_t)n * H * 12) + al((size_t)n * 8) + al((size_t)n) + al((size_t)n * 2) + al((size_t)n * 4) +
+             3 * al((size_t)n_slots * kBuckets * 4) + al((size_t)mt * 12) + al(64 * 4);
+  if (n_in > 0) b += al((size_t)std::min(mt, kChunkTiles) * kTileM * n_in * 4);
+  return b;
+}
+
+int lsnif::ensure_workspace(lsnif_ctx *ctx, Workspace *ws, int64_t n, int H, int n_slots, int n_in) {
+  if (ws->base && n <= ws->cap_rays && H <= ws->cap_H && n_slots <= ws->cap_slots && n_in <= ws->cap_nin)
+    return LSNIF_OK;
+  const int64_t nn = std::max(n, ws->cap_rays);
+  const int HH = std::max(H, ws->cap_H), SS = std::max(n_slots, ws->cap_slots), NI = std::max(n_in, ws->cap_nin);
+  const size_t bytes = workspace_bytes(nn, HH, SS, NI);
+  if (ws->base) {
+    cudaDeviceSynchronize();  // the old scratch may still be in use by queued work
+    dev_free(ctx, ws->base);
+    ws->base = nullptr;
+  }
+  int rc = dev_alloc(ctx, bytes, &ws->base, "query scratch");
+  if (rc) {
+    ws->cap_rays = ws->cap_H = ws->cap_slots = ws->cap_nin = 0;
+    return rc;
+  }
+  ws->bytes = bytes;
+  ws->cap_rays = nn;
+  ws->cap_H = HH;
+  ws->cap_slots = SS;
+  ws->cap_nin = NI;
+  return LSNIF_OK;
+}
+
+void lsnif::free_workspace(lsnif_ctx *ctx, Workspace *ws) {
+  if (ws->base) dev_free(ctx, ws->base);
+  if (ws->stage) dev_free(ctx, ws->stage);
+  *ws = Workspace{};
+}
+
+static QueryScratch carve(Workspace *ws, int64_t n, int H, int n_slots, int n_in) {
+  // carve with the workspace's capacity so pointers stay valid for any
+  // request that fits it
+  const int64_t N = ws->cap_rays;
+  const int HH = ws->cap_H, SS = ws->cap_slots;
+  (void)n; (void)H; (void)n_slots; (void)n_in;
+  Carve c{reinterpret_cast<uint8_t *>(ws->base)};
+  QueryScratch s{};
+  s.pts = c.take<float>((size_t)N * HH * 12);
+  s.t01 = c.take<float>((size_t)N * 8);
+  s.k = c.take<uint8_t>((size_t)N);
+  s.slot = c.take<int16_t>((size_t)N * 2);
+  s.order = c.take<int32_t>((size_t)N * 4);
+  s.counts = c.take<int32_t>((size_t)SS * kBuckets * 4);
+  s.offsets = c.take<int32_t>((size_t)SS * kBuckets * 4);
+  s.cursor = c.take<int32_t>((size_t)SS * kBuckets * 4);
+  const int mt = max_tiles_for(N, SS);
+  s.tiles = c.take<int32_t>((size_t)mt * 12);
+  s.meta = c.take<int32_t>(64 * 4);
+  s.X = ws->cap_nin > 0 ? c.take<float>((size_t)std::min(mt, kChunkTiles) * kTileM * ws->cap_nin * 4) : nullptr;
+  s.max_tiles = max_tiles_for(n, n_slots);
+  return s;
+}
+
+// Objects a query can touch and the shape parameters its kernels need.
+struct Shape {
+  int H = 0, n_in = 0, wmax = 0, n_slots = 0;
+  const Object *rep = nullptr;   // representative object (fused: F/width)
+  uint32_t umma_max = 0;
+  bool mixed_fused = false;      // objects differ in F or width
+};
+
+static int shape_of(lsnif_ctx *ctx, const lsnif_rays *r, Shape *sh) {
+  auto add = [&](const Object *o) {
+    sh->H = std::max(sh->H, o->cfg.H);
+    sh->n_in = std::max(sh->n_in, o->d.n_in);
+    sh->wmax = std::max(sh->wmax, std::max(o->d.width, o->d.n_out_pad));
+    sh->umma_max = std::max(sh->umma_max, o->d.umma_bytes);
+    if (!sh->rep) sh->rep = o;
+    else if (sh->rep->d.F != o->d.F || sh->rep->d.width != o->d.width || o->d.L > 16) sh->mixed_fused = true;
+  };
+  if (!r->obj) {
+    const Object *o = find_object(ctx, r->single_obj);
+    if (!o) return fail(LSNIF_ERR_BAD_HANDLE, "query: bad object handle %u", r->single_obj);
+    add(o);
+  } else {
+    for (int s = 0; s < ctx->n_slots_used; ++s)
+      if (ctx->slots[s]) add(ctx->slots[s]);
+    if (!sh->rep) return fail(LSNIF_ERR_BAD_HANDLE, "query: no objects are loaded");
+  }
+  sh->n_slots = std::max(ctx->n_slots_used, 1);
+  return LSNIF_OK;
+}
+
+static int check_rays(const lsnif_rays *r, const lsnif_hits *h) {
+  if (!r || !h) return fail(LSNIF_ERR_INVALID_ARG, "query: rays or hits is NULL");
+  if (r->n < 0) return fail(LSNIF_ERR_INVALID_ARG, "query: n = %lld", (long long)r->n);
+  if (r->n > ((int64_t)1 << 31) - 1) return fail(LSNIF_ERR_INVALID_ARG, "query: n = %lld exceeds 2^31-1", (long long)r->n);
+  if (r->n > 0 && (!r->ox || !r->oy || !r->oz || !r->dx || !r->dy || !r->dz || !r->tmin || !r->tmax))
+    return fail(LSNIF_ERR_INVALID_ARG, "query: every ray array must be given");
+  return LSNIF_OK;
+}
+
+int lsnif::run_query(lsnif_ctx *ctx, Workspace *ws, const lsnif_rays *r, lsnif_hits *h, int precision,
+                     cudaStream_t st, bool profile) {
+  int rc = check_rays(r, h);
+  if (rc) return rc;
+  if (precision != LSNIF_FP32_PLAIN && precision != LSNIF_BF16_FUSED)
+    return fail(LSNIF_ERR_INVALID_ARG, "query: unknown precision %d", precision);
+  if (r->n == 0) return LSNIF_OK;
+  Shape sh;
+  if ((rc = shape_of(ctx, r, &sh))) return rc;
+  DevObject rep = sh.rep->d;
+  if (precision == LSNIF_BF16_FUSED) {
+    rep.umma_bytes = sh.umma_max;
+    if (sh.mixed_fused || !fused_supported(rep) || fused_smem_bytes(rep) > 232448)
+      return fail(LSNIF_ERR_UNSUPPORTED, "query: the fused BF16 path needs F in {2,4}, width 64/128, L <= 16, "
+                                         "one shape for all objects and weights that fit shared memory");
+  }
+  const int n_in = precision == LSNIF_FP32_PLAIN ? sh.n_in : 0;
+  if ((rc = ensure_workspace(ctx, ws, r->n, sh.H, sh.n_slots, n_in))) return rc;
+  QueryLaunch q{};
+  q.objs = ctx->d_objs;
+  q.n_slots = sh.n_slots;
+  q.H_max = ws->cap_H;
+  q.rays = RaysArg{r->ox, r->oy, r->oz, r->dx, r->dy, r->dz, r->tmin, r->tmax, r->obj, r->single_obj, r->n};
+  q.hits = HitsArg{h->hit, h->t, h->nx, h->ny, h->nz, h->mat, h->ar, h->ag, h->ab, h->logits};
+  q.s = carve(ws, r->n, sh.H, sh.n_slots, n_in);
+  q.s.wmax = sh.wmax;
+  q.err = ctx->d_err;
+  q.stream = st;
+  int launches = 0;
+  if (profile) cudaEventRecord(ctx->ev[0], st);
+  cudaError_t e = launch_trace(q, &launches);
+  if (profile) cudaEventRecord(ctx->ev[1], st);
+  if (e == cudaSuccess) e = launch_group(q, &launches);
+  if (profile) cudaEventRecord(ctx->ev[2], st);
+  if (e == cudaSuccess) {
+    if (precision == LSNIF_FP32_PLAIN) e = launch_plain_tail(q, ws->cap_nin, kChunkTiles, &launches);
+    else e = launch_fused(q, rep, &launches);
+  }
+  if (profile) {
+    cudaEventRecord(ctx->ev[3], st);
+    cudaMemcpyAsync(ctx->d_prof_meta, q.s.meta, 16, cudaMemcpyDeviceToDevice, st);
+    ctx->prof_stream = st;
+    ctx->prof = lsnif_profile{};
+    ctx->prof.n_rays = r->n;
+    ctx->prof.launches = launches + 1;  // + the counts reset
+    ctx->prof_valid = true;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "query launch");
+  return LSNIF_OK;
+}
+
+extern "C" int lsnif_query_rays(lsnif_ctx *ctx, const lsnif_rays *rays, lsnif_hits *hits, int precision,
+                                void *stream) {
+  if (!ctx) return fail(LSNIF_ERR_INVALID_ARG, "lsnif_query_rays: ctx is NULL");
+  cudaSetDevice(ctx->device);
+  return run_query(ctx, &ctx->ws, rays, hits, precision, (cudaStream_t)stream, ctx->profiling);
+}
+
+extern "C" int lsnif_query_rays_host(lsnif_ctx *ctx, const lsnif_rays *rays, lsnif_hits *hits, int precision,
+                                     void *stream) {
+  if (!ctx) return fail(LSNIF_ERR_INVALID_ARG, "lsnif_query_rays_host: ctx is NULL");
+  int rc = check_rays(rays, hits);
+  if (rc) return rc;
+  if (rays->n == 0) return LSNIF_OK;
+  cudaSetDevice(ctx->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  Shape sh;
+  if ((rc = shape_of(ctx, rays, &sh))) return rc;
+  const int64_t n = rays->n;
+  const int n_out = sh.rep ? 8 + 56 : 64;
+  const size_t need = al(n * 4) * 8 + al(n * 4) + al(n) + al(n * 4) * 8 + al(n * 4) + al((size_t)n * 4 * n_out);
+  Workspace *ws = &ctx->ws;
+  if (ws->stage_bytes < need) {
+    if (ws->stage) {
+      cudaDeviceSynchronize();
+      dev_free(ctx, ws->stage);
+      ws->stage = nullptr;
+      ws->stage_bytes = 0;
+    }
+    if ((rc = dev_alloc(ctx, need, &ws->stage, "host-query staging"))) return rc;
+    ws->stage_bytes = need;
+  }
+  Carve c{reinterpret_cast<uint8_t *>(ws->stage)};
+  lsnif_rays dr = *rays;
+  const float *src[8] = {rays->ox, rays->oy, rays->oz, rays->dx, rays->dy, rays->dz, rays->tmin, rays->tmax};
+  const float **dst[8] = {&dr.ox, &dr.oy, &dr.oz, &dr.dx, &dr.dy, &dr.dz, &dr.tmin, &dr.tmax};
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < 8 && e == cudaSuccess; ++i) {
+    float *d = c.take<float>(n * 4);
+    e = cudaMemcpyAsync(d, src[i], n * 4, cudaMemcpyHostToDevice, st);
+    *dst[i] = d;
+  }
+  uint32_t *dobj = c.take<uint32_t>(n * 4);
+  if (rays->obj && e == cudaSuccess) {
+    e = cudaMemcpyAsync(dobj, rays->obj, n * 4, cudaMemcpyHostToDevice, st);
+    dr.obj = dobj;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "lsnif_query_rays_host: upload");
+  lsnif_hits dh{};
+  dh.hit = hits->hit ? c.take<uint8_t>(n) : nullptr;
+  float **hf_dst[8] = {&dh.t, &dh.nx, &dh.ny, &dh.nz, &dh.ar, &dh.ag, &dh.ab, nullptr};
+  float *hf_src[8] = {hits->t, hits->nx, hits->ny, hits->nz, hits->ar, hits->ag, hits->ab, nullptr};
+  for (int i = 0; i < 7; ++i) *hf_dst[i] = hf_src[i] ? c.take<float>(n * 4) : nullptr;
+  dh.mat = hits->mat ? c.take<int32_t>(n * 4) : nullptr;
+  int n_out_q = 0;
+  if (hits->logits) {
+    if (rays->obj) return fail(LSNIF_ERR_INVALID_ARG, "lsnif_query_rays_host: logits need a single object");
+    n_out_q = sh.rep->d.n_out;
+    dh.logits = c.take<float>((size_t)n * 4 * n_out_q);
+  }
+  if ((rc = run_query(ctx, ws, &dr, &dh, precision, st, ctx->profiling))) return rc;
+  if (hits->hit) e = cudaMemcpyAsync(hits->hit, dh.hit, n, cudaMemcpyDeviceToHost, st);
+  for (int i = 0; i < 7 && e == cudaSuccess; ++i)
+    if (hf_src[i]) e = cudaMemcpyAsync(hf_src[i], *hf_dst[i], n * 4, cudaMemcpyDeviceToHost, st);
+  if (hits->mat && e == cudaSuccess) e = cudaMemcpyAsync(hits->mat, dh.mat, n * 4, cudaMemcpyDeviceToHost, st);
+  if (hits->logits && e == cudaSuccess)
+    e = cudaMemcpyAsync(hits->logits, dh.logits, (size_t)n * 4 * n_out_q, cudaMemcpyDeviceToHost, st);
+  if (e != cudaSuccess) return cuda_fail(e, "lsnif_query_rays_host: download");
+  (void)n_out;
+  return check_device(ctx, st);
+}
+
+// ---- stage entry points ------------------------------------------------------
+
+extern "C" int lsnif_trace(lsnif_ctx *ctx, const lsnif_rays *rays, lsnif_trace_out *out, void *stream) {
+  if (!ctx || !rays || !out) return fail(LSNIF_ERR_INVALID_ARG, "lsnif_trace: NULL argument");
+  Object *o = find_object(ctx, rays->single_obj);
+  if (!o) return fail(LSNIF_ERR_BAD_HANDLE, "lsnif_trace: bad handle %u", rays->single_obj);
+  lsnif_hits dummy{};
+  int rc = check_rays(rays, &dummy);
+  if (rc) return rc;
+  if (rays->n == 0) return LSNIF_OK;
+  cudaSetDevice(ctx->device);
+  RaysArg ra{rays->ox, rays->oy, rays->oz, rays->dx, rays->dy, rays->dz, rays->tmin, rays->tmax, nullptr, o->handle,
+             rays->n};
+  cudaError_t e = launch_trace_only(ctx->d_objs + o->slot, ra, out->k, out->t01, out->pts, out->vox, ctx->d_err,
+                                    (cudaStream_t)stream);
+  return e == cudaSuccess ? LSNIF_OK : cuda_fail(e, "lsnif_trace");
+}
+
+extern "C" int lsnif_encode(lsnif_ctx *ctx, lsnif_obj h, const float *pts, int64_t n, float *feats, int precision,
+                            void *stream) {
+  Object *o = find_object(ctx, h);
+  if (!o) return fail(LSNIF_ERR_BAD_HANDLE, "lsnif_encode: bad handle %u", h);
+  if (n < 0 || (n > 0 && (!pts || !feats))) return fail(LSNIF_ERR_INVALID_ARG, "lsnif_encode: bad arguments");
+  if (n == 0) return LSNIF_OK;
+  cudaSetDevice(ctx->device);
+  cudaError_t e = launch_encode(ctx->d_objs + o->slot, o->d, pts, n, feats, precision, (cudaStream_t)stream);
+  return e == cudaSuccess ? LSNIF_OK : cuda_fail(e, "lsnif_encode");
+}
+
+extern "C" int lsnif_corner_indices(lsnif_ctx *ctx, lsnif_obj h, const float *pts, int64_t n, uint32_t *out,
+                                    void *stream) {
+  Object *o = find_object(ctx, h);
+  if (!o) return fail(LSNIF_ERR_BAD_HANDLE, "lsnif_corner_indices: bad handle %u", h);
+  if (n < 0 || (n > 0 && (!pts || !out))) return fail(LSNIF_ERR_INVALID_ARG, "lsnif_corner_indices: bad arguments");
+  if (n == 0) return LSNIF_OK;
+  cudaSetDevice(ctx->device);
+  cudaError_t e = launch_corners(ctx->d_objs + o->slot, o->d, pts, n, out, (cudaStream_t)stream);
+  return e == cudaSuccess ? LSNIF_OK : cuda_fail(e, "lsnif_corner_indices");
+}
+
+extern "C" int lsnif_mlp(lsnif_ctx *ctx, lsnif_obj h, const float *X, int64_t n, float *Z, int precision,
+                         void *stream) {
+  Object *o = find_object(ctx, h);
+  if (!o) return fail(LSNIF_ERR_BAD_HANDLE, "lsnif_mlp: bad handle %u", h);
+  if (n < 0 || (n > 0 && (!X || !Z))) return fail(LSNIF_ERR_INVALID_ARG, "lsnif_mlp: bad arguments");
+  if (n == 0) return LSNIF_OK;
+  cudaSetDevice(ctx->device);
+  cudaError_t e;
+  if (precision == LSNIF_FP32_PLAIN) {
+    e = launch_mlp_plain(ctx->d_objs + o->slot, o->d, X, n, Z, (cudaStream_t)stream);
+  } else if (precision == LSNIF_BF16_FUSED) {
+    if (!fused_supported(o->d) || fused_smem_bytes(o->d) > 232448)
+      return fail(LSNIF_ERR_UNSUPPORTED, "lsnif_mlp: shape not covered by the tensor-core kernel");
+    e = launch_mlp_fused(ctx->d_objs + o->slot, o->d, X, n, Z, ctx->d_err, (cudaStream_t)stream);
+  } else {
+    return fail(LSNIF_ERR_INVALID_ARG, "lsnif_mlp: unknown precision %d", precision);
+  }
+  return e == cudaSuccess ? LSNIF_OK : cuda_fail(e, "lsnif_mlp");
+}
+
+// ---- profiling ---------------------------------------------------------------
+
+extern "C" int lsnif_set_profiling(lsnif_ctx *ctx, int on) {
+  if (!ctx) return fail(LSNIF_ERR_INVALID_ARG, "lsnif_set_profiling: ctx is NULL");
+  ctx->profiling = on != 0;
+  return LSNIF_OK;
+}
+
+extern "C" int lsnif_last_profile(lsnif_ctx *ctx, lsnif_profile *out) {
+  if (!ctx || !out) return fail(LSNIF_ERR_INVALID_ARG, "lsnif_last_profile: NULL argument");
+  if (!ctx->prof_valid) return fail(LSNIF_ERR_INVALID_ARG, "lsnif_last_profile: no profiled query yet");
+  cudaSetDevice(ctx->device);
+  int rc = check_device(ctx, ctx->prof_stream);
+  if (rc) return rc;
+  lsnif_profile p = ctx->prof;
+  cudaEventElapsedTime(&p.ms_trace, ctx->ev[0], ctx->ev[1]);
+  cudaEventElapsedTime(&p.ms_group, ctx->ev[1], ctx->ev[2]);
+  cudaEventElapsedTime(&p.ms_mlp, ctx->ev[2], ctx->ev[3]);
+  cudaEventElapsedTime(&p.ms_total, ctx->ev[0], ctx->ev[3]);
+  p.ms_encode = 0.f;
+  int32_t meta[4] = {0, 0, 0, 0};
+  cudaMemcpy(meta, ctx->d_prof_meta, 16, cudaMemcpyDeviceToHost);
+  p.n_live = meta[0];
+  p.n_points = meta[2];
+  *out = p;
+  return LSNIF_OK;
+}

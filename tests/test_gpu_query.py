@@ -1,0 +1,407 @@
+"""GPU parity of the query path against the FP64 oracle, through the C ABI.
+
+Tolerances (stated per test, derived in the design doc):
+  occupancy, lattice-corner indices: bit-exact
+  voxel lists: exact except near-face rays (counted)
+  FP32 path: logits within 1e-4 of the oracle, relative to the batch's max |logit|
+  BF16 path: logits against the oracle run with the same BF16/FP16 rounding of
+  operands, decisions identical except where |logit| is within the rounding
+  noise; against the pure FP64 oracle the error is reported
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import oracle as O  # noqa: E402
+from paper_2504_21627_gb300 import inputs as I  # noqa: E402
+from paper_2504_21627_gb300 import lsnif  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = lsnif.Context(0)
+    yield c
+    c.close()
+
+
+def _make(ctx, mesh, cfg, seed, table_range=0.5, bias_range=0.1):
+    p = I.random_params(cfg, seed, table_range=table_range, bias_range=bias_range)
+    orc = O.build_object(mesh, cfg, p)
+    h = ctx.load_object(mesh, cfg, tables=p.tables, mlp=p.packed_mlp(), keep_mesh=True)
+    return h, orc, p
+
+
+@pytest.fixture(scope="module")
+def sphere(ctx):
+    cfg = I.cfg_icosphere_small()
+    mesh = I.icosphere(3)
+    h, orc, p = _make(ctx, mesh, cfg, seed=3)
+    return dict(h=h, orc=orc, p=p, mesh=mesh, cfg=cfg)
+
+
+@pytest.fixture(scope="module")
+def torus(ctx):
+    cfg = I.cfg_torus_4m()
+    mesh = I.noise_torus(seed=2)
+    h, orc, p = _make(ctx, mesh, cfg, seed=5, table_range=0.05)
+    return dict(h=h, orc=orc, p=p, mesh=mesh, cfg=cfg)
+
+
+def _cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+# FP32 points carry an absolute error of a few ulps (2^-24 in the unit cube);
+# at lattice resolution N that moves a lattice coordinate by ~N * 4 * 2^-24 and
+# a trilinear feature by up to twice that times the table range per axis. For
+# N_max <= 128 the bound is below 1e-4; above it grows with N_max.
+def fp32_tol(cfg):
+    return max(1e-4, 8 * 2.0 ** -24 * cfg.N_max)
+
+
+# BF16 operands: GPU (FP32 accumulation) and oracle (FP64 accumulation of the
+# same BF16-rounded operands) can round a hidden activation to neighbouring
+# BF16 values; one such step is 2^-8 of that activation.
+BF16_TOL = 2.0 ** -7
+
+
+# ---------------------------------------------------------------------------
+# geometry and traversal
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("which", ["sphere", "torus"])
+def test_occupancy_and_levels_bit_exact(ctx, which, request):
+    o = request.getfixturevalue(which)
+    occ = ctx.read_params(o["h"], lsnif.PARAM_OCCUPANCY)
+    assert np.array_equal(occ, O.occupancy_bits(o["orc"].occ))
+    info = ctx.object_info(o["h"])
+    assert list(info.res[: o["cfg"].L]) == list(o["orc"].res)
+    assert np.array_equal(np.array(info.bmin, np.float32), o["orc"].bmin)
+    assert np.array_equal(np.array(info.bmax, np.float32), o["orc"].bmax)
+    assert info.n_occupied == int(o["orc"].occ.sum())
+
+
+def _trace_compare(ctx, o, rays):
+    k, t01, pts, vox = ctx.trace(_cuda(rays), o["h"])
+    torch.cuda.synchronize()
+    seg = O.ray_segments(o["orc"], rays)
+    k, t01, pts, vox = (x.cpu().numpy() for x in (k, t01, pts, vox))
+    ok = ~seg.near
+    assert np.array_equal(k[ok], seg.k[ok])
+    assert np.array_equal(vox[ok], seg.vox[ok])
+    live = ok & (seg.k > 0)
+    H = o["cfg"].H
+    slot = np.arange(H)[None, :] < 2 * seg.k[:, None]
+    m = live[:, None] & slot
+    err = np.abs(pts[m] - seg.pts[m]).max() if m.any() else 0.0
+    assert err < 2e-5, f"boundary points differ by {err}"
+    fin = ok & np.isfinite(seg.t01[:, 0])
+    assert np.allclose(t01[fin], seg.t01[fin], rtol=2e-6, atol=2e-6)
+    assert np.all(np.isnan(t01[ok & ~np.isfinite(seg.t01[:, 0])]))
+    return seg, int((~ok).sum())
+
+
+def test_traversal_matches_oracle_sphere(ctx, sphere):
+    rays = I.rays_sphere_to_box(4096, 3.0, sphere["orc"].bmin, sphere["orc"].bmax, seed=21)
+    seg, near = _trace_compare(ctx, sphere, rays)
+    assert near < 0.02 * rays.shape[1], f"{near} near-face rays"
+    assert (seg.k == 9).any() and (seg.k == 0).any()
+    print(f"near-face rays: {near} of {rays.shape[1]}")
+
+
+def test_traversal_matches_oracle_torus_sample(ctx, torus):
+    cam = I.seeded_camera(2)
+    rays = I.rays_pinhole(cam, px0=700, py0=900, w=32, h=16)
+    g = np.random.default_rng(1)
+    more = I.rays_pinhole(cam)[:, g.choice(2048 * 2048, 512, replace=False)]
+    rays = np.ascontiguousarray(np.concatenate([rays, more], axis=1))
+    seg, near = _trace_compare(ctx, torus, rays)
+    assert (seg.k > 0).mean() > 0.2
+    print(f"torus: near-face rays {near} of {rays.shape[1]}")
+
+
+def test_traversal_edge_cases(ctx, sphere):
+    b0, b1 = sphere["orc"].bmin.astype(np.float64), sphere["orc"].bmax.astype(np.float64)
+    c = 0.5 * (b0 + b1)
+    o = np.array([[5, 5, 5], [-3, c[1] + 0.013, c[2] + 0.021], [c[0], c[1], c[2]], [0.1, 0.2, 0.3], [-3, 0.01, 0.02],
+                  [np.nan, 0, 0], [-3, 0.05, 0.07], [0.0, 0.0, -5.0]], np.float64)
+    d = np.array([[1, 0, 0], [1, 0, 0], [0.3, 0.5, -0.2], [0, 0, 0], [1, 1e-9, 0], [1, 0, 0], [1, 0.01, 0.0],
+                  [0, 0, 1]], np.float64)
+    rays = I.pack_rays(o, d)
+    rays[6, 6] = 4.5   # tmin past the object
+    rays[6, 7] = 4.8   # tmin inside the box: interior first point
+    _trace_compare(ctx, sphere, np.ascontiguousarray(rays))
+
+
+def test_corner_indices_bit_exact(ctx, torus):
+    g = np.random.default_rng(4)
+    n = 20000
+    p = g.random((n, 3)).astype(np.float32)
+    V = torus["cfg"].V
+    axis = g.integers(0, 3, n)
+    face = n // 2
+    p[np.arange(face), axis[:face]] = (g.integers(0, V + 1, face) / V).astype(np.float32)
+    p[:8] = [[0, 0, 0], [1, 1, 1], [0.5, 0.25, 0.125], [1, 0, 0.5], [1e-9, 0.999999, 0.5], [0, 1, 0],
+             [0.3, 0.3, 0.3], [0.9999999, 0.5, 0.5]]
+    got = ctx.corner_indices(torus["h"], _cuda(p)).cpu().numpy().view(np.uint32)
+    zeros = np.zeros((torus["cfg"].L, 1 << torus["cfg"].log2_T, torus["cfg"].F))
+    _, want, _ = O.encode(p.astype(np.float64), torus["orc"].res, torus["cfg"].F, torus["cfg"].log2_T, zeros,
+                          debug=True)
+    assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("prec", [lsnif.FP32_PLAIN, lsnif.BF16_FUSED])
+def test_encoding_matches_oracle(ctx, torus, prec):
+    g = np.random.default_rng(5)
+    n = 4099
+    p = g.random((n, 3)).astype(np.float32)
+    p[: n // 2, 0] = (g.integers(0, 129, n // 2) / 128).astype(np.float32)
+    got = ctx.encode(torus["h"], _cuda(p), precision=prec).cpu().numpy().astype(np.float64)
+    tab = torus["orc"].tables if prec == lsnif.FP32_PLAIN else O.round_fp16(torus["orc"].tables)
+    want = O.encode(p.astype(np.float64), torus["orc"].res, torus["cfg"].F, torus["cfg"].log2_T, tab)
+    scale = np.abs(tab).max()
+    err = np.abs(got - want).max() / scale
+    assert err < 1e-5, err   # FP32 rounding of an 8-term weighted sum
+
+
+# ---------------------------------------------------------------------------
+# network
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n", [1, 127, 128, 129, 1000, 5001])
+def test_mlp_fp32_matches_oracle(ctx, torus, n):
+    g = np.random.default_rng(n)
+    X = g.normal(scale=0.05, size=(n, torus["cfg"].n_in)).astype(np.float32)
+    got = ctx.mlp(torus["h"], _cuda(X), lsnif.FP32_PLAIN).cpu().numpy()
+    want = O.mlp_forward(X.astype(np.float64), torus["orc"].weights, torus["cfg"].activation)
+    err = np.abs(got - want).max() / np.abs(want).max()
+    assert err < 1e-5, err
+
+
+@pytest.mark.parametrize("n", [1, 127, 128, 129, 1000, 5001])
+def test_mlp_tensor_core_matches_oracle(ctx, torus, n):
+    g = np.random.default_rng(100 + n)
+    X = g.normal(scale=0.05, size=(n, torus["cfg"].n_in)).astype(np.float32)
+    got = ctx.mlp(torus["h"], _cuda(X), lsnif.BF16_FUSED).cpu().numpy()
+    ctx.check()
+    want16 = O.mlp_forward(X.astype(np.float64), torus["orc"].weights, torus["cfg"].activation, precision="bf16")
+    want64 = O.mlp_forward(X.astype(np.float64), torus["orc"].weights, torus["cfg"].activation)
+    scale = np.abs(want64).max()
+    e16 = np.abs(got - want16).max() / scale
+    e64 = np.abs(got - want64).max() / scale
+    assert e16 < BF16_TOL, f"vs BF16-rounded oracle: {e16}"
+    assert e64 < 3e-2, f"vs FP64 oracle: {e64}"
+
+
+# ---------------------------------------------------------------------------
+# end to end
+# ---------------------------------------------------------------------------
+
+def _query_compare(ctx, o, rays, prec, tol_logit):
+    out = ctx.query_rays(_cuda(rays), obj=o["h"], precision=prec, logits=True)
+    ctx.check()
+    ref, seg = O.query(o["orc"], rays, precision="bf16" if prec == lsnif.BF16_FUSED else "f64")
+    ok = ~seg.near
+    live = ref.live & ok
+    lg = out.logits.cpu().numpy()
+    scale = np.abs(ref.logits[live]).max()
+    err = np.abs(lg[live] - ref.logits[live]).max() / scale
+    assert err < tol_logit, f"logit error {err:.3g}"
+    # rays that never reach the network: exact miss record
+    miss = ~ref.live & ok
+    assert not out.hit.cpu().numpy()[miss].any()
+    assert np.all(np.isinf(out.t.cpu().numpy()[miss]))
+    assert np.all(out.mat.cpu().numpy()[miss] == -1)
+    assert np.all(np.isnan(lg[miss]))
+    # decisions: identical away from the decision boundary
+    z0 = ref.logits[live, 0]
+    firm = np.abs(z0) > 4 * tol_logit * scale
+    hit = out.hit.cpu().numpy().astype(bool)[live]
+    assert np.array_equal(hit[firm], ref.hit[live][firm])
+    zm = np.sort(ref.logits[live, 8:], axis=1)
+    firm_m = (zm[:, -1] - zm[:, -2]) > 8 * tol_logit * scale if zm.shape[1] > 1 else np.ones(live.sum(), bool)
+    assert np.array_equal(out.mat.cpu().numpy()[live][firm_m], ref.mat[live][firm_m])
+    # t = t0 + sigmoid(z1)(t1 - t0) and sigmoid' <= 1/4: the hit-distance error
+    # is at most a quarter of the z1 error times the interval length
+    t = out.t.cpu().numpy()[live]
+    span = np.nanmax(seg.t01[live, 1] - seg.t01[live, 0])
+    assert np.allclose(t, ref.t[live], rtol=0, atol=0.25 * tol_logit * scale * span * 2 + 1e-5)
+    return out, ref, seg
+
+
+def test_query_fp32_sphere(ctx, sphere):
+    rays = I.rays_sphere_to_box(4096, 3.0, sphere["orc"].bmin, sphere["orc"].bmax, seed=31)
+    _query_compare(ctx, sphere, rays, lsnif.FP32_PLAIN, fp32_tol(sphere["cfg"]))
+
+
+def test_query_fp32_torus_sample(ctx, torus):
+    cam = I.seeded_camera(2)
+    g = np.random.default_rng(3)
+    rays = np.ascontiguousarray(I.rays_pinhole(cam)[:, g.choice(2048 * 2048, 768, replace=False)])
+    _query_compare(ctx, torus, rays, lsnif.FP32_PLAIN, fp32_tol(torus["cfg"]))
+
+
+def test_query_bf16_torus_sample(ctx, torus):
+    cam = I.seeded_camera(2)
+    g = np.random.default_rng(4)
+    rays = np.ascontiguousarray(I.rays_pinhole(cam)[:, g.choice(2048 * 2048, 768, replace=False)])
+    _query_compare(ctx, torus, rays, lsnif.BF16_FUSED, BF16_TOL + fp32_tol(torus["cfg"]))
+
+
+def test_query_bf16_sphere_unsupported_shape_is_refused(ctx, sphere):
+    # the sphere object fits the fused kernel (F=2, width 64): it must run
+    rays = I.rays_sphere_to_box(1000, 3.0, sphere["orc"].bmin, sphere["orc"].bmax, seed=32)
+    _query_compare(ctx, sphere, rays, lsnif.BF16_FUSED, BF16_TOL + fp32_tol(sphere["cfg"]))
+    # a width the tensor-core kernel does not instantiate is refused, not run
+    cfg = I.Config(V=8, H=8, L=2, F=4, log2_T=8, N_min=4, N_max=8, n_hidden=1, width=32, n_mat=2)
+    h = ctx.load_object(I.icosphere(1), cfg)
+    r = _cuda(I.rays_sphere_to_box(10, 3.0, (-1, -1, -1), (1, 1, 1), seed=1))
+    with pytest.raises(lsnif.LsnifError) as e:
+        ctx.query_rays(r, obj=h, precision=lsnif.BF16_FUSED)
+    assert e.value.code == -10
+    ctx.query_rays(r, obj=h, precision=lsnif.FP32_PLAIN)
+    ctx.check()
+    ctx.unload_object(h)
+
+
+@pytest.mark.parametrize("prec", [lsnif.FP32_PLAIN, lsnif.BF16_FUSED])
+def test_full_size_torus_4m_rays(ctx, torus, prec):
+    """The benchmark's workload and launch configuration: 2048 x 2048 primary
+    rays. A seeded sample is checked against the oracle ray by ray; all
+    outputs are checked for the properties that hold at any size."""
+    cam = I.seeded_camera(2)
+    rays = I.rays_pinhole(cam)
+    r = _cuda(rays)
+    out = ctx.query_rays(r, obj=torus["h"], precision=prec)
+    ctx.check()
+    torch.cuda.synchronize()
+    g = np.random.default_rng(8)
+    idx = np.sort(g.choice(rays.shape[1], 256, replace=False))
+    sub = np.ascontiguousarray(rays[:, idx])
+    ref, seg = O.query(torus["orc"], sub, precision="bf16" if prec == lsnif.BF16_FUSED else "f64")
+    ok = ~seg.near & ref.live
+    t = out.t.cpu().numpy()
+    tol_logit = fp32_tol(torus["cfg"]) + (0 if prec == lsnif.FP32_PLAIN else BF16_TOL)
+    scale = np.abs(ref.logits[ok]).max()
+    span = np.nanmax(seg.t01[ok, 1] - seg.t01[ok, 0])
+    assert np.allclose(t[idx][ok], ref.t[ok], atol=0.25 * tol_logit * scale * span * 2 + 1e-5)
+    assert np.array_equal(np.isinf(t[idx])[~seg.near], ~ref.live[~seg.near])
+    # properties of every ray
+    hit = out.hit.cpu().numpy().astype(bool)
+    mat = out.mat.cpu().numpy()
+    nrm = out.normal.cpu().numpy()
+    assert np.all(np.isfinite(t[hit])) and np.all(t[hit] >= 0)
+    assert np.all((mat == -1) == np.isinf(t))
+    assert np.all((mat >= -1) & (mat < torus["cfg"].n_mat))
+    ln = np.linalg.norm(nrm[:, np.isfinite(t)], axis=0)
+    assert np.all((np.abs(ln - 1) < 1e-4) | (ln == 0))
+
+
+def test_host_buffer_query_equals_device_query(ctx, sphere):
+    rays = I.rays_sphere_to_box(3000, 3.0, sphere["orc"].bmin, sphere["orc"].bmax, seed=41)
+    for prec in (lsnif.FP32_PLAIN, lsnif.BF16_FUSED):
+        dev = ctx.query_rays(_cuda(rays), obj=sphere["h"], precision=prec)
+        torch.cuda.synchronize()
+        host = ctx.query_rays_host(torch.from_numpy(rays).pin_memory(), obj=sphere["h"], precision=prec)
+        for a, b in ((dev.hit, host.hit), (dev.t, host.t), (dev.mat, host.mat), (dev.normal, host.normal)):
+            assert torch.equal(a.cpu(), b.cpu())
+
+
+def test_multi_object_batch_equals_single_object_queries(ctx, sphere, torus):
+    cam = I.seeded_camera(2)
+    ra = I.rays_sphere_to_box(2000, 3.0, sphere["orc"].bmin, sphere["orc"].bmax, seed=51)
+    rb = np.ascontiguousarray(I.rays_pinhole(cam, px0=600, py0=1000, w=64, h=40))
+    both = np.ascontiguousarray(np.concatenate([ra, rb], axis=1))
+    handles = np.concatenate([np.full(ra.shape[1], sphere["h"]), np.full(rb.shape[1], torus["h"])]).astype(np.uint32)
+    perm = np.random.default_rng(5).permutation(both.shape[1])
+    both = np.ascontiguousarray(both[:, perm])
+    handles = np.ascontiguousarray(handles[perm])
+    for prec in (lsnif.FP32_PLAIN, lsnif.BF16_FUSED):
+        mixed = ctx.query_rays(_cuda(both), obj_per_ray=_cuda(handles.view(np.int32)), precision=prec)
+        a = ctx.query_rays(_cuda(ra), obj=sphere["h"], precision=prec)
+        b = ctx.query_rays(_cuda(rb), obj=torus["h"], precision=prec)
+        ctx.check()
+        inv = np.argsort(perm)
+        for f in ("hit", "t", "mat"):
+            m = getattr(mixed, f).cpu().numpy()[inv]
+            single = np.concatenate([getattr(a, f).cpu().numpy(), getattr(b, f).cpu().numpy()])
+            assert np.array_equal(m, single), f
+
+
+def test_unknown_handle_is_reported_not_run(ctx, sphere):
+    rays = I.rays_sphere_to_box(300, 3.0, sphere["orc"].bmin, sphere["orc"].bmax, seed=61)
+    handles = np.full(300, sphere["h"], np.uint32)
+    handles[7] = 0xDEAD0001
+    out = ctx.query_rays(_cuda(rays), obj_per_ray=_cuda(handles.view(np.int32)), precision=lsnif.FP32_PLAIN)
+    with pytest.raises(lsnif.LsnifError) as e:
+        ctx.check()
+    assert e.value.code == -8
+    assert out.mat[7].item() == -1 and not out.hit[7].item()
+    ctx.check()  # the flag is cleared
+
+
+def test_empty_batch_is_a_noop(ctx, sphere):
+    r = torch.zeros((8, 0), device="cuda")
+    out = ctx.query_rays(r, obj=sphere["h"], precision=lsnif.BF16_FUSED)
+    assert out.t.numel() == 0
+
+
+# ---------------------------------------------------------------------------
+# objects: serialization, budget, fault injection
+# ---------------------------------------------------------------------------
+
+def test_save_load_roundtrip_bit_exact(ctx, sphere):
+    blob = ctx.save_object(sphere["h"])
+    h2 = ctx.load_object(blob=blob)
+    for w in (lsnif.PARAM_OCCUPANCY, lsnif.PARAM_TABLES, lsnif.PARAM_MLP):
+        assert np.array_equal(ctx.read_params(h2, w), ctx.read_params(sphere["h"], w))
+    assert ctx.save_object(h2) == blob
+    rays = _cuda(I.rays_sphere_to_box(1000, 3.0, sphere["orc"].bmin, sphere["orc"].bmax, seed=71))
+    a = ctx.query_rays(rays, obj=sphere["h"], precision=lsnif.BF16_FUSED)
+    b = ctx.query_rays(rays, obj=h2, precision=lsnif.BF16_FUSED)
+    assert torch.equal(a.t, b.t) and torch.equal(a.mat, b.mat)
+    ctx.unload_object(h2)
+    bad = bytearray(blob)
+    bad[200] ^= 0xFF
+    with pytest.raises(lsnif.LsnifError) as e:
+        ctx.load_object(blob=bytes(bad))
+    assert e.value.code == -5
+    with pytest.raises(lsnif.LsnifError) as e:
+        ctx.load_object(blob=blob[:-9])
+    assert e.value.code == -5
+    with pytest.raises(lsnif.LsnifError) as e:
+        ctx.unload_object(h2)
+    assert e.value.code == -2
+
+
+def test_budget_and_injected_allocation_failure():
+    cfg = I.cfg_icosphere_small()
+    mesh = I.icosphere(2)
+    with lsnif.Context(0, budget_bytes=2 << 20) as c:
+        with pytest.raises(lsnif.LsnifError) as e:
+            c.load_object(mesh, cfg)
+        assert e.value.code == -4
+    with lsnif.Context(0) as c:
+        base = c.device_bytes()
+        for k in range(0, 6):
+            c.debug_fail_alloc_after(k)
+            try:
+                h = c.load_object(mesh, cfg)
+                c.unload_object(h)
+            except lsnif.LsnifError as e:
+                assert e.code == -3
+            assert c.device_bytes() == base, "a failed load leaked device memory"
+        c.debug_fail_alloc_after(-1)
+        h = c.load_object(mesh, cfg)
+        assert c.device_bytes() > base
+
+
+def test_invalid_configs_are_rejected(ctx):
+    mesh = I.icosphere(1)
+    for bad in (dict(V=30), dict(H=7), dict(F=3), dict(width=40), dict(log2_T=30), dict(n_mat=0)):
+        cfg = I.Config(**{**I.cfg_icosphere_small().__dict__, **bad})
+        with pytest.raises(lsnif.LsnifError) as e:
+            ctx.load_object(mesh, cfg)
+        assert e.value.code == -1, bad

@@ -82,18 +82,18 @@ def test_face_points_need_four_corners():
     assert np.all(nz <= 4) and (nz == 4).mean() > 0.95
 
 
-def test_fp32_corner_indices_agree_with_fp64_off_the_lattice():
+def test_fp32_points_have_exact_fp64_lattice_products():
+    """The cell decision is the floor of p * N for an FP32 point p: in FP64
+    that product of a 24-bit and an (at most) 21-bit integer is exact, so the
+    oracle's decision is the mathematical one."""
     g = np.random.default_rng(3)
-    pts = g.random((2000, 3)).astype(np.float32)
-    res = np.array([16, 31, 213, 2048], np.int32)
-    i32 = O.corner_indices_f32(pts, res, 19)
-    _, i64, _ = O.encode(pts.astype(np.float64), res, 2, 19, np.zeros((4, 1 << 19, 2)), debug=True)
-    # where FP32 and FP64 products fall in the same cell the indices agree
-    x64 = pts.astype(np.float64)[:, None, :] * res[None, :, None]
-    x32 = (pts[:, None, :] * res[None, :, None].astype(np.float32)).astype(np.float64)
-    same = np.all(np.floor(x64) == np.floor(x32), axis=-1)
-    assert same.mean() > 0.99
-    assert np.array_equal(i32[same], i64[same])
+    p = g.random(10000).astype(np.float32)
+    for N in (16, 213, 2048, 1 << 20):
+        x = p.astype(np.float64) * N
+        # exact: splitting p into integer mantissa m and exponent gives m * N exactly
+        m, e = np.frexp(p.astype(np.float64))
+        mi = (m * 2 ** 24).astype(np.int64)
+        assert np.array_equal(x, np.ldexp((mi * N).astype(np.float64), e - 24))
 
 
 def test_backward_is_the_adjoint_of_the_encoding():

@@ -240,3 +240,21 @@ def test_storage_model_against_printed_numbers():
     per_obj = round(fp["total"] / 2 ** 20, 2)
     for key, count in (("scene_statues", 4), ("scene_junkshop", 9), ("scene_classroom", 15)):
         assert round(count * per_obj * 2 ** 20) == round(gf[key])
+
+
+def test_rays_without_points_take_no_part_in_the_loss():
+    cfg, m, obj = _tiny_object(4)
+    rays = I.rays_sphere_to_box(80, 3.0, 2.5 * obj.bmin, 2.5 * obj.bmax, seed=9)   # some miss the object
+    seg = O.ray_segments(obj, rays)
+    assert (seg.k == 0).any() and (seg.k > 0).any()
+    lab = O.labels(m, rays, np.nan_to_num(seg.t01))
+    terms, grads, gt = O.forward_backward(obj, rays, lab, seg)
+    keep = seg.k > 0
+    sub = rays[:, keep]
+    seg2 = O.ray_segments(obj, sub)
+    lab2 = O.Labels(lab.occ[keep], lab.t_local[keep], lab.normal[keep], lab.albedo[keep], lab.mat[keep])
+    terms2, grads2, gt2 = O.forward_backward(obj, sub, lab2, seg2)
+    assert abs(terms["total"] - terms2["total"]) < 1e-13
+    for (a, b), (c, d) in zip(grads, grads2):
+        assert np.allclose(a, c, atol=1e-15) and np.allclose(b, d, atol=1e-15)
+    assert np.allclose(gt, gt2, atol=1e-15)
