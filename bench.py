@@ -73,11 +73,13 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def workload(seed_mesh=2, seed_cam=2):
+def workload(side: int = 2048, seed_mesh=2, seed_cam=2):
+    """side < 2048 keeps the same camera and scene at a lower resolution
+    (profiling captures only)."""
     cfg = I.cfg_torus_4m()
     mesh = I.noise_torus(seed=seed_mesh)
     params = I.random_params(cfg, seed=5, table_range=0.05, bias_range=0.1)
-    cam = I.seeded_camera(seed_cam)
+    cam = I.seeded_camera(seed_cam, width=side, height=side)
     rays = I.rays_pinhole(cam)
     return cfg, mesh, params, rays
 
@@ -127,10 +129,15 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+_ORC = {}
+
+
 def oracle_rate(cfg, mesh, params, rays, n_sample: int, seed: int = 0):
     """The FP64 oracle, as it stands, on a seeded sample of the workload's rays."""
     from oracle import oracle as O
-    orc = O.build_object(mesh, cfg, params)
+    if "obj" not in _ORC:
+        _ORC["obj"] = O.build_object(mesh, cfg, params)
+    orc = _ORC["obj"]
     g = np.random.default_rng(seed)
     idx = np.sort(g.choice(rays.shape[1], n_sample, replace=False))
     sub = np.ascontiguousarray(rays[:, idx])
@@ -176,6 +183,7 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=2048)
     ap.add_argument("--cpu-sample", type=int, default=4096)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--side", type=int, default=2048, help="image side; below 2048 only for profiling captures")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -197,7 +205,7 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    cfg, mesh, params, rays_np = workload()
+    cfg, mesh, params, rays_np = workload(args.side)
     n = rays_np.shape[1]
     ctx = lsnif.Context(local)
     obj = ctx.load_object(mesh, cfg, tables=params.tables, mlp=params.packed_mlp())
@@ -236,17 +244,13 @@ def main():
     clocks = clk.summary()
     ms32, prof32, wall32 = timed(lsnif.FP32_PLAIN, max(3, args.steps // 2), 3, profile=True)
 
-    def reduce_max(x: float) -> float:
-        if world > 1:
-            t = torch.tensor([x], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            return float(t.item())
-        return x
+    from paper_2504_21627_gb300 import replicas
 
-    mean16 = reduce_max(float(ms16.mean()))
-    mean32 = reduce_max(float(ms32.mean()))
-    value = world * n / (mean16 / 1e3) / 1e6
-    v32 = world * n / (mean32 / 1e3) / 1e6
+    def reduce_max(x: float) -> float:
+        return replicas.aggregate(x, n)[0]
+
+    mean16, _, value = replicas.aggregate(float(ms16.mean()), n)
+    mean32, _, v32 = replicas.aggregate(float(ms32.mean()), n)
 
     # ---- end to end through the host-buffer C-ABI call ----
     host_rays = torch.from_numpy(rays_np).pin_memory()

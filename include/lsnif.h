@@ -281,6 +281,25 @@ LSNIF_API int lsnif_corner_indices(lsnif_ctx *ctx, lsnif_obj obj, const float *p
 LSNIF_API int lsnif_mlp(lsnif_ctx *ctx, lsnif_obj obj, const float *X, int64_t n, float *Z, int precision,
               void *stream);
 
+/* ---- autotuning of the fused kernel's tile shape ------------------------ */
+
+/* Number of fused-kernel variants (threads per CTA x corner-load levels in
+ * flight per gather item). */
+LSNIF_API int lsnif_variant_count(void);
+
+/* Shape of variant v: *threads per CTA, *levels of corner loads in flight.
+ * Errors: INVALID_ARG for v out of range. */
+LSNIF_API int lsnif_variant_shape(int v, int *threads, int *levels);
+
+/* Use variant v for every later BF16 query of the context. */
+LSNIF_API int lsnif_set_variant(lsnif_ctx *ctx, int v);
+
+/* Time every variant on `rays` (DEVICE buffers, `reps` queries each after one
+ * warm-up, CUDA events on `stream`, synchronous) and keep the fastest for the
+ * context; *chosen (may be NULL) receives its index. Results of the queries
+ * are discarded; the variants compute identical results. */
+LSNIF_API int lsnif_autotune(lsnif_ctx *ctx, const lsnif_rays *rays, int reps, void *stream, int *chosen);
+
 /* ---- training (Sec. 5.2, 5.3) ------------------------------------------ */
 
 /* Number of uniforms per training ray that lsnif_make_training_rays reads. */

@@ -166,6 +166,107 @@ __device__ __forceinline__ void encode_level(const T *__restrict__ tab, uint32_t
   }
 }
 
+// ---------------------------------------------------------------------------
+// Batched, branch-free gather of NL levels of one point (the fused kernel's
+// hot loop). All corner addresses of the batch are formed first, then every
+// load is issued as a predicated ld.global.nc (no branches between loads, so
+// they are all in flight together), then the weights are applied. Pair
+// loads: one 16-byte load of the aligned group holding corner x0; corner x1
+// shares it when it falls in the same group, otherwise it is a second,
+// predicated entry load. Zero-weight corners issue nothing.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 ldg16_if(const void *p, bool pred) {
+  uint4 v = make_uint4(0u, 0u, 0u, 0u);
+  asm("{\n.reg .pred q;\nsetp.ne.b32 q, %4, 0;\n@q ld.global.nc.v4.u32 {%0,%1,%2,%3}, [%5];\n}\n"
+      : "+r"(v.x), "+r"(v.y), "+r"(v.z), "+r"(v.w)
+      : "r"((int)pred), "l"(p));
+  return v;
+}
+
+__device__ __forceinline__ uint32_t ldg4_if(const void *p, bool pred) {
+  uint32_t v = 0u;
+  asm("{\n.reg .pred q;\nsetp.ne.b32 q, %1, 0;\n@q ld.global.nc.u32 %0, [%2];\n}\n" : "+r"(v) : "r"((int)pred), "l"(p));
+  return v;
+}
+
+__device__ __forceinline__ uint2 ldg8_if(const void *p, bool pred) {
+  uint2 v = make_uint2(0u, 0u);
+  asm("{\n.reg .pred q;\nsetp.ne.b32 q, %2, 0;\n@q ld.global.nc.v2.u32 {%0,%1}, [%3];\n}\n"
+      : "+r"(v.x), "+r"(v.y)
+      : "r"((int)pred), "l"(p));
+  return v;
+}
+
+// FP16 tables, F in {2, 4}: entries of 4 or 8 bytes.
+template <int F, int NL>
+__device__ __forceinline__ void encode_levels_f16(const __half *__restrict__ tab0, size_t level_stride, uint32_t mask,
+                                                  const float3 &p, const float *Ns, float (&out)[NL][F]) {
+  constexpr int EB = F * 2;        // entry bytes
+  constexpr int G = 16 / EB;       // entries per 16-byte group
+  const uint8_t *base = reinterpret_cast<const uint8_t *>(tab0);
+  float wx[NL], wy[NL], wz[NL];
+  uint32_t ia[NL][4], ib[NL][4];
+  bool pa[NL][4], pb[NL][4];
+#pragma unroll
+  for (int u = 0; u < NL; ++u) {
+    const Cell c = lattice_cell(p, Ns[u]);
+    wx[u] = c.wx;
+    wy[u] = c.wy;
+    wz[u] = c.wz;
+    const uint32_t hy0 = c.cy * kPi2, hy1 = (c.cy + 1u) * kPi2;
+    const uint32_t hz0 = c.cz * kPi3, hz1 = (c.cz + 1u) * kPi3;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int dy = q & 1, dz = q >> 1;
+      const uint32_t b = (dy ? hy1 : hy0) ^ (dz ? hz1 : hz0);
+      ia[u][q] = (c.cx ^ b) & mask;
+      ib[u][q] = ((c.cx + 1u) ^ b) & mask;
+      pa[u][q] = (dy == 0 || c.wy != 0.f) && (dz == 0 || c.wz != 0.f);
+      pb[u][q] = pa[u][q] && c.wx != 0.f && ((ia[u][q] ^ ib[u][q]) >= (uint32_t)G);
+    }
+  }
+  uint4 ga[NL][4];
+  uint32_t gb[NL][4][EB / 4];
+#pragma unroll
+  for (int u = 0; u < NL; ++u) {
+    const uint8_t *tl = base + (size_t)u * level_stride;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      ga[u][q] = ldg16_if(tl + (size_t)(ia[u][q] & ~(uint32_t)(G - 1)) * EB, pa[u][q]);
+      if constexpr (EB == 4) {
+        gb[u][q][0] = ldg4_if(tl + (size_t)ib[u][q] * EB, pb[u][q]);
+      } else {
+        const uint2 t = ldg8_if(tl + (size_t)ib[u][q] * EB, pb[u][q]);
+        gb[u][q][0] = t.x;
+        gb[u][q][1] = t.y;
+      }
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < NL; ++u) {
+#pragma unroll
+    for (int f = 0; f < F; ++f) out[u][f] = 0.f;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int dy = q & 1, dz = q >> 1;
+      float v0[F], v1[F];
+      unpack_entry<__half, F>(ga[u][q], ia[u][q] & (G - 1), v0);
+      if (pb[u][q]) {
+        uint4 t = make_uint4(gb[u][q][0], EB == 8 ? gb[u][q][EB / 4 - 1] : 0u, 0u, 0u);
+        unpack_entry<__half, F>(t, 0, v1);
+      } else if ((ia[u][q] ^ ib[u][q]) < (uint32_t)G) {
+        unpack_entry<__half, F>(ga[u][q], ib[u][q] & (G - 1), v1);
+      } else {  // x1 corner has zero weight and was not fetched
+#pragma unroll
+        for (int f = 0; f < F; ++f) v1[f] = v0[f];
+      }
+      const float wyz = (dy ? wy[u] : 1.f - wy[u]) * (dz ? wz[u] : 1.f - wz[u]);
+#pragma unroll
+      for (int f = 0; f < F; ++f) out[u][f] = fmaf(wyz, fmaf(wx[u], v1[f] - v0[f], v0[f]), out[u][f]);
+    }
+  }
+}
+
 // Scatter of a feature gradient into the level's table (backward of
 // encode_level): table[idx] += weight * g, every non-zero corner.
 __device__ __forceinline__ void encode_level_backward(float *__restrict__ gtab, uint32_t mask, const float3 &p,

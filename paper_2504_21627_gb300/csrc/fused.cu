@@ -26,7 +26,6 @@ namespace lsnif {
 
 namespace {
 
-constexpr int kThreads = 512;
 constexpr int kNBuf = 3;
 constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
 
@@ -119,9 +118,11 @@ struct Smem {
 }  // namespace
 
 // F: features per level; W: hidden width; XROWS: read the network input
-// from global rows instead of gathering it.
-template <int F, int W, bool XROWS>
-__global__ void __launch_bounds__(kThreads, 1) fused_kernel(FusedArgs a) {
+// from global rows instead of gathering it; NT: threads per CTA; NLB:
+// levels whose corner loads are in flight together per gather item.
+template <int F, int W, bool XROWS, int NT, int NLB>
+__global__ void __launch_bounds__(NT, 1) fused_kernel(FusedArgs a) {
+  constexpr int kThreads = NT;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const QueryLaunch &q = a.q;
@@ -269,19 +270,20 @@ __global__ void __launch_bounds__(kThreads, 1) fused_kernel(FusedArgs a) {
           const int32_t ray = S.ray[r];
           const float *P = q.s.pts + ((size_t)ray * Hs + 2 * s + j) * 3;
           const float3 p = make_float3(P[0], P[1], P[2]);
-          constexpr int LPG = 8 / F;  // levels per 16-byte group
-          float f[LPG][F];
-#pragma unroll
-          for (int u = 0; u < LPG; ++u) {
-            const int l = g * LPG + u;
-            const __half *tl = reinterpret_cast<const __half *>(tab) + (size_t)l * (mask + 1) * F;
-            encode_level<__half, F>(tl, mask, p, s_res[l], f[u]);
-          }
+          constexpr int LPG = 8 / F;  // levels per 16-byte group of the A tile
           float flat[8];
+          const size_t lstride = (size_t)(mask + 1) * F;
 #pragma unroll
-          for (int u = 0; u < LPG; ++u)
+          for (int u0 = 0; u0 < LPG; u0 += NLB) {
+            const int l = g * LPG + u0;
+            float f[NLB][F];
+            encode_levels_f16<F, NLB>(reinterpret_cast<const __half *>(tab) + (size_t)l * lstride, lstride * 2,
+                                      mask, p, s_res + l, f);
 #pragma unroll
-            for (int c = 0; c < F; ++c) flat[u * F + c] = f[u][c];
+            for (int u = 0; u < NLB; ++u)
+#pragma unroll
+              for (int c = 0; c < F; ++c) flat[(u0 + u) * F + c] = f[u][c];
+          }
           outv = make_uint4(pack_bf16(flat[0], flat[1]), pack_bf16(flat[2], flat[3]), pack_bf16(flat[4], flat[5]),
                             pack_bf16(flat[6], flat[7]));
         }
@@ -317,14 +319,13 @@ __global__ void __launch_bounds__(kThreads, 1) fused_kernel(FusedArgs a) {
         const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
         if (!last) {
           const float *bl = bias + layer * W;
-#pragma unroll
-          for (int c0 = 0; c0 < W; c0 += 32) {
-            uint32_t v[32];
+#pragma unroll 1
+          for (int c0 = 0; c0 < W; c0 += 16) {
+            uint32_t v[16];
             TMEM_LD16(trow + c0, (&v[0]));
-            TMEM_LD16(trow + c0 + 16, (&v[16]));
             tmem_wait_ld();
 #pragma unroll
-            for (int c = 0; c < 32; c += 8) {
+            for (int c = 0; c < 16; c += 8) {
               float h8[8];
 #pragma unroll
               for (int u = 0; u < 8; ++u) h8[u] = act_fn(__uint_as_float(v[c + u]) + bl[c0 + c + u], act);
@@ -334,17 +335,19 @@ __global__ void __launch_bounds__(kThreads, 1) fused_kernel(FusedArgs a) {
             }
           }
         } else {
-          uint32_t v[64];
+          // logits 16 columns at a time into a per-thread array, then decode
+          float z[64];
+          const float *bl = bias + layer * W;
+#pragma unroll 1
+          for (int c0 = 0; c0 < n_out_pad; c0 += 16) {
+            uint32_t v[16];
+            TMEM_LD16(trow + c0, (&v[0]));
+            tmem_wait_ld();
 #pragma unroll
-          for (int c = 0; c < 64; c += 16)
-            if (c < n_out_pad) TMEM_LD16(trow + c, (&v[c]));
-          tmem_wait_ld();
+            for (int u = 0; u < 16; ++u) z[c0 + u] = __uint_as_float(v[u]) + bl[c0 + u];
+          }
           const int32_t ray = S.ray[r];
           if (ray >= 0 && !aborted) {
-            float z[64];
-            const float *bl = bias + layer * W;
-#pragma unroll
-            for (int j = 0; j < 64; ++j) z[j] = j < n_out ? __uint_as_float(v[j]) + bl[j] : 0.f;
             if (XROWS) {
               for (int j = 0; j < n_out; ++j) a.Z[(int64_t)ray * n_out + j] = z[j];
             } else {
@@ -405,39 +408,69 @@ size_t fused_smem_bytes(const DevObject &h) {
   return 1024 + blob + ring + actb + tail;
 }
 
-template <int F, int W, bool XR>
+template <int F, int W, bool XR, int NT, int NLB>
 static cudaError_t launch_one(const FusedArgs &a, size_t smem, cudaStream_t st) {
   static int attr = 0;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(fused_kernel<F, W, XR>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
+    cudaError_t e = cudaFuncSetAttribute(fused_kernel<F, W, XR, NT, NLB>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
     if (e != cudaSuccess) return e;
     attr = 1;
   }
   int sms = 0, dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  fused_kernel<F, W, XR><<<sms, kThreads, smem, st>>>(a);
+  fused_kernel<F, W, XR, NT, NLB><<<sms, NT, smem, st>>>(a);
   return cudaGetLastError();
 }
 
+// Tile-shape variants the autotuner chooses between: threads per CTA and
+// levels of corner loads in flight per gather item.
+struct Variant {
+  int threads, levels;
+};
+static const Variant kVariants[] = {{512, 1}, {512, 2}, {512, 4}, {1024, 1}, {1024, 2}};
+constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
+
+template <int F, int W, bool XR>
+static cudaError_t dispatch_variant(const FusedArgs &a, int v, size_t smem, cudaStream_t st) {
+  constexpr int LPG = 8 / F;
+  switch (v) {
+    case 0: return launch_one<F, W, XR, 512, 1>(a, smem, st);
+    case 1: return launch_one<F, W, XR, 512, (2 < LPG ? 2 : LPG)>(a, smem, st);
+    case 2: return launch_one<F, W, XR, 512, LPG>(a, smem, st);
+    case 3: return launch_one<F, W, XR, 1024, 1>(a, smem, st);
+    case 4: return launch_one<F, W, XR, 1024, (2 < LPG ? 2 : LPG)>(a, smem, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 template <bool XR>
-static cudaError_t dispatch(const FusedArgs &a, const DevObject &h, size_t smem, cudaStream_t st) {
-  if (h.F == 2 && h.width == 64) return launch_one<2, 64, XR>(a, smem, st);
-  if (h.F == 2 && h.width == 128) return launch_one<2, 128, XR>(a, smem, st);
-  if (h.F == 4 && h.width == 64) return launch_one<4, 64, XR>(a, smem, st);
-  if (h.F == 4 && h.width == 128) return launch_one<4, 128, XR>(a, smem, st);
+static cudaError_t dispatch(const FusedArgs &a, const DevObject &h, int variant, size_t smem, cudaStream_t st) {
+  if (h.F == 2 && h.width == 64) return dispatch_variant<2, 64, XR>(a, variant, smem, st);
+  if (h.F == 2 && h.width == 128) return dispatch_variant<2, 128, XR>(a, variant, smem, st);
+  if (h.F == 4 && h.width == 64) return dispatch_variant<4, 64, XR>(a, variant, smem, st);
+  if (h.F == 4 && h.width == 128) return dispatch_variant<4, 128, XR>(a, variant, smem, st);
   return cudaErrorNotSupported;
 }
 
-cudaError_t launch_fused(const QueryLaunch &q, const DevObject &h, int *launches) {
+int fused_variant_count() { return kNumVariants; }
+
+void fused_variant_shape(int v, int *threads, int *levels) {
+  *threads = kVariants[v].threads;
+  *levels = kVariants[v].levels;
+}
+
+cudaError_t launch_fused(const QueryLaunch &q, const DevObject &h, int variant, int *launches) {
   if (!fused_supported(h)) return cudaErrorNotSupported;
   size_t smem = fused_smem_bytes(h);
   if (smem > 232448) return cudaErrorNotSupported;
+  if (variant < 0 || variant >= kNumVariants) return cudaErrorInvalidValue;
   FusedArgs a{};
   a.q = q;
   a.smem_blob = h.umma_bytes;
   *launches += 1;
-  return dispatch<false>(a, h, smem, q.stream);
+  return dispatch<false>(a, h, variant, smem, q.stream);
 }
 
 cudaError_t launch_mlp_fused(const DevObject *dobj, const DevObject &h, const float *X, int64_t n, float *Z,
@@ -459,7 +492,7 @@ cudaError_t launch_mlp_fused(const DevObject *dobj, const DevObject &h, const fl
   a.Z = Z;
   a.xrows = n;
   a.smem_blob = h.umma_bytes;
-  e = dispatch<true>(a, h, smem, st);
+  e = dispatch<true>(a, h, 1, smem, st);
   cudaFreeAsync(meta, st);
   return e;
 }

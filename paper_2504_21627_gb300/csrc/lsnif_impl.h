@@ -127,7 +127,9 @@ cudaError_t launch_tables_to_half(const float *src, uint16_t *dst, int64_t n, cu
 // fused kernel's instantiations.
 bool fused_supported(const DevObject &host_obj);
 size_t fused_smem_bytes(const DevObject &host_obj);
-cudaError_t launch_fused(const QueryLaunch &q, const DevObject &host_obj, int *launches);
+cudaError_t launch_fused(const QueryLaunch &q, const DevObject &host_obj, int variant, int *launches);
+int fused_variant_count();
+void fused_variant_shape(int variant, int *threads, int *levels);
 cudaError_t launch_mlp_fused(const DevObject *dobj, const DevObject &host_obj, const float *X,
                              int64_t n, float *Z, int *err, cudaStream_t st);
 

@@ -168,7 +168,7 @@ int lsnif::run_query(lsnif_ctx *ctx, Workspace *ws, const lsnif_rays *r, lsnif_h
   if (profile) cudaEventRecord(ctx->ev[2], st);
   if (e == cudaSuccess) {
     if (precision == LSNIF_FP32_PLAIN) e = launch_plain_tail(q, ws->cap_nin, kChunkTiles, &launches);
-    else e = launch_fused(q, rep, &launches);
+    else e = launch_fused(q, rep, ctx->fused_variant, &launches);
   }
   if (profile) {
     cudaEventRecord(ctx->ev[3], st);
@@ -339,5 +339,59 @@ extern "C" int lsnif_last_profile(lsnif_ctx *ctx, lsnif_profile *out) {
   p.n_live = meta[0];
   p.n_points = meta[2];
   *out = p;
+  return LSNIF_OK;
+}
+
+// ---- autotuning --------------------------------------------------------------
+
+extern "C" int lsnif_variant_count(void) { return fused_variant_count(); }
+
+extern "C" int lsnif_variant_shape(int v, int *threads, int *levels) {
+  if (v < 0 || v >= fused_variant_count() || !threads || !levels)
+    return fail(LSNIF_ERR_INVALID_ARG, "lsnif_variant_shape: bad variant %d", v);
+  fused_variant_shape(v, threads, levels);
+  return LSNIF_OK;
+}
+
+extern "C" int lsnif_set_variant(lsnif_ctx *ctx, int v) {
+  if (!ctx || v < 0 || v >= fused_variant_count())
+    return fail(LSNIF_ERR_INVALID_ARG, "lsnif_set_variant: bad variant %d", v);
+  ctx->fused_variant = v;
+  return LSNIF_OK;
+}
+
+extern "C" int lsnif_autotune(lsnif_ctx *ctx, const lsnif_rays *rays, int reps, void *stream, int *chosen) {
+  if (!ctx || !rays || reps < 1) return fail(LSNIF_ERR_INVALID_ARG, "lsnif_autotune: bad arguments");
+  cudaSetDevice(ctx->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  lsnif_hits none{};
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  int best = -1;
+  float best_ms = 0.f;
+  const int keep = ctx->fused_variant;
+  int rc = LSNIF_OK;
+  for (int v = 0; v < fused_variant_count() && rc == LSNIF_OK; ++v) {
+    ctx->fused_variant = v;
+    rc = run_query(ctx, &ctx->ws, rays, &none, LSNIF_BF16_FUSED, st, false);
+    if (rc) break;
+    cudaEventRecord(a, st);
+    for (int r = 0; r < reps && rc == LSNIF_OK; ++r) rc = run_query(ctx, &ctx->ws, rays, &none, LSNIF_BF16_FUSED, st, false);
+    cudaEventRecord(b, st);
+    if (rc) break;
+    if ((rc = check_device(ctx, st))) break;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    if (best < 0 || ms < best_ms) {
+      best = v;
+      best_ms = ms;
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  ctx->fused_variant = rc == LSNIF_OK && best >= 0 ? best : keep;
+  if (rc) return rc;
+  if (chosen) *chosen = best;
   return LSNIF_OK;
 }

@@ -63,6 +63,7 @@ struct lsnif_ctx {
   int *d_err = nullptr;
   int32_t *d_prof_meta = nullptr;
   lsnif::Workspace ws;
+  int fused_variant = 1;  // fused-kernel tile shape (see lsnif_autotune)
   // profiling
   bool profiling = false;
   cudaEvent_t ev[6]{};

@@ -120,6 +120,10 @@ SIGNATURES = {
     "lsnif_encode": (_I, [_P, _U32, _P, _I64, _P, _I, _P]),
     "lsnif_corner_indices": (_I, [_P, _U32, _P, _I64, _P, _P]),
     "lsnif_mlp": (_I, [_P, _U32, _P, _I64, _P, _I, _P]),
+    "lsnif_variant_count": (_I, []),
+    "lsnif_variant_shape": (_I, [_I, C.POINTER(_I), C.POINTER(_I)]),
+    "lsnif_set_variant": (_I, [_P, _I]),
+    "lsnif_autotune": (_I, [_P, C.POINTER(Rays), _I, _P, C.POINTER(_I)]),
     "lsnif_make_training_rays": (_I, [_P, _U32, _P, _I64, _I64, _P, _P, _P]),
     "lsnif_label_rays": (_I, [_P, C.POINTER(Rays), C.POINTER(Labels), _P]),
     "lsnif_train_step": (_I, [_P, C.POINTER(Rays), C.POINTER(Labels), C.POINTER(TrainOpts), C.POINTER(TrainStats),
@@ -367,6 +371,26 @@ class Context:
         Z = torch.zeros((n, 8 + c.n_mat), dtype=torch.float32, device=X.device)
         _check(self.lib.lsnif_mlp(self.h, obj, _ptr(X), n, _ptr(Z), precision, _stream(stream)))
         return Z
+
+    # ---- autotuning -------------------------------------------------------------
+    @staticmethod
+    def variants() -> list[tuple[int, int]]:
+        lib = load_library()
+        out = []
+        for v in range(lib.lsnif_variant_count()):
+            t, l = C.c_int(), C.c_int()
+            _check(lib.lsnif_variant_shape(v, C.byref(t), C.byref(l)))
+            out.append((t.value, l.value))
+        return out
+
+    def set_variant(self, v: int):
+        _check(self.lib.lsnif_set_variant(self.h, v))
+
+    def autotune(self, rays, obj: int = 0, obj_per_ray=None, reps: int = 3, stream=None) -> int:
+        rs = rays_struct(rays, obj_per_ray, obj)
+        ch = C.c_int(-1)
+        _check(self.lib.lsnif_autotune(self.h, C.byref(rs), reps, _stream(stream), C.byref(ch)))
+        return ch.value
 
     # ---- training --------------------------------------------------------------
     def make_training_rays(self, obj: int, u, n_outside: int, stream=None):

@@ -75,14 +75,27 @@ def test_labels_match_the_judge(ctx, sphere):
     assert np.array_equal(lab["k"][ok], seg.k[ok])
 
 
-def _batch(sphere, n, seed):
-    """Seeded rays with their oracle labels; rays the network never sees and
-    near-face rays (whose point lists are not unique) are left out."""
+def _batch(sphere, n, seed, margin=1e-3):
+    """Seeded rays with their oracle labels. Left out: rays the network never
+    sees, near-face rays (point lists not unique), and rays whose gradient is
+    not unique between FP32 and FP64 -- a hidden pre-activation within
+    `margin` (relative to its layer's scale) of the ReLU kink, or a hit
+    distance at the MAE term's sign change. One such ray flips its whole
+    contribution to the summed gradient."""
     orc = sphere["orc"]
     rays = I.rays_sphere_to_box(n, 2.2, orc.bmin, orc.bmax, seed=seed)
     seg = O.ray_segments(orc, rays)
     keep = (seg.k > 0) & ~seg.near
     rays = np.ascontiguousarray(rays[:, keep])
+    seg = O.ray_segments(orc, rays)
+    lab = O.labels(sphere["mesh"], rays, seg.t01)
+    Z, cache = O.mlp_forward(O.features(orc, seg), orc.weights, orc.cfg.activation, keep=True)
+    ok = np.ones(rays.shape[1], bool)
+    for _, z in cache[:-1]:
+        ok &= np.all(np.abs(z) > margin * np.abs(z).max(), axis=1)
+    ok &= np.abs(O.sigmoid(Z[:, 1]) - lab.t_local) > margin
+    assert ok.mean() > 0.8
+    rays = np.ascontiguousarray(rays[:, ok])
     seg = O.ray_segments(orc, rays)
     lab = O.labels(sphere["mesh"], rays, seg.t01)
     return rays, seg, lab
@@ -124,7 +137,7 @@ def test_adam_step_matches_oracle(ctx, sphere):
     st = O.adam_init([p0, sphere["orc"].tables])
     want_mlp, want_tab = O.adam_step([p0, sphere["orc"].tables], [g, gt], st, lr=0.01)
     for got, want, grad in ((new_mlp, want_mlp, g), (new_tab, want_tab, gt)):
-        firm = np.abs(grad) > 1e-3 * np.abs(grad).max()
+        firm = np.abs(grad) > 1e-2 * np.abs(grad).max()
         assert np.allclose(got[firm], want[firm], atol=2e-5)
         # every entry moves by at most the learning rate on the first step
         base = p0 if got is new_mlp else sphere["orc"].tables
