@@ -75,12 +75,13 @@ def test_labels_match_the_judge(ctx, sphere):
     assert np.array_equal(lab["k"][ok], seg.k[ok])
 
 
-def _batch(sphere, n, seed, margin=1e-3):
+def _batch(sphere, n, seed, margin=3e-4):
     """Seeded rays with their oracle labels. Left out: rays the network never
     sees, near-face rays (point lists not unique), and rays whose gradient is
     not unique between FP32 and FP64 -- a hidden pre-activation within
-    `margin` (relative to its layer's scale) of the ReLU kink, or a hit
-    distance at the MAE term's sign change. One such ray flips its whole
+    `margin` times its layer's RMS of the ReLU kink (about three times the
+    FP32 pre-activation error at this lattice resolution), or a hit distance
+    within 1e-3 of the MAE term's sign change. One such ray flips its whole
     contribution to the summed gradient."""
     orc = sphere["orc"]
     rays = I.rays_sphere_to_box(n, 2.2, orc.bmin, orc.bmax, seed=seed)
@@ -92,9 +93,9 @@ def _batch(sphere, n, seed, margin=1e-3):
     Z, cache = O.mlp_forward(O.features(orc, seg), orc.weights, orc.cfg.activation, keep=True)
     ok = np.ones(rays.shape[1], bool)
     for _, z in cache[:-1]:
-        ok &= np.all(np.abs(z) > margin * np.abs(z).max(), axis=1)
-    ok &= np.abs(O.sigmoid(Z[:, 1]) - lab.t_local) > margin
-    assert ok.mean() > 0.8
+        ok &= np.all(np.abs(z) > margin * np.sqrt(np.mean(z * z)), axis=1)
+    ok &= np.abs(O.sigmoid(Z[:, 1]) - lab.t_local) > 1e-3
+    assert ok.mean() > 0.8, ok.mean()
     rays = np.ascontiguousarray(rays[:, ok])
     seg = O.ray_segments(orc, rays)
     lab = O.labels(sphere["mesh"], rays, seg.t01)
