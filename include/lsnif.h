@@ -245,6 +245,26 @@ LSNIF_API int lsnif_query_rays(lsnif_ctx *ctx, const lsnif_rays *rays, lsnif_hit
 LSNIF_API int lsnif_query_rays_host(lsnif_ctx *ctx, const lsnif_rays *rays, lsnif_hits *hits, int precision,
                           void *stream);
 
+/* lsnif_query_rays for callers that cannot allocate device memory while they
+ * run -- for example a renderer whose frame loop forbids cudaMalloc/cudaFree
+ * because they can synchronise the whole device, or a plug-in inside a host
+ * engine that owns every allocation. The paper has no counterpart; this is
+ * an integration convenience of this library.
+ *
+ * Runs the BF16 fused query (precision LSNIF_BF16_FUSED) on DEVICE ray and
+ * hit buffers like lsnif_query_rays, but its scratch lives in one static
+ * device array of 32 MiB compiled into the library (every GPU that loads the
+ * library holds it until the process exits) and it calls no cudaMalloc,
+ * cudaFree or other allocating routine. The first call on a device looks up
+ * that array's device address (once per device); make that first call
+ * before any stream capture. Every call shares the array and it keeps the
+ * previous call's contents, so calls that overlap on the GPU (other
+ * streams, other threads, other contexts of the process) race: serialise
+ * them. A batch whose scratch does not fit (about 230 bytes per ray for H =
+ * 18, i.e. some 140k rays) is rejected with LSNIF_ERR_INVALID_ARG and a
+ * message giving the sizes. Errors otherwise as lsnif_query_rays. */
+LSNIF_API int lsnif_query_rays_noalloc(lsnif_ctx *ctx, const lsnif_rays *rays, lsnif_hits *hits, void *stream);
+
 /* Stage outputs of the traversal (a1-a5 of the query) for one object, all
  * DEVICE pointers, any may be NULL: k[n] kept occupied voxels (<= H/2);
  * t01[2n] the clipped AABB interval (NaN on a miss); pts[n*H*3] boundary

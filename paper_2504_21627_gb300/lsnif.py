@@ -116,6 +116,7 @@ SIGNATURES = {
     "lsnif_write_params": (_I, [_P, _U32, _I, _P, _SZ]),
     "lsnif_query_rays": (_I, [_P, C.POINTER(Rays), C.POINTER(Hits), _I, _P]),
     "lsnif_query_rays_host": (_I, [_P, C.POINTER(Rays), C.POINTER(Hits), _I, _P]),
+    "lsnif_query_rays_noalloc": (_I, [_P, C.POINTER(Rays), C.POINTER(Hits), _P]),
     "lsnif_trace": (_I, [_P, C.POINTER(Rays), C.POINTER(TraceOut), _P]),
     "lsnif_encode": (_I, [_P, _U32, _P, _I64, _P, _I, _P]),
     "lsnif_corner_indices": (_I, [_P, _U32, _P, _I64, _P, _P]),
@@ -333,6 +334,14 @@ class Context:
         hs = self.hits_struct(res)
         _check(self.lib.lsnif_query_rays_host(self.h, C.byref(rs), C.byref(hs), precision, _stream(stream)))
         return res
+
+    def query_rays_noalloc(self, rays, out: QueryResult, obj: int = 0, obj_per_ray=None, stream=None):
+        """BF16 fused query that allocates nothing (its scratch is a static
+        device array); `out` must be preallocated (see lsnif.h)."""
+        rs = rays_struct(rays, obj_per_ray, obj)
+        hs = self.hits_struct(out)
+        _check(self.lib.lsnif_query_rays_noalloc(self.h, C.byref(rs), C.byref(hs), _stream(stream)))
+        return out
 
     def trace(self, rays, obj: int, stream=None):
         import torch
