@@ -19,6 +19,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import subprocess
 import sys
@@ -174,6 +175,216 @@ def run_reference(args):
     del torch
 
 
+# ---------------------------------------------------------------------------
+# other workloads (not the headline line): many objects in one launch,
+# serving, training
+# ---------------------------------------------------------------------------
+
+def _timed_graph(ctx, torch, rays, handles, precision, steps, warmup, stream, flush):
+    out = ctx._alloc_hits(rays.shape[1], 0, False)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            ctx.query_rays(rays, obj_per_ray=handles, precision=precision, out=out, stream=stream)
+        for s in range(steps):
+            flush.zero_()
+            evs[s][0].record(stream)
+            ctx.query_rays(rays, obj_per_ray=handles, precision=precision, out=out, stream=stream)
+            evs[s][1].record(stream)
+    stream.synchronize()
+    ctx.check(stream)
+    return np.array([a.elapsed_time(b) for a, b in evs])
+
+
+def bench_batched(args):
+    """64 objects (5k..500k triangles, V 64..256, T 2^16..2^20, 4 x 64 BF16
+    network), power-law rays per object, ~16M rays shuffled together, queried
+    by one grouped launch sequence replayed as a CUDA graph."""
+    import torch
+    from paper_2504_21627_gb300 import lsnif
+    spec = I.batched_objects()
+    ctx = lsnif.Context(0)
+    rays_l, hand_l = [], []
+    for i, (mesh, cfg, n) in enumerate(spec):
+        p = I.random_params(cfg, seed=1000 + i, table_range=0.05, bias_range=0.1)
+        h = ctx.load_object(mesh, cfg, tables=p.tables, mlp=p.packed_mlp())
+        lo, hi = mesh.verts.min(0), mesh.verts.max(0)
+        rays_l.append(I.rays_sphere_to_box(n, 3.0, lo, hi, seed=2000 + i))
+        hand_l.append(np.full(n, h, np.uint32))
+    perm = I.rng(7).permutation(sum(r.shape[1] for r in rays_l))
+    rays = torch.from_numpy(np.ascontiguousarray(np.concatenate(rays_l, 1)[:, perm])).cuda()
+    handles = torch.from_numpy(np.concatenate(hand_l)[perm].view(np.int32)).cuda()
+    n = rays.shape[1]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.Stream()
+    variant = ctx.autotune(rays, obj_per_ray=handles, reps=2)
+    ctx.set_profiling(True)
+    ctx.query_rays(rays, obj_per_ray=handles, precision=lsnif.BF16_FUSED)
+    prof = ctx.last_profile()
+    ctx.set_profiling(False)
+    ctx.set_graph_mode(True)
+    ms16 = _timed_graph(ctx, torch, rays, handles, lsnif.BF16_FUSED, args.steps, args.warmup, stream, flush)
+    ms32 = _timed_graph(ctx, torch, rays, handles, lsnif.FP32_PLAIN, max(3, args.steps // 2), 3, stream, flush)
+    print(json.dumps({
+        "workload": "batched", "metric": "Mrays/s, 64 objects in one grouped launch sequence (CUDA graph)",
+        "objects": len(spec), "rays_per_step": n, "value_bf16": n / (ms16.mean() / 1e3) / 1e6,
+        "value_fp32": n / (ms32.mean() / 1e3) / 1e6, "ms_bf16": float(ms16.mean()), "ms_fp32": float(ms32.mean()),
+        "p50_ms_bf16": float(np.percentile(ms16, 50)), "p99_ms_bf16": float(np.percentile(ms16, 99)),
+        "live_frac": prof.n_live / n, "mean_points_per_live_ray": prof.n_points / max(prof.n_live, 1),
+        "fused_variant": lsnif.Context.variants()[variant], "device_gb": ctx.device_bytes() / 1e9,
+        "l2": "flushed before every timed step", "graph": True}))
+    ctx.close()
+
+
+def _serving_requests(ctx, torch, objs, n_req, seed):
+    """Uneven requests: 40% primary pinhole, 30% shadow rays to a point light
+    (tmax = distance), 30% cosine bounce rays from surface hit points; sizes
+    log-uniform in [256, 262144]."""
+    from paper_2504_21627_gb300 import lsnif
+    g = I.rng(seed)
+    reqs = []
+    for i in range(n_req):
+        n = int(math.exp(g.uniform(math.log(256), math.log(262144))))
+        h, mesh = objs[int(g.integers(0, len(objs)))]
+        lo, hi = mesh.verts.min(0).astype(np.float64), mesh.verts.max(0).astype(np.float64)
+        c, rad = 0.5 * (lo + hi), 0.5 * np.linalg.norm(hi - lo)
+        u = g.random()
+        side = int(math.ceil(math.sqrt(n)))
+        cam = I.seeded_camera(int(g.integers(0, 1 << 30)), radius=2.5 * rad, width=side, height=side)
+        cam.eye = cam.eye + c
+        prim = I.rays_pinhole(cam)[:, :n]
+        if u < 0.4:
+            r = prim
+        else:
+            pr = torch.from_numpy(np.ascontiguousarray(prim)).cuda()
+            lab = ctx.label_rays(pr, h)
+            hit = lab["tri"].cpu().numpy() >= 0
+            th = lab["t_hit"].cpu().numpy()
+            nrm = lab["normal"].cpu().numpy().astype(np.float64)
+            o = prim[0:3].T.astype(np.float64)
+            d = prim[3:6].T.astype(np.float64)
+            p = np.where(hit[:, None], o + np.nan_to_num(th, posinf=0)[:, None] * d, g.uniform(lo, hi, (n, 3)))
+            nrm = np.where(hit[:, None], nrm, np.array([0.0, 0.0, 1.0]))
+            nrm *= -np.sign(np.sum(nrm * d, 1, keepdims=True) + 1e-30)      # face the incoming ray
+            p = p + 1e-4 * rad * nrm
+            if u < 0.7:   # shadow rays
+                light = c + np.array([3.0, 2.0, 4.0]) * rad
+                dl = light - p
+                dist = np.linalg.norm(dl, axis=1)
+                r = I.pack_rays(p, dl / dist[:, None], 0.0, dist)
+            else:         # cosine bounce rays about the facing normal
+                uu = g.random((n, 2))
+                rr, ph = np.sqrt(uu[:, 0]), 2 * np.pi * uu[:, 1]
+                sgn = np.where(nrm[:, 2] >= 0, 1.0, -1.0)
+                a = -1.0 / (sgn + nrm[:, 2])
+                bb = nrm[:, 0] * nrm[:, 1] * a
+                t = np.stack([1 + sgn * nrm[:, 0] ** 2 * a, sgn * bb, -sgn * nrm[:, 0]], 1)
+                b = np.stack([bb, sgn + nrm[:, 1] ** 2 * a, -nrm[:, 1]], 1)
+                dd = (rr * np.cos(ph))[:, None] * t + (rr * np.sin(ph))[:, None] * b + \
+                    np.sqrt(1 - uu[:, 0])[:, None] * nrm
+                r = I.pack_rays(p, dd)
+        rt = torch.from_numpy(np.ascontiguousarray(r)).cuda()
+        reqs.append((h, rt, ctx._alloc_hits(n, 0, False)))
+    del lsnif
+    return reqs
+
+
+def _serve(ctx, reqs, precision, rate_rps, seed):
+    """Open loop (Poisson arrivals at rate_rps) or closed loop (rate None):
+    returns per-request latency (us) and throughput (Mrays/s)."""
+    g = I.rng(seed)
+    t_start = time.perf_counter()
+    arrivals = np.cumsum(g.exponential(1.0 / rate_rps, len(reqs))) if rate_rps else np.zeros(len(reqs))
+    pending, lat, done_rays = {}, [], 0
+    i = 0
+    while i < len(reqs) or pending:
+        now = time.perf_counter() - t_start
+        while i < len(reqs) and arrivals[i] <= now:
+            h, r, out = reqs[i]
+            pending[ctx.submit(r, out, obj=h, precision=precision)] = r.shape[1]
+            i += 1
+        for tk in list(pending):
+            st = ctx.poll(tk, timeout_us=0)
+            if st is not None:
+                lat.append(st.done_us - st.submit_us)
+                done_rays += pending.pop(tk)
+    wall = time.perf_counter() - t_start
+    return np.array(lat), done_rays / wall / 1e6, wall
+
+
+def bench_serving(args):
+    """16 resident objects, requests of uneven size and kind, admission under
+    an 8 GB budget; p50/p99 latency at 0.5x and 0.9x of the saturation rate."""
+    import torch
+    from paper_2504_21627_gb300 import lsnif
+    spec = I.batched_objects()[:16]
+    ctx = lsnif.Context(0, budget_bytes=8 << 30)
+    objs = []
+    for i, (mesh, cfg, _) in enumerate(spec):
+        p = I.random_params(cfg, seed=1000 + i, table_range=0.05, bias_range=0.1)
+        objs.append((ctx.load_object(mesh, cfg, tables=p.tables, mlp=p.packed_mlp(), keep_mesh=True), mesh))
+    reqs = _serving_requests(ctx, torch, objs, args.requests, seed=11)
+    torch.cuda.synchronize()
+    res = {"workload": "serving", "metric": "request latency (submit -> done) and Mrays/s, 16 resident objects",
+           "requests": len(reqs), "rays": int(sum(r[1].shape[1] for r in reqs)), "budget_gb": 8}
+    for name, prec in (("bf16", lsnif.BF16_FUSED), ("fp32", lsnif.FP32_PLAIN)):
+        _serve(ctx, reqs[:8], prec, None, 0)                      # warm the streams
+        lat, thr, wall = _serve(ctx, reqs, prec, None, 1)          # saturation (closed loop)
+        sat_rps = len(reqs) / wall
+        res[name] = {"saturation_mrays_s": thr, "saturation_req_s": sat_rps}
+        for frac in (0.5, 0.9):
+            lat, thr, _ = _serve(ctx, reqs, prec, frac * sat_rps, 2)
+            res[name][f"at_{frac}x"] = {"p50_ms": float(np.percentile(lat, 50)) / 1e3,
+                                        "p99_ms": float(np.percentile(lat, 99)) / 1e3, "mrays_s": thr}
+    res["device_gb"] = ctx.device_bytes() / 1e9
+    print(json.dumps(res))
+    ctx.close()
+
+
+def bench_train(args):
+    """Training step throughput at the paper's batch of 2^18 rays (the paper
+    trains 2000 steps in about 15 s on its GPU) for the icosphere and torus
+    objects, from GPU-generated balanced rays and labels."""
+    import torch
+    from paper_2504_21627_gb300 import lsnif
+    out = {"workload": "train", "metric": "training steps/s at batch 2^18 (forward, loss, backward, Adam)"}
+    for name, cfg, mesh in (("icosphere", I.cfg_icosphere_small(), I.icosphere(3)),
+                            ("torus", I.cfg_torus_4m(), I.noise_torus(seed=2))):
+        ctx = lsnif.Context(0)
+        h = ctx.load_object(mesh, cfg, keep_mesh=True)
+        n_pool, B = 1 << 22, 1 << 18
+        u = torch.rand((n_pool, lsnif.TRAIN_UNIFORMS), device="cuda", generator=torch.Generator("cuda").manual_seed(1))
+        t0 = time.perf_counter()
+        pool, _ = ctx.make_training_rays(h, u, n_outside=n_pool // 2)
+        lab = ctx.label_rays(pool, h)
+        torch.cuda.synchronize()
+        t_data = time.perf_counter() - t0
+        keep = lab["k"] > 0
+        pool = pool[:, keep].contiguous()
+        lab = {k: v[keep].contiguous() for k, v in lab.items()}
+        gen = torch.Generator("cuda").manual_seed(2)
+        batches = []
+        for _ in range(8):
+            idx = torch.randint(0, pool.shape[1], (B,), device="cuda", generator=gen)
+            batches.append((pool[:, idx].contiguous(), {k: v[idx].contiguous() for k, v in lab.items()}))
+        first = ctx.train_step(*batches[0], h).total
+        for s in range(3):
+            ctx.train_step(*batches[s % 8], h, stats=False)
+        torch.cuda.synchronize()
+        steps = max(20, args.steps)
+        t0 = time.perf_counter()
+        for s in range(steps):
+            ctx.train_step(*batches[s % 8], h, stats=False)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        last = ctx.train_step(*batches[0], h).total
+        out[name] = {"steps_per_s": steps / dt, "ms_per_step": dt / steps * 1e3,
+                     "seconds_for_2000_steps": 2000 * dt / steps, "data_generation_s": t_data,
+                     "pool_rays": int(pool.shape[1]), "loss_first": first, "loss_after": last}
+        ctx.close()
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -184,10 +395,19 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=65536)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--side", type=int, default=2048, help="image side; below 2048 only for profiling captures")
+    ap.add_argument("--workload", default="torus4m", choices=["torus4m", "batched", "serving", "train"],
+                    help="torus4m is the headline; the others print their own line")
+    ap.add_argument("--requests", type=int, default=200)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched":
+        return bench_batched(args)
+    if args.workload == "serving":
+        return bench_serving(args)
+    if args.workload == "train":
+        return bench_train(args)
 
     import torch
     import torch.distributed as dist

@@ -301,6 +301,16 @@ LSNIF_API int lsnif_corner_indices(lsnif_ctx *ctx, lsnif_obj obj, const float *p
 LSNIF_API int lsnif_mlp(lsnif_ctx *ctx, lsnif_obj obj, const float *X, int64_t n, float *Z, int precision,
               void *stream);
 
+/* Graph mode (on = 1): lsnif_query_rays on a non-default stream captures each
+ * distinct query -- same ray and hit buffers, ray count, precision, object
+ * handle, fused-kernel variant and number of object slots -- into a CUDA
+ * graph the first time and replays that graph afterwards (one launch instead
+ * of the query's kernel sequence). Object parameters may change between
+ * replays (kernels read them at run time). Graphs are dropped when the
+ * scratch is reallocated or graph mode is switched off. Queries on the
+ * legacy default stream, and profiled queries, run without graphs. */
+LSNIF_API int lsnif_set_graph_mode(lsnif_ctx *ctx, int on);
+
 /* ---- autotuning of the fused kernel's tile shape ------------------------ */
 
 /* Number of fused-kernel variants (threads per CTA x corner-load levels in
@@ -314,11 +324,20 @@ LSNIF_API int lsnif_variant_shape(int v, int *threads, int *levels);
 /* Use variant v for every later BF16 query of the context. */
 LSNIF_API int lsnif_set_variant(lsnif_ctx *ctx, int v);
 
-/* Time every variant on `rays` (DEVICE buffers, `reps` queries each after one
- * warm-up, CUDA events on `stream`, synchronous) and keep the fastest for the
- * context; *chosen (may be NULL) receives its index. Results of the queries
- * are discarded; the variants compute identical results. */
+/* Traversal kernel for later queries: 0 = one ray per thread, 1 = persistent
+ * lanes (a lane whose ray finished takes the next ray from a global counter).
+ * Both compute identical results. */
+LSNIF_API int lsnif_set_trace_mode(lsnif_ctx *ctx, int mode);
+
+/* Time every fused-kernel variant on `rays` (DEVICE buffers, `reps` BF16
+ * queries each after one warm-up, CUDA events on `stream`, synchronous), keep
+ * the fastest, then time the other traversal kernel with it and keep the
+ * faster; *chosen (may be NULL) receives the variant index. Results of the
+ * queries are discarded; all choices compute identical results. */
 LSNIF_API int lsnif_autotune(lsnif_ctx *ctx, const lsnif_rays *rays, int reps, void *stream, int *chosen);
+
+/* The context's current fused-kernel variant and traversal kernel. */
+LSNIF_API int lsnif_get_tuning(lsnif_ctx *ctx, int *variant, int *trace_mode);
 
 /* ---- training (Sec. 5.2, 5.3) ------------------------------------------ */
 
@@ -391,13 +410,16 @@ typedef struct lsnif_req_stats {
 } lsnif_req_stats;
 
 /* Queue a query. rays/hits are DEVICE buffers that must stay valid until
- * lsnif_poll returns OK or an error for the ticket. A request is admitted
+ * lsnif_poll returns OK or an error for the ticket. `stream` is the stream on
+ * which the caller produced (or last used) those buffers: the request runs
+ * only after the work enqueued on `stream` up to this call, so initialising
+ * the buffers there and submitting right away is safe. A request is admitted
  * to the device when one of the context's streams is free and its scratch
  * fits the memory budget; admitted requests run concurrently with those
  * already on the device. Errors: INVALID_ARG, BUSY (queue full),
  * OVER_BUDGET (the request alone can never fit the budget). */
-LSNIF_API int lsnif_submit(lsnif_ctx *ctx, const lsnif_rays *rays, lsnif_hits *hits, int precision,
-                 uint64_t *ticket);
+LSNIF_API int lsnif_submit(lsnif_ctx *ctx, const lsnif_rays *rays, lsnif_hits *hits, int precision, void *stream,
+                           uint64_t *ticket);
 
 /* Advance the queue and report a request: OK (done; *st filled if not
  * NULL), PENDING (not done and timeout_us == 0), TIMEOUT (not done within

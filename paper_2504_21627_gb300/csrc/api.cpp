@@ -127,6 +127,7 @@ extern "C" int lsnif_destroy(lsnif_ctx *ctx) {
   cudaSetDevice(ctx->device);
   server_shutdown(ctx);
   cudaDeviceSynchronize();
+  clear_graphs(ctx);
   for (int s = 0; s < kMaxSlots; ++s)
     if (ctx->slots[s]) free_object(ctx, ctx->slots[s]);
   free_workspace(ctx, &ctx->ws);

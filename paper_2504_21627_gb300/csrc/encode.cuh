@@ -28,7 +28,7 @@ __device__ __forceinline__ void exact_cell(float p, float N, uint32_t &c, float 
   const float x = p * N;
   const float e = fmaf(p, N, -x);
   float f = floorf(x);
-  if (x == f && e < 0.f) f -= 1.f;
+  f -= (x == f && e < 0.f) ? 1.f : 0.f;
   c = (uint32_t)(int)f;
   w = (x - f) + e;
 }
@@ -249,17 +249,15 @@ __device__ __forceinline__ void encode_levels_f16(const __half *__restrict__ tab
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int dy = q & 1, dz = q >> 1;
-      float v0[F], v1[F];
+      // all three sources of the x1 corner are formed, then selected
+      float v0[F], vg[F], vb[F], v1[F];
       unpack_entry<__half, F>(ga[u][q], ia[u][q] & (G - 1), v0);
-      if (pb[u][q]) {
-        uint4 t = make_uint4(gb[u][q][0], EB == 8 ? gb[u][q][EB / 4 - 1] : 0u, 0u, 0u);
-        unpack_entry<__half, F>(t, 0, v1);
-      } else if ((ia[u][q] ^ ib[u][q]) < (uint32_t)G) {
-        unpack_entry<__half, F>(ga[u][q], ib[u][q] & (G - 1), v1);
-      } else {  // x1 corner has zero weight and was not fetched
+      unpack_entry<__half, F>(ga[u][q], ib[u][q] & (G - 1), vg);
+      const uint4 t = make_uint4(gb[u][q][0], EB == 8 ? gb[u][q][EB / 4 - 1] : 0u, 0u, 0u);
+      unpack_entry<__half, F>(t, 0, vb);
+      const bool same = (ia[u][q] ^ ib[u][q]) < (uint32_t)G;
 #pragma unroll
-        for (int f = 0; f < F; ++f) v1[f] = v0[f];
-      }
+      for (int f = 0; f < F; ++f) v1[f] = pb[u][q] ? vb[f] : (same ? vg[f] : v0[f]);
       const float wyz = (dy ? wy[u] : 1.f - wy[u]) * (dz ? wz[u] : 1.f - wz[u]);
 #pragma unroll
       for (int f = 0; f < F; ++f) out[u][f] = fmaf(wyz, fmaf(wx[u], v1[f] - v0[f], v0[f]), out[u][f]);

@@ -61,6 +61,10 @@ __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.a
 __device__ __forceinline__ void tc_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
+__device__ __forceinline__ void mbar_arrive(uint32_t addr) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(addr) : "memory");
+}
+
 __device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity) {
   long long t0 = clock64();
   while (true) {
@@ -110,7 +114,8 @@ struct Smem {
   int32_t *ray;
   int32_t *kk;
   float *t0, *t1;
-  uint64_t *mbar;  // kNBuf ring barriers, then the accumulator barrier
+  uint64_t *mbar;  // kNBuf "empty" ring barriers (MMA done), the accumulator
+                   // barrier, then kNBuf "full" ring barriers (tile written)
   uint32_t *tmem_slot;
   int32_t *misc;   // [0] tile, [1] abort
 };
@@ -148,7 +153,7 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(FusedArgs a) {
   S.t1 = reinterpret_cast<float *>(base + off);
   off += kTileM * 4;
   S.mbar = reinterpret_cast<uint64_t *>(base + off);
-  off += 8 * (kNBuf + 1);
+  off += 8 * (2 * kNBuf + 1);
   S.tmem_slot = reinterpret_cast<uint32_t *>(base + off);
   off += 16;
   S.misc = reinterpret_cast<int32_t *>(base + off);
@@ -159,6 +164,8 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(FusedArgs a) {
   if (tid == 0) {
     for (int i = 0; i < kNBuf + 1; ++i)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&S.mbar[i])) : "memory");
+    for (int i = kNBuf + 1; i < 2 * kNBuf + 1; ++i)   // every thread arrives once per chunk
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&S.mbar[i])), "r"(kThreads) : "memory");
     S.misc[1] = 0;
   }
   if (warp == 0) {
@@ -290,9 +297,12 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(FusedArgs a) {
         const int kg = j * G + g;
         *reinterpret_cast<uint4 *>(A + core_off(r, kg, a_sbo)) = outv;
       }
+      // publish this thread's part of the tile to the tensor core; only the
+      // issuing thread waits for the whole tile, the other warps run ahead
       fence_async_smem();
-      __syncthreads();
+      mbar_arrive(su32(&S.mbar[kNBuf + 1 + buf]));
       if (tid == 0) {
+        if (!mbar_wait(su32(&S.mbar[kNBuf + 1 + buf]), (uint32_t)(use & 1))) aborted = true;
         tc_after();
         const uint32_t a0 = su32(A), b0 = su32(S.blob);
         for (int ks = 0; ks < CHK / 16; ++ks) {
@@ -404,7 +414,7 @@ size_t fused_smem_bytes(const DevObject &h) {
   size_t blob = ((size_t)h.umma_bytes + 1023) & ~size_t(1023);
   size_t ring = (size_t)kNBuf * kTileM * (2 * 16 * h.F) * 2;
   size_t actb = (size_t)kTileM * h.width * 2;
-  size_t tail = kTileM * 16 + 8 * (kNBuf + 1) + 16 + 16 + 4 * LSNIF_MAX_LEVELS;
+  size_t tail = kTileM * 16 + 8 * (2 * kNBuf + 1) + 16 + 16 + 4 * LSNIF_MAX_LEVELS;
   return 1024 + blob + ring + actb + tail;
 }
 

@@ -104,6 +104,7 @@ struct QueryLaunch {
   QueryScratch s;
   int *err;               // device error word
   cudaStream_t stream;
+  int trace_mode;         // traversal kernel: 0 one ray per thread, 1 persistent lanes
 };
 
 // ---- launchers (query.cu) ----

@@ -2,6 +2,7 @@
 // FP32 path (gather kernel, SIMT network + decode kernel), plus the stage
 // kernels behind lsnif_trace / lsnif_encode / lsnif_corner_indices /
 // lsnif_mlp.
+#include <algorithm>
 #include <cstdio>
 
 #include "device.cuh"
@@ -67,6 +68,177 @@ __global__ void __launch_bounds__(256) trace_kernel(QueryLaunch q, int smem_hist
     if (k > 0) {
       if (smem_hist) atomicAdd(&sh_hist[s * kBuckets + k], 1);
       else atomicAdd(&q.s.counts[s * kBuckets + k], 1);
+    }
+  }
+  if (smem_hist) {
+    __syncthreads();
+    for (int b = threadIdx.x; b < nb; b += blockDim.x)
+      if (sh_hist[b]) atomicAdd(&q.s.counts[b], sh_hist[b]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Persistent-lane traversal: a warp keeps all 32 lanes busy by handing a new
+// ray to every lane whose ray finished (global ray counter, warp-aggregated).
+// Rays need anywhere from 0 to 3V DDA steps; with one ray per thread a warp
+// runs as long as its longest ray. Same per-ray arithmetic as trace_kernel
+// (same DDA, same outputs), so results are identical.
+// ---------------------------------------------------------------------------
+struct LaneRay {
+  int64_t i;
+  int s;           // object slot
+  float3 o, d;
+  float inv0, inv1, inv2;
+  int ix0, ix1, ix2, st0, st1, st2;
+  float tn0, tn1, tn2;
+  float tcur, t0, t1;
+  int ain;
+  float fin;
+  int k, cap;
+};
+
+__device__ __forceinline__ float sel3(int a, float x, float y, float z) { return a == 0 ? x : (a == 1 ? y : z); }
+__device__ __forceinline__ int sel3i(int a, int x, int y, int z) { return a == 0 ? x : (a == 1 ? y : z); }
+
+__global__ void __launch_bounds__(256) trace_pool_kernel(QueryLaunch q, int smem_hist, int steps_per_round) {
+  extern __shared__ int sh_hist[];
+  const int nb = q.n_slots * kBuckets;
+  if (smem_hist) {
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) sh_hist[i] = 0;
+    __syncthreads();
+  }
+  const int64_t n = q.rays.n;
+  const int Hs = q.H_max;
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  LaneRay R;
+  R.i = -1;
+  bool exhausted = false;
+  int* counter = q.s.meta + 4;
+
+  auto finish = [&](void) {
+    const int64_t i = R.i;
+    q.s.k[i] = (uint8_t)R.k;
+    q.s.slot[i] = (int16_t)R.s;
+    reinterpret_cast<float2 *>(q.s.t01)[i] = make_float2(R.t0, R.t1);
+    if (R.k == 0) miss_store(q.hits, i, q.objs[R.s].n_out);
+    else if (smem_hist) atomicAdd(&sh_hist[R.s * kBuckets + R.k], 1);
+    else atomicAdd(&q.s.counts[R.s * kBuckets + R.k], 1);
+    R.i = -1;
+  };
+
+  for (;;) {
+    const bool need = R.i < 0 && !exhausted;
+    const unsigned m = __ballot_sync(FULL, need);
+    if (m) {
+      const int leader = __ffs(m) - 1;
+      int base = 0;
+      if (lane == leader) base = atomicAdd(counter, __popc(m));
+      base = __shfl_sync(FULL, base, leader);
+      if (need) {
+        const int64_t my = (int64_t)base + __popc(m & ((1u << lane) - 1u));
+        if (my >= n) {
+          exhausted = true;
+        } else {
+          // start ray `my`
+          R.i = my;
+          const uint32_t h = q.rays.obj ? q.rays.obj[my] : q.rays.single_handle;
+          R.s = slot_of(q.objs, q.n_slots, h);
+          R.k = 0;
+          R.t0 = R.t1 = CUDART_NAN_F;
+          if (R.s < 0) {
+            atomicOr(q.err, kErrBadHandle);
+            q.s.slot[my] = -1;
+            q.s.k[my] = 0;
+            miss_store(q.hits, my, 0);
+            R.i = -1;
+          } else {
+            const DevObject &ob = q.objs[R.s];
+            int ea;
+            float t0, t1;
+            bool live = to_unit(ob, q.rays.ox[my], q.rays.oy[my], q.rays.oz[my], q.rays.dx[my], q.rays.dy[my],
+                                q.rays.dz[my], R.o, R.d) &&
+                        unit_slab(R.o, R.d, q.rays.tmin[my], t0, t1, ea);
+            if (!live) {
+              finish();
+            } else {
+              R.t0 = t0;
+              R.t1 = t1;
+              R.cap = ob.H >> 1;
+              const int V = ob.V;
+              const float invV = ob.invV;
+              const float3 p = make_float3(fmaf(t0, R.d.x, R.o.x), fmaf(t0, R.d.y, R.o.y), fmaf(t0, R.d.z, R.o.z));
+              int c[3];
+              float dd[3] = {R.d.x, R.d.y, R.d.z}, oo[3] = {R.o.x, R.o.y, R.o.z}, pp[3] = {p.x, p.y, p.z};
+              int stv[3];
+              float invv[3], tnv[3];
+#pragma unroll
+              for (int a = 0; a < 3; ++a) {
+                int cc = (int)floorf(pp[a] * (float)V);
+                cc = min(max(cc, 0), V - 1);
+                if (a == ea) cc = dd[a] > 0.f ? 0 : V - 1;
+                c[a] = cc;
+                stv[a] = dd[a] > 0.f ? 1 : (dd[a] < 0.f ? -1 : 0);
+                invv[a] = dd[a] != 0.f ? 1.f / dd[a] : 0.f;
+                tnv[a] = dd[a] != 0.f ? ((float)(cc + (stv[a] > 0)) * invV - oo[a]) * invv[a] : CUDART_INF_F;
+              }
+              R.ix0 = c[0]; R.ix1 = c[1]; R.ix2 = c[2];
+              R.st0 = stv[0]; R.st1 = stv[1]; R.st2 = stv[2];
+              R.inv0 = invv[0]; R.inv1 = invv[1]; R.inv2 = invv[2];
+              R.tn0 = tnv[0]; R.tn1 = tnv[1]; R.tn2 = tnv[2];
+              R.tcur = t0;
+              R.ain = ea;
+              R.fin = ea >= 0 ? (dd[ea] > 0.f ? 0.f : 1.f) : 0.f;
+            }
+          }
+        }
+      }
+    }
+    if (__all_sync(FULL, R.i < 0 && exhausted)) break;
+    if (R.i < 0) continue;
+    // a few DDA steps of this lane's ray
+    const DevObject &ob = q.objs[R.s];
+    const int V = ob.V;
+    const float invV = ob.invV;
+    const uint32_t *occ = ob.occ;
+    float *P = q.s.pts + (size_t)R.i * Hs * 3;
+    for (int it = 0; it < steps_per_round; ++it) {
+      const int a = (R.tn0 <= R.tn1) ? (R.tn0 <= R.tn2 ? 0 : 2) : (R.tn1 <= R.tn2 ? 1 : 2);
+      const float tna = sel3(a, R.tn0, R.tn1, R.tn2);
+      const float tx = fminf(tna, R.t1);
+      const uint32_t vid = ((uint32_t)R.ix2 * V + R.ix1) * V + R.ix0;
+      bool done = false;
+      if (tx > R.tcur && occupied(occ, vid)) {
+        const int ia = sel3i(a, R.ix0, R.ix1, R.ix2), sa = sel3i(a, R.st0, R.st1, R.st2);
+        const float3 pa = seg_point(R.o, R.d, R.tcur, R.ain, R.fin);
+        const float3 pb = seg_point(R.o, R.d, tx, a, (float)(ia + (sa > 0)) * invV);
+        float *w = P + 6 * R.k;
+        reinterpret_cast<float2 *>(w)[0] = make_float2(pa.x, pa.y);
+        reinterpret_cast<float2 *>(w)[1] = make_float2(pa.z, pb.x);
+        reinterpret_cast<float2 *>(w)[2] = make_float2(pb.y, pb.z);
+        if (++R.k >= R.cap) done = true;
+      }
+      if (!done && tna >= R.t1) done = true;
+      if (!done) {
+        int ia = sel3i(a, R.ix0, R.ix1, R.ix2);
+        const int sa = sel3i(a, R.st0, R.st1, R.st2);
+        ia += sa;
+        if (ia < 0 || ia >= V) {
+          done = true;
+        } else {
+          R.tcur = tna;
+          R.ain = a;
+          R.fin = (float)(ia + (sa < 0)) * invV;
+          const float tn = ((float)(ia + (sa > 0)) * invV - comp(R.o, a)) * sel3(a, R.inv0, R.inv1, R.inv2);
+          if (a == 0) { R.ix0 = ia; R.tn0 = tn; }
+          else if (a == 1) { R.ix1 = ia; R.tn1 = tn; }
+          else { R.ix2 = ia; R.tn2 = tn; }
+        }
+      }
+      if (done) {
+        finish();
+        break;
+      }
     }
   }
   if (smem_hist) {
@@ -372,6 +544,17 @@ cudaError_t launch_trace(const QueryLaunch &q, int *launches) {
   const int nb = q.n_slots * kBuckets;
   const int smem_hist = nb <= 12288;
   const size_t smem = smem_hist ? nb * sizeof(int) : 0;
+  if (q.trace_mode == 1) {
+    cudaMemsetAsync(q.s.meta + 4, 0, sizeof(int32_t), q.stream);
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t need = (q.rays.n + 255) / 256;
+    const int grid = (int)std::min<int64_t>(need, (int64_t)sms * 8);
+    trace_pool_kernel<<<grid, 256, smem, q.stream>>>(q, smem_hist, 8);
+    *launches += 1;
+    return cudaGetLastError();
+  }
   const int grid = grid_for(q.rays.n, 256, 152 * 16);
   trace_kernel<<<grid, 256, smem, q.stream>>>(q, smem_hist);
   *launches += 1;

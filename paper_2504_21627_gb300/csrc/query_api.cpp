@@ -47,6 +47,7 @@ int lsnif::ensure_workspace(lsnif_ctx *ctx, Workspace *ws, int64_t n, int H, int
   const size_t bytes = workspace_bytes(nn, HH, SS, NI);
   if (ws->base) {
     cudaDeviceSynchronize();  // the old scratch may still be in use by queued work
+    if (ctx->graphs_ws == ws->base) clear_graphs(ctx);
     dev_free(ctx, ws->base);
     ws->base = nullptr;
   }
@@ -160,6 +161,7 @@ int lsnif::run_query(lsnif_ctx *ctx, Workspace *ws, const lsnif_rays *r, lsnif_h
   q.s.wmax = sh.wmax;
   q.err = ctx->d_err;
   q.stream = st;
+  q.trace_mode = ctx->trace_mode;
   int launches = 0;
   if (profile) cudaEventRecord(ctx->ev[0], st);
   cudaError_t e = launch_trace(q, &launches);
@@ -183,11 +185,70 @@ int lsnif::run_query(lsnif_ctx *ctx, Workspace *ws, const lsnif_rays *r, lsnif_h
   return LSNIF_OK;
 }
 
+void lsnif::clear_graphs(lsnif_ctx *ctx) {
+  for (auto &kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
+  ctx->graphs.clear();
+  ctx->graphs_ws = nullptr;
+}
+
+// Replay a captured graph of this exact query, capturing it first. The key
+// holds everything the launch sequence depends on; the scratch must already
+// be large enough so that nothing is allocated while capturing.
+static int query_graph(lsnif_ctx *ctx, const lsnif_rays *r, lsnif_hits *h, int precision, cudaStream_t st) {
+  int rc = check_rays(r, h);
+  if (rc) return rc;
+  if (r->n == 0) return LSNIF_OK;
+  Shape sh;
+  if ((rc = shape_of(ctx, r, &sh))) return rc;
+  const int n_in = precision == LSNIF_FP32_PLAIN ? sh.n_in : 0;
+  if ((rc = ensure_workspace(ctx, &ctx->ws, r->n, sh.H, sh.n_slots, n_in))) return rc;
+  if (ctx->graphs_ws != ctx->ws.base) clear_graphs(ctx);
+  std::vector<uint64_t> key = {(uint64_t)r->n, (uint64_t)precision, (uint64_t)ctx->fused_variant,
+                               (uint64_t)ctx->trace_mode, (uint64_t)sh.n_slots, (uint64_t)r->single_obj};
+  for (const void *p : {(const void *)r->ox, (const void *)r->oy, (const void *)r->oz, (const void *)r->dx,
+                        (const void *)r->dy, (const void *)r->dz, (const void *)r->tmin, (const void *)r->tmax,
+                        (const void *)r->obj, (const void *)h->hit, (const void *)h->t, (const void *)h->nx,
+                        (const void *)h->ny, (const void *)h->nz, (const void *)h->mat, (const void *)h->ar,
+                        (const void *)h->ag, (const void *)h->ab, (const void *)h->logits})
+    key.push_back((uint64_t)(uintptr_t)p);
+  auto it = ctx->graphs.find(key);
+  if (it == ctx->graphs.end()) {
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(e, "lsnif_query_rays: begin graph capture");
+    rc = run_query(ctx, &ctx->ws, r, h, precision, st, false);
+    e = cudaStreamEndCapture(st, &g);
+    if (rc) {
+      if (g) cudaGraphDestroy(g);
+      return rc;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "lsnif_query_rays: end graph capture");
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "lsnif_query_rays: instantiate graph");
+    it = ctx->graphs.emplace(key, ex).first;
+    ctx->graphs_ws = ctx->ws.base;
+  }
+  cudaError_t e = cudaGraphLaunch(it->second, st);
+  return e == cudaSuccess ? LSNIF_OK : cuda_fail(e, "lsnif_query_rays: graph launch");
+}
+
 extern "C" int lsnif_query_rays(lsnif_ctx *ctx, const lsnif_rays *rays, lsnif_hits *hits, int precision,
                                 void *stream) {
   if (!ctx) return fail(LSNIF_ERR_INVALID_ARG, "lsnif_query_rays: ctx is NULL");
   cudaSetDevice(ctx->device);
+  if (ctx->graph_mode && !ctx->profiling && stream != nullptr)
+    return query_graph(ctx, rays, hits, precision, (cudaStream_t)stream);
   return run_query(ctx, &ctx->ws, rays, hits, precision, (cudaStream_t)stream, ctx->profiling);
+}
+
+extern "C" int lsnif_set_graph_mode(lsnif_ctx *ctx, int on) {
+  if (!ctx) return fail(LSNIF_ERR_INVALID_ARG, "lsnif_set_graph_mode: ctx is NULL");
+  cudaSetDevice(ctx->device);
+  ctx->graph_mode = on != 0;
+  if (!on) clear_graphs(ctx);
+  return LSNIF_OK;
 }
 
 extern "C" int lsnif_query_rays_host(lsnif_ctx *ctx, const lsnif_rays *rays, lsnif_hits *hits, int precision,
@@ -368,30 +429,60 @@ extern "C" int lsnif_autotune(lsnif_ctx *ctx, const lsnif_rays *rays, int reps, 
   cudaEvent_t a, b;
   cudaEventCreate(&a);
   cudaEventCreate(&b);
-  int best = -1;
-  float best_ms = 0.f;
-  const int keep = ctx->fused_variant;
-  int rc = LSNIF_OK;
-  for (int v = 0; v < fused_variant_count() && rc == LSNIF_OK; ++v) {
-    ctx->fused_variant = v;
-    rc = run_query(ctx, &ctx->ws, rays, &none, LSNIF_BF16_FUSED, st, false);
-    if (rc) break;
+  const int keep_v = ctx->fused_variant, keep_t = ctx->trace_mode;
+  auto time_it = [&](float *ms) -> int {
+    int rc = run_query(ctx, &ctx->ws, rays, &none, LSNIF_BF16_FUSED, st, false);
+    if (rc) return rc;
     cudaEventRecord(a, st);
     for (int r = 0; r < reps && rc == LSNIF_OK; ++r) rc = run_query(ctx, &ctx->ws, rays, &none, LSNIF_BF16_FUSED, st, false);
     cudaEventRecord(b, st);
-    if (rc) break;
-    if ((rc = check_device(ctx, st))) break;
+    if (rc) return rc;
+    if ((rc = check_device(ctx, st))) return rc;
+    cudaEventElapsedTime(ms, a, b);
+    return LSNIF_OK;
+  };
+  int best = -1, rc = LSNIF_OK;
+  float best_ms = 0.f;
+  // the fused kernel's tile shape first, then the traversal kernel
+  for (int v = 0; v < fused_variant_count() && rc == LSNIF_OK; ++v) {
+    ctx->fused_variant = v;
     float ms = 0.f;
-    cudaEventElapsedTime(&ms, a, b);
-    if (best < 0 || ms < best_ms) {
-      best = v;
-      best_ms = ms;
+    if ((rc = time_it(&ms))) break;
+    if (best < 0 || ms < best_ms) { best = v; best_ms = ms; }
+  }
+  int best_t = ctx->trace_mode;
+  if (rc == LSNIF_OK) {
+    ctx->fused_variant = best;
+    for (int t = 0; t < 2 && rc == LSNIF_OK; ++t) {
+      if (t == best_t) continue;
+      ctx->trace_mode = t;
+      float ms = 0.f;
+      if ((rc = time_it(&ms))) break;
+      if (ms < best_ms) { best_t = t; best_ms = ms; }
     }
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
-  ctx->fused_variant = rc == LSNIF_OK && best >= 0 ? best : keep;
-  if (rc) return rc;
+  if (rc) {
+    ctx->fused_variant = keep_v;
+    ctx->trace_mode = keep_t;
+    return rc;
+  }
+  ctx->fused_variant = best;
+  ctx->trace_mode = best_t;
   if (chosen) *chosen = best;
+  return LSNIF_OK;
+}
+
+extern "C" int lsnif_get_tuning(lsnif_ctx *ctx, int *variant, int *trace_mode) {
+  if (!ctx || !variant || !trace_mode) return fail(LSNIF_ERR_INVALID_ARG, "lsnif_get_tuning: NULL argument");
+  *variant = ctx->fused_variant;
+  *trace_mode = ctx->trace_mode;
+  return LSNIF_OK;
+}
+
+extern "C" int lsnif_set_trace_mode(lsnif_ctx *ctx, int mode) {
+  if (!ctx || (mode != 0 && mode != 1)) return fail(LSNIF_ERR_INVALID_ARG, "lsnif_set_trace_mode: bad mode %d", mode);
+  ctx->trace_mode = mode;
   return LSNIF_OK;
 }

@@ -64,6 +64,11 @@ struct lsnif_ctx {
   int32_t *d_prof_meta = nullptr;
   lsnif::Workspace ws;
   int fused_variant = 1;  // fused-kernel tile shape (see lsnif_autotune)
+  int trace_mode = 1;     // traversal kernel (see lsnif_autotune)
+  // CUDA-graph cache of queries (see lsnif_set_graph_mode)
+  bool graph_mode = false;
+  std::map<std::vector<uint64_t>, cudaGraphExec_t> graphs;
+  void *graphs_ws = nullptr;  // workspace the cached graphs point into
   // profiling
   bool profiling = false;
   cudaEvent_t ev[6]{};
@@ -95,6 +100,7 @@ void free_workspace(lsnif_ctx *ctx, Workspace *ws);
 int run_query(lsnif_ctx *ctx, Workspace *ws, const lsnif_rays *rays, lsnif_hits *hits, int precision,
               cudaStream_t st, bool profile);
 int query_shape(lsnif_ctx *ctx, const lsnif_rays *rays, int precision, int *H, int *n_in);
+void clear_graphs(lsnif_ctx *ctx);
 
 // training
 void free_train_state(lsnif_ctx *ctx, Object *o);

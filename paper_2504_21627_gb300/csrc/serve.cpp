@@ -29,6 +29,7 @@ struct Request {
   int stream = -1;
   int rc = LSNIF_OK;
   double submit_us = 0, start_us = 0, done_us = 0;
+  cudaEvent_t ev_ready = nullptr;  // the caller's stream reached submit: inputs are ready
   cudaEvent_t ev_start = nullptr, ev_done = nullptr;
   float gpu_ms = 0.f;
 };
@@ -61,6 +62,7 @@ void server_shutdown(lsnif_ctx *ctx) {
     free_workspace(ctx, &sl.ws);
   }
   for (auto &kv : sv->all) {
+    if (kv.second->ev_ready) cudaEventDestroy(kv.second->ev_ready);
     if (kv.second->ev_start) cudaEventDestroy(kv.second->ev_start);
     if (kv.second->ev_done) cudaEventDestroy(kv.second->ev_done);
     delete kv.second;
@@ -151,6 +153,7 @@ static void advance(lsnif_ctx *ctx, Server *sv) {
     sv->queue.pop_front();
     r->start_us = now_us();
     if (rc == LSNIF_OK) {
+      cudaStreamWaitEvent(sl.s, r->ev_ready, 0);   // after the caller's writes to the buffers
       cudaEventRecord(r->ev_start, sl.s);
       rc = run_query(ctx, &sl.ws, &r->rays, &r->hits, r->precision, sl.s, false);
       cudaEventRecord(r->ev_done, sl.s);
@@ -170,7 +173,7 @@ static void advance(lsnif_ctx *ctx, Server *sv) {
 }  // namespace lsnif
 
 extern "C" int lsnif_submit(lsnif_ctx *ctx, const lsnif_rays *rays, lsnif_hits *hits, int precision,
-                            uint64_t *ticket) {
+                            void *stream, uint64_t *ticket) {
   if (!ctx || !rays || !hits || !ticket) return fail(LSNIF_ERR_INVALID_ARG, "lsnif_submit: NULL argument");
   if (precision != LSNIF_FP32_PLAIN && precision != LSNIF_BF16_FUSED)
     return fail(LSNIF_ERR_INVALID_ARG, "lsnif_submit: unknown precision %d", precision);
@@ -202,6 +205,8 @@ extern "C" int lsnif_submit(lsnif_ctx *ctx, const lsnif_rays *rays, lsnif_hits *
   r->hits = *hits;
   r->precision = precision;
   r->submit_us = now_us();
+  cudaEventCreateWithFlags(&r->ev_ready, cudaEventDisableTiming);
+  cudaEventRecord(r->ev_ready, (cudaStream_t)stream);
   cudaEventCreate(&r->ev_start);
   cudaEventCreate(&r->ev_done);
   sv->queue.push_back(r);
@@ -234,6 +239,7 @@ extern "C" int lsnif_poll(lsnif_ctx *ctx, uint64_t ticket, int64_t timeout_us, l
     st->gpu_ms = r->gpu_ms;
     st->n_rays = r->rays.n;
   }
+  cudaEventDestroy(r->ev_ready);
   cudaEventDestroy(r->ev_start);
   cudaEventDestroy(r->ev_done);
   sv->all.erase(it);

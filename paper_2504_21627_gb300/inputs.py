@@ -169,11 +169,40 @@ def noise_torus(seed: int, R: float = 1.0, r: float = 0.35, nu: int = 500, nv: i
     return Mesh(v, tris, _vertex_normals(v, tris), quad_mat, _albedo_table(n_mat, seed), n_mat=n_mat)
 
 
+def icosphere_vec(subdiv: int, seed: int = 1) -> Mesh:
+    """The icosphere of icosphere() (vertex positions equal to within one
+    FP32 ulp, another vertex order), built with vectorised edge splitting
+    (shared midpoints found with np.unique) for large subdivision levels."""
+    base = icosphere(0, seed=seed)
+    v = base.verts.astype(np.float64)
+    f = base.tris.astype(np.int64)
+    for _ in range(subdiv):
+        e = np.concatenate([f[:, [0, 1]], f[:, [1, 2]], f[:, [2, 0]]])
+        es = np.sort(e, axis=1)
+        uniq, inv = np.unique(es, axis=0, return_inverse=True)
+        inv = inv.reshape(-1)
+        m = v[uniq[:, 0]] + v[uniq[:, 1]]
+        m /= np.linalg.norm(m, axis=1, keepdims=True)
+        mid = len(v) + inv
+        nf = len(f)
+        ab, bc, ca = mid[:nf], mid[nf:2 * nf], mid[2 * nf:]
+        a, b, c = f[:, 0], f[:, 1], f[:, 2]
+        f = np.concatenate([np.stack([a, ab, ca], 1), np.stack([b, bc, ab], 1), np.stack([c, ca, bc], 1),
+                            np.stack([ab, bc, ca], 1)])
+        v = np.concatenate([v, m])
+    v32 = v.astype(np.float32)
+    f32 = f.astype(np.int32)
+    cen = v32[f32].astype(np.float64).mean(axis=1)
+    octant = (cen[:, 0] > 0).astype(np.int32) | ((cen[:, 1] > 0).astype(np.int32) << 1) \
+        | ((cen[:, 2] > 0).astype(np.int32) << 2)
+    return Mesh(v32, f32, _vertex_normals(v32, f32), (octant % 2).astype(np.int32), _albedo_table(2, seed), n_mat=2)
+
+
 def noise_icosphere(seed: int, target_tris: int, amplitude: float = 0.05, n_mat: int = 4) -> Mesh:
     """Icosphere with about `target_tris` triangles (20 * 4**s, rounded to the
     nearest level), displaced by value noise; materials by octant mod n_mat."""
     s = int(round(math.log(max(target_tris, 20) / 20.0, 4)))
-    m = icosphere(max(s, 0), seed=seed)
+    m = icosphere(max(s, 0), seed=seed) if s <= 4 else icosphere_vec(s, seed=seed)
     v = m.verts.astype(np.float64)
     n = m.vnormals.astype(np.float64)
     v = v + n * (amplitude * value_noise(v, seed))[:, None]
@@ -183,6 +212,13 @@ def noise_icosphere(seed: int, target_tris: int, amplitude: float = 0.05, n_mat:
         | ((cen[:, 2] > 0).astype(np.int32) << 2)
     return Mesh(v, m.tris, _vertex_normals(v, m.tris), (octant % n_mat).astype(np.int32),
                 _albedo_table(n_mat, seed), n_mat=n_mat)
+
+
+def noise_torus_tris(seed: int, target_tris: int, amplitude: float = 0.05, n_mat: int = 4) -> Mesh:
+    """Noise torus with about `target_tris` triangles (quad grid 5:2)."""
+    nv = max(8, int(round(math.sqrt(target_tris / 2 / 2.5))))
+    nu = max(8, int(round(2.5 * nv)))
+    return noise_torus(seed, nu=nu, nv=nv, amplitude=amplitude, n_mat=n_mat)
 
 
 def single_triangle(a, b, c, n_mat: int = 1) -> Mesh:
@@ -327,6 +363,33 @@ class Params:
     def packed_mlp(self) -> np.ndarray:
         return np.concatenate([np.concatenate([W.reshape(-1), b.reshape(-1)])
                                for W, b in self.weights]).astype(np.float32)
+
+
+def batched_objects(n_obj: int = 64, seed: int = 3, total_rays: int = 16 << 20):
+    """The many-object workload: n_obj seeded noise-displaced icospheres or
+    tori of 5k..500k triangles (log-uniform), V in {64, 128, 256} and table
+    size 2^16..2^20 (log-uniform), L = 16, F = 2, 4 x 64 network, and a
+    power-law ray count per object (Pareto, clipped to [1k, 1M]) rescaled to
+    about total_rays in all. Returns [(mesh, cfg, n_rays)]."""
+    g = rng(seed)
+    raw = 1000.0 * (1.0 + g.pareto(1.1, size=n_obj))
+    counts = raw
+    for _ in range(20):
+        counts = np.clip(raw * total_rays / raw.sum(), 1000, 1 << 20)
+        raw = counts
+    counts = counts.astype(np.int64)
+    out = []
+    for i in range(n_obj):
+        tris = int(math.exp(g.uniform(math.log(5000), math.log(500000))))
+        V = int(64 * 2 ** g.integers(0, 3))
+        log2_T = int(g.integers(16, 21))
+        kind = g.integers(0, 2)
+        mesh = noise_icosphere(seed + 100 + i, tris, n_mat=4) if kind == 0 else \
+            noise_torus_tris(seed + 100 + i, tris, n_mat=4)
+        cfg = Config(V=V, H=18, L=16, F=2, log2_T=log2_T, N_min=16, N_max=max(512, 8 * V), n_hidden=4, width=64,
+                     n_mat=4, seed=seed + i)
+        out.append((mesh, cfg, int(counts[i])))
+    return out
 
 
 def random_params(cfg: Config, seed: int, table_range: float | None = None,

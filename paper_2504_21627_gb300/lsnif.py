@@ -121,15 +121,18 @@ SIGNATURES = {
     "lsnif_encode": (_I, [_P, _U32, _P, _I64, _P, _I, _P]),
     "lsnif_corner_indices": (_I, [_P, _U32, _P, _I64, _P, _P]),
     "lsnif_mlp": (_I, [_P, _U32, _P, _I64, _P, _I, _P]),
+    "lsnif_set_graph_mode": (_I, [_P, _I]),
     "lsnif_variant_count": (_I, []),
     "lsnif_variant_shape": (_I, [_I, C.POINTER(_I), C.POINTER(_I)]),
     "lsnif_set_variant": (_I, [_P, _I]),
     "lsnif_autotune": (_I, [_P, C.POINTER(Rays), _I, _P, C.POINTER(_I)]),
+    "lsnif_set_trace_mode": (_I, [_P, _I]),
+    "lsnif_get_tuning": (_I, [_P, C.POINTER(_I), C.POINTER(_I)]),
     "lsnif_make_training_rays": (_I, [_P, _U32, _P, _I64, _I64, _P, _P, _P]),
     "lsnif_label_rays": (_I, [_P, C.POINTER(Rays), C.POINTER(Labels), _P]),
     "lsnif_train_step": (_I, [_P, C.POINTER(Rays), C.POINTER(Labels), C.POINTER(TrainOpts), C.POINTER(TrainStats),
                               _P]),
-    "lsnif_submit": (_I, [_P, C.POINTER(Rays), C.POINTER(Hits), _I, C.POINTER(_U64)]),
+    "lsnif_submit": (_I, [_P, C.POINTER(Rays), C.POINTER(Hits), _I, _P, C.POINTER(_U64)]),
     "lsnif_poll": (_I, [_P, _U64, _I64, C.POINTER(ReqStats)]),
     "lsnif_pending": (_I64, [_P]),
     "lsnif_set_profiling": (_I, [_P, _I]),
@@ -392,8 +395,19 @@ class Context:
             out.append((t.value, l.value))
         return out
 
+    def set_graph_mode(self, on: bool):
+        _check(self.lib.lsnif_set_graph_mode(self.h, 1 if on else 0))
+
     def set_variant(self, v: int):
         _check(self.lib.lsnif_set_variant(self.h, v))
+
+    def set_trace_mode(self, mode: int):
+        _check(self.lib.lsnif_set_trace_mode(self.h, mode))
+
+    def tuning(self) -> tuple[int, int]:
+        v, t = C.c_int(), C.c_int()
+        _check(self.lib.lsnif_get_tuning(self.h, C.byref(v), C.byref(t)))
+        return v.value, t.value
 
     def autotune(self, rays, obj: int = 0, obj_per_ray=None, reps: int = 3, stream=None) -> int:
         rs = rays_struct(rays, obj_per_ray, obj)
@@ -439,11 +453,14 @@ class Context:
         return st if stats else None
 
     # ---- serving -----------------------------------------------------------------
-    def submit(self, rays, res: QueryResult, obj: int = 0, obj_per_ray=None, precision: int = BF16_FUSED) -> int:
+    def submit(self, rays, res: QueryResult, obj: int = 0, obj_per_ray=None, precision: int = BF16_FUSED,
+               stream=None) -> int:
+        """Queue a query; it runs after the work already enqueued on `stream`
+        (default: the current stream), where the buffers were produced."""
         rs = rays_struct(rays, obj_per_ray, obj)
         hs = self.hits_struct(res)
         tk = C.c_uint64()
-        _check(self.lib.lsnif_submit(self.h, C.byref(rs), C.byref(hs), precision, C.byref(tk)))
+        _check(self.lib.lsnif_submit(self.h, C.byref(rs), C.byref(hs), precision, _stream(stream), C.byref(tk)))
         return tk.value
 
     def poll(self, ticket: int, timeout_us: int = 0):

@@ -405,3 +405,46 @@ def test_invalid_configs_are_rejected(ctx):
         with pytest.raises(lsnif.LsnifError) as e:
             ctx.load_object(mesh, cfg)
         assert e.value.code == -1, bad
+
+
+def test_graph_mode_replays_the_query(ctx, sphere, torus):
+    """Captured once, replayed afterwards: same results as direct launches,
+    for a multi-object batch, and parameter updates reach the replays."""
+    cam = I.seeded_camera(2)
+    ra = I.rays_sphere_to_box(3000, 3.0, sphere["orc"].bmin, sphere["orc"].bmax, seed=91)
+    rb = np.ascontiguousarray(I.rays_pinhole(cam, px0=600, py0=1000, w=64, h=40))
+    both = _cuda(np.concatenate([ra, rb], axis=1))
+    handles = _cuda(np.concatenate([np.full(ra.shape[1], sphere["h"]),
+                                    np.full(rb.shape[1], torus["h"])]).astype(np.uint32).view(np.int32))
+    side = torch.cuda.Stream()
+    for prec in (lsnif.FP32_PLAIN, lsnif.BF16_FUSED):
+        direct = ctx.query_rays(both, obj_per_ray=handles, precision=prec)
+        torch.cuda.synchronize()
+        ctx.set_graph_mode(True)
+        out = ctx._alloc_hits(both.shape[1], 0, False)
+        with torch.cuda.stream(side):
+            for _ in range(3):   # capture, then replays
+                out.t.zero_()
+                ctx.query_rays(both, obj_per_ray=handles, precision=prec, out=out, stream=side)
+        side.synchronize()
+        ctx.check()
+        for f in ("hit", "t", "mat", "normal"):
+            assert torch.equal(getattr(direct, f), getattr(out, f)), f
+        ctx.set_graph_mode(False)
+    # parameter updates are read by replays
+    ctx.set_graph_mode(True)
+    mlp = ctx.read_params(sphere["h"], lsnif.PARAM_MLP)
+    out = ctx._alloc_hits(both.shape[1], 0, False)
+    with torch.cuda.stream(side):
+        ctx.query_rays(both, obj_per_ray=handles, precision=lsnif.BF16_FUSED, out=out, stream=side)
+    side.synchronize()
+    before = out.t.clone()
+    ctx.write_params(sphere["h"], lsnif.PARAM_MLP, mlp * 1.5)
+    with torch.cuda.stream(side):
+        ctx.query_rays(both, obj_per_ray=handles, precision=lsnif.BF16_FUSED, out=out, stream=side)
+    side.synchronize()
+    changed = ~torch.isclose(before[: ra.shape[1]], out.t[: ra.shape[1]]) & torch.isfinite(before[: ra.shape[1]])
+    assert changed.any()
+    assert torch.equal(before[ra.shape[1]:], out.t[ra.shape[1]:])   # the other object is untouched
+    ctx.write_params(sphere["h"], lsnif.PARAM_MLP, mlp)
+    ctx.set_graph_mode(False)
