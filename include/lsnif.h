@@ -331,13 +331,22 @@ LSNIF_API int lsnif_set_trace_mode(lsnif_ctx *ctx, int mode);
 
 /* Time every fused-kernel variant on `rays` (DEVICE buffers, `reps` BF16
  * queries each after one warm-up, CUDA events on `stream`, synchronous), keep
- * the fastest, then time the other traversal kernel with it and keep the
- * faster; *chosen (may be NULL) receives the variant index. Results of the
- * queries are discarded; all choices compute identical results. */
+ * the fastest, then the other traversal kernel and (single-object rays) the
+ * other grouping, keeping each if faster; *chosen (may be NULL) receives the
+ * variant index. Results of the queries are discarded; all choices compute
+ * identical results. */
 LSNIF_API int lsnif_autotune(lsnif_ctx *ctx, const lsnif_rays *rays, int reps, void *stream, int *chosen);
 
-/* The context's current fused-kernel variant and traversal kernel. */
-LSNIF_API int lsnif_get_tuning(lsnif_ctx *ctx, int *variant, int *trace_mode);
+/* How live rays are grouped into 128-ray tiles: 0 = by object, then by
+ * number of occupied voxels (descending); 1 = single-object queries keep the
+ * rays' original order (neighbouring primary rays share voxels and lattice
+ * cells, which the gather's L1 cache exploits); multi-object queries always
+ * use 0. Both compute identical results. */
+LSNIF_API int lsnif_set_group_mode(lsnif_ctx *ctx, int mode);
+
+/* The context's current fused-kernel variant, traversal kernel and
+ * grouping (lsnif_autotune sets all three). */
+LSNIF_API int lsnif_get_tuning(lsnif_ctx *ctx, int *variant, int *trace_mode, int *group_mode);
 
 /* ---- training (Sec. 5.2, 5.3) ------------------------------------------ */
 

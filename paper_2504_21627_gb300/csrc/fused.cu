@@ -194,6 +194,7 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(FusedArgs a) {
     if (tid == 0) {
       int t = XROWS ? atomicAdd(a.q.s.meta + 3, 1) : atomicAdd(q.s.meta + 3, 1);
       S.misc[0] = t;
+      S.misc[2] = 0;   // the tile's largest segment count
     }
     __syncthreads();
     const int64_t tile = S.misc[0];
@@ -230,10 +231,12 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(FusedArgs a) {
         if (XROWS) {
           S.ray[r] = start + r;
           S.kk[r] = H / 2;
+          atomicMax(&S.misc[2], H / 2);
         } else {
           int32_t ray = q.s.order[start + r];
           S.ray[r] = ray;
           S.kk[r] = q.s.k[ray];
+          atomicMax(&S.misc[2], S.kk[r]);
           float2 tt = reinterpret_cast<const float2 *>(q.s.t01)[ray];
           S.t0[r] = tt.x;
           S.t1[r] = tt.y;
@@ -244,7 +247,7 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(FusedArgs a) {
       }
     }
     __syncthreads();
-    const int kmax = S.kk[0];  // rows are sorted by k, descending
+    const int kmax = S.misc[2];  // chunks no ray of the tile reaches are skipped
     const int CHK = 2 * L * F;              // columns per chunk (one segment)
     const int G = (L * F) / 8;              // 16-byte column groups per point
     const uint32_t a_sbo = (uint32_t)(CHK / 8) * 128u;

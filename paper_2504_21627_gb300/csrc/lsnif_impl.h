@@ -91,6 +91,7 @@ struct QueryScratch {
   int32_t *tiles;    // max_tiles x 3 (slot, start, count)
   int32_t *meta;     // [0] n_live, [1] n_tiles, [2] n_points, [3] tile cursor
   float *X;          // FP32 path: chunk of tiles x kTileM rows x ldx features
+  int32_t *blk;      // coherent grouping: live rays and points per block of kGroupBlock rays, then offsets
   int32_t max_tiles; // upper bound on tiles (n / kTileM + n_slots)
   int32_t wmax;      // FP32 path: widest layer (hidden width or padded output)
 };
@@ -105,7 +106,11 @@ struct QueryLaunch {
   int *err;               // device error word
   cudaStream_t stream;
   int trace_mode;         // traversal kernel: 0 one ray per thread, 1 persistent lanes
+  int group_mode;         // 0: live rays grouped by (object, k desc); 1: one object, original order kept
+  int single_slot;        // object slot of a single-object query (group_mode 1)
 };
+
+constexpr int kGroupBlock = 4096;  // rays per block of the order-keeping grouping
 
 // ---- launchers (query.cu) ----
 // Traversal + histogram; returns kernels launched (adds to *launches).

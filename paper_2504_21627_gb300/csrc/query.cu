@@ -330,6 +330,112 @@ __global__ void __launch_bounds__(256) scatter_kernel(QueryLaunch q) {
 }
 
 // ---------------------------------------------------------------------------
+// Order-keeping grouping for single-object queries: live rays are compacted
+// in their original order, so a 128-ray tile holds neighbouring rays (for
+// primary rays: neighbouring pixels, which share voxels and lattice cells).
+// count: live rays and points per block of kGroupBlock rays; scan: block
+// offsets, totals and the tile table; scatter: stable ranks within a block.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) group_count_kernel(QueryLaunch q, int nblk) {
+  __shared__ int s_live[32], s_pts[32];
+  const int b = blockIdx.x;
+  int live = 0, pts = 0;
+  for (int r = 0; r < kGroupBlock / 1024; ++r) {
+    const int64_t i = (int64_t)b * kGroupBlock + r * 1024 + threadIdx.x;
+    if (i < q.rays.n && q.s.slot[i] >= 0) {
+      const int k = q.s.k[i];
+      live += k > 0;
+      pts += 2 * k;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    live += __shfl_down_sync(0xffffffffu, live, o);
+    pts += __shfl_down_sync(0xffffffffu, pts, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    s_live[threadIdx.x >> 5] = live;
+    s_pts[threadIdx.x >> 5] = pts;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int a = 0, c = 0;
+    for (int w = 0; w < 32; ++w) { a += s_live[w]; c += s_pts[w]; }
+    q.s.blk[b] = a;
+    q.s.blk[nblk + b] = c;
+  }
+}
+
+__global__ void __launch_bounds__(1024) group_scan_kernel(QueryLaunch q, int nblk) {
+  __shared__ int s_part[1024];
+  __shared__ int s_pts[1024];
+  const int per = (nblk + 1023) / 1024;
+  const int b0 = threadIdx.x * per;
+  int sum = 0, pts = 0;
+  for (int b = b0; b < min(b0 + per, nblk); ++b) { sum += q.s.blk[b]; pts += q.s.blk[nblk + b]; }
+  s_part[threadIdx.x] = sum;
+  s_pts[threadIdx.x] = pts;
+  __syncthreads();
+  if (threadIdx.x == 0) {   // exclusive scan of the 1024 partial sums
+    int run = 0, pr = 0;
+    for (int t = 0; t < 1024; ++t) {
+      const int v = s_part[t];
+      s_part[t] = run;
+      run += v;
+      pr += s_pts[t];
+    }
+    int tiles = (run + kTileM - 1) / kTileM;
+    if (tiles > q.s.max_tiles) {
+      atomicOr(q.err, kErrCheck);
+      tiles = q.s.max_tiles;
+    }
+    q.s.meta[0] = run;
+    q.s.meta[1] = tiles;
+    q.s.meta[2] = pr;
+    q.s.meta[3] = 0;
+  }
+  __syncthreads();
+  int run = s_part[threadIdx.x];
+  for (int b = b0; b < min(b0 + per, nblk); ++b) {   // block offsets replace the counts
+    const int v = q.s.blk[b];
+    q.s.blk[b] = run;
+    run += v;
+  }
+  const int n_live = q.s.meta[0], tiles = q.s.meta[1];
+  for (int t = threadIdx.x; t < tiles; t += blockDim.x) {
+    q.s.tiles[3 * t + 0] = q.single_slot;
+    q.s.tiles[3 * t + 1] = t * kTileM;
+    q.s.tiles[3 * t + 2] = min(kTileM, n_live - t * kTileM);
+  }
+}
+
+__global__ void __launch_bounds__(1024) group_scatter_kernel(QueryLaunch q) {
+  __shared__ int s_warp[32];
+  __shared__ int s_total;
+  const int b = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int base = q.s.blk[b];
+  for (int r = 0; r < kGroupBlock / 1024; ++r) {
+    const int64_t i = (int64_t)b * kGroupBlock + r * 1024 + threadIdx.x;
+    const bool live = i < q.rays.n && q.s.slot[i] >= 0 && q.s.k[i] > 0;
+    const unsigned m = __ballot_sync(0xffffffffu, live);
+    if (lane == 0) s_warp[warp] = __popc(m);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int run = 0;
+      for (int w = 0; w < 32; ++w) {
+        const int v = s_warp[w];
+        s_warp[w] = run;
+        run += v;
+      }
+      s_total = run;
+    }
+    __syncthreads();
+    if (live) q.s.order[base + s_warp[warp] + __popc(m & ((1u << lane) - 1u))] = (int32_t)i;
+    base += s_total;
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
 // FP32 path: gather into X, one chunk of tiles at a time. Row (t, r) of the
 // chunk is ray r of tile t; the row stride is the largest input width.
 // ---------------------------------------------------------------------------
@@ -562,6 +668,14 @@ cudaError_t launch_trace(const QueryLaunch &q, int *launches) {
 }
 
 cudaError_t launch_group(const QueryLaunch &q, int *launches) {
+  if (q.group_mode == 1) {
+    const int nblk = (int)((q.rays.n + kGroupBlock - 1) / kGroupBlock);
+    group_count_kernel<<<nblk, 1024, 0, q.stream>>>(q, nblk);
+    group_scan_kernel<<<1, 1024, 0, q.stream>>>(q, nblk);
+    group_scatter_kernel<<<nblk, 1024, 0, q.stream>>>(q);
+    *launches += 3;
+    return cudaGetLastError();
+  }
   scan_kernel<<<1, 1024, 0, q.stream>>>(q);
   const int grid = grid_for(q.rays.n, 256, 152 * 16);
   scatter_kernel<<<grid, 256, 0, q.stream>>>(q);

@@ -34,7 +34,8 @@ int max_tiles_for(int64_t n, int n_slots) { return (int)(n / kTileM + n_slots + 
 size_t lsnif::workspace_bytes(int64_t n, int H, int n_slots, int n_in) {
   const int mt = max_tiles_for(n, n_slots);
   size_t b = al((size_t)n * H * 12) + al((size_t)n * 8) + al((size_t)n) + al((size_t)n * 2) + al((size_t)n * 4) +
-             3 * al((size_t)n_slots * kBuckets * 4) + al((size_t)mt * 12) + al(64 * 4);
+             3 * al((size_t)n_slots * kBuckets * 4) + al((size_t)mt * 12) + al(64 * 4) +
+             al((size_t)(n / kGroupBlock + 2) * 8);
   if (n_in > 0) b += al((size_t)std::min(mt, kChunkTiles) * kTileM * n_in * 4);
   return b;
 }
@@ -89,6 +90,7 @@ static QueryScratch carve(Workspace *ws, int64_t n, int H, int n_slots, int n_in
   const int mt = max_tiles_for(N, SS);
   s.tiles = c.take<int32_t>((size_t)mt * 12);
   s.meta = c.take<int32_t>(64 * 4);
+  s.blk = c.take<int32_t>((size_t)(N / kGroupBlock + 2) * 8);
   s.X = ws->cap_nin > 0 ? c.take<float>((size_t)std::min(mt, kChunkTiles) * kTileM * ws->cap_nin * 4) : nullptr;
   s.max_tiles = max_tiles_for(n, n_slots);
   return s;
@@ -162,6 +164,8 @@ int lsnif::run_query(lsnif_ctx *ctx, Workspace *ws, const lsnif_rays *r, lsnif_h
   q.err = ctx->d_err;
   q.stream = st;
   q.trace_mode = ctx->trace_mode;
+  q.group_mode = (ctx->group_mode == 1 && !r->obj) ? 1 : 0;
+  q.single_slot = r->obj ? 0 : sh.rep->slot;
   int launches = 0;
   if (profile) cudaEventRecord(ctx->ev[0], st);
   cudaError_t e = launch_trace(q, &launches);
@@ -204,7 +208,8 @@ static int query_graph(lsnif_ctx *ctx, const lsnif_rays *r, lsnif_hits *h, int p
   if ((rc = ensure_workspace(ctx, &ctx->ws, r->n, sh.H, sh.n_slots, n_in))) return rc;
   if (ctx->graphs_ws != ctx->ws.base) clear_graphs(ctx);
   std::vector<uint64_t> key = {(uint64_t)r->n, (uint64_t)precision, (uint64_t)ctx->fused_variant,
-                               (uint64_t)ctx->trace_mode, (uint64_t)sh.n_slots, (uint64_t)r->single_obj};
+                               (uint64_t)ctx->trace_mode, (uint64_t)ctx->group_mode, (uint64_t)sh.n_slots,
+                               (uint64_t)r->single_obj};
   for (const void *p : {(const void *)r->ox, (const void *)r->oy, (const void *)r->oz, (const void *)r->dx,
                         (const void *)r->dy, (const void *)r->dz, (const void *)r->tmin, (const void *)r->tmax,
                         (const void *)r->obj, (const void *)h->hit, (const void *)h->t, (const void *)h->nx,
@@ -429,7 +434,7 @@ extern "C" int lsnif_autotune(lsnif_ctx *ctx, const lsnif_rays *rays, int reps, 
   cudaEvent_t a, b;
   cudaEventCreate(&a);
   cudaEventCreate(&b);
-  const int keep_v = ctx->fused_variant, keep_t = ctx->trace_mode;
+  const int keep_v = ctx->fused_variant, keep_t = ctx->trace_mode, keep_g = ctx->group_mode;
   auto time_it = [&](float *ms) -> int {
     int rc = run_query(ctx, &ctx->ws, rays, &none, LSNIF_BF16_FUSED, st, false);
     if (rc) return rc;
@@ -450,7 +455,7 @@ extern "C" int lsnif_autotune(lsnif_ctx *ctx, const lsnif_rays *rays, int reps, 
     if ((rc = time_it(&ms))) break;
     if (best < 0 || ms < best_ms) { best = v; best_ms = ms; }
   }
-  int best_t = ctx->trace_mode;
+  int best_t = ctx->trace_mode, best_g = ctx->group_mode;
   if (rc == LSNIF_OK) {
     ctx->fused_variant = best;
     for (int t = 0; t < 2 && rc == LSNIF_OK; ++t) {
@@ -460,24 +465,44 @@ extern "C" int lsnif_autotune(lsnif_ctx *ctx, const lsnif_rays *rays, int reps, 
       if ((rc = time_it(&ms))) break;
       if (ms < best_ms) { best_t = t; best_ms = ms; }
     }
+    ctx->trace_mode = best_t;
+    // grouping: only single-object queries can keep the original order
+    if (rc == LSNIF_OK && !rays->obj) {
+      for (int g = 0; g < 2 && rc == LSNIF_OK; ++g) {
+        if (g == best_g) continue;
+        ctx->group_mode = g;
+        float ms = 0.f;
+        if ((rc = time_it(&ms))) break;
+        if (ms < best_ms) { best_g = g; best_ms = ms; }
+      }
+    }
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   if (rc) {
     ctx->fused_variant = keep_v;
     ctx->trace_mode = keep_t;
+    ctx->group_mode = keep_g;
     return rc;
   }
   ctx->fused_variant = best;
   ctx->trace_mode = best_t;
+  ctx->group_mode = best_g;
   if (chosen) *chosen = best;
   return LSNIF_OK;
 }
 
-extern "C" int lsnif_get_tuning(lsnif_ctx *ctx, int *variant, int *trace_mode) {
-  if (!ctx || !variant || !trace_mode) return fail(LSNIF_ERR_INVALID_ARG, "lsnif_get_tuning: NULL argument");
+extern "C" int lsnif_get_tuning(lsnif_ctx *ctx, int *variant, int *trace_mode, int *group_mode) {
+  if (!ctx || !variant || !trace_mode || !group_mode) return fail(LSNIF_ERR_INVALID_ARG, "lsnif_get_tuning: NULL argument");
   *variant = ctx->fused_variant;
   *trace_mode = ctx->trace_mode;
+  *group_mode = ctx->group_mode;
+  return LSNIF_OK;
+}
+
+extern "C" int lsnif_set_group_mode(lsnif_ctx *ctx, int mode) {
+  if (!ctx || (mode != 0 && mode != 1)) return fail(LSNIF_ERR_INVALID_ARG, "lsnif_set_group_mode: bad mode %d", mode);
+  ctx->group_mode = mode;
   return LSNIF_OK;
 }
 

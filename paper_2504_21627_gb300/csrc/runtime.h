@@ -65,6 +65,7 @@ struct lsnif_ctx {
   lsnif::Workspace ws;
   int fused_variant = 1;  // fused-kernel tile shape (see lsnif_autotune)
   int trace_mode = 1;     // traversal kernel (see lsnif_autotune)
+  int group_mode = 0;     // grouping of live rays (see lsnif_set_group_mode)
   // CUDA-graph cache of queries (see lsnif_set_graph_mode)
   bool graph_mode = false;
   std::map<std::vector<uint64_t>, cudaGraphExec_t> graphs;

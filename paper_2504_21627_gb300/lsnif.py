@@ -127,7 +127,8 @@ SIGNATURES = {
     "lsnif_set_variant": (_I, [_P, _I]),
     "lsnif_autotune": (_I, [_P, C.POINTER(Rays), _I, _P, C.POINTER(_I)]),
     "lsnif_set_trace_mode": (_I, [_P, _I]),
-    "lsnif_get_tuning": (_I, [_P, C.POINTER(_I), C.POINTER(_I)]),
+    "lsnif_get_tuning": (_I, [_P, C.POINTER(_I), C.POINTER(_I), C.POINTER(_I)]),
+    "lsnif_set_group_mode": (_I, [_P, _I]),
     "lsnif_make_training_rays": (_I, [_P, _U32, _P, _I64, _I64, _P, _P, _P]),
     "lsnif_label_rays": (_I, [_P, C.POINTER(Rays), C.POINTER(Labels), _P]),
     "lsnif_train_step": (_I, [_P, C.POINTER(Rays), C.POINTER(Labels), C.POINTER(TrainOpts), C.POINTER(TrainStats),
@@ -404,10 +405,14 @@ class Context:
     def set_trace_mode(self, mode: int):
         _check(self.lib.lsnif_set_trace_mode(self.h, mode))
 
-    def tuning(self) -> tuple[int, int]:
-        v, t = C.c_int(), C.c_int()
-        _check(self.lib.lsnif_get_tuning(self.h, C.byref(v), C.byref(t)))
-        return v.value, t.value
+    def set_group_mode(self, mode: int):
+        _check(self.lib.lsnif_set_group_mode(self.h, mode))
+
+    def tuning(self) -> tuple[int, int, int]:
+        """(fused-kernel variant, traversal kernel, grouping)"""
+        v, t, g = C.c_int(), C.c_int(), C.c_int()
+        _check(self.lib.lsnif_get_tuning(self.h, C.byref(v), C.byref(t), C.byref(g)))
+        return v.value, t.value, g.value
 
     def autotune(self, rays, obj: int = 0, obj_per_ray=None, reps: int = 3, stream=None) -> int:
         rs = rays_struct(rays, obj_per_ray, obj)

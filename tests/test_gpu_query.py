@@ -448,3 +448,31 @@ def test_graph_mode_replays_the_query(ctx, sphere, torus):
     assert torch.equal(before[ra.shape[1]:], out.t[ra.shape[1]:])   # the other object is untouched
     ctx.write_params(sphere["h"], lsnif.PARAM_MLP, mlp)
     ctx.set_graph_mode(False)
+
+
+def test_tuning_choices_give_identical_results(ctx, torus):
+    """Traversal kernel, grouping and fused-kernel variant change only the
+    schedule: every combination returns the same bits."""
+    cam = I.seeded_camera(2)
+    rays = _cuda(np.ascontiguousarray(I.rays_pinhole(cam, px0=500, py0=700, w=512, h=256)))
+    ref = {}
+    keep = ctx.tuning()
+    for prec in (lsnif.FP32_PLAIN, lsnif.BF16_FUSED):
+        for tm in (0, 1):
+            for gm in (0, 1):
+                for v in (range(len(lsnif.Context.variants())) if prec == lsnif.BF16_FUSED else [0]):
+                    ctx.set_trace_mode(tm)
+                    ctx.set_group_mode(gm)
+                    ctx.set_variant(v)
+                    out = ctx.query_rays(rays, obj=torus["h"], precision=prec, logits=True)
+                    ctx.check()
+                    got = (out.hit.cpu(), out.t.cpu(), out.mat.cpu(), out.logits.cpu())
+                    if prec not in ref:
+                        ref[prec] = got
+                        continue
+                    for a, b in zip(ref[prec], got):
+                        assert torch.equal(torch.nan_to_num(a, nan=-1e30), torch.nan_to_num(b, nan=-1e30)), \
+                            (prec, tm, gm, v)
+    ctx.set_variant(keep[0])
+    ctx.set_trace_mode(keep[1])
+    ctx.set_group_mode(keep[2])
