@@ -265,6 +265,76 @@ __device__ __forceinline__ void encode_levels_f16(const __half *__restrict__ tab
   }
 }
 
+// FP16 tables with F = 2 (one half2 word per entry), interpolated in half2
+// arithmetic: corner words are selected from the loaded groups without
+// unpacking, and each corner pair costs one HSUB2 and two HFMA2. The FP16
+// accumulation error (about 2^-11 of the feature range) is far below the
+// BF16 rounding the fused kernel applies to the result.
+__device__ __forceinline__ uint32_t word4(const uint4 &g, uint32_t j) {
+  const uint32_t lo = (j & 1u) ? g.y : g.x;
+  const uint32_t hi = (j & 1u) ? g.w : g.z;
+  return (j & 2u) ? hi : lo;
+}
+
+template <int NL>
+__device__ __forceinline__ void encode_levels_h2(const __half *__restrict__ tab0, size_t level_stride, uint32_t mask,
+                                                 const float3 &p, const float *Ns, __half2 (&out)[NL]) {
+  const uint8_t *base = reinterpret_cast<const uint8_t *>(tab0);
+  float wx[NL], wy[NL], wz[NL];
+  uint32_t ia[NL][4], ib[NL][4];
+  bool pa[NL][4], pb[NL][4];
+#pragma unroll
+  for (int u = 0; u < NL; ++u) {
+    const Cell c = lattice_cell(p, Ns[u]);
+    wx[u] = c.wx;
+    wy[u] = c.wy;
+    wz[u] = c.wz;
+    const uint32_t hy0 = c.cy * kPi2, hy1 = hy0 + kPi2;
+    const uint32_t hz0 = c.cz * kPi3, hz1 = hz0 + kPi3;
+    const bool ny = c.wy != 0.f, nz = c.wz != 0.f, nx = c.wx != 0.f;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int dy = q & 1, dz = q >> 1;
+      const uint32_t b = (dy ? hy1 : hy0) ^ (dz ? hz1 : hz0);
+      ia[u][q] = (c.cx ^ b) & mask;
+      ib[u][q] = ((c.cx + 1u) ^ b) & mask;
+      pa[u][q] = (dy == 0 || ny) && (dz == 0 || nz);
+      pb[u][q] = pa[u][q] && nx && ((ia[u][q] ^ ib[u][q]) >= 4u);
+    }
+  }
+  uint4 ga[NL][4];
+  uint32_t gb[NL][4];
+#pragma unroll
+  for (int u = 0; u < NL; ++u) {
+    const uint8_t *tl = base + (size_t)u * level_stride;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      ga[u][q] = ldg16_if(tl + (size_t)(ia[u][q] & ~3u) * 4, pa[u][q]);
+      gb[u][q] = ldg4_if(tl + (size_t)ib[u][q] * 4, pb[u][q]);
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < NL; ++u) {
+    const float w0y = 1.f - wy[u], w0z = 1.f - wz[u];
+    const float wq[4] = {w0y * w0z, wy[u] * w0z, w0y * wz[u], wy[u] * wz[u]};
+    const __half2 wx2 = __float2half2_rn(wx[u]);
+    __half2 acc = __float2half2_rn(0.f);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const uint32_t w0 = word4(ga[u][q], ia[u][q] & 3u);
+      const uint32_t wg = word4(ga[u][q], ib[u][q] & 3u);
+      const bool same = (ia[u][q] ^ ib[u][q]) < 4u;
+      // x1 corner: its own load, the shared group, or (zero weight) the x0 value
+      const uint32_t w1 = pb[u][q] ? gb[u][q] : (same ? wg : w0);
+      const __half2 v0 = *reinterpret_cast<const __half2 *>(&w0);
+      const __half2 v1 = *reinterpret_cast<const __half2 *>(&w1);
+      const __half2 lerp = __hfma2(wx2, __hsub2(v1, v0), v0);
+      acc = __hfma2(__float2half2_rn(wq[q]), lerp, acc);
+    }
+    out[u] = acc;
+  }
+}
+
 // Scatter of a feature gradient into the level's table (backward of
 // encode_level): table[idx] += weight * g, every non-zero corner.
 __device__ __forceinline__ void encode_level_backward(float *__restrict__ gtab, uint32_t mask, const float3 &p,

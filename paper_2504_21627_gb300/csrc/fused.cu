@@ -286,13 +286,25 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(FusedArgs a) {
 #pragma unroll
           for (int u0 = 0; u0 < LPG; u0 += NLB) {
             const int l = g * LPG + u0;
-            float f[NLB][F];
-            encode_levels_f16<F, NLB>(reinterpret_cast<const __half *>(tab) + (size_t)l * lstride, lstride * 2,
-                                      mask, p, s_res + l, f);
+            if constexpr (F == 2) {
+              __half2 h[NLB];
+              encode_levels_h2<NLB>(reinterpret_cast<const __half *>(tab) + (size_t)l * lstride, lstride * 2, mask, p,
+                                    s_res + l, h);
 #pragma unroll
-            for (int u = 0; u < NLB; ++u)
+              for (int u = 0; u < NLB; ++u) {
+                const float2 f2 = __half22float2(h[u]);
+                flat[(u0 + u) * 2] = f2.x;
+                flat[(u0 + u) * 2 + 1] = f2.y;
+              }
+            } else {
+              float f[NLB][F];
+              encode_levels_f16<F, NLB>(reinterpret_cast<const __half *>(tab) + (size_t)l * lstride, lstride * 2,
+                                        mask, p, s_res + l, f);
 #pragma unroll
-              for (int c = 0; c < F; ++c) flat[(u0 + u) * F + c] = f[u][c];
+              for (int u = 0; u < NLB; ++u)
+#pragma unroll
+                for (int c = 0; c < F; ++c) flat[(u0 + u) * F + c] = f[u][c];
+            }
           }
           outv = make_uint4(pack_bf16(flat[0], flat[1]), pack_bf16(flat[2], flat[3]), pack_bf16(flat[4], flat[5]),
                             pack_bf16(flat[6], flat[7]));
