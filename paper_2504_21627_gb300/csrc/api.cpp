@@ -402,6 +402,18 @@ extern "C" int lsnif_load_object(lsnif_ctx *ctx, const lsnif_object_desc *desc, 
   }                                                                        \
   d.field = (type)p;
   OALLOC(occ, const uint32_t *, 4 * occ.size(), "occupancy");
+  // brick mask for empty-space skipping in the traversal: 32 bricks per axis
+  // (bricks of at least 2 voxels, so fewer for V < 64)
+  d.log2B = std::max(1, d.log2V - 5);
+  const int nbk = cfg.V >> d.log2B;
+  std::vector<uint32_t> brick(((size_t)nbk * nbk * nbk + 31) / 32, 0u);
+  for (size_t id = 0; id < (size_t)cfg.V * cfg.V * cfg.V; ++id) {
+    if (!((occ[id >> 5] >> (id & 31)) & 1u)) continue;
+    const size_t x = id % cfg.V, y = (id / cfg.V) % cfg.V, z = id / ((size_t)cfg.V * cfg.V);
+    const size_t b = ((z >> d.log2B) * nbk + (y >> d.log2B)) * nbk + (x >> d.log2B);
+    brick[b >> 5] |= 1u << (b & 31);
+  }
+  OALLOC(brick, const uint32_t *, 4 * brick.size(), "brick mask");
   OALLOC(tab32, const float *, 4 * nt, "tables");
   OALLOC(tab16, const uint16_t *, 2 * nt, "FP16 tables");
   OALLOC(mlp32, const float *, 4 * (size_t)o->n_params_mlp, "network");
@@ -414,6 +426,7 @@ extern "C" int lsnif_load_object(lsnif_ctx *ctx, const lsnif_object_desc *desc, 
   OALLOC(umma, const uint8_t *, d.umma_bytes, "tensor-core weights");
   OALLOC(plain_out, const float *, 4 * ((size_t)d.n_out_pad * cfg.width + d.n_out_pad), "padded output layer");
   cudaError_t e = cudaMemcpy((void *)d.occ, occ.data(), 4 * occ.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy((void *)d.brick, brick.data(), 4 * brick.size(), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) { free_object(ctx, o); return cuda_fail(e, "upload occupancy"); }
   cudaMemset((void *)d.umma, 0, d.umma_bytes);
   if ((rc = upload_params(ctx, o, tab_src, mlp_src)) != LSNIF_OK) { free_object(ctx, o); return rc; }

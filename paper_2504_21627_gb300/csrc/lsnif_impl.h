@@ -34,6 +34,8 @@ struct DevObject {
   int32_t log2V;
   float invV;
   const uint32_t *occ;  // ceil(V^3/32) words
+  const uint32_t *brick;  // coarse mask: brick (bz*nb + by)*nb + bx occupied if any of its voxels is
+  int32_t log2B;          // bricks are 2^log2B voxels wide, nb = V >> log2B per axis
 
   int32_t L, F, log2T;
   uint32_t mask;

@@ -95,6 +95,7 @@ struct LaneRay {
   int ain;
   float fin;
   int k, cap;
+  bool chk;        // the ray just entered a brick whose mask has not been read
 };
 
 __device__ __forceinline__ float sel3(int a, float x, float y, float z) { return a == 0 ? x : (a == 1 ? y : z); }
@@ -189,6 +190,7 @@ __global__ void __launch_bounds__(256) trace_pool_kernel(QueryLaunch q, int smem
               R.tcur = t0;
               R.ain = ea;
               R.fin = ea >= 0 ? (dd[ea] > 0.f ? 0.f : 1.f) : 0.f;
+              R.chk = true;
             }
           }
         }
@@ -196,18 +198,81 @@ __global__ void __launch_bounds__(256) trace_pool_kernel(QueryLaunch q, int smem
     }
     if (__all_sync(FULL, R.i < 0 && exhausted)) break;
     if (R.i < 0) continue;
-    // a few DDA steps of this lane's ray
+    // a few DDA steps (or brick jumps) of this lane's ray
     const DevObject &ob = q.objs[R.s];
     const int V = ob.V;
     const float invV = ob.invV;
     const uint32_t *occ = ob.occ;
+    const int lb = ob.log2B, nbk = V >> lb;
     float *P = q.s.pts + (size_t)R.i * Hs * 3;
     for (int it = 0; it < steps_per_round; ++it) {
+      bool done = false;
+      if (R.chk) {
+        // entered a new brick: if it is empty, jump to where the ray leaves it.
+        // The step-by-step traversal visits no occupied voxel in between, and
+        // the state it reaches is rebuilt exactly: crossing times use the same
+        // expression, and the exit axis follows the same lowest-axis tie rule.
+        R.chk = false;
+        const uint32_t bid = ((uint32_t)(R.ix2 >> lb) * nbk + (R.ix1 >> lb)) * nbk + (R.ix0 >> lb);
+        if (!((__ldg(ob.brick + (bid >> 5)) >> (bid & 31)) & 1u)) {
+          const int p0 = R.st0 > 0 ? ((R.ix0 >> lb) + 1) << lb : (R.ix0 >> lb) << lb;
+          const int p1 = R.st1 > 0 ? ((R.ix1 >> lb) + 1) << lb : (R.ix1 >> lb) << lb;
+          const int p2 = R.st2 > 0 ? ((R.ix2 >> lb) + 1) << lb : (R.ix2 >> lb) << lb;
+          const float e0 = R.st0 != 0 ? ((float)p0 * invV - R.o.x) * R.inv0 : CUDART_INF_F;
+          const float e1 = R.st1 != 0 ? ((float)p1 * invV - R.o.y) * R.inv1 : CUDART_INF_F;
+          const float e2 = R.st2 != 0 ? ((float)p2 * invV - R.o.z) * R.inv2 : CUDART_INF_F;
+          const int a = (e0 <= e1) ? (e0 <= e2 ? 0 : 2) : (e1 <= e2 ? 1 : 2);
+          const float tbe = sel3(a, e0, e1, e2);
+          if (tbe >= R.t1) {
+            done = true;
+          } else {
+            // the other axes cross their planes that come before (tbe, a)
+            for (int g = 0; g <= (1 << lb); ++g) {
+              if (a != 0 && (R.tn0 < tbe || (R.tn0 == tbe && 0 < a))) {
+                R.ix0 += R.st0;
+                R.tn0 = ((float)(R.ix0 + (R.st0 > 0)) * invV - R.o.x) * R.inv0;
+              } else break;
+            }
+            for (int g = 0; g <= (1 << lb); ++g) {
+              if (a != 1 && (R.tn1 < tbe || (R.tn1 == tbe && 1 < a))) {
+                R.ix1 += R.st1;
+                R.tn1 = ((float)(R.ix1 + (R.st1 > 0)) * invV - R.o.y) * R.inv1;
+              } else break;
+            }
+            for (int g = 0; g <= (1 << lb); ++g) {
+              if (a != 2 && (R.tn2 < tbe)) {
+                R.ix2 += R.st2;
+                R.tn2 = ((float)(R.ix2 + (R.st2 > 0)) * invV - R.o.z) * R.inv2;
+              } else break;
+            }
+            // then axis a crosses into the next brick
+            const int pa = a == 0 ? p0 : (a == 1 ? p1 : p2);
+            const int sa = sel3i(a, R.st0, R.st1, R.st2);
+            const int ia = sa > 0 ? pa : pa - 1;
+            if (ia < 0 || ia >= V) {
+              done = true;
+            } else {
+              R.tcur = tbe;
+              R.ain = a;
+              R.fin = (float)pa * invV;
+              const float tn = ((float)(ia + (sa > 0)) * invV - comp(R.o, a)) * sel3(a, R.inv0, R.inv1, R.inv2);
+              if (a == 0) { R.ix0 = ia; R.tn0 = tn; }
+              else if (a == 1) { R.ix1 = ia; R.tn1 = tn; }
+              else { R.ix2 = ia; R.tn2 = tn; }
+              R.chk = true;
+            }
+          }
+          if (done) {
+            finish();
+            break;
+          }
+          continue;
+        }
+      }
       const int a = (R.tn0 <= R.tn1) ? (R.tn0 <= R.tn2 ? 0 : 2) : (R.tn1 <= R.tn2 ? 1 : 2);
       const float tna = sel3(a, R.tn0, R.tn1, R.tn2);
       const float tx = fminf(tna, R.t1);
       const uint32_t vid = ((uint32_t)R.ix2 * V + R.ix1) * V + R.ix0;
-      bool done = false;
       if (tx > R.tcur && occupied(occ, vid)) {
         const int ia = sel3i(a, R.ix0, R.ix1, R.ix2), sa = sel3i(a, R.st0, R.st1, R.st2);
         const float3 pa = seg_point(R.o, R.d, R.tcur, R.ain, R.fin);
@@ -233,6 +298,8 @@ __global__ void __launch_bounds__(256) trace_pool_kernel(QueryLaunch q, int smem
           if (a == 0) { R.ix0 = ia; R.tn0 = tn; }
           else if (a == 1) { R.ix1 = ia; R.tn1 = tn; }
           else { R.ix2 = ia; R.tn2 = tn; }
+          // a new brick starts where the stepped index crosses a brick boundary
+          R.chk = (ia & ((1 << lb) - 1)) == (sa > 0 ? 0 : (1 << lb) - 1);
         }
       }
       if (done) {

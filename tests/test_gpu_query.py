@@ -476,3 +476,67 @@ def test_tuning_choices_give_identical_results(ctx, torus):
     ctx.set_variant(keep[0])
     ctx.set_trace_mode(keep[1])
     ctx.set_group_mode(keep[2])
+
+
+def _tie_rays(orc, n_random, seed):
+    """Rays that meet many lattice planes at the same parameter: along the
+    axes on lattice-aligned lines, along the diagonals through lattice points,
+    starting inside the box, plus seeded random rays."""
+    V = orc.cfg.V
+    lo, hi = orc.bmin.astype(np.float64), orc.bmax.astype(np.float64)
+    ext = hi - lo
+    g = np.random.default_rng(seed)
+    cols = []
+    j = np.arange(0, V + 1, max(3, V // 16)) / V
+    for ax in range(3):
+        for sgn in (1.0, -1.0):
+            u, v = np.meshgrid(j, j, indexing="ij")
+            o = np.zeros((u.size, 3))
+            o[:, ax] = -0.5 if sgn > 0 else 1.5
+            o[:, (ax + 1) % 3], o[:, (ax + 2) % 3] = u.ravel(), v.ravel()
+            d = np.zeros_like(o)
+            d[:, ax] = sgn
+            cols.append((o, d))
+    for sx in (1.0, -1.0):
+        for sy in (1.0, -1.0):
+            for sz in (1.0, -1.0):
+                c = g.integers(0, V + 1, size=(1000, 3)) / V
+                d = np.tile([sx, sy, sz], (1000, 1))
+                cols.append((c - 2.0 * d, d))
+    inside = g.random((2000, 3))
+    dirs = g.normal(size=(2000, 3))
+    cols.append((inside, dirs))
+    o = np.concatenate([c[0] for c in cols])
+    d = np.concatenate([c[1] for c in cols])
+    rays = np.zeros((8, o.shape[0]), np.float32)
+    rays[0:3] = (lo + o * ext).T
+    rays[3:6] = (d * ext).T
+    rays[6] = 0.0
+    rays[7] = np.inf
+    rnd = I.rays_sphere_to_box(n_random, 2.2, orc.bmin, orc.bmax, seed=seed)
+    return np.ascontiguousarray(np.concatenate([rays, rnd], axis=1))
+
+
+@pytest.mark.parametrize("name", ["sphere", "torus"])
+def test_brick_skipping_keeps_traversal_exact(ctx, request, name):
+    """The persistent-lane traversal jumps over empty bricks; the one-ray-per-
+    thread traversal steps every voxel. On rays full of ties between lattice
+    planes both must give the same bits, and the points the oracle's
+    traversal gives."""
+    ob = request.getfixturevalue(name)
+    rays = _tie_rays(ob["orc"], 5000, seed=31)
+    keep = ctx.tuning()
+    got = {}
+    for tm in (0, 1):
+        ctx.set_trace_mode(tm)
+        out = ctx.query_rays(_cuda(rays), obj=ob["h"], precision=lsnif.FP32_PLAIN, logits=True)
+        ctx.check()
+        got[tm] = [torch.nan_to_num(x.cpu(), nan=-1e30) for x in (out.hit, out.t, out.mat, out.logits)]
+    ctx.set_trace_mode(keep[1])
+    for a, b in zip(got[0], got[1]):
+        assert torch.equal(a, b)
+    seg = O.ray_segments(ob["orc"], rays)
+    live = (seg.k > 0) & ~seg.near
+    assert live.sum() > 500
+    hit = got[1][0].numpy().astype(bool)
+    assert not hit[(seg.k == 0) & ~seg.near].any()
