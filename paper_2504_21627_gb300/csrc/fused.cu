@@ -4,19 +4,35 @@
 // on its own hardware (Sec. 5); here the gather is fused in as well, so the
 // concatenated input vector (Sec. 3.2) never leaves shared memory.
 //
-// Per 128-ray tile (the tcgen05 M), for each occupied-voxel segment s
-// (= points 2s and 2s+1, the K chunk of 2*L*F input columns):
-//   all 16 warps gather the chunk's features into a BF16 A tile in shared
-//   memory (no-swizzle K-major core-matrix layout), one thread issues the
-//   chunk's MMAs against the resident first-layer weights, and a ring of
-//   buffers lets the next chunk's gather overlap the MMAs. Chunks no ray of
-//   the tile reaches are skipped (tiles are sorted by point count).
-// Hidden and output layers: warps 0-3 (one TMEM lane = one ray each) read
-// the accumulator, add bias, apply the activation, write BF16 activations
-// back to shared memory for the next MMA, and finally decode the logits.
+// Work unit: a tile of 128 rays (the tcgen05 M). The first layer's K runs
+// over the tile's occupied-voxel segments: chunk s holds the features of
+// points 2s and 2s+1 (2*L*F BF16 columns, no-swizzle K-major core-matrix
+// layout). Chunks no ray of the tile reaches are skipped (tiles are sorted
+// by point count).
 //
-// Every mbarrier wait is bounded by a clock limit; on expiry the kernel sets
-// the device error word, stops, frees its TMEM and returns.
+// Warp roles:
+//   gather warps (NG): build the tile's work lists, then fill chunk after
+//     chunk into a ring of shared-memory A tiles;
+//   one MMA warp: issues each filled chunk's MMAs against the resident
+//     first-layer weights into the tile's TMEM accumulator;
+//   four epilogue warps (TMEM lane = ray): hidden and output layers (bias,
+//     activation, BF16 activations back to shared memory, next MMA) and the
+//     decode, while the gather warps fill the next tile. Two TMEM
+//     accumulators alternate between tiles.
+//
+// Shared boundary points: consecutive occupied voxels along a ray share a
+// face, and the traversal marks an entry point that is bit-identical to the
+// previous segment's exit (bit s of the ray's dup mask). Such a point is
+// gathered once: its chunk copies the features from the previous chunk's A
+// tile. A chunk's work is thus a list of gathers, copies and zero fills (two
+// entries per ray); gathers go round-robin over the gather warps in blocks
+// of 32 items (item = one point x one 16-byte column group), so every warp
+// gets the same share whatever the mix.
+//
+// Every mbarrier wait is bounded by a clock limit; on expiry the kernel flags
+// an abort, every role stops, the device error word is set, in-flight MMAs
+// are waited for (again bounded), TMEM is freed and the kernel returns.
+#include <climits>
 #include <cstdio>
 
 #include "device.cuh"
@@ -26,7 +42,9 @@ namespace lsnif {
 
 namespace {
 
-constexpr int kNBuf = 3;
+constexpr int kNBufMax = 4;
+constexpr int kEpiWarps = 4;
+constexpr int kListStride = 2 * kTileM;  // work-list entries per chunk: two per ray
 constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
 
 __device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -61,22 +79,49 @@ __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.a
 __device__ __forceinline__ void tc_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
+__device__ __forceinline__ void mbar_init(uint32_t addr, int count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(addr), "r"(count) : "memory");
+}
+
 __device__ __forceinline__ void mbar_arrive(uint32_t addr) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(addr) : "memory");
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity) {
-  long long t0 = clock64();
+__device__ __forceinline__ bool mbar_try(uint32_t addr, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(addr), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+// Bounded wait for the phase of the given parity. Gives up at once when
+// another thread has flagged an abort, and flags one itself on expiry.
+__device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity, volatile int *abort_flag) {
+  const long long t0 = clock64();
   while (true) {
-    uint32_t done;
-    asm volatile(
-        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(addr), "r"(parity)
-        : "memory");
-    if (done) return true;
-    if (clock64() - t0 > kWaitCycles) return false;
+    if (mbar_try(addr, parity)) return true;
+    if (*abort_flag) return false;
+    if (clock64() - t0 > kWaitCycles) {
+      *abort_flag = 1;
+      return false;
+    }
   }
+}
+
+// Bounded wait that ignores the abort flag (teardown: in-flight MMAs).
+__device__ __forceinline__ bool mbar_wait_teardown(uint32_t addr, uint32_t parity) {
+  const long long t0 = clock64();
+  while (!mbar_try(addr, parity))
+    if (clock64() - t0 > kWaitCycles) return false;
+  return true;
+}
+
+// named barrier among `count` threads (id 0 is __syncthreads)
+__device__ __forceinline__ void named_sync(int id, int count) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 
 #define TMEM_LD16(taddr, r)                                                                                        \
@@ -106,70 +151,114 @@ struct FusedArgs {
   const float *X;
   float *Z;
   int64_t xrows;
-  uint32_t smem_blob;  // bytes reserved for the weight blob
+  uint32_t smem_blob;  // bytes of the weight blob
+  int nbuf;            // ring buffers (2..kNBufMax)
+  int list_chunks;     // work-list capacity in chunks (H_max / 2)
 };
 
-struct Smem {
-  uint8_t *blob, *ring, *act;
-  int32_t *ray;
-  int32_t *kk;
-  float *t0, *t1;
-  uint64_t *mbar;  // kNBuf "empty" ring barriers (MMA done), the accumulator
-                   // barrier, then kNBuf "full" ring barriers (tile written)
-  uint32_t *tmem_slot;
-  int32_t *misc;   // [0] tile, [1] abort
+struct TileInfo {
+  int32_t kmax, slot, stop, pad;
 };
+
+// Shared-memory layout (byte offsets from a 1024-aligned base), the same on
+// host (sizing) and device (carving).
+struct Layout {
+  uint32_t blob, ring, ring_stride, act, ray, t0, t1, list, wsum, info, bars, tmem, misc, res, total;
+};
+
+__host__ __device__ inline uint32_t lay_take(uint32_t &off, uint32_t bytes, uint32_t align) {
+  off = (off + align - 1) & ~(align - 1);
+  const uint32_t r = off;
+  off += bytes;
+  return r;
+}
+
+// mbarriers: full[kNBufMax], empty[kNBufMax], tile_ready[2], acc_full[2],
+// acc_empty[2], layer_done, fin[2]
+constexpr int kNumBars = 2 * kNBufMax + 2 + 2 + 2 + 1 + 2;
+
+__host__ __device__ inline Layout make_layout(uint32_t blob_bytes, int F, int W, int nbuf, int list_chunks) {
+  Layout o{};
+  uint32_t off = 0;
+  o.ring_stride = (uint32_t)kTileM * (uint32_t)(2 * 16 * F) * 2u;  // one chunk for L <= 16
+  o.blob = lay_take(off, blob_bytes, 1024);
+  o.ring = lay_take(off, (uint32_t)nbuf * o.ring_stride, 1024);
+  o.act = lay_take(off, (uint32_t)kTileM * W * 2u, 1024);
+  o.ray = lay_take(off, 2 * kTileM * 4, 16);
+  o.t0 = lay_take(off, 2 * kTileM * 4, 16);
+  o.t1 = lay_take(off, 2 * kTileM * 4, 16);
+  o.list = lay_take(off, (uint32_t)list_chunks * kListStride * 2u, 16);
+  o.wsum = lay_take(off, (uint32_t)list_chunks * 4u * 4u, 16);
+  o.info = lay_take(off, 2 * sizeof(TileInfo), 16);
+  o.bars = lay_take(off, 8 * kNumBars, 8);
+  o.tmem = lay_take(off, 16, 16);
+  o.misc = lay_take(off, 16 * 4, 16);
+  o.res = lay_take(off, 4 * LSNIF_MAX_LEVELS, 16);
+  o.total = off + 1024;  // slack for aligning the dynamic base
+  return o;
+}
+
+// work-list counts of one ray for chunk s, packed: gathers | copies << 10 |
+// zero fills << 20 (always two entries per ray)
+__device__ __forceinline__ uint32_t row_counts(int kk, uint32_t dm, int s) {
+  if (kk <= s) return 2u << 20;
+  const bool dup = s > 0 && ((dm >> s) & 1u);
+  return dup ? (1u | (1u << 10)) : 2u;
+}
 
 }  // namespace
 
 // F: features per level; W: hidden width; XROWS: read the network input
-// from global rows instead of gathering it; NT: threads per CTA; NLB:
-// levels whose corner loads are in flight together per gather item.
-template <int F, int W, bool XROWS, int NT, int NLB>
-__global__ void __launch_bounds__(NT, 1) fused_kernel(FusedArgs a) {
-  constexpr int kThreads = NT;
+// from global rows instead of gathering it; NG: gather warps; NLB: levels
+// whose corner loads are in flight together per gather item.
+template <int F, int W, bool XROWS, int NG, int NLB>
+__global__ void __launch_bounds__((NG + 1 + kEpiWarps) * 32, 1) fused_kernel(FusedArgs a) {
+  constexpr int kGatherThreads = NG * 32;
+  constexpr int kMmaWarp = NG;
+  constexpr int kEpiWarp0 = NG + 1;
+  constexpr int kTmemCols = 2 * W;  // two accumulators
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const QueryLaunch &q = a.q;
-
-  // carve shared memory (offsets are multiples of 1024)
-  uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  Smem S;
-  S.blob = base;
   const DevObject *objs = q.objs;
-  uint32_t off = (a.smem_blob + 1023u) & ~1023u;
-  S.ring = base + off;
-  // ring buffers hold one K chunk (2 points x L x F columns) for L <= 16
-  const uint32_t ring_stride = (uint32_t)kTileM * (uint32_t)(2 * 16 * F) * 2u;
-  off += kNBuf * ring_stride;
-  S.act = base + off;
-  off += (uint32_t)kTileM * W * 2u;
-  S.ray = reinterpret_cast<int32_t *>(base + off);
-  off += kTileM * 4;
-  S.kk = reinterpret_cast<int32_t *>(base + off);
-  off += kTileM * 4;
-  S.t0 = reinterpret_cast<float *>(base + off);
-  off += kTileM * 4;
-  S.t1 = reinterpret_cast<float *>(base + off);
-  off += kTileM * 4;
-  S.mbar = reinterpret_cast<uint64_t *>(base + off);
-  off += 8 * (2 * kNBuf + 1);
-  S.tmem_slot = reinterpret_cast<uint32_t *>(base + off);
-  off += 16;
-  S.misc = reinterpret_cast<int32_t *>(base + off);
-  off += 16;
-  float *s_res = reinterpret_cast<float *>(base + off);  // lattice resolution per level
+  const int nbuf = a.nbuf;
 
-  constexpr int kTmemCols = W < 32 ? 32 : W;
+  uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const Layout lay = make_layout(a.smem_blob, F, W, nbuf, a.list_chunks);
+  uint8_t *s_blob = base + lay.blob;
+  uint8_t *s_ring = base + lay.ring;
+  uint8_t *s_act = base + lay.act;
+  int32_t *s_ray = reinterpret_cast<int32_t *>(base + lay.ray);
+  float *s_t0 = reinterpret_cast<float *>(base + lay.t0);
+  float *s_t1 = reinterpret_cast<float *>(base + lay.t1);
+  uint16_t *s_list = reinterpret_cast<uint16_t *>(base + lay.list);
+  uint32_t *s_wsum = reinterpret_cast<uint32_t *>(base + lay.wsum);
+  TileInfo *s_info = reinterpret_cast<TileInfo *>(base + lay.info);
+  uint64_t *bars = reinterpret_cast<uint64_t *>(base + lay.bars);
+  uint64_t *b_full = bars, *b_empty = bars + kNBufMax, *b_ready = bars + 2 * kNBufMax;
+  uint64_t *b_accf = b_ready + 2, *b_acce = b_ready + 4, *b_layer = b_ready + 6, *b_fin = b_ready + 7;
+  uint32_t *s_tmem = reinterpret_cast<uint32_t *>(base + lay.tmem);
+  int32_t *s_misc = reinterpret_cast<int32_t *>(base + lay.misc);  // [0] tile [1] kmax [2] epi stop [4] abort
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(s_misc + 4);
+  float *s_res = reinterpret_cast<float *>(base + lay.res);
+  const uint32_t ring_stride = lay.ring_stride;
+
   if (tid == 0) {
-    for (int i = 0; i < kNBuf + 1; ++i)
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&S.mbar[i])) : "memory");
-    for (int i = kNBuf + 1; i < 2 * kNBuf + 1; ++i)   // every thread arrives once per chunk
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&S.mbar[i])), "r"(kThreads) : "memory");
-    S.misc[1] = 0;
+    for (int b = 0; b < nbuf; ++b) {
+      mbar_init(su32(&b_full[b]), kGatherThreads);
+      mbar_init(su32(&b_empty[b]), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(su32(&b_ready[b]), 1);
+      mbar_init(su32(&b_accf[b]), 1);
+      mbar_init(su32(&b_acce[b]), kEpiWarps * 32);
+      mbar_init(su32(&b_fin[b]), 1);
+    }
+    mbar_init(su32(b_layer), 1);
+    *abort_flag = 0;
   }
   if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(S.tmem_slot)),
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(s_tmem)),
                  "r"(kTmemCols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
@@ -177,173 +266,325 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(FusedArgs a) {
   tc_before();
   __syncthreads();
   tc_after();
-  const uint32_t tmem = *S.tmem_slot;
-
-  int chunk_ctr = 0;  // chunks issued (ring phase tracking)
-  int acc_ctr = 0;    // accumulator-barrier completions consumed
-  int cur_slot = -1;
-  int L = 0, H = 0, n_hidden = 0, n_out = 0, n_out_pad = 0, n_mat = 0, act = 0, n_in = 0, Hs = q.H_max;
-  uint32_t mask = 0;
-  const uint16_t *tab = nullptr;
-  uint32_t w0_sbo = 0, bias_off = 0;
-  bool aborted = false;
-
+  const uint32_t tmem = *s_tmem;
   const int64_t n_tiles = XROWS ? (a.xrows + kTileM - 1) / kTileM : (int64_t)q.s.meta[1];
-  for (;;) {
-    // ---- fetch the next tile ----
-    if (tid == 0) {
-      int t = XROWS ? atomicAdd(a.q.s.meta + 3, 1) : atomicAdd(q.s.meta + 3, 1);
-      S.misc[0] = t;
-      S.misc[2] = 0;   // the tile's largest segment count
-    }
-    __syncthreads();
-    const int64_t tile = S.misc[0];
-    if (tile >= n_tiles || S.misc[1]) break;
-    int slot, start, cnt;
-    if (XROWS) {
-      slot = 0;
-      start = (int)(tile * kTileM);
-      cnt = (int)min((int64_t)kTileM, a.xrows - tile * kTileM);
-    } else {
-      slot = q.s.tiles[3 * tile + 0];
-      start = q.s.tiles[3 * tile + 1];
-      cnt = q.s.tiles[3 * tile + 2];
-    }
-    // ---- (re)load the object's weights ----
-    if (slot != cur_slot) {
-      const DevObject &ob = objs[slot];
-      L = ob.L; H = ob.H; n_hidden = ob.n_hidden; n_out = ob.n_out; n_out_pad = ob.n_out_pad;
-      n_mat = ob.n_mat; act = ob.act; n_in = ob.n_in; mask = ob.mask; tab = ob.tab16;
-      w0_sbo = (uint32_t)(n_in / 8) * 128u;
-      bias_off = ob.umma_bias_off;
-      const uint4 *src = reinterpret_cast<const uint4 *>(ob.umma);
-      uint4 *dst = reinterpret_cast<uint4 *>(S.blob);
-      const int nvec = (int)(ob.umma_bytes / 16);
-      for (int i = tid; i < nvec; i += kThreads) dst[i] = __ldg(src + i);
-      if (tid < LSNIF_MAX_LEVELS) s_res[tid] = (float)ob.res[tid];
-      fence_async_smem();
-      __syncthreads();
-      cur_slot = slot;
-    }
-    if (tid < kTileM) {
-      int r = tid;
-      if (r < cnt) {
-        if (XROWS) {
-          S.ray[r] = start + r;
-          S.kk[r] = H / 2;
-          atomicMax(&S.misc[2], H / 2);
-        } else {
-          int32_t ray = q.s.order[start + r];
-          S.ray[r] = ray;
-          S.kk[r] = q.s.k[ray];
-          atomicMax(&S.misc[2], S.kk[r]);
-          float2 tt = reinterpret_cast<const float2 *>(q.s.t01)[ray];
-          S.t0[r] = tt.x;
-          S.t1[r] = tt.y;
-        }
-      } else {
-        S.ray[r] = -1;
-        S.kk[r] = 0;
-      }
-    }
-    __syncthreads();
-    const int kmax = S.misc[2];  // chunks no ray of the tile reaches are skipped
-    const int CHK = 2 * L * F;              // columns per chunk (one segment)
-    const int G = (L * F) / 8;              // 16-byte column groups per point
-    const uint32_t a_sbo = (uint32_t)(CHK / 8) * 128u;
-    const uint32_t idesc_h = idesc_bf16(W);
+  const int Hs = q.H_max;
 
-    // ---- layer 0: gather chunk by chunk, MMA against resident W0 ----
-    for (int s = 0; s < kmax; ++s) {
-      const int buf = chunk_ctr % kNBuf;
-      const int use = chunk_ctr / kNBuf;
-      if (use > 0) {
-        if (!mbar_wait(su32(&S.mbar[buf]), (uint32_t)((use - 1) & 1))) { aborted = true; }
-      }
-      uint8_t *A = S.ring + buf * ring_stride;
-      const int items = kTileM * 2 * G;
-      for (int e = tid; e < items; e += kThreads) {
-        const int r = e & (kTileM - 1);
-        const int rest = e >> 7;
-        const int j = rest % 2, g = rest / 2;
-        uint4 outv = make_uint4(0, 0, 0, 0);
-        if (XROWS) {
-          const int row = S.ray[r];
-          if (row >= 0) {
-            const float *xr = a.X + (int64_t)row * n_in + (size_t)(2 * s + j) * L * F + g * 8;
-            float4 x0 = *reinterpret_cast<const float4 *>(xr);
-            float4 x1 = *reinterpret_cast<const float4 *>(xr + 4);
-            outv = make_uint4(pack_bf16(x0.x, x0.y), pack_bf16(x0.z, x0.w), pack_bf16(x1.x, x1.y),
-                              pack_bf16(x1.z, x1.w));
-          }
-        } else if (S.kk[r] > s) {
-          const int32_t ray = S.ray[r];
-          const float *P = q.s.pts + ((size_t)ray * Hs + 2 * s + j) * 3;
-          const float3 p = make_float3(P[0], P[1], P[2]);
-          constexpr int LPG = 8 / F;  // levels per 16-byte group of the A tile
-          float flat[8];
-          const size_t lstride = (size_t)(mask + 1) * F;
-#pragma unroll
-          for (int u0 = 0; u0 < LPG; u0 += NLB) {
-            const int l = g * LPG + u0;
-            if constexpr (F == 2) {
-              __half2 h[NLB];
-              encode_levels_h2<NLB>(reinterpret_cast<const __half *>(tab) + (size_t)l * lstride, lstride * 2, mask, p,
-                                    s_res + l, h);
-#pragma unroll
-              for (int u = 0; u < NLB; ++u) {
-                const float2 f2 = __half22float2(h[u]);
-                flat[(u0 + u) * 2] = f2.x;
-                flat[(u0 + u) * 2 + 1] = f2.y;
-              }
-            } else {
-              float f[NLB][F];
-              encode_levels_f16<F, NLB>(reinterpret_cast<const __half *>(tab) + (size_t)l * lstride, lstride * 2,
-                                        mask, p, s_res + l, f);
-#pragma unroll
-              for (int u = 0; u < NLB; ++u)
-#pragma unroll
-                for (int c = 0; c < F; ++c) flat[(u0 + u) * F + c] = f[u][c];
-            }
-          }
-          outv = make_uint4(pack_bf16(flat[0], flat[1]), pack_bf16(flat[2], flat[3]), pack_bf16(flat[4], flat[5]),
-                            pack_bf16(flat[6], flat[7]));
-        }
-        const int kg = j * G + g;
-        *reinterpret_cast<uint4 *>(A + core_off(r, kg, a_sbo)) = outv;
-      }
-      // publish this thread's part of the tile to the tensor core; only the
-      // issuing thread waits for the whole tile, the other warps run ahead
-      fence_async_smem();
-      mbar_arrive(su32(&S.mbar[kNBuf + 1 + buf]));
+  if (warp < NG) {
+    // =================== gather warps ===================
+    int cur_slot = -1;
+    int L = 0, n_in = 0, H = 0;
+    uint32_t mask = 0;
+    const uint16_t *tab = nullptr;
+    int chunk_ctr = 0;
+    int rot_g = 0, rot_o = 0;  // round-robin origin of the gather / other blocks
+    for (int i = 0;; ++i) {
+      const int tb = i & 1;
+      // the tile-info slot tb is free once the epilogue of tile i-2 is done
       if (tid == 0) {
-        if (!mbar_wait(su32(&S.mbar[kNBuf + 1 + buf]), (uint32_t)(use & 1))) aborted = true;
-        tc_after();
-        const uint32_t a0 = su32(A), b0 = su32(S.blob);
-        for (int ks = 0; ks < CHK / 16; ++ks) {
-          const uint64_t ad = umma_desc(a0 + ks * 256, 128, a_sbo);
-          const uint64_t bd = umma_desc(b0 + (uint32_t)((s * CHK) / 8 + 2 * ks) * 128u, 128, w0_sbo);
-          mma_bf16(tmem, ad, bd, idesc_h, (s > 0 || ks > 0) ? 1u : 0u);
-        }
-        mma_commit(su32(&S.mbar[buf]));
+        const bool ok = i < 2 || mbar_wait(su32(&b_acce[tb]), (uint32_t)(((i - 2) >> 1) & 1), abort_flag);
+        int t = INT_MAX;
+        if (ok && !*abort_flag) t = atomicAdd(q.s.meta + 3, 1);
+        s_misc[0] = t;
+        s_misc[1] = 0;
       }
-      ++chunk_ctr;
-    }
-    if (tid == 0) mma_commit(su32(&S.mbar[kNBuf]));
+      named_sync(1, kGatherThreads);
+      const int tile = s_misc[0];
+      if ((int64_t)tile >= n_tiles) {
+        if (tid == 0) {
+          s_info[tb].stop = 1;
+          mbar_arrive(su32(&b_ready[tb]));
+        }
+        break;
+      }
+      int slot, start, cnt;
+      if (XROWS) {
+        slot = 0;
+        start = tile * kTileM;
+        cnt = (int)min((int64_t)kTileM, a.xrows - (int64_t)tile * kTileM);
+      } else {
+        slot = q.s.tiles[3 * tile + 0];
+        start = q.s.tiles[3 * tile + 1];
+        cnt = q.s.tiles[3 * tile + 2];
+      }
+      // ---- (re)load the object's weights once the previous tile is done with them ----
+      if (slot != cur_slot) {
+        if (tid == 0 && i >= 1) mbar_wait(su32(&b_acce[(i - 1) & 1]), (uint32_t)(((i - 1) >> 1) & 1), abort_flag);
+        named_sync(1, kGatherThreads);
+        const DevObject &ob = objs[slot];
+        L = ob.L;
+        n_in = ob.n_in;
+        H = ob.H;
+        mask = ob.mask;
+        tab = ob.tab16;
+        const uint4 *src = reinterpret_cast<const uint4 *>(ob.umma);
+        uint4 *dst = reinterpret_cast<uint4 *>(s_blob);
+        const int nvec = (int)(ob.umma_bytes / 16);
+        for (int k = tid; k < nvec; k += kGatherThreads) dst[k] = __ldg(src + k);
+        if (tid < LSNIF_MAX_LEVELS) s_res[tid] = (float)ob.res[tid];
+        fence_async_smem();
+        named_sync(1, kGatherThreads);
+        cur_slot = slot;
+      }
+      // ---- rows of the tile ----
+      int my_kk = 0;
+      uint32_t my_dm = 0u;
+      if (tid < kTileM) {
+        const int r = tid;
+        int ray = -1;
+        float t0v = 0.f, t1v = 0.f;
+        if (r < cnt) {
+          if (XROWS) {
+            ray = start + r;
+            my_kk = H / 2;
+          } else {
+            ray = q.s.order[start + r];
+            my_kk = q.s.k[ray];
+            my_dm = q.s.dup[ray];
+            const float2 tt = reinterpret_cast<const float2 *>(q.s.t01)[ray];
+            t0v = tt.x;
+            t1v = tt.y;
+          }
+        }
+        s_ray[tb * kTileM + r] = ray;
+        s_t0[tb * kTileM + r] = t0v;
+        s_t1[tb * kTileM + r] = t1v;
+        const int wm = __reduce_max_sync(0xffffffffu, my_kk);
+        if (lane == 0) atomicMax(&s_misc[1], wm);
+      }
+      named_sync(1, kGatherThreads);
+      const int kmax = s_misc[1];
+      // ---- work lists: per chunk, [gathers | copies | zero fills] ----
+      if (tid < kTileM) {
+        for (int s = 0; s < kmax; ++s) {
+          const uint32_t tot = __reduce_add_sync(0xffffffffu, row_counts(my_kk, my_dm, s));
+          if (lane == 0) s_wsum[s * 4 + warp] = tot;
+        }
+      }
+      named_sync(1, kGatherThreads);
+      if (tid < kTileM) {
+        const int r = tid;
+        for (int s = 0; s < kmax; ++s) {
+          const uint32_t v = row_counts(my_kk, my_dm, s);
+          uint32_t incl = v;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+          }
+          uint32_t woff = 0, all = 0;
+#pragma unroll
+          for (int w = 0; w < 4; ++w) {
+            const uint32_t x = s_wsum[s * 4 + w];
+            all += x;
+            woff += w < warp ? x : 0u;
+          }
+          const uint32_t pos = incl - v + woff;
+          const int ngt = (int)(all & 1023u), nct = (int)((all >> 10) & 1023u);
+          uint16_t *Ls = s_list + s * kListStride;
+          if (v & 1023u) {
+            const int pg = (int)(pos & 1023u);
+            if (v & (1023u << 10)) {  // entry point shared with the previous exit
+              Ls[pg] = (uint16_t)(r | 128);
+              Ls[ngt + (int)((pos >> 10) & 1023u)] = (uint16_t)r;
+            } else {
+              Ls[pg] = (uint16_t)r;
+              Ls[pg + 1] = (uint16_t)(r | 128);
+            }
+          } else {
+            const int pz = ngt + nct + (int)((pos >> 20) & 1023u);
+            Ls[pz] = (uint16_t)r;
+            Ls[pz + 1] = (uint16_t)(r | 128);
+          }
+        }
+      }
+      named_sync(1, kGatherThreads);
+      if (tid == 0) {
+        s_info[tb].kmax = kmax;
+        s_info[tb].slot = slot;
+        s_info[tb].stop = 0;
+        mbar_arrive(su32(&b_ready[tb]));
+      }
 
-    // ---- hidden layers and the output layer ----
-    const uint32_t act_sbo = (uint32_t)(W / 8) * 128u;
-    uint32_t wl_off = (uint32_t)W * n_in * 2u;  // byte offset of W1 in the blob
-    const float *bias = reinterpret_cast<const float *>(S.blob + bias_off);
-    for (int layer = 0; layer <= n_hidden; ++layer) {
-      const bool last = layer == n_hidden;
-      if (warp < 4) {
-        if (!mbar_wait(su32(&S.mbar[kNBuf]), (uint32_t)(acc_ctr & 1))) aborted = true;
+      // ---- chunks ----
+      const int G = (L * F) / 8;  // 16-byte column groups per point
+      const int CHK = 2 * L * F;  // columns per chunk
+      const uint32_t a_sbo = (uint32_t)(CHK / 8) * 128u;
+      const float invG = 1.f / (float)G;
+      const size_t lstride = (size_t)(mask + 1) * F;
+      for (int s = 0; s < kmax; ++s) {
+        const int c = chunk_ctr + s;
+        const int buf = c % nbuf, use = c / nbuf;
+        uint8_t *A = s_ring + buf * ring_stride;
+        uint32_t all = 0;
+#pragma unroll
+        for (int w = 0; w < 4; ++w) all += s_wsum[s * 4 + w];
+        const int ngt = (int)(all & 1023u), nct = (int)((all >> 10) & 1023u);
+        const int n_gi = ngt * G, n_oi = (kListStride - ngt) * G;
+        const int nb_g = (n_gi + 31) >> 5, nb_o = (n_oi + 31) >> 5;
+        const int first_g = (warp - rot_g + NG) % NG, first_o = (warp - rot_o + NG) % NG;
+        // The buffer is free once the MMAs of chunk c - nbuf are done and the
+        // copies of chunk c - nbuf + 1 (which read it) are written. Every
+        // thread waits, with or without items: an arrival on the full barrier
+        // must not land in the phase of chunk c - nbuf.
+        if (use > 0) mbar_wait(su32(&b_empty[buf]), (uint32_t)((use - 1) & 1), abort_flag);
+        {
+          const int cp = c - nbuf + 1;
+          if (cp >= 0 && cp < c) mbar_wait(su32(&b_full[cp % nbuf]), (uint32_t)((cp / nbuf) & 1), abort_flag);
+        }
+        // gathers
+        for (int b = first_g; b < nb_g; b += NG) {
+          const int it = b * 32 + lane;
+          if (it < n_gi) {
+            const int t = __float2int_rz(((float)it + 0.5f) * invG);
+            const int g = it - t * G;
+            const int e = s_list[s * kListStride + t];
+            const int r = e & 127, j = e >> 7;
+            const int ray = s_ray[tb * kTileM + r];
+            uint4 outv;
+            if (XROWS) {
+              const float *xr = a.X + (int64_t)ray * n_in + (size_t)(2 * s + j) * L * F + g * 8;
+              const float4 x0 = *reinterpret_cast<const float4 *>(xr);
+              const float4 x1 = *reinterpret_cast<const float4 *>(xr + 4);
+              outv = make_uint4(pack_bf16(x0.x, x0.y), pack_bf16(x0.z, x0.w), pack_bf16(x1.x, x1.y),
+                                pack_bf16(x1.z, x1.w));
+            } else {
+              const float *P = q.s.pts + ((size_t)ray * Hs + 2 * s + j) * 3;
+              const float3 p = make_float3(P[0], P[1], P[2]);
+              constexpr int LPG = 8 / F;  // levels per 16-byte group
+              float flat[8];
+#pragma unroll
+              for (int u0 = 0; u0 < LPG; u0 += NLB) {
+                const int l = g * LPG + u0;
+                if constexpr (F == 2) {
+                  __half2 h[NLB];
+                  encode_levels_h2<NLB>(reinterpret_cast<const __half *>(tab) + (size_t)l * lstride, lstride * 2,
+                                        mask, p, s_res + l, h);
+#pragma unroll
+                  for (int u = 0; u < NLB; ++u) {
+                    const float2 f2 = __half22float2(h[u]);
+                    flat[(u0 + u) * 2] = f2.x;
+                    flat[(u0 + u) * 2 + 1] = f2.y;
+                  }
+                } else {
+                  float f[NLB][F];
+                  encode_levels_f16<F, NLB>(reinterpret_cast<const __half *>(tab) + (size_t)l * lstride,
+                                            lstride * 2, mask, p, s_res + l, f);
+#pragma unroll
+                  for (int u = 0; u < NLB; ++u)
+#pragma unroll
+                    for (int cc = 0; cc < F; ++cc) flat[(u0 + u) * F + cc] = f[u][cc];
+                }
+              }
+              outv = make_uint4(pack_bf16(flat[0], flat[1]), pack_bf16(flat[2], flat[3]),
+                                pack_bf16(flat[4], flat[5]), pack_bf16(flat[6], flat[7]));
+            }
+            *reinterpret_cast<uint4 *>(A + core_off(r, j * G + g, a_sbo)) = outv;
+          }
+        }
+        // copies (entry point = previous chunk's exit point) and zero fills
+        const int n_ci = nct * G;
+        for (int b = first_o; b < nb_o; b += NG) {
+          if (b * 32 < n_ci) {  // this block copies: the previous chunk must be complete
+            const int cq = c - 1;
+            mbar_wait(su32(&b_full[cq % nbuf]), (uint32_t)((cq / nbuf) & 1), abort_flag);
+          }
+          const int it = b * 32 + lane;
+          if (it < n_oi) {
+            const int t = __float2int_rz(((float)it + 0.5f) * invG);
+            const int g = it - t * G;
+            const int e = s_list[s * kListStride + ngt + t];
+            const int r = e & 127, j = e >> 7;
+            uint4 outv = make_uint4(0u, 0u, 0u, 0u);
+            if (it < n_ci) {
+              const uint8_t *Ap = s_ring + ((c - 1) % nbuf) * ring_stride;
+              outv = *reinterpret_cast<const uint4 *>(Ap + core_off(r, G + g, a_sbo));
+            }
+            *reinterpret_cast<uint4 *>(A + core_off(r, j * G + g, a_sbo)) = outv;
+          }
+        }
+        rot_g = (rot_g + nb_g) % NG;
+        rot_o = (rot_o + nb_o) % NG;
+        fence_async_smem();
+        mbar_arrive(su32(&b_full[buf]));
+      }
+      chunk_ctr += kmax;
+    }
+  } else if (warp == kMmaWarp) {
+    // =================== MMA warp ===================
+    int chunk_ctr = 0;
+    const uint32_t idesc0 = idesc_bf16(W);
+    for (int i = 0;; ++i) {
+      const int tb = i & 1;
+      if (!mbar_wait(su32(&b_ready[tb]), (uint32_t)((i >> 1) & 1), abort_flag)) break;
+      const TileInfo ti = s_info[tb];
+      if (ti.stop) break;
+      const DevObject &ob = objs[ti.slot];
+      const int CHK = 2 * ob.L * F;
+      const uint32_t a_sbo = (uint32_t)(CHK / 8) * 128u, w0_sbo = (uint32_t)(ob.n_in / 8) * 128u;
+      if (i >= 2 && !mbar_wait(su32(&b_acce[tb]), (uint32_t)(((i - 2) >> 1) & 1), abort_flag)) break;
+      tc_after();
+      const uint32_t dacc = tmem + (uint32_t)(tb * W);
+      bool ok = true;
+      for (int s = 0; s < ti.kmax; ++s) {
+        const int c = chunk_ctr + s;
+        const int buf = c % nbuf;
+        if (!mbar_wait(su32(&b_full[buf]), (uint32_t)((c / nbuf) & 1), abort_flag)) {
+          ok = false;
+          break;
+        }
         tc_after();
-        const int r = warp * 32 + lane;
-        const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+        if (lane == 0) {
+          const uint32_t a0 = su32(s_ring + buf * ring_stride), b0 = su32(s_blob);
+          for (int ks = 0; ks < CHK / 16; ++ks) {
+            const uint64_t ad = umma_desc(a0 + ks * 256, 128, a_sbo);
+            const uint64_t bd = umma_desc(b0 + (uint32_t)((s * CHK) / 8 + 2 * ks) * 128u, 128, w0_sbo);
+            mma_bf16(dacc, ad, bd, idesc0, (s > 0 || ks > 0) ? 1u : 0u);
+          }
+          mma_commit(su32(&b_empty[buf]));
+        }
+        __syncwarp();
+      }
+      if (!ok) break;
+      chunk_ctr += ti.kmax;
+      if (lane == 0) mma_commit(su32(&b_accf[tb]));
+      __syncwarp();
+    }
+    if (lane == 0) {
+      mma_commit(su32(&b_fin[0]));
+      if (!mbar_wait_teardown(su32(&b_fin[0]), 0u)) *abort_flag = 1;
+    }
+    __syncwarp();
+  } else {
+    // =================== epilogue warps ===================
+    const int etid = tid - kEpiWarp0 * 32;  // 0..127
+    const int quarter = warp & 3;          // the TMEM lane quarter this warp may access
+    const int r = quarter * 32 + lane;
+    const uint32_t act_sbo = (uint32_t)(W / 8) * 128u;
+    int layer_ctr = 0;
+    for (int i = 0;; ++i) {
+      const int tb = i & 1;
+      named_sync(2, kEpiWarps * 32);
+      if (etid == 0) {
+        bool ok = mbar_wait(su32(&b_ready[tb]), (uint32_t)((i >> 1) & 1), abort_flag);
+        const bool stop = !ok || s_info[tb].stop;
+        if (!stop) ok = mbar_wait(su32(&b_accf[tb]), (uint32_t)((i >> 1) & 1), abort_flag);
+        s_misc[2] = (stop || !ok) ? 1 : 0;
+      }
+      named_sync(2, kEpiWarps * 32);
+      if (s_misc[2]) break;
+      tc_after();
+      const TileInfo ti = s_info[tb];
+      const DevObject &ob = objs[ti.slot];
+      const int n_hidden = ob.n_hidden, n_out = ob.n_out, n_out_pad = ob.n_out_pad, n_mat = ob.n_mat, act = ob.act;
+      const float *bias = reinterpret_cast<const float *>(s_blob + ob.umma_bias_off);
+      uint32_t wl_off = (uint32_t)W * ob.n_in * 2u;  // byte offset of W1 in the blob
+      const uint32_t dacc = tmem + (uint32_t)(tb * W);
+      const uint32_t trow = dacc + ((uint32_t)(quarter * 32) << 16);
+      for (int layer = 0; layer <= n_hidden; ++layer) {
+        const bool last = layer == n_hidden;
+        const float *bl = bias + layer * W;
         if (!last) {
-          const float *bl = bias + layer * W;
 #pragma unroll 1
           for (int c0 = 0; c0 < W; c0 += 16) {
             uint32_t v[16];
@@ -354,15 +595,34 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(FusedArgs a) {
               float h8[8];
 #pragma unroll
               for (int u = 0; u < 8; ++u) h8[u] = act_fn(__uint_as_float(v[c + u]) + bl[c0 + c + u], act);
-              uint4 pk = make_uint4(pack_bf16(h8[0], h8[1]), pack_bf16(h8[2], h8[3]), pack_bf16(h8[4], h8[5]),
-                                    pack_bf16(h8[6], h8[7]));
-              *reinterpret_cast<uint4 *>(S.act + core_off(r, (c0 + c) / 8, act_sbo)) = pk;
+              const uint4 pk = make_uint4(pack_bf16(h8[0], h8[1]), pack_bf16(h8[2], h8[3]),
+                                          pack_bf16(h8[4], h8[5]), pack_bf16(h8[6], h8[7]));
+              *reinterpret_cast<uint4 *>(s_act + core_off(r, (c0 + c) / 8, act_sbo)) = pk;
             }
           }
+          fence_async_smem();
+          tc_before();
+          named_sync(2, kEpiWarps * 32);
+          const int N = (layer + 1 < n_hidden) ? W : n_out_pad;
+          if (etid == 0) {
+            tc_after();
+            const uint32_t a0 = su32(s_act), b0 = su32(s_blob) + wl_off;
+            const uint32_t idesc = idesc_bf16(N);
+            for (int ks = 0; ks < W / 16; ++ks) {
+              const uint64_t ad = umma_desc(a0 + ks * 256, 128, act_sbo);
+              const uint64_t bd = umma_desc(b0 + ks * 256, 128, act_sbo);
+              mma_bf16(dacc, ad, bd, idesc, ks > 0 ? 1u : 0u);
+            }
+            mma_commit(su32(b_layer));
+            mbar_wait(su32(b_layer), (uint32_t)(layer_ctr & 1), abort_flag);
+          }
+          ++layer_ctr;
+          named_sync(2, kEpiWarps * 32);
+          tc_after();
+          wl_off += (uint32_t)N * W * 2u;
         } else {
           // logits 16 columns at a time into a per-thread array, then decode
           float z[64];
-          const float *bl = bias + layer * W;
 #pragma unroll 1
           for (int c0 = 0; c0 < n_out_pad; c0 += 16) {
             uint32_t v[16];
@@ -371,43 +631,30 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(FusedArgs a) {
 #pragma unroll
             for (int u = 0; u < 16; ++u) z[c0 + u] = __uint_as_float(v[u]) + bl[c0 + u];
           }
-          const int32_t ray = S.ray[r];
-          if (ray >= 0 && !aborted) {
+          const int32_t ray = s_ray[tb * kTileM + r];
+          if (ray >= 0 && !*abort_flag) {
             if (XROWS) {
               for (int j = 0; j < n_out; ++j) a.Z[(int64_t)ray * n_out + j] = z[j];
             } else {
-              decode_store(q.hits, ray, z, n_out, n_mat, S.t0[r], S.t1[r], q.rays.tmin[ray], q.rays.tmax[ray]);
+              decode_store(q.hits, ray, z, n_out, n_mat, s_t0[tb * kTileM + r], s_t1[tb * kTileM + r],
+                           q.rays.tmin[ray], q.rays.tmax[ray]);
             }
           }
         }
-        if (!last) fence_async_smem();
-        tc_before();
       }
-      ++acc_ctr;
-      if (aborted) S.misc[1] = 1;
-      __syncthreads();
-      if (!last && tid == 0) {
-        tc_after();
-        const int N = (layer + 1 < n_hidden) ? W : n_out_pad;
-        const uint32_t a0 = su32(S.act), b0 = su32(S.blob) + wl_off;
-        const uint32_t idesc = idesc_bf16(N);
-        for (int ks = 0; ks < W / 16; ++ks) {
-          const uint64_t ad = umma_desc(a0 + ks * 256, 128, act_sbo);
-          const uint64_t bd = umma_desc(b0 + ks * 256, 128, act_sbo);
-          mma_bf16(tmem, ad, bd, idesc, ks > 0 ? 1u : 0u);
-        }
-        mma_commit(su32(&S.mbar[kNBuf]));
-      }
-      if (!last) wl_off += (uint32_t)((layer + 1 < n_hidden) ? W : n_out_pad) * W * 2u;
+      tc_before();
+      mbar_arrive(su32(&b_acce[tb]));
     }
-    if (aborted) S.misc[1] = 1;
+    if (etid == 0) {
+      mma_commit(su32(&b_fin[1]));
+      if (!mbar_wait_teardown(su32(&b_fin[1]), 0u)) *abort_flag = 1;
+    }
   }
-  if (aborted || S.misc[1]) {
-    if (tid == 0) atomicOr(q.err, kErrWaitTimeout);
-  }
+
   tc_before();
   __syncthreads();
   tc_after();
+  if (tid == 0 && *abort_flag) atomicOr(q.err, kErrWaitTimeout);
   if (warp == 0) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
   }
@@ -425,19 +672,24 @@ bool fused_supported(const DevObject &h) {
   return true;
 }
 
-size_t fused_smem_bytes(const DevObject &h) {
-  size_t blob = ((size_t)h.umma_bytes + 1023) & ~size_t(1023);
-  size_t ring = (size_t)kNBuf * kTileM * (2 * 16 * h.F) * 2;
-  size_t actb = (size_t)kTileM * h.width * 2;
-  size_t tail = kTileM * 16 + 8 * (2 * kNBuf + 1) + 16 + 16 + 4 * LSNIF_MAX_LEVELS;
-  return 1024 + blob + ring + actb + tail;
+static uint32_t blob_bytes(const DevObject &h) { return (h.umma_bytes + 15u) & ~15u; }
+
+// with the smallest ring (2 buffers); launches use up to kNBufMax that fit
+size_t fused_smem_bytes(const DevObject &h, int H_max) {
+  return make_layout(blob_bytes(h), h.F, h.width, 2, std::max(H_max, h.H) / 2).total;
 }
 
-template <int F, int W, bool XR, int NT, int NLB>
+static int pick_nbuf(const DevObject &h, int list_chunks) {
+  for (int nb = kNBufMax; nb >= 2; --nb)
+    if (make_layout(blob_bytes(h), h.F, h.width, nb, list_chunks).total <= 232448) return nb;
+  return 0;
+}
+
+template <int F, int W, bool XR, int NG, int NLB>
 static cudaError_t launch_one(const FusedArgs &a, size_t smem, cudaStream_t st) {
   static int attr = 0;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(fused_kernel<F, W, XR, NT, NLB>,
+    cudaError_t e = cudaFuncSetAttribute(fused_kernel<F, W, XR, NG, NLB>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
     if (e != cudaSuccess) return e;
     attr = 1;
@@ -445,27 +697,29 @@ static cudaError_t launch_one(const FusedArgs &a, size_t smem, cudaStream_t st) 
   int sms = 0, dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  fused_kernel<F, W, XR, NT, NLB><<<sms, NT, smem, st>>>(a);
+  fused_kernel<F, W, XR, NG, NLB><<<sms, (NG + 1 + kEpiWarps) * 32, smem, st>>>(a);
   return cudaGetLastError();
 }
 
-// Tile-shape variants the autotuner chooses between: threads per CTA and
-// levels of corner loads in flight per gather item.
+// Shapes the autotuner chooses between: gather warps per CTA and levels of
+// corner loads in flight per gather item.
 struct Variant {
-  int threads, levels;
+  int gather_warps, levels;
 };
-static const Variant kVariants[] = {{512, 1}, {512, 2}, {512, 4}, {1024, 1}, {1024, 2}};
+// 11 or 15 gather warps + 5 others: 4 or 5 warps per SM sub-partition
+// (at most 128 or 96 registers per thread)
+static const Variant kVariants[] = {{11, 1}, {11, 2}, {11, 4}, {15, 1}, {15, 2}};
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
 template <int F, int W, bool XR>
 static cudaError_t dispatch_variant(const FusedArgs &a, int v, size_t smem, cudaStream_t st) {
   constexpr int LPG = 8 / F;
   switch (v) {
-    case 0: return launch_one<F, W, XR, 512, 1>(a, smem, st);
-    case 1: return launch_one<F, W, XR, 512, (2 < LPG ? 2 : LPG)>(a, smem, st);
-    case 2: return launch_one<F, W, XR, 512, LPG>(a, smem, st);
-    case 3: return launch_one<F, W, XR, 1024, 1>(a, smem, st);
-    case 4: return launch_one<F, W, XR, 1024, (2 < LPG ? 2 : LPG)>(a, smem, st);
+    case 0: return launch_one<F, W, XR, 11, 1>(a, smem, st);
+    case 1: return launch_one<F, W, XR, 11, (2 < LPG ? 2 : LPG)>(a, smem, st);
+    case 2: return launch_one<F, W, XR, 11, LPG>(a, smem, st);
+    case 3: return launch_one<F, W, XR, 15, 1>(a, smem, st);
+    case 4: return launch_one<F, W, XR, 15, (2 < LPG ? 2 : LPG)>(a, smem, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -482,18 +736,20 @@ static cudaError_t dispatch(const FusedArgs &a, const DevObject &h, int variant,
 int fused_variant_count() { return kNumVariants; }
 
 void fused_variant_shape(int v, int *threads, int *levels) {
-  *threads = kVariants[v].threads;
+  *threads = kVariants[v].gather_warps * 32;
   *levels = kVariants[v].levels;
 }
 
 cudaError_t launch_fused(const QueryLaunch &q, const DevObject &h, int variant, int *launches) {
   if (!fused_supported(h)) return cudaErrorNotSupported;
-  size_t smem = fused_smem_bytes(h);
-  if (smem > 232448) return cudaErrorNotSupported;
   if (variant < 0 || variant >= kNumVariants) return cudaErrorInvalidValue;
   FusedArgs a{};
   a.q = q;
-  a.smem_blob = h.umma_bytes;
+  a.smem_blob = blob_bytes(h);
+  a.list_chunks = std::max(q.H_max, h.H) / 2;
+  a.nbuf = pick_nbuf(h, a.list_chunks);
+  if (!a.nbuf) return cudaErrorNotSupported;
+  const size_t smem = make_layout(a.smem_blob, h.F, h.width, a.nbuf, a.list_chunks).total;
   *launches += 1;
   return dispatch<false>(a, h, variant, smem, q.stream);
 }
@@ -501,13 +757,16 @@ cudaError_t launch_fused(const QueryLaunch &q, const DevObject &h, int variant, 
 cudaError_t launch_mlp_fused(const DevObject *dobj, const DevObject &h, const float *X, int64_t n, float *Z,
                              int *err, cudaStream_t st) {
   if (!fused_supported(h)) return cudaErrorNotSupported;
-  size_t smem = fused_smem_bytes(h);
-  if (smem > 232448) return cudaErrorNotSupported;
+  FusedArgs a{};
+  a.smem_blob = blob_bytes(h);
+  a.list_chunks = h.H / 2;
+  a.nbuf = pick_nbuf(h, a.list_chunks);
+  if (!a.nbuf) return cudaErrorNotSupported;
+  const size_t smem = make_layout(a.smem_blob, h.F, h.width, a.nbuf, a.list_chunks).total;
   int32_t *meta = nullptr;
   cudaError_t e = cudaMallocAsync(&meta, 16 * sizeof(int32_t), st);
   if (e != cudaSuccess) return e;
   cudaMemsetAsync(meta, 0, 16 * sizeof(int32_t), st);
-  FusedArgs a{};
   a.q.objs = dobj;
   a.q.n_slots = 1;
   a.q.H_max = h.H;
@@ -516,7 +775,6 @@ cudaError_t launch_mlp_fused(const DevObject *dobj, const DevObject &h, const fl
   a.X = X;
   a.Z = Z;
   a.xrows = n;
-  a.smem_blob = h.umma_bytes;
   e = dispatch<true>(a, h, 1, smem, st);
   cudaFreeAsync(meta, st);
   return e;

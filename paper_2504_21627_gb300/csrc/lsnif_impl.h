@@ -85,6 +85,7 @@ struct QueryScratch {
   float *pts;        // n x H x 3
   float *t01;        // n x 2
   uint8_t *k;        // n
+  uint32_t *dup;     // n: bit s set when boundary point 2s is bit-identical to point 2s-1
   int16_t *slot;     // n object slot per ray (-1 invalid)
   int32_t *order;    // n ray indices grouped by (object, k desc)
   int32_t *counts;   // n_slots x kBuckets
@@ -134,7 +135,7 @@ cudaError_t launch_tables_to_half(const float *src, uint16_t *dst, int64_t n, cu
 // Returns cudaErrorNotSupported when the object's shape is outside the
 // fused kernel's instantiations.
 bool fused_supported(const DevObject &host_obj);
-size_t fused_smem_bytes(const DevObject &host_obj);
+size_t fused_smem_bytes(const DevObject &host_obj, int H_max);  // smallest ring; H_max: query's largest H
 cudaError_t launch_fused(const QueryLaunch &q, const DevObject &host_obj, int variant, int *launches);
 int fused_variant_count();
 void fused_variant_shape(int variant, int *threads, int *levels);

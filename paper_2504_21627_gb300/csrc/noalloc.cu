@@ -85,13 +85,14 @@ extern "C" int lsnif_query_rays_noalloc(lsnif_ctx *ctx, const lsnif_rays *r, lsn
   }
   DevObject hobj = rep->d;
   hobj.umma_bytes = umma_max;
-  if (mixed || !fused_supported(hobj) || fused_smem_bytes(hobj) > 232448)
+  if (mixed || !fused_supported(hobj) || fused_smem_bytes(hobj, H) > 232448)
     return fail(LSNIF_ERR_UNSUPPORTED, "lsnif_query_rays_noalloc: objects outside the fused BF16 kernel's shapes");
 
   // carve the static scratch; reject what does not fit
   const int64_t n = r->n;
   const int max_tiles = (int)(n / kTileM + n_slots + 1);
-  const size_t need = al256((size_t)n * H * 12) + al256((size_t)n * 8) + al256((size_t)n) + al256((size_t)n * 2) +
+  const size_t need = al256((size_t)n * H * 12) + al256((size_t)n * 8) + al256((size_t)n) + al256((size_t)n * 4) +
+                      al256((size_t)n * 2) +
                       al256((size_t)n * 4) + 3 * al256((size_t)n_slots * kBuckets * 4) +
                       al256((size_t)max_tiles * 12) + al256(64 * 4);
   if (need > kNoAllocBytes)
@@ -112,6 +113,7 @@ extern "C" int lsnif_query_rays_noalloc(lsnif_ctx *ctx, const lsnif_rays *r, lsn
   s.pts = reinterpret_cast<float *>(take((size_t)n * H * 12));
   s.t01 = reinterpret_cast<float *>(take((size_t)n * 8));
   s.k = take((size_t)n);
+  s.dup = reinterpret_cast<uint32_t *>(take((size_t)n * 4));
   s.slot = reinterpret_cast<int16_t *>(take((size_t)n * 2));
   s.order = reinterpret_cast<int32_t *>(take((size_t)n * 4));
   s.counts = reinterpret_cast<int32_t *>(take((size_t)n_slots * kBuckets * 4));

@@ -32,12 +32,14 @@ __global__ void __launch_bounds__(256) trace_kernel(QueryLaunch q, int smem_hist
       atomicOr(q.err, kErrBadHandle);
       q.s.slot[i] = -1;
       q.s.k[i] = 0;
+      q.s.dup[i] = 0u;
       miss_store(q.hits, i, 0);
       continue;
     }
     const DevObject &ob = q.objs[s];
     float3 o, d;
     int ea;
+    uint32_t dupm = 0u;
     float tmin = q.rays.tmin[i];
     bool live = to_unit(ob, q.rays.ox[i], q.rays.oy[i], q.rays.oz[i], q.rays.dx[i], q.rays.dy[i], q.rays.dz[i], o,
                         d) &&
@@ -46,9 +48,18 @@ __global__ void __launch_bounds__(256) trace_kernel(QueryLaunch q, int smem_hist
       float *P = q.s.pts + (size_t)i * Hs * 3;
       const int cap = ob.H >> 1;
       const uint32_t *occ = ob.occ;
+      // exit of the previous segment: an entry with the same (t, axis, face)
+      // is the same point, bit for bit
+      uint32_t lt = 0u, lf = 0u;
+      int la = -2;
       dda_walk(
           ob, o, d, t0, t1, ea, [&](uint32_t vid) { return occupied(occ, vid); },
           [&](const Seg &sg) {
+            if (k > 0 && __float_as_uint(sg.tin) == lt && sg.ain == la && __float_as_uint(sg.fin) == lf)
+              dupm |= 1u << k;
+            lt = __float_as_uint(sg.tout);
+            la = sg.aout;
+            lf = __float_as_uint(sg.fout);
             float3 a = seg_point(o, d, sg.tin, sg.ain, sg.fin);
             float3 b = seg_point(o, d, sg.tout, sg.aout, sg.fout);
             float *w = P + 6 * k;
@@ -62,6 +73,7 @@ __global__ void __launch_bounds__(256) trace_kernel(QueryLaunch q, int smem_hist
       t0 = t1 = CUDART_NAN_F;
     }
     q.s.k[i] = (uint8_t)k;
+    q.s.dup[i] = dupm;
     q.s.slot[i] = (int16_t)s;
     reinterpret_cast<float2 *>(q.s.t01)[i] = make_float2(t0, t1);
     if (k == 0) miss_store(q.hits, i, ob.n_out);
@@ -96,6 +108,9 @@ struct LaneRay {
   float fin;
   int k, cap;
   bool chk;        // the ray just entered a brick whose mask has not been read
+  uint32_t dup;    // bit k: entry point of segment k equals the exit of segment k-1
+  uint32_t lt, lf; // exit (t, face) of the last segment, as bits
+  int la;          // and its axis
 };
 
 __device__ __forceinline__ float sel3(int a, float x, float y, float z) { return a == 0 ? x : (a == 1 ? y : z); }
@@ -120,6 +135,7 @@ __global__ void __launch_bounds__(256) trace_pool_kernel(QueryLaunch q, int smem
   auto finish = [&](void) {
     const int64_t i = R.i;
     q.s.k[i] = (uint8_t)R.k;
+    q.s.dup[i] = R.dup;
     q.s.slot[i] = (int16_t)R.s;
     reinterpret_cast<float2 *>(q.s.t01)[i] = make_float2(R.t0, R.t1);
     if (R.k == 0) miss_store(q.hits, i, q.objs[R.s].n_out);
@@ -146,11 +162,14 @@ __global__ void __launch_bounds__(256) trace_pool_kernel(QueryLaunch q, int smem
           const uint32_t h = q.rays.obj ? q.rays.obj[my] : q.rays.single_handle;
           R.s = slot_of(q.objs, q.n_slots, h);
           R.k = 0;
+          R.dup = 0u;
+          R.la = -2;
           R.t0 = R.t1 = CUDART_NAN_F;
           if (R.s < 0) {
             atomicOr(q.err, kErrBadHandle);
             q.s.slot[my] = -1;
             q.s.k[my] = 0;
+            q.s.dup[my] = 0u;
             miss_store(q.hits, my, 0);
             R.i = -1;
           } else {
@@ -275,8 +294,14 @@ __global__ void __launch_bounds__(256) trace_pool_kernel(QueryLaunch q, int smem
       const uint32_t vid = ((uint32_t)R.ix2 * V + R.ix1) * V + R.ix0;
       if (tx > R.tcur && occupied(occ, vid)) {
         const int ia = sel3i(a, R.ix0, R.ix1, R.ix2), sa = sel3i(a, R.st0, R.st1, R.st2);
+        const float fx = (float)(ia + (sa > 0)) * invV;
+        if (R.k > 0 && __float_as_uint(R.tcur) == R.lt && R.ain == R.la && __float_as_uint(R.fin) == R.lf)
+          R.dup |= 1u << R.k;
+        R.lt = __float_as_uint(tx);
+        R.la = a;
+        R.lf = __float_as_uint(fx);
         const float3 pa = seg_point(R.o, R.d, R.tcur, R.ain, R.fin);
-        const float3 pb = seg_point(R.o, R.d, tx, a, (float)(ia + (sa > 0)) * invV);
+        const float3 pb = seg_point(R.o, R.d, tx, a, fx);
         float *w = P + 6 * R.k;
         reinterpret_cast<float2 *>(w)[0] = make_float2(pa.x, pa.y);
         reinterpret_cast<float2 *>(w)[1] = make_float2(pa.z, pb.x);

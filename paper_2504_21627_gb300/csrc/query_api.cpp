@@ -33,7 +33,8 @@ int max_tiles_for(int64_t n, int n_slots) { return (int)(n / kTileM + n_slots + 
 
 size_t lsnif::workspace_bytes(int64_t n, int H, int n_slots, int n_in) {
   const int mt = max_tiles_for(n, n_slots);
-  size_t b = al((size_t)n * H * 12) + al((size_t)n * 8) + al((size_t)n) + al((size_t)n * 2) + al((size_t)n * 4) +
+  size_t b = al((size_t)n * H * 12) + al((size_t)n * 8) + al((size_t)n) + al((size_t)n * 4) + al((size_t)n * 2) +
+             al((size_t)n * 4) +
              3 * al((size_t)n_slots * kBuckets * 4) + al((size_t)mt * 12) + al(64 * 4) +
              al((size_t)(n / kGroupBlock + 2) * 8);
   if (n_in > 0) b += al((size_t)std::min(mt, kChunkTiles) * kTileM * n_in * 4);
@@ -82,6 +83,7 @@ static QueryScratch carve(Workspace *ws, int64_t n, int H, int n_slots, int n_in
   s.pts = c.take<float>((size_t)N * HH * 12);
   s.t01 = c.take<float>((size_t)N * 8);
   s.k = c.take<uint8_t>((size_t)N);
+  s.dup = c.take<uint32_t>((size_t)N * 4);
   s.slot = c.take<int16_t>((size_t)N * 2);
   s.order = c.take<int32_t>((size_t)N * 4);
   s.counts = c.take<int32_t>((size_t)SS * kBuckets * 4);
@@ -147,7 +149,7 @@ int lsnif::run_query(lsnif_ctx *ctx, Workspace *ws, const lsnif_rays *r, lsnif_h
   DevObject rep = sh.rep->d;
   if (precision == LSNIF_BF16_FUSED) {
     rep.umma_bytes = sh.umma_max;
-    if (sh.mixed_fused || !fused_supported(rep) || fused_smem_bytes(rep) > 232448)
+    if (sh.mixed_fused || !fused_supported(rep) || fused_smem_bytes(rep, sh.H) > 232448)
       return fail(LSNIF_ERR_UNSUPPORTED, "query: the fused BF16 path needs F in {2,4}, width 64/128, L <= 16, "
                                          "one shape for all objects and weights that fit shared memory");
   }
@@ -371,7 +373,7 @@ extern "C" int lsnif_mlp(lsnif_ctx *ctx, lsnif_obj h, const float *X, int64_t n,
   if (precision == LSNIF_FP32_PLAIN) {
     e = launch_mlp_plain(ctx->d_objs + o->slot, o->d, X, n, Z, (cudaStream_t)stream);
   } else if (precision == LSNIF_BF16_FUSED) {
-    if (!fused_supported(o->d) || fused_smem_bytes(o->d) > 232448)
+    if (!fused_supported(o->d) || fused_smem_bytes(o->d, o->d.H) > 232448)
       return fail(LSNIF_ERR_UNSUPPORTED, "lsnif_mlp: shape not covered by the tensor-core kernel");
     e = launch_mlp_fused(ctx->d_objs + o->slot, o->d, X, n, Z, ctx->d_err, (cudaStream_t)stream);
   } else {
