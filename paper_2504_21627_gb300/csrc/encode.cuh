@@ -276,13 +276,32 @@ __device__ __forceinline__ uint32_t word4(const uint4 &g, uint32_t j) {
   return (j & 2u) ? hi : lo;
 }
 
+// Four predicated 4-byte loads sharing one predicate.
+__device__ __forceinline__ void ldg4x4_if(uint32_t (&v)[4], const void *a0, const void *a1, const void *a2,
+                                          const void *a3, bool pred) {
+  asm("{\n.reg .pred q;\nsetp.ne.b32 q, %4, 0;\n"
+      "@q ld.global.nc.u32 %0, [%5];\n@q ld.global.nc.u32 %1, [%6];\n"
+      "@q ld.global.nc.u32 %2, [%7];\n@q ld.global.nc.u32 %3, [%8];\n}\n"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3])
+      : "r"((int)pred), "l"(a0), "l"(a1), "l"(a2), "l"(a3));
+}
+
+// The four (y, z) rows of a level always load their 16-byte group of corner
+// x0 (rows of zero weight too: their product is an exact zero, and skipping
+// them saves too few requests to pay for the predicate logic). Corner x1
+// lies in the same group unless cx = 3 mod 4 (the indices differ only in the
+// bits of cx ^ (cx + 1), the same for all four rows); only then, and only
+// when its weight wx is non-zero, it is a second 4-byte load. With wx = 0
+// the x1 word is any word of the group: it enters with weight exactly 0
+// (table values are finite FP16, so the difference v1 - v0 is finite for
+// |v| < 32768).
 template <int NL>
 __device__ __forceinline__ void encode_levels_h2(const __half *__restrict__ tab0, size_t level_stride, uint32_t mask,
                                                  const float3 &p, const float *Ns, __half2 (&out)[NL]) {
   const uint8_t *base = reinterpret_cast<const uint8_t *>(tab0);
   float wx[NL], wy[NL], wz[NL];
   uint32_t ia[NL][4], ib[NL][4];
-  bool pa[NL][4], pb[NL][4];
+  bool far[NL];
 #pragma unroll
   for (int u = 0; u < NL; ++u) {
     const Cell c = lattice_cell(p, Ns[u]);
@@ -291,16 +310,14 @@ __device__ __forceinline__ void encode_levels_h2(const __half *__restrict__ tab0
     wz[u] = c.wz;
     const uint32_t hy0 = c.cy * kPi2, hy1 = hy0 + kPi2;
     const uint32_t hz0 = c.cz * kPi3, hz1 = hz0 + kPi3;
-    const bool ny = c.wy != 0.f, nz = c.wz != 0.f, nx = c.wx != 0.f;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int dy = q & 1, dz = q >> 1;
       const uint32_t b = (dy ? hy1 : hy0) ^ (dz ? hz1 : hz0);
       ia[u][q] = (c.cx ^ b) & mask;
       ib[u][q] = ((c.cx + 1u) ^ b) & mask;
-      pa[u][q] = (dy == 0 || ny) && (dz == 0 || nz);
-      pb[u][q] = pa[u][q] && nx && ((ia[u][q] ^ ib[u][q]) >= 4u);
     }
+    far[u] = ((ia[u][0] ^ ib[u][0]) >= 4u) && c.wx != 0.f;
   }
   uint4 ga[NL][4];
   uint32_t gb[NL][4];
@@ -308,10 +325,9 @@ __device__ __forceinline__ void encode_levels_h2(const __half *__restrict__ tab0
   for (int u = 0; u < NL; ++u) {
     const uint8_t *tl = base + (size_t)u * level_stride;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      ga[u][q] = ldg16_if(tl + (size_t)(ia[u][q] & ~3u) * 4, pa[u][q]);
-      gb[u][q] = ldg4_if(tl + (size_t)ib[u][q] * 4, pb[u][q]);
-    }
+    for (int q = 0; q < 4; ++q) ga[u][q] = __ldg(reinterpret_cast<const uint4 *>(tl + (size_t)(ia[u][q] & ~3u) * 4));
+    ldg4x4_if(gb[u], tl + (size_t)ib[u][0] * 4, tl + (size_t)ib[u][1] * 4, tl + (size_t)ib[u][2] * 4,
+              tl + (size_t)ib[u][3] * 4, far[u]);
   }
 #pragma unroll
   for (int u = 0; u < NL; ++u) {
@@ -322,16 +338,82 @@ __device__ __forceinline__ void encode_levels_h2(const __half *__restrict__ tab0
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const uint32_t w0 = word4(ga[u][q], ia[u][q] & 3u);
-      const uint32_t wg = word4(ga[u][q], ib[u][q] & 3u);
-      const bool same = (ia[u][q] ^ ib[u][q]) < 4u;
-      // x1 corner: its own load, the shared group, or (zero weight) the x0 value
-      const uint32_t w1 = pb[u][q] ? gb[u][q] : (same ? wg : w0);
+      const uint32_t w1 = far[u] ? gb[u][q] : word4(ga[u][q], ib[u][q] & 3u);
       const __half2 v0 = *reinterpret_cast<const __half2 *>(&w0);
       const __half2 v1 = *reinterpret_cast<const __half2 *>(&w1);
       const __half2 lerp = __hfma2(wx2, __hsub2(v1, v0), v0);
       acc = __hfma2(__float2half2_rn(wq[q]), lerp, acc);
     }
     out[u] = acc;
+  }
+}
+
+// The same gather split into issue and interpolation, so that the loads of
+// the next level are in flight while the current level is interpolated
+// (a two-stage software pipeline over the levels of a column group).
+struct LevelLoads {
+  uint4 ga[4];
+  uint32_t gb[4];
+  uint32_t sel;  // row q: bits 4q..4q+1 = low bits of the x0 index, 4q+2..4q+3 of the x1 index
+  float wx, wy, wz;
+  bool far;
+};
+
+__device__ __forceinline__ void level_issue(const uint8_t *tl, uint32_t mask, const float3 &p, float N, LevelLoads &s) {
+  const Cell c = lattice_cell(p, N);
+  s.wx = c.wx;
+  s.wy = c.wy;
+  s.wz = c.wz;
+  const uint32_t hy0 = c.cy * kPi2, hy1 = hy0 + kPi2;
+  const uint32_t hz0 = c.cz * kPi3, hz1 = hz0 + kPi3;
+  uint32_t ia[4], ib[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int dy = q & 1, dz = q >> 1;
+    const uint32_t b = (dy ? hy1 : hy0) ^ (dz ? hz1 : hz0);
+    ia[q] = (c.cx ^ b) & mask;
+    ib[q] = ((c.cx + 1u) ^ b) & mask;
+  }
+  s.far = ((ia[0] ^ ib[0]) >= 4u) && c.wx != 0.f;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) s.ga[q] = __ldg(reinterpret_cast<const uint4 *>(tl + (size_t)(ia[q] & ~3u) * 4));
+  ldg4x4_if(s.gb, tl + (size_t)ib[0] * 4, tl + (size_t)ib[1] * 4, tl + (size_t)ib[2] * 4, tl + (size_t)ib[3] * 4,
+            s.far);
+  uint32_t sel = 0;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) sel |= ((ia[q] & 3u) | ((ib[q] & 3u) << 2)) << (4 * q);
+  s.sel = sel;
+}
+
+__device__ __forceinline__ __half2 level_finish(const LevelLoads &s) {
+  const float w0y = 1.f - s.wy, w0z = 1.f - s.wz;
+  const float wq[4] = {w0y * w0z, s.wy * w0z, w0y * s.wz, s.wy * s.wz};
+  const __half2 wx2 = __float2half2_rn(s.wx);
+  __half2 acc = __float2half2_rn(0.f);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const uint32_t w0 = word4(s.ga[q], (s.sel >> (4 * q)) & 3u);
+    const uint32_t w1 = s.far ? s.gb[q] : word4(s.ga[q], (s.sel >> (4 * q + 2)) & 3u);
+    const __half2 v0 = *reinterpret_cast<const __half2 *>(&w0);
+    const __half2 v1 = *reinterpret_cast<const __half2 *>(&w1);
+    const __half2 lerp = __hfma2(wx2, __hsub2(v1, v0), v0);
+    acc = __hfma2(__float2half2_rn(wq[q]), lerp, acc);
+  }
+  return acc;
+}
+
+// NL consecutive levels (tables level_stride bytes apart) of one point.
+template <int NL>
+__device__ __forceinline__ void encode_levels_h2_pipelined(const __half *__restrict__ tab0, size_t level_stride,
+                                                           uint32_t mask, const float3 &p, const float *Ns,
+                                                           __half2 (&out)[NL]) {
+  const uint8_t *base = reinterpret_cast<const uint8_t *>(tab0);
+  LevelLoads st[2];
+  level_issue(base, mask, p, Ns[0], st[0]);
+#pragma unroll
+  for (int u = 0; u < NL; ++u) {
+    if (u + 1 < NL) level_issue(base + (size_t)(u + 1) * level_stride, mask, p, Ns[u + 1], st[(u + 1) & 1]);
+    out[u] = level_finish(st[u & 1]);
   }
 }
 

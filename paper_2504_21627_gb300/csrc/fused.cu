@@ -87,12 +87,14 @@ __device__ __forceinline__ void mbar_arrive(uint32_t addr) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(addr) : "memory");
 }
 
+// One test of the phase; a thread whose phase is not complete is suspended
+// (it issues nothing) until the phase completes or about 0.1 ms pass.
 __device__ __forceinline__ bool mbar_try(uint32_t addr, uint32_t parity) {
   uint32_t done;
   asm volatile(
-      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\nselp.u32 %0, 1, 0, p;\n}\n"
       : "=r"(done)
-      : "r"(addr), "r"(parity)
+      : "r"(addr), "r"(parity), "r"(100000)
       : "memory");
   return done != 0;
 }
@@ -410,7 +412,6 @@ __global__ void __launch_bounds__((NG + 1 + kEpiWarps) * 32, 1) fused_kernel(Fus
       const int G = (L * F) / 8;  // 16-byte column groups per point
       const int CHK = 2 * L * F;  // columns per chunk
       const uint32_t a_sbo = (uint32_t)(CHK / 8) * 128u;
-      const float invG = 1.f / (float)G;
       const size_t lstride = (size_t)(mask + 1) * F;
       for (int s = 0; s < kmax; ++s) {
         const int c = chunk_ctr + s;
@@ -432,12 +433,15 @@ __global__ void __launch_bounds__((NG + 1 + kEpiWarps) * 32, 1) fused_kernel(Fus
           const int cp = c - nbuf + 1;
           if (cp >= 0 && cp < c) mbar_wait(su32(&b_full[cp % nbuf]), (uint32_t)((cp / nbuf) & 1), abort_flag);
         }
-        // gathers
+        // gathers: the lanes of a warp take consecutive entries (neighbouring
+        // rays) at the same column group, so at coarse levels they share
+        // corners and cache sectors
+        const float inv_g = 1.f / (float)max(ngt, 1);
         for (int b = first_g; b < nb_g; b += NG) {
           const int it = b * 32 + lane;
           if (it < n_gi) {
-            const int t = __float2int_rz(((float)it + 0.5f) * invG);
-            const int g = it - t * G;
+            const int g = __float2int_rz(((float)it + 0.5f) * inv_g);
+            const int t = it - g * ngt;
             const int e = s_list[s * kListStride + t];
             const int r = e & 127, j = e >> 7;
             const int ray = s_ray[tb * kTileM + r];
@@ -453,6 +457,18 @@ __global__ void __launch_bounds__((NG + 1 + kEpiWarps) * 32, 1) fused_kernel(Fus
               const float3 p = make_float3(P[0], P[1], P[2]);
               constexpr int LPG = 8 / F;  // levels per 16-byte group
               float flat[8];
+              if constexpr (F == 2 && NLB == 2) {
+                // all LPG levels of the group, the next level's loads in flight
+                __half2 h[LPG];
+                encode_levels_h2_pipelined<LPG>(reinterpret_cast<const __half *>(tab) + (size_t)(g * LPG) * lstride,
+                                                lstride * 2, mask, p, s_res + g * LPG, h);
+#pragma unroll
+                for (int u = 0; u < LPG; ++u) {
+                  const float2 f2 = __half22float2(h[u]);
+                  flat[u * 2] = f2.x;
+                  flat[u * 2 + 1] = f2.y;
+                }
+              } else
 #pragma unroll
               for (int u0 = 0; u0 < LPG; u0 += NLB) {
                 const int l = g * LPG + u0;
@@ -483,20 +499,21 @@ __global__ void __launch_bounds__((NG + 1 + kEpiWarps) * 32, 1) fused_kernel(Fus
           }
         }
         // copies (entry point = previous chunk's exit point) and zero fills
-        const int n_ci = nct * G;
+        const int n_o = kListStride - ngt;
+        if (nct > 0 && first_o < nb_o) {  // copies read the previous chunk: it must be complete
+          const int cq = c - 1;
+          mbar_wait(su32(&b_full[cq % nbuf]), (uint32_t)((cq / nbuf) & 1), abort_flag);
+        }
+        const float inv_o = 1.f / (float)max(n_o, 1);
         for (int b = first_o; b < nb_o; b += NG) {
-          if (b * 32 < n_ci) {  // this block copies: the previous chunk must be complete
-            const int cq = c - 1;
-            mbar_wait(su32(&b_full[cq % nbuf]), (uint32_t)((cq / nbuf) & 1), abort_flag);
-          }
           const int it = b * 32 + lane;
           if (it < n_oi) {
-            const int t = __float2int_rz(((float)it + 0.5f) * invG);
-            const int g = it - t * G;
+            const int g = __float2int_rz(((float)it + 0.5f) * inv_o);
+            const int t = it - g * n_o;
             const int e = s_list[s * kListStride + ngt + t];
             const int r = e & 127, j = e >> 7;
             uint4 outv = make_uint4(0u, 0u, 0u, 0u);
-            if (it < n_ci) {
+            if (t < nct) {
               const uint8_t *Ap = s_ring + ((c - 1) % nbuf) * ring_stride;
               outv = *reinterpret_cast<const uint4 *>(Ap + core_off(r, G + g, a_sbo));
             }
