@@ -93,8 +93,18 @@ __global__ void __launch_bounds__(256) trace_kernel(QueryLaunch q, int smem_hist
 // Persistent-lane traversal: a warp keeps all 32 lanes busy by handing a new
 // ray to every lane whose ray finished (global ray counter, warp-aggregated).
 // Rays need anywhere from 0 to 3V DDA steps; with one ray per thread a warp
-// runs as long as its longest ray. Same per-ray arithmetic as trace_kernel
-// (same DDA, same outputs), so results are identical.
+// runs as long as its longest ray.
+//
+// Empty-space skipping: every iteration crosses one cell, a voxel, or, when
+// the ray is inside a brick (2^log2B voxels a side) that holds no occupied
+// voxel, the whole brick. Both are the same instruction sequence (exit plane
+// per axis at the cell's granularity, earliest axis with the lowest axis on
+// ties, cross it), so lanes of a warp do not split between a voxel path and
+// a brick path. Crossing times are the same expression of the plane index as
+// in the voxel-by-voxel walk (dda_walk), and when a brick is crossed the
+// other axes first step over every plane the walk would cross before it, so
+// the voxels visited, the boundary points and the shared-point marks are
+// exactly those of the voxel-by-voxel walk (trace_kernel).
 // ---------------------------------------------------------------------------
 struct LaneRay {
   int64_t i;
@@ -102,12 +112,11 @@ struct LaneRay {
   float3 o, d;
   float inv0, inv1, inv2;
   int ix0, ix1, ix2, st0, st1, st2;
-  float tn0, tn1, tn2;
   float tcur, t0, t1;
   int ain;
   float fin;
   int k, cap;
-  bool chk;        // the ray just entered a brick whose mask has not been read
+  bool eb;         // the current brick holds no occupied voxel
   uint32_t dup;    // bit k: entry point of segment k equals the exit of segment k-1
   uint32_t lt, lf; // exit (t, face) of the last segment, as bits
   int la;          // and its axis
@@ -115,6 +124,14 @@ struct LaneRay {
 
 __device__ __forceinline__ float sel3(int a, float x, float y, float z) { return a == 0 ? x : (a == 1 ? y : z); }
 __device__ __forceinline__ int sel3i(int a, int x, int y, int z) { return a == 0 ? x : (a == 1 ? y : z); }
+
+// crossing time of plane index P on one axis (the expression dda_walk uses)
+__device__ __forceinline__ float plane_t(int P, float invV, float o, float inv) { return ((float)P * invV - o) * inv; }
+
+__device__ __forceinline__ bool brick_empty(const DevObject &ob, int lb, int nbk, int x, int y, int z) {
+  const uint32_t bid = ((uint32_t)(z >> lb) * nbk + (uint32_t)(y >> lb)) * nbk + (uint32_t)(x >> lb);
+  return !((__ldg(ob.brick + (bid >> 5)) >> (bid & 31)) & 1u);
+}
 
 __global__ void __launch_bounds__(256) trace_pool_kernel(QueryLaunch q, int smem_hist, int steps_per_round) {
   extern __shared__ int sh_hist[];
@@ -186,12 +203,11 @@ __global__ void __launch_bounds__(256) trace_pool_kernel(QueryLaunch q, int smem
               R.t1 = t1;
               R.cap = ob.H >> 1;
               const int V = ob.V;
-              const float invV = ob.invV;
               const float3 p = make_float3(fmaf(t0, R.d.x, R.o.x), fmaf(t0, R.d.y, R.o.y), fmaf(t0, R.d.z, R.o.z));
               int c[3];
-              float dd[3] = {R.d.x, R.d.y, R.d.z}, oo[3] = {R.o.x, R.o.y, R.o.z}, pp[3] = {p.x, p.y, p.z};
+              float dd[3] = {R.d.x, R.d.y, R.d.z}, pp[3] = {p.x, p.y, p.z};
               int stv[3];
-              float invv[3], tnv[3];
+              float invv[3];
 #pragma unroll
               for (int a = 0; a < 3; ++a) {
                 int cc = (int)floorf(pp[a] * (float)V);
@@ -200,16 +216,14 @@ __global__ void __launch_bounds__(256) trace_pool_kernel(QueryLaunch q, int smem
                 c[a] = cc;
                 stv[a] = dd[a] > 0.f ? 1 : (dd[a] < 0.f ? -1 : 0);
                 invv[a] = dd[a] != 0.f ? 1.f / dd[a] : 0.f;
-                tnv[a] = dd[a] != 0.f ? ((float)(cc + (stv[a] > 0)) * invV - oo[a]) * invv[a] : CUDART_INF_F;
               }
               R.ix0 = c[0]; R.ix1 = c[1]; R.ix2 = c[2];
               R.st0 = stv[0]; R.st1 = stv[1]; R.st2 = stv[2];
               R.inv0 = invv[0]; R.inv1 = invv[1]; R.inv2 = invv[2];
-              R.tn0 = tnv[0]; R.tn1 = tnv[1]; R.tn2 = tnv[2];
               R.tcur = t0;
               R.ain = ea;
               R.fin = ea >= 0 ? (dd[ea] > 0.f ? 0.f : 1.f) : 0.f;
-              R.chk = true;
+              R.eb = brick_empty(ob, ob.log2B, V >> ob.log2B, c[0], c[1], c[2]);
             }
           }
         }
@@ -217,84 +231,29 @@ __global__ void __launch_bounds__(256) trace_pool_kernel(QueryLaunch q, int smem
     }
     if (__all_sync(FULL, R.i < 0 && exhausted)) break;
     if (R.i < 0) continue;
-    // a few DDA steps (or brick jumps) of this lane's ray
+    // a few cells of this lane's ray
     const DevObject &ob = q.objs[R.s];
     const int V = ob.V;
     const float invV = ob.invV;
     const uint32_t *occ = ob.occ;
-    const int lb = ob.log2B, nbk = V >> lb;
+    const int LB = ob.log2B, nbk = V >> LB;
     float *P = q.s.pts + (size_t)R.i * Hs * 3;
     for (int it = 0; it < steps_per_round; ++it) {
       bool done = false;
-      if (R.chk) {
-        // entered a new brick: if it is empty, jump to where the ray leaves it.
-        // The step-by-step traversal visits no occupied voxel in between, and
-        // the state it reaches is rebuilt exactly: crossing times use the same
-        // expression, and the exit axis follows the same lowest-axis tie rule.
-        R.chk = false;
-        const uint32_t bid = ((uint32_t)(R.ix2 >> lb) * nbk + (R.ix1 >> lb)) * nbk + (R.ix0 >> lb);
-        if (!((__ldg(ob.brick + (bid >> 5)) >> (bid & 31)) & 1u)) {
-          const int p0 = R.st0 > 0 ? ((R.ix0 >> lb) + 1) << lb : (R.ix0 >> lb) << lb;
-          const int p1 = R.st1 > 0 ? ((R.ix1 >> lb) + 1) << lb : (R.ix1 >> lb) << lb;
-          const int p2 = R.st2 > 0 ? ((R.ix2 >> lb) + 1) << lb : (R.ix2 >> lb) << lb;
-          const float e0 = R.st0 != 0 ? ((float)p0 * invV - R.o.x) * R.inv0 : CUDART_INF_F;
-          const float e1 = R.st1 != 0 ? ((float)p1 * invV - R.o.y) * R.inv1 : CUDART_INF_F;
-          const float e2 = R.st2 != 0 ? ((float)p2 * invV - R.o.z) * R.inv2 : CUDART_INF_F;
-          const int a = (e0 <= e1) ? (e0 <= e2 ? 0 : 2) : (e1 <= e2 ? 1 : 2);
-          const float tbe = sel3(a, e0, e1, e2);
-          if (tbe >= R.t1) {
-            done = true;
-          } else {
-            // the other axes cross their planes that come before (tbe, a)
-            for (int g = 0; g <= (1 << lb); ++g) {
-              if (a != 0 && (R.tn0 < tbe || (R.tn0 == tbe && 0 < a))) {
-                R.ix0 += R.st0;
-                R.tn0 = ((float)(R.ix0 + (R.st0 > 0)) * invV - R.o.x) * R.inv0;
-              } else break;
-            }
-            for (int g = 0; g <= (1 << lb); ++g) {
-              if (a != 1 && (R.tn1 < tbe || (R.tn1 == tbe && 1 < a))) {
-                R.ix1 += R.st1;
-                R.tn1 = ((float)(R.ix1 + (R.st1 > 0)) * invV - R.o.y) * R.inv1;
-              } else break;
-            }
-            for (int g = 0; g <= (1 << lb); ++g) {
-              if (a != 2 && (R.tn2 < tbe)) {
-                R.ix2 += R.st2;
-                R.tn2 = ((float)(R.ix2 + (R.st2 > 0)) * invV - R.o.z) * R.inv2;
-              } else break;
-            }
-            // then axis a crosses into the next brick
-            const int pa = a == 0 ? p0 : (a == 1 ? p1 : p2);
-            const int sa = sel3i(a, R.st0, R.st1, R.st2);
-            const int ia = sa > 0 ? pa : pa - 1;
-            if (ia < 0 || ia >= V) {
-              done = true;
-            } else {
-              R.tcur = tbe;
-              R.ain = a;
-              R.fin = (float)pa * invV;
-              const float tn = ((float)(ia + (sa > 0)) * invV - comp(R.o, a)) * sel3(a, R.inv0, R.inv1, R.inv2);
-              if (a == 0) { R.ix0 = ia; R.tn0 = tn; }
-              else if (a == 1) { R.ix1 = ia; R.tn1 = tn; }
-              else { R.ix2 = ia; R.tn2 = tn; }
-              R.chk = true;
-            }
-          }
-          if (done) {
-            finish();
-            break;
-          }
-          continue;
-        }
-      }
-      const int a = (R.tn0 <= R.tn1) ? (R.tn0 <= R.tn2 ? 0 : 2) : (R.tn1 <= R.tn2 ? 1 : 2);
-      const float tna = sel3(a, R.tn0, R.tn1, R.tn2);
-      const float tx = fminf(tna, R.t1);
-      const uint32_t vid = ((uint32_t)R.ix2 * V + R.ix1) * V + R.ix0;
-      if (tx > R.tcur && occupied(occ, vid)) {
-        const int ia = sel3i(a, R.ix0, R.ix1, R.ix2), sa = sel3i(a, R.st0, R.st1, R.st2);
-        const float fx = (float)(ia + (sa > 0)) * invV;
+      const int lg = R.eb ? LB : 0;  // cell granularity: voxel or empty brick
+      // exit plane of the cell on each axis, and its crossing time
+      const int P0 = R.st0 > 0 ? ((R.ix0 >> lg) + 1) << lg : (R.ix0 >> lg) << lg;
+      const int P1 = R.st1 > 0 ? ((R.ix1 >> lg) + 1) << lg : (R.ix1 >> lg) << lg;
+      const int P2 = R.st2 > 0 ? ((R.ix2 >> lg) + 1) << lg : (R.ix2 >> lg) << lg;
+      const float e0 = R.st0 != 0 ? plane_t(P0, invV, R.o.x, R.inv0) : CUDART_INF_F;
+      const float e1 = R.st1 != 0 ? plane_t(P1, invV, R.o.y, R.inv1) : CUDART_INF_F;
+      const float e2 = R.st2 != 0 ? plane_t(P2, invV, R.o.z, R.inv2) : CUDART_INF_F;
+      const int a = (e0 <= e1) ? (e0 <= e2 ? 0 : 2) : (e1 <= e2 ? 1 : 2);
+      const float ea = sel3(a, e0, e1, e2);
+      const int Pa = sel3i(a, P0, P1, P2);
+      const float tx = fminf(ea, R.t1);
+      if (!R.eb && tx > R.tcur && occupied(occ, ((uint32_t)R.ix2 * V + R.ix1) * V + R.ix0)) {
+        const float fx = (float)Pa * invV;
         if (R.k > 0 && __float_as_uint(R.tcur) == R.lt && R.ain == R.la && __float_as_uint(R.fin) == R.lf)
           R.dup |= 1u << R.k;
         R.lt = __float_as_uint(tx);
@@ -308,23 +267,43 @@ __global__ void __launch_bounds__(256) trace_pool_kernel(QueryLaunch q, int smem
         reinterpret_cast<float2 *>(w)[2] = make_float2(pb.y, pb.z);
         if (++R.k >= R.cap) done = true;
       }
-      if (!done && tna >= R.t1) done = true;
+      if (!done && ea >= R.t1) done = true;
       if (!done) {
-        int ia = sel3i(a, R.ix0, R.ix1, R.ix2);
+        // when a brick is crossed, the other axes first cross the planes the
+        // voxel walk crosses before (ea, a); for a voxel there are none
+        if (R.eb) {
+          for (int g = 0; g < (1 << LB); ++g) {
+            const int nx = R.ix0 + (R.st0 > 0);
+            if (a != 0 && R.st0 != 0 && plane_t(nx, invV, R.o.x, R.inv0) <= ea) R.ix0 += R.st0;  // 0 < a
+            else break;
+          }
+          for (int g = 0; g < (1 << LB); ++g) {
+            const int ny = R.ix1 + (R.st1 > 0);
+            const float ty = plane_t(ny, invV, R.o.y, R.inv1);
+            if (a != 1 && R.st1 != 0 && (ty < ea || (ty == ea && a == 2))) R.ix1 += R.st1;
+            else break;
+          }
+          for (int g = 0; g < (1 << LB); ++g) {
+            const int nz = R.ix2 + (R.st2 > 0);
+            const float tz = plane_t(nz, invV, R.o.z, R.inv2);
+            if (a != 2 && R.st2 != 0 && tz < ea) R.ix2 += R.st2;
+            else break;
+          }
+        }
+        // then axis a crosses its plane
         const int sa = sel3i(a, R.st0, R.st1, R.st2);
-        ia += sa;
+        const int ia = sa > 0 ? Pa : Pa - 1;
         if (ia < 0 || ia >= V) {
           done = true;
         } else {
-          R.tcur = tna;
+          R.tcur = ea;
           R.ain = a;
-          R.fin = (float)(ia + (sa < 0)) * invV;
-          const float tn = ((float)(ia + (sa > 0)) * invV - comp(R.o, a)) * sel3(a, R.inv0, R.inv1, R.inv2);
-          if (a == 0) { R.ix0 = ia; R.tn0 = tn; }
-          else if (a == 1) { R.ix1 = ia; R.tn1 = tn; }
-          else { R.ix2 = ia; R.tn2 = tn; }
-          // a new brick starts where the stepped index crosses a brick boundary
-          R.chk = (ia & ((1 << lb) - 1)) == (sa > 0 ? 0 : (1 << lb) - 1);
+          R.fin = (float)Pa * invV;
+          if (a == 0) R.ix0 = ia;
+          else if (a == 1) R.ix1 = ia;
+          else R.ix2 = ia;
+          // a brick plane was crossed: look up the new brick
+          if ((Pa & ((1 << LB) - 1)) == 0) R.eb = brick_empty(ob, LB, nbk, R.ix0, R.ix1, R.ix2);
         }
       }
       if (done) {
