@@ -212,8 +212,10 @@ __device__ __forceinline__ uint32_t row_counts(int kk, uint32_t dm, int s) {
 
 // F: features per level; W: hidden width; XROWS: read the network input
 // from global rows instead of gathering it; NG: gather warps; NLB: levels
-// whose corner loads are in flight together per gather item.
-template <int F, int W, bool XROWS, int NG, int NLB>
+// whose corner loads are in flight together per gather item; GS (F = 2):
+// 0 = 16-byte corner groups, 1 = the same with the next level's loads in
+// flight during interpolation, 2 = 8-byte corner pairs (fewer registers).
+template <int F, int W, bool XROWS, int NG, int NLB, int GS>
 __global__ void __launch_bounds__((NG + 1 + kEpiWarps) * 32, 1) fused_kernel(FusedArgs a) {
   constexpr int kGatherThreads = NG * 32;
   constexpr int kMmaWarp = NG;
@@ -457,7 +459,7 @@ __global__ void __launch_bounds__((NG + 1 + kEpiWarps) * 32, 1) fused_kernel(Fus
               const float3 p = make_float3(P[0], P[1], P[2]);
               constexpr int LPG = 8 / F;  // levels per 16-byte group
               float flat[8];
-              if constexpr (F == 2 && NLB == 2) {
+              if constexpr (F == 2 && GS == 1) {
                 // all LPG levels of the group, the next level's loads in flight
                 __half2 h[LPG];
                 encode_levels_h2_pipelined<LPG>(reinterpret_cast<const __half *>(tab) + (size_t)(g * LPG) * lstride,
@@ -474,8 +476,12 @@ __global__ void __launch_bounds__((NG + 1 + kEpiWarps) * 32, 1) fused_kernel(Fus
                 const int l = g * LPG + u0;
                 if constexpr (F == 2) {
                   __half2 h[NLB];
-                  encode_levels_h2<NLB>(reinterpret_cast<const __half *>(tab) + (size_t)l * lstride, lstride * 2,
-                                        mask, p, s_res + l, h);
+                  if constexpr (GS == 2)
+                    encode_levels_h2_pairs<NLB>(reinterpret_cast<const __half *>(tab) + (size_t)l * lstride,
+                                                lstride * 2, mask, p, s_res + l, h);
+                  else
+                    encode_levels_h2<NLB>(reinterpret_cast<const __half *>(tab) + (size_t)l * lstride, lstride * 2,
+                                          mask, p, s_res + l, h);
 #pragma unroll
                   for (int u = 0; u < NLB; ++u) {
                     const float2 f2 = __half22float2(h[u]);
@@ -702,11 +708,11 @@ static int pick_nbuf(const DevObject &h, int list_chunks) {
   return 0;
 }
 
-template <int F, int W, bool XR, int NG, int NLB>
+template <int F, int W, bool XR, int NG, int NLB, int GS>
 static cudaError_t launch_one(const FusedArgs &a, size_t smem, cudaStream_t st) {
   static int attr = 0;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(fused_kernel<F, W, XR, NG, NLB>,
+    cudaError_t e = cudaFuncSetAttribute(fused_kernel<F, W, XR, NG, NLB, GS>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
     if (e != cudaSuccess) return e;
     attr = 1;
@@ -714,29 +720,30 @@ static cudaError_t launch_one(const FusedArgs &a, size_t smem, cudaStream_t st) 
   int sms = 0, dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  fused_kernel<F, W, XR, NG, NLB><<<sms, (NG + 1 + kEpiWarps) * 32, smem, st>>>(a);
+  fused_kernel<F, W, XR, NG, NLB, GS><<<sms, (NG + 1 + kEpiWarps) * 32, smem, st>>>(a);
   return cudaGetLastError();
 }
 
-// Shapes the autotuner chooses between: gather warps per CTA and levels of
-// corner loads in flight per gather item.
+// Shapes the autotuner chooses between: gather warps per CTA (with the MMA
+// warp and 4 epilogue warps: 4, 5 or 6 warps per SM sub-partition, so at
+// most 128, 96 or 80 registers per thread), levels of corner loads in flight
+// per gather item, and the F = 2 gather style.
 struct Variant {
-  int gather_warps, levels;
+  int gather_warps, levels, style;
 };
-// 11 or 15 gather warps + 5 others: 4 or 5 warps per SM sub-partition
-// (at most 128 or 96 registers per thread)
-static const Variant kVariants[] = {{11, 1}, {11, 2}, {11, 4}, {15, 1}, {15, 2}};
+static const Variant kVariants[] = {{11, 2, 1}, {15, 1, 0}, {19, 1, 0}, {19, 1, 2}, {23, 1, 2}};
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
 template <int F, int W, bool XR>
 static cudaError_t dispatch_variant(const FusedArgs &a, int v, size_t smem, cudaStream_t st) {
   constexpr int LPG = 8 / F;
+  constexpr int NL2 = 2 < LPG ? 2 : LPG;
   switch (v) {
-    case 0: return launch_one<F, W, XR, 11, 1>(a, smem, st);
-    case 1: return launch_one<F, W, XR, 11, (2 < LPG ? 2 : LPG)>(a, smem, st);
-    case 2: return launch_one<F, W, XR, 11, LPG>(a, smem, st);
-    case 3: return launch_one<F, W, XR, 15, 1>(a, smem, st);
-    case 4: return launch_one<F, W, XR, 15, (2 < LPG ? 2 : LPG)>(a, smem, st);
+    case 0: return launch_one<F, W, XR, 11, NL2, F == 2 ? 1 : 0>(a, smem, st);
+    case 1: return launch_one<F, W, XR, 15, 1, 0>(a, smem, st);
+    case 2: return launch_one<F, W, XR, 19, 1, 0>(a, smem, st);
+    case 3: return launch_one<F, W, XR, 19, 1, F == 2 ? 2 : 0>(a, smem, st);
+    case 4: return launch_one<F, W, XR, 23, 1, F == 2 ? 2 : 0>(a, smem, st);
     default: return cudaErrorInvalidValue;
   }
 }
