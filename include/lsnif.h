@@ -311,22 +311,24 @@ LSNIF_API int lsnif_mlp(lsnif_ctx *ctx, lsnif_obj obj, const float *X, int64_t n
  * legacy default stream, and profiled queries, run without graphs. */
 LSNIF_API int lsnif_set_graph_mode(lsnif_ctx *ctx, int on);
 
-/* ---- autotuning of the fused kernel's tile shape ------------------------ */
+/* ---- autotuning of the fused kernel's shape ----------------------------- */
 
-/* Number of fused-kernel variants (threads per CTA x corner-load levels in
- * flight per gather item). */
+/* Number of fused-kernel variants (gather threads per CTA x corner-load
+ * levels in flight per gather item x gather style). */
 LSNIF_API int lsnif_variant_count(void);
 
-/* Shape of variant v: *threads per CTA, *levels of corner loads in flight.
- * Errors: INVALID_ARG for v out of range. */
+/* Shape of variant v: *threads = gather threads per CTA (the CTA also has
+ * one MMA warp and four epilogue warps), *levels = levels of corner loads in
+ * flight per gather item. Errors: INVALID_ARG for v out of range. */
 LSNIF_API int lsnif_variant_shape(int v, int *threads, int *levels);
 
 /* Use variant v for every later BF16 query of the context. */
 LSNIF_API int lsnif_set_variant(lsnif_ctx *ctx, int v);
 
-/* Traversal kernel for later queries: 0 = one ray per thread, 1 = persistent
- * lanes (a lane whose ray finished takes the next ray from a global counter).
- * Both compute identical results. */
+/* Traversal kernel for later queries: 0 = one ray per thread, voxel by
+ * voxel; 1 = persistent lanes (a lane whose ray finished takes the next ray
+ * from a global counter) that cross bricks without occupied voxels in one
+ * step. Both compute identical results. */
 LSNIF_API int lsnif_set_trace_mode(lsnif_ctx *ctx, int mode);
 
 /* Time every fused-kernel variant on `rays` (DEVICE buffers, `reps` BF16
