@@ -359,8 +359,10 @@ __device__ __forceinline__ void encode_levels_h2_pairs(const __half *__restrict_
                                                        __half2 (&out)[NL]) {
   const uint8_t *base = reinterpret_cast<const uint8_t *>(tab0);
   float wx[NL], wy[NL], wz[NL];
-  uint32_t ia[NL][4], ib[NL][4];
+  uint32_t lo[NL];  // bit q: corner x0 of row q is the odd word of its pair
   bool odd[NL];
+  uint2 ga[NL][4];
+  uint32_t gb[NL][4];
 #pragma unroll
   for (int u = 0; u < NL; ++u) {
     const Cell c = lattice_cell(p, Ns[u]);
@@ -369,24 +371,22 @@ __device__ __forceinline__ void encode_levels_h2_pairs(const __half *__restrict_
     wz[u] = c.wz;
     const uint32_t hy0 = c.cy * kPi2, hy1 = hy0 + kPi2;
     const uint32_t hz0 = c.cz * kPi3, hz1 = hz0 + kPi3;
+    const uint8_t *tl = base + (size_t)u * level_stride;
+    odd[u] = (c.cx & 1u) && c.wx != 0.f;
+    const void *pb[4];
+    uint32_t bits = 0;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int dy = q & 1, dz = q >> 1;
       const uint32_t b = (dy ? hy1 : hy0) ^ (dz ? hz1 : hz0);
-      ia[u][q] = (c.cx ^ b) & mask;
-      ib[u][q] = ((c.cx + 1u) ^ b) & mask;
+      const uint32_t ia = (c.cx ^ b) & mask;
+      const uint32_t ib = ((c.cx + 1u) ^ b) & mask;
+      bits |= (ia & 1u) << q;
+      ga[u][q] = __ldg(reinterpret_cast<const uint2 *>(tl + (size_t)(ia & ~1u) * 4));
+      pb[q] = tl + (size_t)ib * 4;
     }
-    odd[u] = (c.cx & 1u) && c.wx != 0.f;
-  }
-  uint2 ga[NL][4];
-  uint32_t gb[NL][4];
-#pragma unroll
-  for (int u = 0; u < NL; ++u) {
-    const uint8_t *tl = base + (size_t)u * level_stride;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) ga[u][q] = __ldg(reinterpret_cast<const uint2 *>(tl + (size_t)(ia[u][q] & ~1u) * 4));
-    ldg4x4_if(gb[u], tl + (size_t)ib[u][0] * 4, tl + (size_t)ib[u][1] * 4, tl + (size_t)ib[u][2] * 4,
-              tl + (size_t)ib[u][3] * 4, odd[u]);
+    lo[u] = bits;
+    ldg4x4_if(gb[u], pb[0], pb[1], pb[2], pb[3], odd[u]);
   }
 #pragma unroll
   for (int u = 0; u < NL; ++u) {
@@ -396,10 +396,11 @@ __device__ __forceinline__ void encode_levels_h2_pairs(const __half *__restrict_
     __half2 acc = __float2half2_rn(0.f);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const uint32_t w0 = (ia[u][q] & 1u) ? ga[u][q].y : ga[u][q].x;
+      const bool hi = (lo[u] >> q) & 1u;
+      const uint32_t w0 = hi ? ga[u][q].y : ga[u][q].x;
       // x1: the other word of the pair (even cx), its own load (odd cx), or,
       // with wx = 0, a word of weight exactly 0
-      const uint32_t w1 = odd[u] ? gb[u][q] : ((ia[u][q] & 1u) ? ga[u][q].x : ga[u][q].y);
+      const uint32_t w1 = odd[u] ? gb[u][q] : (hi ? ga[u][q].x : ga[u][q].y);
       const __half2 v0 = *reinterpret_cast<const __half2 *>(&w0);
       const __half2 v1 = *reinterpret_cast<const __half2 *>(&w1);
       const __half2 lerp = __hfma2(wx2, __hsub2(v1, v0), v0);

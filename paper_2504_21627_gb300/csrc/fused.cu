@@ -189,8 +189,8 @@ __host__ __device__ inline Layout make_layout(uint32_t blob_bytes, int F, int W,
   o.ray = lay_take(off, 2 * kTileM * 4, 16);
   o.t0 = lay_take(off, 2 * kTileM * 4, 16);
   o.t1 = lay_take(off, 2 * kTileM * 4, 16);
-  o.list = lay_take(off, (uint32_t)list_chunks * kListStride * 2u, 16);
-  o.wsum = lay_take(off, (uint32_t)list_chunks * 4u * 4u, 16);
+  o.list = lay_take(off, 2u * (uint32_t)list_chunks * kListStride * 2u, 16);  // two tiles
+  o.wsum = lay_take(off, 2u * (uint32_t)list_chunks * 4u * 4u, 16);
   o.info = lay_take(off, 2 * sizeof(TileInfo), 16);
   o.bars = lay_take(off, 8 * kNumBars, 8);
   o.tmem = lay_take(off, 16, 16);
@@ -210,13 +210,341 @@ __device__ __forceinline__ uint32_t row_counts(int kk, uint32_t dm, int s) {
 
 }  // namespace
 
+// The MMA warp's work (see epilogue_role for why it is a function).
+template <int F, int W, bool XROWS, int NG>
+__device__ __noinline__ void mma_role(const FusedArgs *ap, uint8_t *base, uint32_t tmem) {
+  const FusedArgs &a = *ap;
+  const int lane = threadIdx.x & 31;
+  const DevObject *objs = a.q.objs;
+  const int nbuf = a.nbuf;
+  const Layout lay = make_layout(a.smem_blob, F, W, nbuf, a.list_chunks);
+  uint8_t *s_blob = base + lay.blob;
+  uint8_t *s_ring = base + lay.ring;
+  TileInfo *s_info = reinterpret_cast<TileInfo *>(base + lay.info);
+  uint64_t *bars = reinterpret_cast<uint64_t *>(base + lay.bars);
+  uint64_t *b_full = bars, *b_empty = bars + kNBufMax, *b_ready = bars + 2 * kNBufMax;
+  uint64_t *b_accf = b_ready + 2, *b_acce = b_ready + 4, *b_fin = b_ready + 7;
+  int32_t *s_misc = reinterpret_cast<int32_t *>(base + lay.misc);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(s_misc + 4);
+  const uint32_t ring_stride = lay.ring_stride;
+  {
+    // =================== MMA warp ===================
+    int chunk_ctr = 0;
+    const uint32_t idesc0 = idesc_bf16(W);
+    for (int i = 0;; ++i) {
+      const int tb = i & 1;
+      if (!mbar_wait(su32(&b_ready[tb]), (uint32_t)((i >> 1) & 1), abort_flag)) break;
+      const TileInfo ti = s_info[tb];
+      if (ti.stop) break;
+      const DevObject &ob = objs[ti.slot];
+      const int CHK = 2 * ob.L * F;
+      const uint32_t a_sbo = (uint32_t)(CHK / 8) * 128u, w0_sbo = (uint32_t)(ob.n_in / 8) * 128u;
+      if (i >= 2 && !mbar_wait(su32(&b_acce[tb]), (uint32_t)(((i - 2) >> 1) & 1), abort_flag)) break;
+      tc_after();
+      const uint32_t dacc = tmem + (uint32_t)(tb * W);
+      bool ok = true;
+      for (int s = 0; s < ti.kmax; ++s) {
+        const int c = chunk_ctr + s;
+        const int buf = c % nbuf;
+        if (!mbar_wait(su32(&b_full[buf]), (uint32_t)((c / nbuf) & 1), abort_flag)) {
+          ok = false;
+          break;
+        }
+        tc_after();
+        if (lane == 0) {
+          const uint32_t a0 = su32(s_ring + buf * ring_stride), b0 = su32(s_blob);
+          for (int ks = 0; ks < CHK / 16; ++ks) {
+            const uint64_t ad = umma_desc(a0 + ks * 256, 128, a_sbo);
+            const uint64_t bd = umma_desc(b0 + (uint32_t)((s * CHK) / 8 + 2 * ks) * 128u, 128, w0_sbo);
+            mma_bf16(dacc, ad, bd, idesc0, (s > 0 || ks > 0) ? 1u : 0u);
+          }
+          mma_commit(su32(&b_empty[buf]));
+        }
+        __syncwarp();
+      }
+      if (!ok) break;
+      chunk_ctr += ti.kmax;
+      if (lane == 0) mma_commit(su32(&b_accf[tb]));
+      __syncwarp();
+    }
+    if (lane == 0) {
+      mma_commit(su32(&b_fin[0]));
+      if (!mbar_wait_teardown(su32(&b_fin[0]), 0u)) *abort_flag = 1;
+    }
+    __syncwarp();
+    }
+}
+
+// The epilogue warps' work, compiled as its own function so that its
+// registers do not add to the gather warps' allocation.
+template <int F, int W, bool XROWS, int NG>
+__device__ __noinline__ void epilogue_role(const FusedArgs *ap, uint8_t *base, uint32_t tmem) {
+  const FusedArgs &a = *ap;
+  constexpr int kEpiWarp0 = NG + 1;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const QueryLaunch &q = a.q;
+  const DevObject *objs = q.objs;
+  const Layout lay = make_layout(a.smem_blob, F, W, a.nbuf, a.list_chunks);
+  uint8_t *s_blob = base + lay.blob;
+  uint8_t *s_act = base + lay.act;
+  int32_t *s_ray = reinterpret_cast<int32_t *>(base + lay.ray);
+  float *s_t0 = reinterpret_cast<float *>(base + lay.t0);
+  float *s_t1 = reinterpret_cast<float *>(base + lay.t1);
+  uint16_t *s_list = reinterpret_cast<uint16_t *>(base + lay.list);
+  uint32_t *s_wsum = reinterpret_cast<uint32_t *>(base + lay.wsum);
+  TileInfo *s_info = reinterpret_cast<TileInfo *>(base + lay.info);
+  uint64_t *bars = reinterpret_cast<uint64_t *>(base + lay.bars);
+  uint64_t *b_ready = bars + 2 * kNBufMax;
+  uint64_t *b_accf = b_ready + 2, *b_acce = b_ready + 4, *b_layer = b_ready + 6, *b_fin = b_ready + 7;
+  int32_t *s_misc = reinterpret_cast<int32_t *>(base + lay.misc);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(s_misc + 4);
+  float *s_res = reinterpret_cast<float *>(base + lay.res);
+  const int64_t n_tiles = XROWS ? (a.xrows + kTileM - 1) / kTileM : (int64_t)q.s.meta[1];
+  {
+    // =================== epilogue warps ===================
+    // Besides the layers after the first, these four warps set up every
+    // tile (fetch, rows, work lists, weights on an object change) one tile
+    // ahead, so the gather warps never stop between tiles.
+    constexpr int kEpiThreads = kEpiWarps * 32;
+    const int etid = tid - kEpiWarp0 * 32;  // 0..127: the row a setup thread handles
+    const int ew = etid >> 5;
+    const int quarter = warp & 3;           // the TMEM lane quarter this warp may access
+    const int r = quarter * 32 + lane;      // the row (ray) of the layers
+    const uint32_t act_sbo = (uint32_t)(W / 8) * 128u;
+    int layer_ctr = 0;
+    int su_slot = -1;  // object whose weights are in shared memory
+
+    // next tile index (INT_MAX once aborted), uniform over the epilogue warps
+    auto fetch = [&]() -> int {
+      named_sync(2, kEpiThreads);
+      if (etid == 0) s_misc[0] = *abort_flag ? INT_MAX : atomicAdd(q.s.meta + 3, 1);
+      named_sync(2, kEpiThreads);
+      return s_misc[0];
+    };
+    auto slot_of_tile = [&](int tile) -> int { return XROWS ? 0 : q.s.tiles[3 * tile + 0]; };
+    // Set tile `tile` up as the j-th tile (slot j & 1). The slot's previous
+    // tile (j - 2) is finished by every role; a weight reload is only asked
+    // for once the previous tile's layers are done.
+    auto setup = [&](int j, int tile) {
+      const int sb = j & 1;
+      if ((int64_t)tile >= n_tiles) {
+        if (etid == 0) {
+          s_info[sb].stop = 1;
+          mbar_arrive(su32(&b_ready[sb]));
+        }
+        return;
+      }
+      int slot, start, cnt;
+      if (XROWS) {
+        slot = 0;
+        start = tile * kTileM;
+        cnt = (int)min((int64_t)kTileM, a.xrows - (int64_t)tile * kTileM);
+      } else {
+        slot = q.s.tiles[3 * tile + 0];
+        start = q.s.tiles[3 * tile + 1];
+        cnt = q.s.tiles[3 * tile + 2];
+      }
+      const DevObject &ob = objs[slot];
+      if (slot != su_slot) {
+        const uint4 *src = reinterpret_cast<const uint4 *>(ob.umma);
+        uint4 *dst = reinterpret_cast<uint4 *>(s_blob);
+        const int nvec = (int)(ob.umma_bytes / 16);
+        for (int k = etid; k < nvec; k += kEpiThreads) dst[k] = __ldg(src + k);
+        if (etid < LSNIF_MAX_LEVELS) s_res[etid] = (float)ob.res[etid];
+        fence_async_smem();
+        su_slot = slot;
+      }
+      if (etid == 0) s_misc[1] = 0;
+      named_sync(2, kEpiThreads);
+      // rows
+      int my_kk = 0;
+      uint32_t my_dm = 0u;
+      {
+        int ray = -1;
+        float t0v = 0.f, t1v = 0.f;
+        if (etid < cnt) {
+          if (XROWS) {
+            ray = start + etid;
+            my_kk = ob.H / 2;
+          } else {
+            ray = q.s.order[start + etid];
+            my_kk = q.s.k[ray];
+            my_dm = q.s.dup[ray];
+            const float2 tt = reinterpret_cast<const float2 *>(q.s.t01)[ray];
+            t0v = tt.x;
+            t1v = tt.y;
+          }
+        }
+        s_ray[sb * kTileM + etid] = ray;
+        s_t0[sb * kTileM + etid] = t0v;
+        s_t1[sb * kTileM + etid] = t1v;
+        const int wm = __reduce_max_sync(0xffffffffu, my_kk);
+        if (lane == 0) atomicMax(&s_misc[1], wm);
+      }
+      named_sync(2, kEpiThreads);
+      const int kmax = s_misc[1];
+      // work lists: per chunk, [gathers | copies | zero fills]
+      uint16_t *lst = s_list + (size_t)sb * a.list_chunks * kListStride;
+      uint32_t *ws = s_wsum + (size_t)sb * a.list_chunks * 4;
+      for (int s = 0; s < kmax; ++s) {
+        const uint32_t tot = __reduce_add_sync(0xffffffffu, row_counts(my_kk, my_dm, s));
+        if (lane == 0) ws[s * 4 + ew] = tot;
+      }
+      named_sync(2, kEpiThreads);
+      for (int s = 0; s < kmax; ++s) {
+        const uint32_t v = row_counts(my_kk, my_dm, s);
+        uint32_t incl = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += y;
+        }
+        uint32_t woff = 0, all = 0;
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+          const uint32_t x = ws[s * 4 + w];
+          all += x;
+          woff += w < ew ? x : 0u;
+        }
+        const uint32_t pos = incl - v + woff;
+        const int ngt = (int)(all & 1023u), nct = (int)((all >> 10) & 1023u);
+        uint16_t *Ls = lst + s * kListStride;
+        if (v & 1023u) {
+          const int pg = (int)(pos & 1023u);
+          if (v & (1023u << 10)) {  // entry point shared with the previous exit
+            Ls[pg] = (uint16_t)(etid | 128);
+            Ls[ngt + (int)((pos >> 10) & 1023u)] = (uint16_t)etid;
+          } else {
+            Ls[pg] = (uint16_t)etid;
+            Ls[pg + 1] = (uint16_t)(etid | 128);
+          }
+        } else {
+          const int pz = ngt + nct + (int)((pos >> 20) & 1023u);
+          Ls[pz] = (uint16_t)etid;
+          Ls[pz + 1] = (uint16_t)(etid | 128);
+        }
+      }
+      named_sync(2, kEpiThreads);
+      if (etid == 0) {
+        s_info[sb].kmax = kmax;
+        s_info[sb].slot = slot;
+        s_info[sb].stop = 0;
+        mbar_arrive(su32(&b_ready[sb]));
+      }
+    };
+
+    int stop_at = INT_MAX;
+    {
+      const int t0i = fetch();
+      setup(0, t0i);
+      if ((int64_t)t0i >= n_tiles) stop_at = 0;
+    }
+    for (int i = 0; i < stop_at; ++i) {
+      const int tb = i & 1;
+      // set up tile i+1 now, unless it needs other weights: then after the
+      // layers of tile i, which still read the current ones
+      const int tn = fetch();
+      const bool last = (int64_t)tn >= n_tiles;
+      const bool deferred = !last && slot_of_tile(tn) != su_slot;
+      if (!deferred) setup(i + 1, tn);
+      if (last) stop_at = i + 1;
+
+      // ---- layers after the first, decode ----
+      if (etid == 0) s_misc[2] = mbar_wait(su32(&b_accf[tb]), (uint32_t)((i >> 1) & 1), abort_flag) ? 0 : 1;
+      named_sync(2, kEpiThreads);
+      if (!s_misc[2]) {
+        tc_after();
+        const TileInfo ti = s_info[tb];
+        const DevObject &ob = objs[ti.slot];
+        const int n_hidden = ob.n_hidden, n_out = ob.n_out, n_out_pad = ob.n_out_pad, n_mat = ob.n_mat,
+                  act = ob.act;
+        const float *bias = reinterpret_cast<const float *>(s_blob + ob.umma_bias_off);
+        uint32_t wl_off = (uint32_t)W * ob.n_in * 2u;  // byte offset of W1 in the blob
+        const uint32_t dacc = tmem + (uint32_t)(tb * W);
+        const uint32_t trow = dacc + ((uint32_t)(quarter * 32) << 16);
+        for (int layer = 0; layer <= n_hidden; ++layer) {
+          const bool out_layer = layer == n_hidden;
+          const float *bl = bias + layer * W;
+          if (!out_layer) {
+#pragma unroll 1
+            for (int c0 = 0; c0 < W; c0 += 16) {
+              uint32_t v[16];
+              TMEM_LD16(trow + c0, (&v[0]));
+              tmem_wait_ld();
+#pragma unroll
+              for (int c = 0; c < 16; c += 8) {
+                float h8[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) h8[u] = act_fn(__uint_as_float(v[c + u]) + bl[c0 + c + u], act);
+                const uint4 pk = make_uint4(pack_bf16(h8[0], h8[1]), pack_bf16(h8[2], h8[3]),
+                                            pack_bf16(h8[4], h8[5]), pack_bf16(h8[6], h8[7]));
+                *reinterpret_cast<uint4 *>(s_act + core_off(r, (c0 + c) / 8, act_sbo)) = pk;
+              }
+            }
+            fence_async_smem();
+            tc_before();
+            named_sync(2, kEpiThreads);
+            const int N = (layer + 1 < n_hidden) ? W : n_out_pad;
+            if (etid == 0) {
+              tc_after();
+              const uint32_t a0 = su32(s_act), b0 = su32(s_blob) + wl_off;
+              const uint32_t idesc = idesc_bf16(N);
+              for (int ks = 0; ks < W / 16; ++ks) {
+                const uint64_t ad = umma_desc(a0 + ks * 256, 128, act_sbo);
+                const uint64_t bd = umma_desc(b0 + ks * 256, 128, act_sbo);
+                mma_bf16(dacc, ad, bd, idesc, ks > 0 ? 1u : 0u);
+              }
+              mma_commit(su32(b_layer));
+              mbar_wait(su32(b_layer), (uint32_t)(layer_ctr & 1), abort_flag);
+            }
+            ++layer_ctr;
+            named_sync(2, kEpiThreads);
+            tc_after();
+            wl_off += (uint32_t)N * W * 2u;
+          } else {
+            // logits 16 columns at a time into a per-thread array, then decode
+            float z[64];
+#pragma unroll 1
+            for (int c0 = 0; c0 < n_out_pad; c0 += 16) {
+              uint32_t v[16];
+              TMEM_LD16(trow + c0, (&v[0]));
+              tmem_wait_ld();
+#pragma unroll
+              for (int u = 0; u < 16; ++u) z[c0 + u] = __uint_as_float(v[u]) + bl[c0 + u];
+            }
+            const int32_t ray = s_ray[tb * kTileM + r];
+            if (ray >= 0 && !*abort_flag) {
+              if (XROWS) {
+                for (int j = 0; j < n_out; ++j) a.Z[(int64_t)ray * n_out + j] = z[j];
+              } else {
+                decode_store(q.hits, ray, z, n_out, n_mat, s_t0[tb * kTileM + r], s_t1[tb * kTileM + r],
+                             q.rays.tmin[ray], q.rays.tmax[ray]);
+              }
+            }
+          }
+        }
+      }
+      tc_before();
+      mbar_arrive(su32(&b_acce[tb]));
+      if (deferred) {
+        named_sync(2, kEpiThreads);  // every thread is done with the old weights
+        setup(i + 1, tn);
+      }
+    }
+    if (etid == 0) {
+      mma_commit(su32(&b_fin[1]));
+      if (!mbar_wait_teardown(su32(&b_fin[1]), 0u)) *abort_flag = 1;
+    }
+    }
+}
+
 // F: features per level; W: hidden width; XROWS: read the network input
 // from global rows instead of gathering it; NG: gather warps; NLB: levels
 // whose corner loads are in flight together per gather item; GS (F = 2):
 // 0 = 16-byte corner groups, 1 = the same with the next level's loads in
 // flight during interpolation, 2 = 8-byte corner pairs (fewer registers).
 template <int F, int W, bool XROWS, int NG, int NLB, int GS>
-__global__ void __launch_bounds__((NG + 1 + kEpiWarps) * 32, 1) fused_kernel(FusedArgs a) {
+__global__ void __launch_bounds__((NG + 1 + kEpiWarps) * 32, 1) fused_kernel(const __grid_constant__ FusedArgs a) {
   constexpr int kGatherThreads = NG * 32;
   constexpr int kMmaWarp = NG;
   constexpr int kEpiWarp0 = NG + 1;
@@ -277,138 +605,28 @@ __global__ void __launch_bounds__((NG + 1 + kEpiWarps) * 32, 1) fused_kernel(Fus
   if (warp < NG) {
     // =================== gather warps ===================
     int cur_slot = -1;
-    int L = 0, n_in = 0, H = 0;
+    int L = 0, n_in = 0;
     uint32_t mask = 0;
     const uint16_t *tab = nullptr;
     int chunk_ctr = 0;
     int rot_g = 0, rot_o = 0;  // round-robin origin of the gather / other blocks
     for (int i = 0;; ++i) {
       const int tb = i & 1;
-      // the tile-info slot tb is free once the epilogue of tile i-2 is done
-      if (tid == 0) {
-        const bool ok = i < 2 || mbar_wait(su32(&b_acce[tb]), (uint32_t)(((i - 2) >> 1) & 1), abort_flag);
-        int t = INT_MAX;
-        if (ok && !*abort_flag) t = atomicAdd(q.s.meta + 3, 1);
-        s_misc[0] = t;
-        s_misc[1] = 0;
-      }
-      named_sync(1, kGatherThreads);
-      const int tile = s_misc[0];
-      if ((int64_t)tile >= n_tiles) {
-        if (tid == 0) {
-          s_info[tb].stop = 1;
-          mbar_arrive(su32(&b_ready[tb]));
-        }
-        break;
-      }
-      int slot, start, cnt;
-      if (XROWS) {
-        slot = 0;
-        start = tile * kTileM;
-        cnt = (int)min((int64_t)kTileM, a.xrows - (int64_t)tile * kTileM);
-      } else {
-        slot = q.s.tiles[3 * tile + 0];
-        start = q.s.tiles[3 * tile + 1];
-        cnt = q.s.tiles[3 * tile + 2];
-      }
-      // ---- (re)load the object's weights once the previous tile is done with them ----
-      if (slot != cur_slot) {
-        if (tid == 0 && i >= 1) mbar_wait(su32(&b_acce[(i - 1) & 1]), (uint32_t)(((i - 1) >> 1) & 1), abort_flag);
-        named_sync(1, kGatherThreads);
-        const DevObject &ob = objs[slot];
+      // the epilogue warps set the tile up: rows, work lists, weights
+      if (!mbar_wait(su32(&b_ready[tb]), (uint32_t)((i >> 1) & 1), abort_flag)) break;
+      const TileInfo ti = s_info[tb];
+      if (ti.stop) break;
+      const int kmax = ti.kmax;
+      if (ti.slot != cur_slot) {
+        const DevObject &ob = objs[ti.slot];
         L = ob.L;
         n_in = ob.n_in;
-        H = ob.H;
         mask = ob.mask;
         tab = ob.tab16;
-        const uint4 *src = reinterpret_cast<const uint4 *>(ob.umma);
-        uint4 *dst = reinterpret_cast<uint4 *>(s_blob);
-        const int nvec = (int)(ob.umma_bytes / 16);
-        for (int k = tid; k < nvec; k += kGatherThreads) dst[k] = __ldg(src + k);
-        if (tid < LSNIF_MAX_LEVELS) s_res[tid] = (float)ob.res[tid];
-        fence_async_smem();
-        named_sync(1, kGatherThreads);
-        cur_slot = slot;
+        cur_slot = ti.slot;
       }
-      // ---- rows of the tile ----
-      int my_kk = 0;
-      uint32_t my_dm = 0u;
-      if (tid < kTileM) {
-        const int r = tid;
-        int ray = -1;
-        float t0v = 0.f, t1v = 0.f;
-        if (r < cnt) {
-          if (XROWS) {
-            ray = start + r;
-            my_kk = H / 2;
-          } else {
-            ray = q.s.order[start + r];
-            my_kk = q.s.k[ray];
-            my_dm = q.s.dup[ray];
-            const float2 tt = reinterpret_cast<const float2 *>(q.s.t01)[ray];
-            t0v = tt.x;
-            t1v = tt.y;
-          }
-        }
-        s_ray[tb * kTileM + r] = ray;
-        s_t0[tb * kTileM + r] = t0v;
-        s_t1[tb * kTileM + r] = t1v;
-        const int wm = __reduce_max_sync(0xffffffffu, my_kk);
-        if (lane == 0) atomicMax(&s_misc[1], wm);
-      }
-      named_sync(1, kGatherThreads);
-      const int kmax = s_misc[1];
-      // ---- work lists: per chunk, [gathers | copies | zero fills] ----
-      if (tid < kTileM) {
-        for (int s = 0; s < kmax; ++s) {
-          const uint32_t tot = __reduce_add_sync(0xffffffffu, row_counts(my_kk, my_dm, s));
-          if (lane == 0) s_wsum[s * 4 + warp] = tot;
-        }
-      }
-      named_sync(1, kGatherThreads);
-      if (tid < kTileM) {
-        const int r = tid;
-        for (int s = 0; s < kmax; ++s) {
-          const uint32_t v = row_counts(my_kk, my_dm, s);
-          uint32_t incl = v;
-#pragma unroll
-          for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += y;
-          }
-          uint32_t woff = 0, all = 0;
-#pragma unroll
-          for (int w = 0; w < 4; ++w) {
-            const uint32_t x = s_wsum[s * 4 + w];
-            all += x;
-            woff += w < warp ? x : 0u;
-          }
-          const uint32_t pos = incl - v + woff;
-          const int ngt = (int)(all & 1023u), nct = (int)((all >> 10) & 1023u);
-          uint16_t *Ls = s_list + s * kListStride;
-          if (v & 1023u) {
-            const int pg = (int)(pos & 1023u);
-            if (v & (1023u << 10)) {  // entry point shared with the previous exit
-              Ls[pg] = (uint16_t)(r | 128);
-              Ls[ngt + (int)((pos >> 10) & 1023u)] = (uint16_t)r;
-            } else {
-              Ls[pg] = (uint16_t)r;
-              Ls[pg + 1] = (uint16_t)(r | 128);
-            }
-          } else {
-            const int pz = ngt + nct + (int)((pos >> 20) & 1023u);
-            Ls[pz] = (uint16_t)r;
-            Ls[pz + 1] = (uint16_t)(r | 128);
-          }
-        }
-      }
-      named_sync(1, kGatherThreads);
-      if (tid == 0) {
-        s_info[tb].kmax = kmax;
-        s_info[tb].slot = slot;
-        s_info[tb].stop = 0;
-        mbar_arrive(su32(&b_ready[tb]));
-      }
+      const uint16_t *s_lst = s_list + (size_t)tb * a.list_chunks * kListStride;
+      const uint32_t *s_ws = s_wsum + (size_t)tb * a.list_chunks * 4;
 
       // ---- chunks ----
       const int G = (L * F) / 8;  // 16-byte column groups per point
@@ -421,7 +639,7 @@ __global__ void __launch_bounds__((NG + 1 + kEpiWarps) * 32, 1) fused_kernel(Fus
         uint8_t *A = s_ring + buf * ring_stride;
         uint32_t all = 0;
 #pragma unroll
-        for (int w = 0; w < 4; ++w) all += s_wsum[s * 4 + w];
+        for (int w = 0; w < 4; ++w) all += s_ws[s * 4 + w];
         const int ngt = (int)(all & 1023u), nct = (int)((all >> 10) & 1023u);
         const int n_gi = ngt * G, n_oi = (kListStride - ngt) * G;
         const int nb_g = (n_gi + 31) >> 5, nb_o = (n_oi + 31) >> 5;
@@ -444,7 +662,7 @@ __global__ void __launch_bounds__((NG + 1 + kEpiWarps) * 32, 1) fused_kernel(Fus
           if (it < n_gi) {
             const int g = __float2int_rz(((float)it + 0.5f) * inv_g);
             const int t = it - g * ngt;
-            const int e = s_list[s * kListStride + t];
+            const int e = s_lst[s * kListStride + t];
             const int r = e & 127, j = e >> 7;
             const int ray = s_ray[tb * kTileM + r];
             uint4 outv;
@@ -516,7 +734,7 @@ __global__ void __launch_bounds__((NG + 1 + kEpiWarps) * 32, 1) fused_kernel(Fus
           if (it < n_oi) {
             const int g = __float2int_rz(((float)it + 0.5f) * inv_o);
             const int t = it - g * n_o;
-            const int e = s_list[s * kListStride + ngt + t];
+            const int e = s_lst[s * kListStride + ngt + t];
             const int r = e & 127, j = e >> 7;
             uint4 outv = make_uint4(0u, 0u, 0u, 0u);
             if (t < nct) {
@@ -534,144 +752,9 @@ __global__ void __launch_bounds__((NG + 1 + kEpiWarps) * 32, 1) fused_kernel(Fus
       chunk_ctr += kmax;
     }
   } else if (warp == kMmaWarp) {
-    // =================== MMA warp ===================
-    int chunk_ctr = 0;
-    const uint32_t idesc0 = idesc_bf16(W);
-    for (int i = 0;; ++i) {
-      const int tb = i & 1;
-      if (!mbar_wait(su32(&b_ready[tb]), (uint32_t)((i >> 1) & 1), abort_flag)) break;
-      const TileInfo ti = s_info[tb];
-      if (ti.stop) break;
-      const DevObject &ob = objs[ti.slot];
-      const int CHK = 2 * ob.L * F;
-      const uint32_t a_sbo = (uint32_t)(CHK / 8) * 128u, w0_sbo = (uint32_t)(ob.n_in / 8) * 128u;
-      if (i >= 2 && !mbar_wait(su32(&b_acce[tb]), (uint32_t)(((i - 2) >> 1) & 1), abort_flag)) break;
-      tc_after();
-      const uint32_t dacc = tmem + (uint32_t)(tb * W);
-      bool ok = true;
-      for (int s = 0; s < ti.kmax; ++s) {
-        const int c = chunk_ctr + s;
-        const int buf = c % nbuf;
-        if (!mbar_wait(su32(&b_full[buf]), (uint32_t)((c / nbuf) & 1), abort_flag)) {
-          ok = false;
-          break;
-        }
-        tc_after();
-        if (lane == 0) {
-          const uint32_t a0 = su32(s_ring + buf * ring_stride), b0 = su32(s_blob);
-          for (int ks = 0; ks < CHK / 16; ++ks) {
-            const uint64_t ad = umma_desc(a0 + ks * 256, 128, a_sbo);
-            const uint64_t bd = umma_desc(b0 + (uint32_t)((s * CHK) / 8 + 2 * ks) * 128u, 128, w0_sbo);
-            mma_bf16(dacc, ad, bd, idesc0, (s > 0 || ks > 0) ? 1u : 0u);
-          }
-          mma_commit(su32(&b_empty[buf]));
-        }
-        __syncwarp();
-      }
-      if (!ok) break;
-      chunk_ctr += ti.kmax;
-      if (lane == 0) mma_commit(su32(&b_accf[tb]));
-      __syncwarp();
-    }
-    if (lane == 0) {
-      mma_commit(su32(&b_fin[0]));
-      if (!mbar_wait_teardown(su32(&b_fin[0]), 0u)) *abort_flag = 1;
-    }
-    __syncwarp();
+    mma_role<F, W, XROWS, NG>(&a, base, tmem);
   } else {
-    // =================== epilogue warps ===================
-    const int etid = tid - kEpiWarp0 * 32;  // 0..127
-    const int quarter = warp & 3;          // the TMEM lane quarter this warp may access
-    const int r = quarter * 32 + lane;
-    const uint32_t act_sbo = (uint32_t)(W / 8) * 128u;
-    int layer_ctr = 0;
-    for (int i = 0;; ++i) {
-      const int tb = i & 1;
-      named_sync(2, kEpiWarps * 32);
-      if (etid == 0) {
-        bool ok = mbar_wait(su32(&b_ready[tb]), (uint32_t)((i >> 1) & 1), abort_flag);
-        const bool stop = !ok || s_info[tb].stop;
-        if (!stop) ok = mbar_wait(su32(&b_accf[tb]), (uint32_t)((i >> 1) & 1), abort_flag);
-        s_misc[2] = (stop || !ok) ? 1 : 0;
-      }
-      named_sync(2, kEpiWarps * 32);
-      if (s_misc[2]) break;
-      tc_after();
-      const TileInfo ti = s_info[tb];
-      const DevObject &ob = objs[ti.slot];
-      const int n_hidden = ob.n_hidden, n_out = ob.n_out, n_out_pad = ob.n_out_pad, n_mat = ob.n_mat, act = ob.act;
-      const float *bias = reinterpret_cast<const float *>(s_blob + ob.umma_bias_off);
-      uint32_t wl_off = (uint32_t)W * ob.n_in * 2u;  // byte offset of W1 in the blob
-      const uint32_t dacc = tmem + (uint32_t)(tb * W);
-      const uint32_t trow = dacc + ((uint32_t)(quarter * 32) << 16);
-      for (int layer = 0; layer <= n_hidden; ++layer) {
-        const bool last = layer == n_hidden;
-        const float *bl = bias + layer * W;
-        if (!last) {
-#pragma unroll 1
-          for (int c0 = 0; c0 < W; c0 += 16) {
-            uint32_t v[16];
-            TMEM_LD16(trow + c0, (&v[0]));
-            tmem_wait_ld();
-#pragma unroll
-            for (int c = 0; c < 16; c += 8) {
-              float h8[8];
-#pragma unroll
-              for (int u = 0; u < 8; ++u) h8[u] = act_fn(__uint_as_float(v[c + u]) + bl[c0 + c + u], act);
-              const uint4 pk = make_uint4(pack_bf16(h8[0], h8[1]), pack_bf16(h8[2], h8[3]),
-                                          pack_bf16(h8[4], h8[5]), pack_bf16(h8[6], h8[7]));
-              *reinterpret_cast<uint4 *>(s_act + core_off(r, (c0 + c) / 8, act_sbo)) = pk;
-            }
-          }
-          fence_async_smem();
-          tc_before();
-          named_sync(2, kEpiWarps * 32);
-          const int N = (layer + 1 < n_hidden) ? W : n_out_pad;
-          if (etid == 0) {
-            tc_after();
-            const uint32_t a0 = su32(s_act), b0 = su32(s_blob) + wl_off;
-            const uint32_t idesc = idesc_bf16(N);
-            for (int ks = 0; ks < W / 16; ++ks) {
-              const uint64_t ad = umma_desc(a0 + ks * 256, 128, act_sbo);
-              const uint64_t bd = umma_desc(b0 + ks * 256, 128, act_sbo);
-              mma_bf16(dacc, ad, bd, idesc, ks > 0 ? 1u : 0u);
-            }
-            mma_commit(su32(b_layer));
-            mbar_wait(su32(b_layer), (uint32_t)(layer_ctr & 1), abort_flag);
-          }
-          ++layer_ctr;
-          named_sync(2, kEpiWarps * 32);
-          tc_after();
-          wl_off += (uint32_t)N * W * 2u;
-        } else {
-          // logits 16 columns at a time into a per-thread array, then decode
-          float z[64];
-#pragma unroll 1
-          for (int c0 = 0; c0 < n_out_pad; c0 += 16) {
-            uint32_t v[16];
-            TMEM_LD16(trow + c0, (&v[0]));
-            tmem_wait_ld();
-#pragma unroll
-            for (int u = 0; u < 16; ++u) z[c0 + u] = __uint_as_float(v[u]) + bl[c0 + u];
-          }
-          const int32_t ray = s_ray[tb * kTileM + r];
-          if (ray >= 0 && !*abort_flag) {
-            if (XROWS) {
-              for (int j = 0; j < n_out; ++j) a.Z[(int64_t)ray * n_out + j] = z[j];
-            } else {
-              decode_store(q.hits, ray, z, n_out, n_mat, s_t0[tb * kTileM + r], s_t1[tb * kTileM + r],
-                           q.rays.tmin[ray], q.rays.tmax[ray]);
-            }
-          }
-        }
-      }
-      tc_before();
-      mbar_arrive(su32(&b_acce[tb]));
-    }
-    if (etid == 0) {
-      mma_commit(su32(&b_fin[1]));
-      if (!mbar_wait_teardown(su32(&b_fin[1]), 0u)) *abort_flag = 1;
-    }
+    epilogue_role<F, W, XROWS, NG>(&a, base, tmem);
   }
 
   tc_before();
@@ -727,23 +810,27 @@ static cudaError_t launch_one(const FusedArgs &a, size_t smem, cudaStream_t st) 
 // Shapes the autotuner chooses between: gather warps per CTA (with the MMA
 // warp and 4 epilogue warps: 4, 5 or 6 warps per SM sub-partition, so at
 // most 128, 96 or 80 registers per thread), levels of corner loads in flight
-// per gather item, and the F = 2 gather style.
+// per gather item, and the F = 2 gather style. On the torus benchmark the
+// first (fewer warps, all four levels of a column group in flight, 8-byte
+// corner pairs) is fastest: latency is hidden by loads per thread rather
+// than by more warps.
 struct Variant {
   int gather_warps, levels, style;
 };
-static const Variant kVariants[] = {{11, 2, 1}, {15, 1, 0}, {19, 1, 0}, {19, 1, 2}, {23, 1, 2}};
+static const Variant kVariants[] = {{11, 4, 2}, {11, 2, 1}, {15, 1, 2}, {19, 1, 2}, {15, 4, 2}};
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
 template <int F, int W, bool XR>
 static cudaError_t dispatch_variant(const FusedArgs &a, int v, size_t smem, cudaStream_t st) {
   constexpr int LPG = 8 / F;
   constexpr int NL2 = 2 < LPG ? 2 : LPG;
+  constexpr int PAIRS = F == 2 ? 2 : 0;
   switch (v) {
-    case 0: return launch_one<F, W, XR, 11, NL2, F == 2 ? 1 : 0>(a, smem, st);
-    case 1: return launch_one<F, W, XR, 15, 1, 0>(a, smem, st);
-    case 2: return launch_one<F, W, XR, 19, 1, 0>(a, smem, st);
-    case 3: return launch_one<F, W, XR, 19, 1, F == 2 ? 2 : 0>(a, smem, st);
-    case 4: return launch_one<F, W, XR, 23, 1, F == 2 ? 2 : 0>(a, smem, st);
+    case 0: return launch_one<F, W, XR, 11, LPG, PAIRS>(a, smem, st);
+    case 1: return launch_one<F, W, XR, 11, NL2, F == 2 ? 1 : 0>(a, smem, st);
+    case 2: return launch_one<F, W, XR, 15, 1, PAIRS>(a, smem, st);
+    case 3: return launch_one<F, W, XR, 19, 1, PAIRS>(a, smem, st);
+    case 4: return launch_one<F, W, XR, 15, LPG, PAIRS>(a, smem, st);
     default: return cudaErrorInvalidValue;
   }
 }

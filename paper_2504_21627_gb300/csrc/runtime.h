@@ -63,7 +63,7 @@ struct lsnif_ctx {
   int *d_err = nullptr;
   int32_t *d_prof_meta = nullptr;
   lsnif::Workspace ws;
-  int fused_variant = 3;  // fused-kernel shape (see lsnif_autotune)
+  int fused_variant = 0;  // fused-kernel shape (see lsnif_autotune)
   int trace_mode = 1;     // traversal kernel (see lsnif_autotune)
   int group_mode = 0;     // grouping of live rays (see lsnif_set_group_mode)
   // CUDA-graph cache of queries (see lsnif_set_graph_mode)
