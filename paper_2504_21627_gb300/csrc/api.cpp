@@ -402,18 +402,24 @@ extern "C" int lsnif_load_object(lsnif_ctx *ctx, const lsnif_object_desc *desc, 
   }                                                                        \
   d.field = (type)p;
   OALLOC(occ, const uint32_t *, 4 * occ.size(), "occupancy");
-  // brick mask for empty-space skipping in the traversal: 32 bricks per axis
-  // (bricks of at least 2 voxels, so fewer for V < 64)
+  // brick masks for empty-space skipping in the traversal: 32 bricks per
+  // axis (bricks of at least 2 voxels, so fewer for V < 64) and 16 bricks
+  // per axis, twice as wide
   d.log2B = std::max(1, d.log2V - 5);
-  const int nbk = cfg.V >> d.log2B;
+  const int nbk = cfg.V >> d.log2B, nbk2 = cfg.V >> (d.log2B + 1);
   std::vector<uint32_t> brick(((size_t)nbk * nbk * nbk + 31) / 32, 0u);
+  std::vector<uint32_t> brick2(((size_t)nbk2 * nbk2 * nbk2 + 31) / 32, 0u);
   for (size_t id = 0; id < (size_t)cfg.V * cfg.V * cfg.V; ++id) {
     if (!((occ[id >> 5] >> (id & 31)) & 1u)) continue;
     const size_t x = id % cfg.V, y = (id / cfg.V) % cfg.V, z = id / ((size_t)cfg.V * cfg.V);
     const size_t b = ((z >> d.log2B) * nbk + (y >> d.log2B)) * nbk + (x >> d.log2B);
     brick[b >> 5] |= 1u << (b & 31);
+    const int l2 = d.log2B + 1;
+    const size_t b2 = ((z >> l2) * nbk2 + (y >> l2)) * nbk2 + (x >> l2);
+    brick2[b2 >> 5] |= 1u << (b2 & 31);
   }
   OALLOC(brick, const uint32_t *, 4 * brick.size(), "brick mask");
+  OALLOC(brick2, const uint32_t *, 4 * brick2.size(), "brick mask");
   OALLOC(tab32, const float *, 4 * nt, "tables");
   OALLOC(tab16, const uint16_t *, 2 * nt, "FP16 tables");
   OALLOC(mlp32, const float *, 4 * (size_t)o->n_params_mlp, "network");
@@ -427,6 +433,7 @@ extern "C" int lsnif_load_object(lsnif_ctx *ctx, const lsnif_object_desc *desc, 
   OALLOC(plain_out, const float *, 4 * ((size_t)d.n_out_pad * cfg.width + d.n_out_pad), "padded output layer");
   cudaError_t e = cudaMemcpy((void *)d.occ, occ.data(), 4 * occ.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy((void *)d.brick, brick.data(), 4 * brick.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy((void *)d.brick2, brick2.data(), 4 * brick2.size(), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) { free_object(ctx, o); return cuda_fail(e, "upload occupancy"); }
   cudaMemset((void *)d.umma, 0, d.umma_bytes);
   if ((rc = upload_params(ctx, o, tab_src, mlp_src)) != LSNIF_OK) { free_object(ctx, o); return rc; }

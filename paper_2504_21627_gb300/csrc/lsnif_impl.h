@@ -34,8 +34,9 @@ struct DevObject {
   int32_t log2V;
   float invV;
   const uint32_t *occ;  // ceil(V^3/32) words
-  const uint32_t *brick;  // coarse mask: brick (bz*nb + by)*nb + bx occupied if any of its voxels is
-  int32_t log2B;          // bricks are 2^log2B voxels wide, nb = V >> log2B per axis
+  const uint32_t *brick;   // bit (bz*nb + by)*nb + bx: brick holds an occupied voxel
+  const uint32_t *brick2;  // the same for bricks twice as wide
+  int32_t log2B;           // bricks are 2^log2B voxels wide, nb = V >> log2B per axis
 
   int32_t L, F, log2T;
   uint32_t mask;

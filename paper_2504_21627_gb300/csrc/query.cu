@@ -95,9 +95,10 @@ __global__ void __launch_bounds__(256) trace_kernel(QueryLaunch q, int smem_hist
 // Rays need anywhere from 0 to 3V DDA steps; with one ray per thread a warp
 // runs as long as its longest ray.
 //
-// Empty-space skipping: every iteration crosses one cell, a voxel, or, when
-// the ray is inside a brick (2^log2B voxels a side) that holds no occupied
-// voxel, the whole brick. Both are the same instruction sequence (exit plane
+// Empty-space skipping: every iteration crosses one cell: a voxel, or, when
+// the ray is inside a brick (2^log2B voxels a side, or one twice as wide)
+// that holds no occupied voxel, the largest such brick. All are the same
+// instruction sequence (exit plane
 // per axis at the cell's granularity, earliest axis with the lowest axis on
 // ties, cross it), so lanes of a warp do not split between a voxel path and
 // a brick path. Crossing times are the same expression of the plane index as
@@ -116,7 +117,7 @@ struct LaneRay {
   int ain;
   float fin;
   int k, cap;
-  bool eb;         // the current brick holds no occupied voxel
+  int lg;          // log2 of the current cell's width: 0 (voxel) or an empty brick's
   uint32_t dup;    // bit k: entry point of segment k equals the exit of segment k-1
   uint32_t lt, lf; // exit (t, face) of the last segment, as bits
   int la;          // and its axis
@@ -128,9 +129,17 @@ __device__ __forceinline__ int sel3i(int a, int x, int y, int z) { return a == 0
 // crossing time of plane index P on one axis (the expression dda_walk uses)
 __device__ __forceinline__ float plane_t(int P, float invV, float o, float inv) { return ((float)P * invV - o) * inv; }
 
-__device__ __forceinline__ bool brick_empty(const DevObject &ob, int lb, int nbk, int x, int y, int z) {
+__device__ __forceinline__ bool bit_clear(const uint32_t *mask, int lb, int nbk, int x, int y, int z) {
   const uint32_t bid = ((uint32_t)(z >> lb) * nbk + (uint32_t)(y >> lb)) * nbk + (uint32_t)(x >> lb);
-  return !((__ldg(ob.brick + (bid >> 5)) >> (bid & 31)) & 1u);
+  return !((__ldg(mask + (bid >> 5)) >> (bid & 31)) & 1u);
+}
+
+// width (log2) of the largest empty brick holding voxel (x, y, z), 0 if none
+__device__ __forceinline__ int cell_level(const DevObject &ob, int x, int y, int z) {
+  const int lb = ob.log2B, V = ob.V;
+  if (bit_clear(ob.brick2, lb + 1, V >> (lb + 1), x, y, z)) return lb + 1;
+  if (bit_clear(ob.brick, lb, V >> lb, x, y, z)) return lb;
+  return 0;
 }
 
 __global__ void __launch_bounds__(256) trace_pool_kernel(QueryLaunch q, int smem_hist, int steps_per_round) {
@@ -223,7 +232,7 @@ __global__ void __launch_bounds__(256) trace_pool_kernel(QueryLaunch q, int smem
               R.tcur = t0;
               R.ain = ea;
               R.fin = ea >= 0 ? (dd[ea] > 0.f ? 0.f : 1.f) : 0.f;
-              R.eb = brick_empty(ob, ob.log2B, V >> ob.log2B, c[0], c[1], c[2]);
+              R.lg = cell_level(ob, c[0], c[1], c[2]);
             }
           }
         }
@@ -236,11 +245,11 @@ __global__ void __launch_bounds__(256) trace_pool_kernel(QueryLaunch q, int smem
     const int V = ob.V;
     const float invV = ob.invV;
     const uint32_t *occ = ob.occ;
-    const int LB = ob.log2B, nbk = V >> LB;
+    const int LB = ob.log2B;
     float *P = q.s.pts + (size_t)R.i * Hs * 3;
     for (int it = 0; it < steps_per_round; ++it) {
       bool done = false;
-      const int lg = R.eb ? LB : 0;  // cell granularity: voxel or empty brick
+      const int lg = R.lg;  // cell granularity: voxel or empty brick
       // exit plane of the cell on each axis, and its crossing time
       const int P0 = R.st0 > 0 ? ((R.ix0 >> lg) + 1) << lg : (R.ix0 >> lg) << lg;
       const int P1 = R.st1 > 0 ? ((R.ix1 >> lg) + 1) << lg : (R.ix1 >> lg) << lg;
@@ -252,7 +261,7 @@ __global__ void __launch_bounds__(256) trace_pool_kernel(QueryLaunch q, int smem
       const float ea = sel3(a, e0, e1, e2);
       const int Pa = sel3i(a, P0, P1, P2);
       const float tx = fminf(ea, R.t1);
-      if (!R.eb && tx > R.tcur && occupied(occ, ((uint32_t)R.ix2 * V + R.ix1) * V + R.ix0)) {
+      if (lg == 0 && tx > R.tcur && occupied(occ, ((uint32_t)R.ix2 * V + R.ix1) * V + R.ix0)) {
         const float fx = (float)Pa * invV;
         if (R.k > 0 && __float_as_uint(R.tcur) == R.lt && R.ain == R.la && __float_as_uint(R.fin) == R.lf)
           R.dup |= 1u << R.k;
@@ -271,19 +280,19 @@ __global__ void __launch_bounds__(256) trace_pool_kernel(QueryLaunch q, int smem
       if (!done) {
         // when a brick is crossed, the other axes first cross the planes the
         // voxel walk crosses before (ea, a); for a voxel there are none
-        if (R.eb) {
-          for (int g = 0; g < (1 << LB); ++g) {
+        if (lg) {
+          for (int g = 0; g < (1 << lg); ++g) {
             const int nx = R.ix0 + (R.st0 > 0);
             if (a != 0 && R.st0 != 0 && plane_t(nx, invV, R.o.x, R.inv0) <= ea) R.ix0 += R.st0;  // 0 < a
             else break;
           }
-          for (int g = 0; g < (1 << LB); ++g) {
+          for (int g = 0; g < (1 << lg); ++g) {
             const int ny = R.ix1 + (R.st1 > 0);
             const float ty = plane_t(ny, invV, R.o.y, R.inv1);
             if (a != 1 && R.st1 != 0 && (ty < ea || (ty == ea && a == 2))) R.ix1 += R.st1;
             else break;
           }
-          for (int g = 0; g < (1 << LB); ++g) {
+          for (int g = 0; g < (1 << lg); ++g) {
             const int nz = R.ix2 + (R.st2 > 0);
             const float tz = plane_t(nz, invV, R.o.z, R.inv2);
             if (a != 2 && R.st2 != 0 && tz < ea) R.ix2 += R.st2;
@@ -303,7 +312,7 @@ __global__ void __launch_bounds__(256) trace_pool_kernel(QueryLaunch q, int smem
           else if (a == 1) R.ix1 = ia;
           else R.ix2 = ia;
           // a brick plane was crossed: look up the new brick
-          if ((Pa & ((1 << LB) - 1)) == 0) R.eb = brick_empty(ob, LB, nbk, R.ix0, R.ix1, R.ix2);
+          if ((Pa & ((1 << LB) - 1)) == 0) R.lg = cell_level(ob, R.ix0, R.ix1, R.ix2);
         }
       }
       if (done) {
