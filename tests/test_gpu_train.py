@@ -153,7 +153,7 @@ def test_training_learns_and_beats_voxel_only(ctx):
     cfg = I.cfg_icosphere_small()
     mesh = I.noise_icosphere(seed=6, target_tris=1280, amplitude=0.08, n_mat=2)
     h = ctx.load_object(mesh, cfg, keep_mesh=True)
-    n_pool, B, steps = 1 << 18, 1 << 14, 400
+    n_pool, B, steps = 1 << 18, 1 << 14, 800
     u = torch.rand((n_pool, lsnif.TRAIN_UNIFORMS), device="cuda", generator=torch.Generator("cuda").manual_seed(3))
     pool, _ = ctx.make_training_rays(h, u, n_outside=n_pool // 2)
     lab = ctx.label_rays(pool, h)
@@ -166,7 +166,7 @@ def test_training_learns_and_beats_voxel_only(ctx):
     for s in range(steps):
         idx = torch.randint(0, n, (B,), device="cuda", generator=gen)
         st = ctx.train_step(pool[:, idx].contiguous(), {k: v[idx].contiguous() for k, v in lab.items()}, h,
-                            lr=0.01, stats=(s % 50 == 0 or s == steps - 1))
+                            lr=0.01, stats=(s % 100 == 0 or s == steps - 1))
         if st is not None:
             losses.append(st.total)
     assert losses[-1] < 0.5 * losses[0], losses
