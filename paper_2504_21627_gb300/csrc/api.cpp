@@ -135,6 +135,10 @@ extern "C" int lsnif_destroy(lsnif_ctx *ctx) {
   dev_free(ctx, ctx->d_err);
   dev_free(ctx, ctx->d_prof_meta);
   for (auto &ev : ctx->ev) cudaEventDestroy(ev);
+  for (auto &ev : ctx->hev)
+    if (ev) cudaEventDestroy(ev);
+  if (ctx->copy_in) cudaStreamDestroy(ctx->copy_in);
+  if (ctx->copy_out) cudaStreamDestroy(ctx->copy_out);
   delete ctx;
   return LSNIF_OK;
 }

@@ -258,6 +258,12 @@ extern "C" int lsnif_set_graph_mode(lsnif_ctx *ctx, int on) {
   return LSNIF_OK;
 }
 
+// Host-buffer query, pipelined: the batch is cut into up to 4 chunks of at
+// least 2^20 rays; chunk c's rays are copied in on one copy stream, queried on
+// the caller's stream and its results copied out on a second copy stream, so
+// the copies of neighbouring chunks overlap the query of chunk c (the two
+// copy directions also overlap each other). Synchronous: returns once every
+// result is in host memory.
 extern "C" int lsnif_query_rays_host(lsnif_ctx *ctx, const lsnif_rays *rays, lsnif_hits *hits, int precision,
                                      void *stream) {
   if (!ctx) return fail(LSNIF_ERR_INVALID_ARG, "lsnif_query_rays_host: ctx is NULL");
@@ -269,8 +275,12 @@ extern "C" int lsnif_query_rays_host(lsnif_ctx *ctx, const lsnif_rays *rays, lsn
   Shape sh;
   if ((rc = shape_of(ctx, rays, &sh))) return rc;
   const int64_t n = rays->n;
-  const int n_out = sh.rep ? 8 + 56 : 64;
-  const size_t need = al(n * 4) * 8 + al(n * 4) + al(n) + al(n * 4) * 8 + al(n * 4) + al((size_t)n * 4 * n_out);
+  int n_out_q = 0;
+  if (hits->logits) {
+    if (rays->obj) return fail(LSNIF_ERR_INVALID_ARG, "lsnif_query_rays_host: logits need a single object");
+    n_out_q = sh.rep->d.n_out;
+  }
+  const size_t need = al(n * 4) * 8 + al(n * 4) + al(n) + al(n * 4) * 8 + al(n * 4) + al((size_t)n * 4 * n_out_q);
   Workspace *ws = &ctx->ws;
   if (ws->stage_bytes < need) {
     if (ws->stage) {
@@ -282,43 +292,84 @@ extern "C" int lsnif_query_rays_host(lsnif_ctx *ctx, const lsnif_rays *rays, lsn
     if ((rc = dev_alloc(ctx, need, &ws->stage, "host-query staging"))) return rc;
     ws->stage_bytes = need;
   }
+  if (!ctx->copy_in) {
+    if (cudaStreamCreateWithFlags(&ctx->copy_in, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&ctx->copy_out, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(LSNIF_ERR_CUDA, "lsnif_query_rays_host: cannot create copy streams");
+    }
+    for (auto &ev : ctx->hev)
+      if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(LSNIF_ERR_CUDA, "lsnif_query_rays_host: cannot create events");
+      }
+  }
+  // device staging for the whole batch (each chunk uses its own slice)
   Carve c{reinterpret_cast<uint8_t *>(ws->stage)};
-  lsnif_rays dr = *rays;
   const float *src[8] = {rays->ox, rays->oy, rays->oz, rays->dx, rays->dy, rays->dz, rays->tmin, rays->tmax};
-  const float **dst[8] = {&dr.ox, &dr.oy, &dr.oz, &dr.dx, &dr.dy, &dr.dz, &dr.tmin, &dr.tmax};
-  cudaError_t e = cudaSuccess;
-  for (int i = 0; i < 8 && e == cudaSuccess; ++i) {
-    float *d = c.take<float>(n * 4);
-    e = cudaMemcpyAsync(d, src[i], n * 4, cudaMemcpyHostToDevice, st);
-    *dst[i] = d;
-  }
+  float *dray[8];
+  for (int i = 0; i < 8; ++i) dray[i] = c.take<float>(n * 4);
   uint32_t *dobj = c.take<uint32_t>(n * 4);
-  if (rays->obj && e == cudaSuccess) {
-    e = cudaMemcpyAsync(dobj, rays->obj, n * 4, cudaMemcpyHostToDevice, st);
-    dr.obj = dobj;
+  uint8_t *dhit = hits->hit ? c.take<uint8_t>(n) : nullptr;
+  float *hf_src[7] = {hits->t, hits->nx, hits->ny, hits->nz, hits->ar, hits->ag, hits->ab};
+  float *dhf[7];
+  for (int i = 0; i < 7; ++i) dhf[i] = hf_src[i] ? c.take<float>(n * 4) : nullptr;
+  int32_t *dmat = hits->mat ? c.take<int32_t>(n * 4) : nullptr;
+  float *dlog = hits->logits ? c.take<float>((size_t)n * 4 * n_out_q) : nullptr;
+
+  const int64_t kMinChunk = int64_t(1) << 20;
+  const int n_chunks = (int)std::max<int64_t>(1, std::min<int64_t>(4, n / kMinChunk));
+  const int64_t chunk = (n + n_chunks - 1) / n_chunks;
+  // the copies start after the caller's earlier work on its stream
+  cudaError_t e = cudaEventRecord(ctx->hev[15], st);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->copy_in, ctx->hev[15], 0);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->copy_out, ctx->hev[15], 0);
+  for (int k = 0; k < n_chunks && e == cudaSuccess; ++k) {
+    const int64_t off = k * chunk, len = std::min(chunk, n - off);
+    cudaEvent_t ev_in = ctx->hev[2 * k], ev_done = ctx->hev[2 * k + 1];
+    for (int i = 0; i < 8 && e == cudaSuccess; ++i)
+      e = cudaMemcpyAsync(dray[i] + off, src[i] + off, len * 4, cudaMemcpyHostToDevice, ctx->copy_in);
+    if (rays->obj && e == cudaSuccess)
+      e = cudaMemcpyAsync(dobj + off, rays->obj + off, len * 4, cudaMemcpyHostToDevice, ctx->copy_in);
+    if (e == cudaSuccess) e = cudaEventRecord(ev_in, ctx->copy_in);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev_in, 0);
+    if (e != cudaSuccess) break;
+    lsnif_rays dr = *rays;
+    dr.ox = dray[0] + off; dr.oy = dray[1] + off; dr.oz = dray[2] + off;
+    dr.dx = dray[3] + off; dr.dy = dray[4] + off; dr.dz = dray[5] + off;
+    dr.tmin = dray[6] + off; dr.tmax = dray[7] + off;
+    dr.obj = rays->obj ? dobj + off : nullptr;
+    dr.n = len;
+    lsnif_hits dh{};
+    dh.hit = dhit ? dhit + off : nullptr;
+    float **dhf_dst[7] = {&dh.t, &dh.nx, &dh.ny, &dh.nz, &dh.ar, &dh.ag, &dh.ab};
+    for (int i = 0; i < 7; ++i) *dhf_dst[i] = dhf[i] ? dhf[i] + off : nullptr;
+    dh.mat = dmat ? dmat + off : nullptr;
+    dh.logits = dlog ? dlog + (size_t)off * n_out_q : nullptr;
+    if ((rc = run_query(ctx, ws, &dr, &dh, precision, st, ctx->profiling))) {
+      cudaStreamSynchronize(ctx->copy_in);  // no copy may outlive the call
+      cudaStreamSynchronize(ctx->copy_out);
+      return rc;
+    }
+    e = cudaEventRecord(ev_done, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->copy_out, ev_done, 0);
+    if (hits->hit && e == cudaSuccess)
+      e = cudaMemcpyAsync(hits->hit + off, dhit + off, len, cudaMemcpyDeviceToHost, ctx->copy_out);
+    for (int i = 0; i < 7 && e == cudaSuccess; ++i)
+      if (hf_src[i]) e = cudaMemcpyAsync(hf_src[i] + off, dhf[i] + off, len * 4, cudaMemcpyDeviceToHost, ctx->copy_out);
+    if (hits->mat && e == cudaSuccess)
+      e = cudaMemcpyAsync(hits->mat + off, dmat + off, len * 4, cudaMemcpyDeviceToHost, ctx->copy_out);
+    if (hits->logits && e == cudaSuccess)
+      e = cudaMemcpyAsync(hits->logits + (size_t)off * n_out_q, dlog + (size_t)off * n_out_q,
+                          (size_t)len * 4 * n_out_q, cudaMemcpyDeviceToHost, ctx->copy_out);
   }
-  if (e != cudaSuccess) return cuda_fail(e, "lsnif_query_rays_host: upload");
-  lsnif_hits dh{};
-  dh.hit = hits->hit ? c.take<uint8_t>(n) : nullptr;
-  float **hf_dst[8] = {&dh.t, &dh.nx, &dh.ny, &dh.nz, &dh.ar, &dh.ag, &dh.ab, nullptr};
-  float *hf_src[8] = {hits->t, hits->nx, hits->ny, hits->nz, hits->ar, hits->ag, hits->ab, nullptr};
-  for (int i = 0; i < 7; ++i) *hf_dst[i] = hf_src[i] ? c.take<float>(n * 4) : nullptr;
-  dh.mat = hits->mat ? c.take<int32_t>(n * 4) : nullptr;
-  int n_out_q = 0;
-  if (hits->logits) {
-    if (rays->obj) return fail(LSNIF_ERR_INVALID_ARG, "lsnif_query_rays_host: logits need a single object");
-    n_out_q = sh.rep->d.n_out;
-    dh.logits = c.take<float>((size_t)n * 4 * n_out_q);
+  if (e == cudaSuccess) e = cudaEventRecord(ctx->hev[14], ctx->copy_out);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ctx->hev[14], 0);
+  if (e != cudaSuccess) {
+    cudaStreamSynchronize(ctx->copy_in);
+    cudaStreamSynchronize(ctx->copy_out);
+    return cuda_fail(e, "lsnif_query_rays_host: copies");
   }
-  if ((rc = run_query(ctx, ws, &dr, &dh, precision, st, ctx->profiling))) return rc;
-  if (hits->hit) e = cudaMemcpyAsync(hits->hit, dh.hit, n, cudaMemcpyDeviceToHost, st);
-  for (int i = 0; i < 7 && e == cudaSuccess; ++i)
-    if (hf_src[i]) e = cudaMemcpyAsync(hf_src[i], *hf_dst[i], n * 4, cudaMemcpyDeviceToHost, st);
-  if (hits->mat && e == cudaSuccess) e = cudaMemcpyAsync(hits->mat, dh.mat, n * 4, cudaMemcpyDeviceToHost, st);
-  if (hits->logits && e == cudaSuccess)
-    e = cudaMemcpyAsync(hits->logits, dh.logits, (size_t)n * 4 * n_out_q, cudaMemcpyDeviceToHost, st);
-  if (e != cudaSuccess) return cuda_fail(e, "lsnif_query_rays_host: download");
-  (void)n_out;
   return check_device(ctx, st);
 }
 

@@ -78,6 +78,9 @@ struct lsnif_ctx {
   bool prof_valid = false;
   // serving
   lsnif::Server *server = nullptr;
+  // host-buffer queries: copy streams and per-chunk events (created on first use)
+  cudaStream_t copy_in = nullptr, copy_out = nullptr;
+  cudaEvent_t hev[16]{};
 };
 
 namespace lsnif {

@@ -309,6 +309,25 @@ def test_host_buffer_query_equals_device_query(ctx, sphere):
             assert torch.equal(a.cpu(), b.cpu())
 
 
+def test_chunked_host_buffer_query_equals_device_query(ctx, torus):
+    """A batch above 2^21 rays goes through the host-buffer query in chunks
+    (copies overlapping the queries of neighbouring chunks); results and
+    logits equal the one-launch device query, rays of every chunk included."""
+    cam = I.seeded_camera(2, width=1792, height=1800)
+    rays = np.ascontiguousarray(I.rays_pinhole(cam))
+    n = rays.shape[1]
+    assert n > 3 * (1 << 20)
+    dev = ctx.query_rays(_cuda(rays), obj=torus["h"], precision=lsnif.BF16_FUSED, logits=True)
+    torch.cuda.synchronize()
+    host_rays = torch.from_numpy(rays).pin_memory()
+    out = ctx._alloc_hits(n, 8 + torus["cfg"].n_mat, True, device=False)
+    host = ctx.query_rays_host(host_rays, obj=torus["h"], precision=lsnif.BF16_FUSED, out=out)
+    for a, b in ((dev.hit, host.hit), (dev.t, host.t), (dev.mat, host.mat), (dev.normal, host.normal),
+                 (dev.logits, host.logits)):
+        assert torch.equal(torch.nan_to_num(a.cpu(), nan=-1e30), torch.nan_to_num(b.cpu(), nan=-1e30))
+    assert dev.hit.sum().item() > 100000
+
+
 def test_multi_object_batch_equals_single_object_queries(ctx, sphere, torus):
     cam = I.seeded_camera(2)
     ra = I.rays_sphere_to_box(2000, 3.0, sphere["orc"].bmin, sphere["orc"].bmax, seed=51)
