@@ -221,6 +221,16 @@ def noise_torus_tris(seed: int, target_tris: int, amplitude: float = 0.05, n_mat
     return noise_torus(seed, nu=nu, nv=nv, amplitude=amplitude, n_mat=n_mat)
 
 
+def cube(n_mat: int = 1) -> Mesh:
+    """Surface of the unit cube [0, 1]^3: 12 triangles, outward winding."""
+    v = np.array([[x, y, z] for z in (0, 1) for y in (0, 1) for x in (0, 1)], dtype=np.float32)
+    f = np.array([[0, 2, 1], [1, 2, 3], [4, 5, 6], [5, 7, 6],      # z = 0, z = 1
+                  [0, 1, 4], [1, 5, 4], [2, 6, 3], [3, 6, 7],      # y = 0, y = 1
+                  [0, 4, 2], [2, 4, 6], [1, 3, 5], [3, 7, 5]],     # x = 0, x = 1
+                 dtype=np.int32)
+    return Mesh(v, f, _vertex_normals(v, f), np.zeros(12, np.int32), _albedo_table(n_mat, 0), n_mat)
+
+
 def single_triangle(a, b, c, n_mat: int = 1) -> Mesh:
     v = np.array([a, b, c], dtype=np.float32)
     f = np.array([[0, 1, 2]], dtype=np.int32)
@@ -407,6 +417,45 @@ def random_params(cfg: Config, seed: int, table_range: float | None = None,
              else np.zeros(fo)).astype(np.float32)
         ws.append((W, b))
     return Params(tables, ws)
+
+
+def constant_params(cfg: Config, out_bias, seed: int = 0) -> Params:
+    """A network whose outputs are the constants out_bias for every input:
+    all weights and hidden biases zero (tables seeded, unused)."""
+    g = rng(seed)
+    tables = g.uniform(-0.1, 0.1, size=(cfg.L, cfg.T, cfg.F)).astype(np.float32)
+    ws = []
+    dims = cfg.layer_dims()
+    for i, (fi, fo) in enumerate(dims):
+        b = np.zeros(fo, np.float32)
+        if i == len(dims) - 1:
+            b[:] = np.asarray(out_bias, np.float32)
+        ws.append((np.zeros((fo, fi), np.float32), b))
+    return Params(tables, ws)
+
+
+def rotation(axis, angle: float) -> np.ndarray:
+    """3 x 3 rotation about a unit axis (Rodrigues)."""
+    k = np.asarray(axis, np.float64)
+    k = k / np.linalg.norm(k)
+    K = np.array([[0, -k[2], k[1]], [k[2], 0, -k[0]], [-k[1], k[0], 0]])
+    return np.eye(3) + math.sin(angle) * K + (1 - math.cos(angle)) * K @ K
+
+
+def seeded_instances(n: int, n_objects: int, seed: int, spread: float = 6.0, scale=(0.5, 2.0)):
+    """n instances of n_objects objects: object index, world -> object map
+    (A, b) of a seeded rotation, uniform scale and translation in a cube of
+    side `spread` (object-to-world p = s R q + c, so A = R^T / s,
+    b = -A c)."""
+    g = rng(seed)
+    out = []
+    for i in range(n):
+        R = rotation(g.normal(size=3), g.uniform(0, 2 * math.pi))
+        sc = math.exp(g.uniform(math.log(scale[0]), math.log(scale[1])))
+        c = g.uniform(-spread / 2, spread / 2, size=3)
+        A = R.T / sc
+        out.append((i % n_objects, A, -A @ c))
+    return out
 
 
 def unpack_mlp(cfg: Config, flat: np.ndarray) -> list:
