@@ -265,6 +265,50 @@ LSNIF_API int lsnif_query_rays_host(lsnif_ctx *ctx, const lsnif_rays *rays, lsni
  * message giving the sizes. Errors otherwise as lsnif_query_rays. */
 LSNIF_API int lsnif_query_rays_noalloc(lsnif_ctx *ctx, const lsnif_rays *rays, lsnif_hits *hits, void *stream);
 
+/* ---- instanced scenes (Sec. 4 wavefront integration, Sec. 6 instancing) -- */
+
+/* One placement of an object in a scene: the affine map from world to
+ * object coordinates, p_obj = A p_world + b, stored row-major as the 3 x 4
+ * matrix [A | b]. A must be invertible (rotation, scale, shear). */
+typedef struct lsnif_instance {
+    lsnif_obj obj;
+    float world_to_obj[12];
+} lsnif_instance;
+
+/* Query world-space rays (DEVICE buffers; rays->obj and rays->single_obj are
+ * ignored) against n_inst instances (HOST array, read during the call).
+ * Every (ray, instance) pair whose ray, mapped into the instance's object
+ * frame (o' = A o + b, d' = A d; t, tmin and tmax unchanged), crosses the
+ * object's box is queried there; the pairs of all instances go through one
+ * launch sequence grouped by object (Sec. 4). Each ray keeps its nearest hit:
+ * smallest t, the lowest instance index on equal t. Results (DEVICE, any
+ * pointer in `hits` may be NULL; logits are not supported and must be NULL):
+ * hit, t, world normal A^T n normalised, material, albedo; inst_hit[n]
+ * (DEVICE, may be NULL) receives the instance index, -1 on a miss. A ray no
+ * pair hits gets hit 0, t +inf, normal 0, material -1, albedo 0. The call
+ * waits once for the pair count on `stream`; the rest is queued on `stream`.
+ * Scratch (about 80 bytes per pair plus the query's) is held by the context.
+ * Errors: INVALID_ARG (NULL arrays, n_inst < 1, logits given, a singular A),
+ * BAD_HANDLE (an instance names an unknown object), OVER_BUDGET,
+ * OUT_OF_MEMORY, UNSUPPORTED (BF16_FUSED over objects of different network
+ * shapes), CUDA, DEVICE_CHECK. */
+LSNIF_API int lsnif_query_scene(lsnif_ctx *ctx, const lsnif_rays *rays, const lsnif_instance *inst, int n_inst,
+                                lsnif_hits *hits, int32_t *inst_hit, int precision, void *stream);
+
+/* Next-bounce rays of a path tracer from query results (all DEVICE): for a
+ * ray with hit != 0 and a non-zero normal, origin = o + t d + eps n_f and a
+ * cosine-weighted direction about n_f, where n_f is the normal turned to
+ * face the incoming ray; the direction is x t + y b + z n_f with (x, y) =
+ * sqrt(u0) (cos 2 pi u1, sin 2 pi u1), z = sqrt(1 - u0), and (t, b) the
+ * orthonormal basis of Duff et al. 2017 about n_f; tmin 0, tmax +inf. Other
+ * rays become dead rays: zero origin and direction (a miss for the query).
+ * u: n x 2 uniforms in [0, 1), row-major. out: 8 x n FP32, rows ox oy oz dx
+ * dy dz tmin tmax (n = rays->n), aliasing nothing in rays, hits or u.
+ * hits->hit, t, nx, ny, nz are required. Errors: INVALID_ARG (NULL pointers,
+ * n < 0), CUDA. */
+LSNIF_API int lsnif_bounce_rays(lsnif_ctx *ctx, const lsnif_rays *rays, const lsnif_hits *hits, const float *u,
+                                float eps, float *out, void *stream);
+
 /* Stage outputs of the traversal (a1-a5 of the query) for one object, all
  * DEVICE pointers, any may be NULL: k[n] kept occupied voxels (<= H/2);
  * t01[2n] the clipped AABB interval (NaN on a miss); pts[n*H*3] boundary

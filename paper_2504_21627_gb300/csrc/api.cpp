@@ -131,6 +131,8 @@ extern "C" int lsnif_destroy(lsnif_ctx *ctx) {
   for (int s = 0; s < kMaxSlots; ++s)
     if (ctx->slots[s]) free_object(ctx, ctx->slots[s]);
   free_workspace(ctx, &ctx->ws);
+  if (ctx->scene_buf) dev_free(ctx, ctx->scene_buf);
+  if (ctx->pair_buf) dev_free(ctx, ctx->pair_buf);
   dev_free(ctx, ctx->d_objs);
   dev_free(ctx, ctx->d_err);
   dev_free(ctx, ctx->d_prof_meta);

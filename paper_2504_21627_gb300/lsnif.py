@@ -64,6 +64,10 @@ class Rays(C.Structure):
                 ("obj", C.c_void_p), ("single_obj", C.c_uint32), ("n", C.c_int64)]
 
 
+class Instance(C.Structure):
+    _fields_ = [("obj", C.c_uint32), ("world_to_obj", C.c_float * 12)]
+
+
 class Hits(C.Structure):
     _fields_ = [("hit", C.c_void_p), ("t", C.c_void_p), ("nx", C.c_void_p), ("ny", C.c_void_p),
                 ("nz", C.c_void_p), ("mat", C.c_void_p), ("ar", C.c_void_p), ("ag", C.c_void_p),
@@ -117,6 +121,8 @@ SIGNATURES = {
     "lsnif_query_rays": (_I, [_P, C.POINTER(Rays), C.POINTER(Hits), _I, _P]),
     "lsnif_query_rays_host": (_I, [_P, C.POINTER(Rays), C.POINTER(Hits), _I, _P]),
     "lsnif_query_rays_noalloc": (_I, [_P, C.POINTER(Rays), C.POINTER(Hits), _P]),
+    "lsnif_query_scene": (_I, [_P, C.POINTER(Rays), C.POINTER(Instance), _I, C.POINTER(Hits), _P, _I, _P]),
+    "lsnif_bounce_rays": (_I, [_P, C.POINTER(Rays), C.POINTER(Hits), _P, C.c_float, _P, _P]),
     "lsnif_trace": (_I, [_P, C.POINTER(Rays), C.POINTER(TraceOut), _P]),
     "lsnif_encode": (_I, [_P, _U32, _P, _I64, _P, _I, _P]),
     "lsnif_corner_indices": (_I, [_P, _U32, _P, _I64, _P, _P]),
@@ -345,6 +351,37 @@ class Context:
         rs = rays_struct(rays, obj_per_ray, obj)
         hs = self.hits_struct(out)
         _check(self.lib.lsnif_query_rays_noalloc(self.h, C.byref(rs), C.byref(hs), _stream(stream)))
+        return out
+
+    def query_scene(self, rays, instances, precision: int = BF16_FUSED, stream=None):
+        """World rays (8, n) CUDA tensor against instances [(handle, A (3x3),
+        b (3,)), ...] with p_obj = A p + b. Returns (QueryResult, instance
+        index per ray, -1 on a miss)."""
+        import torch
+        n = int(rays.shape[1])
+        res = self._alloc_hits(n, 0, False)
+        inst = torch.full((n,), -1, dtype=torch.int32, device=rays.device)
+        arr = (Instance * len(instances))()
+        for k, (h, A, b) in enumerate(instances):
+            m = np.concatenate([np.asarray(A, np.float64), np.asarray(b, np.float64)[:, None]], 1)
+            arr[k].obj = int(h)
+            arr[k].world_to_obj[:] = [float(x) for x in m.astype(np.float32).reshape(-1)]
+        rs = rays_struct(rays)
+        hs = self.hits_struct(res)
+        _check(self.lib.lsnif_query_scene(self.h, C.byref(rs), arr, len(instances), C.byref(hs), _ptr(inst),
+                                          precision, _stream(stream)))
+        return res, inst
+
+    def bounce_rays(self, rays, res: QueryResult, u, eps: float, stream=None):
+        """Next-bounce rays (8, n) from world rays and their query results;
+        u: (n, 2) uniforms, all CUDA tensors."""
+        import torch
+        n = int(rays.shape[1])
+        out = torch.empty((8, n), dtype=torch.float32, device=rays.device)
+        rs = rays_struct(rays)
+        hs = self.hits_struct(res)
+        _check(self.lib.lsnif_bounce_rays(self.h, C.byref(rs), C.byref(hs), _ptr(u), float(eps), _ptr(out),
+                                          _stream(stream)))
         return out
 
     def trace(self, rays, obj: int, stream=None):

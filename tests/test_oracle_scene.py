@@ -16,7 +16,7 @@ OUT_BIAS = [5.0, 0.0, 1.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 2.0, 0.0]
 
 
 def _cube_object():
-    cfg = I.Config(V=8, H=18, L=2, F=2, log2_T=10, N_min=4, N_max=8, n_hidden=1, width=16, n_mat=3)
+    cfg = I.Config(V=8, H=18, L=4, F=2, log2_T=10, N_min=4, N_max=16, n_hidden=1, width=64, n_mat=3)
     mesh = I.cube(n_mat=3)
     return O.build_object(mesh, cfg, I.constant_params(cfg, OUT_BIAS)), mesh, cfg
 
