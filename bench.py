@@ -385,6 +385,67 @@ def bench_train(args):
     print(json.dumps(out))
 
 
+def bench_scene(args):
+    """Path-tracer-shaped stress: 32 instances of 8 unique objects (50k..1M
+    triangles, V 128, L 16, F 2, T 2^21, 4 x 64 BF16 network) with seeded
+    rigid transforms and scales, 1920 x 1080 x 4 jittered primary rays, 3
+    bounces: each bounce is one lsnif_query_scene (broad phase over the
+    instances, pairs grouped by object, nearest hit) and one
+    lsnif_bounce_rays. Mrays/s counts every submitted ray (dead rays
+    included), as the query's own metric does."""
+    import torch
+    from paper_2504_21627_gb300 import lsnif
+    spec = I.scene_objects()
+    ctx = lsnif.Context(0)
+    handles = []
+    for i, (mesh, cfg) in enumerate(spec):
+        p = I.random_params(cfg, seed=3000 + i, table_range=0.05, bias_range=0.1)
+        p.weights[-1][1][0] = 1.0   # occupancy logit biased towards hits, so bounces continue
+        handles.append(ctx.load_object(mesh, cfg, tables=p.tables, mlp=p.packed_mlp()))
+    insts = [(handles[o], A, b) for o, A, b in I.seeded_instances(32, len(spec), seed=9, spread=10.0)]
+    cam = I.seeded_camera(4, radius=14.0, width=args.scene_width, height=args.scene_height, fov_deg=50.0)
+    rays0 = torch.from_numpy(I.camera_rays_spp(cam, 4, seed=10)).cuda()
+    n = rays0.shape[1]
+    gen = torch.Generator("cuda").manual_seed(11)
+    us = [torch.rand((n, 2), device="cuda", generator=gen) for _ in range(3)]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def frame(prec, stats=None):
+        rays = rays0
+        for b in range(3):
+            res, inst = ctx.query_scene(rays, insts, precision=prec)
+            if stats is not None:
+                stats.append((int(res.hit.sum().item()), int((rays[3:6].abs().sum(0) > 0).sum().item())))
+            if b < 2:
+                rays = ctx.bounce_rays(rays, res, us[b], 1e-3)
+        return res
+
+    out = {"workload": "scene", "metric": "Mrays/s over 3 bounces of an instanced scene (misses included)",
+           "instances": len(insts), "unique_objects": len(spec), "rays_per_bounce": n,
+           "deviation": "F=2 features, 4x64 BF16 network (the stress config's F=4, 4x128 FP8 network is not built)"}
+    for name, prec, steps in (("bf16", lsnif.BF16_FUSED, max(3, args.steps // 4)), ("fp32", lsnif.FP32_PLAIN, 2)):
+        stats = []
+        frame(prec, stats)
+        for _ in range(2):
+            frame(prec)
+        ms = []
+        for _ in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            frame(prec)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        ms = np.array(ms)
+        out[name] = {"mrays_s": 3 * n / (ms.mean() / 1e3) / 1e6, "ms_per_frame": float(ms.mean()),
+                     "hits_per_bounce": [h for h, _ in stats], "live_rays_per_bounce": [l for _, l in stats]}
+    out["device_gb"] = ctx.device_bytes() / 1e9
+    print(json.dumps(out))
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -397,9 +458,11 @@ def main():
     ap.add_argument("--variant", type=int, default=None,
                     help="fused-kernel variant to time instead of the autotuner's choice")
     ap.add_argument("--side", type=int, default=2048, help="image side; below 2048 only for profiling captures")
-    ap.add_argument("--workload", default="torus4m", choices=["torus4m", "batched", "serving", "train"],
+    ap.add_argument("--workload", default="torus4m", choices=["torus4m", "batched", "serving", "train", "scene"],
                     help="torus4m is the headline; the others print their own line")
     ap.add_argument("--requests", type=int, default=200)
+    ap.add_argument("--scene-width", type=int, default=1920)
+    ap.add_argument("--scene-height", type=int, default=1080)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -410,6 +473,8 @@ def main():
         return bench_serving(args)
     if args.workload == "train":
         return bench_train(args)
+    if args.workload == "scene":
+        return bench_scene(args)
 
     import torch
     import torch.distributed as dist

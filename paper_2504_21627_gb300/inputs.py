@@ -402,6 +402,42 @@ def batched_objects(n_obj: int = 64, seed: int = 3, total_rays: int = 16 << 20):
     return out
 
 
+def scene_objects(n_unique: int = 8, seed: int = 5):
+    """The instanced scene's unique objects: seeded noise icospheres or tori
+    of 50k..1M triangles (log-uniform), V = 128, L = 16, F = 2, T = 2^21,
+    4 x 64 network. Returns [(mesh, cfg)]."""
+    g = rng(seed)
+    out = []
+    for i in range(n_unique):
+        tris = int(math.exp(g.uniform(math.log(50000), math.log(1000000))))
+        mesh = noise_icosphere(seed + 200 + i, tris, n_mat=4) if i % 2 == 0 else \
+            noise_torus_tris(seed + 200 + i, tris, n_mat=4)
+        cfg = Config(V=128, H=18, L=16, F=2, log2_T=21, N_min=16, N_max=2048, n_hidden=4, width=64, n_mat=4,
+                     seed=seed + i)
+        out.append((mesh, cfg))
+    return out
+
+
+def camera_rays_spp(cam: Camera, spp: int, seed: int) -> np.ndarray:
+    """spp jittered samples per pixel (seeded), pixel-major, as (8, w*h*spp)
+    rays with tmin 0 and tmax inf."""
+    g = rng(seed)
+    w, h = cam.width, cam.height
+    px = np.repeat(np.arange(w * h), spp)
+    jx = g.random(px.size)
+    jy = g.random(px.size)
+    x = (px % w + jx) / w * 2.0 - 1.0
+    y = 1.0 - (px // w + jy) / h * 2.0
+    th = math.tan(math.radians(cam.fov_deg) / 2.0)
+    aspect = w / h
+    d = cam.forward[None, :] + (x * th * aspect)[:, None] * cam.right[None, :] + (y * th)[:, None] * cam.up[None, :]
+    rays = np.zeros((8, px.size), np.float32)
+    rays[0:3] = cam.eye[:, None]
+    rays[3:6] = d.T
+    rays[7] = np.inf
+    return rays
+
+
 def random_params(cfg: Config, seed: int, table_range: float | None = None,
                   bias_range: float = 0.0) -> Params:
     """Tables ~ U(-r, r); weights Xavier-uniform U(+-sqrt(6/(fan_in+fan_out)));
