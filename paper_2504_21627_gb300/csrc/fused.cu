@@ -547,7 +547,6 @@ template <int F, int W, bool XROWS, int NG, int NLB, int GS>
 __global__ void __launch_bounds__((NG + 1 + kEpiWarps) * 32, 1) fused_kernel(const __grid_constant__ FusedArgs a) {
   constexpr int kGatherThreads = NG * 32;
   constexpr int kMmaWarp = NG;
-  constexpr int kEpiWarp0 = NG + 1;
   constexpr int kTmemCols = 2 * W;  // two accumulators
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -557,12 +556,8 @@ __global__ void __launch_bounds__((NG + 1 + kEpiWarps) * 32, 1) fused_kernel(con
 
   uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const Layout lay = make_layout(a.smem_blob, F, W, nbuf, a.list_chunks);
-  uint8_t *s_blob = base + lay.blob;
   uint8_t *s_ring = base + lay.ring;
-  uint8_t *s_act = base + lay.act;
   int32_t *s_ray = reinterpret_cast<int32_t *>(base + lay.ray);
-  float *s_t0 = reinterpret_cast<float *>(base + lay.t0);
-  float *s_t1 = reinterpret_cast<float *>(base + lay.t1);
   uint16_t *s_list = reinterpret_cast<uint16_t *>(base + lay.list);
   uint32_t *s_wsum = reinterpret_cast<uint32_t *>(base + lay.wsum);
   TileInfo *s_info = reinterpret_cast<TileInfo *>(base + lay.info);
@@ -599,7 +594,6 @@ __global__ void __launch_bounds__((NG + 1 + kEpiWarps) * 32, 1) fused_kernel(con
   __syncthreads();
   tc_after();
   const uint32_t tmem = *s_tmem;
-  const int64_t n_tiles = XROWS ? (a.xrows + kTileM - 1) / kTileM : (int64_t)q.s.meta[1];
   const int Hs = q.H_max;
 
   if (warp < NG) {
