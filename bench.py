@@ -596,7 +596,10 @@ def main():
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "kernel": "fused gather+MLP+decode (BF16 tcgen05)",
                      "peak_source": peak_src,
-                     "l2_request_rate_gps": l2_requests / (fused_ms / 1e3) / 1e9},
+                     "l2_request_rate_gps": l2_requests / (fused_ms / 1e3) / 1e9,
+                     # the query's memory ceiling: every corner of every point from HBM, plus
+                     # 32 B of ray in and 33 B of results per submitted ray
+                     "memory_ceiling_mrays_s": peak * 1e9 / ((alg_bytes - live * 54) / n + 65) / 1e6},
         "e2e": {"value": world * n / (e2e_ms / 1e3) / 1e6, "unit": "Mrays/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
         "gpu_launches": launches_per_step * args.steps,

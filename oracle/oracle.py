@@ -241,6 +241,46 @@ def round_fp16(x: np.ndarray) -> np.ndarray:
     return np.asarray(x, np.float64).astype(np.float32).astype(np.float16).astype(np.float64)
 
 
+E4M3_MAX = 448.0
+
+
+def round_e4m3(x: np.ndarray) -> np.ndarray:
+    """Round to the nearest FP8 E4M3 value (1 sign, 4 exponent bits with bias
+    7, 3 mantissa bits; normals down to 2^-6, subnormals in steps of 2^-9,
+    largest finite 448), ties to even, saturating: |x| > 448 gives +-448."""
+    x = np.asarray(x, np.float64)
+    _, e = np.frexp(x)                        # x = m 2^e, 0.5 <= |m| < 1
+    q = np.ldexp(1.0, np.maximum(e - 1, -6) - 3)   # spacing of the binade (subnormal spacing below 2^-6)
+    r = np.round(x / q) * q                   # np.round: half to even
+    return np.clip(np.where(x == 0, 0.0, r), -E4M3_MAX, E4M3_MAX)
+
+
+def pow2_scale(m: float) -> float:
+    """The power of two s with 448 / 2 < s m <= 448 (1 when m is 0): the scale
+    that brings a magnitude m to the top binade of E4M3."""
+    if not m > 0:
+        return 1.0
+    _, e = math.frexp(E4M3_MAX / m)           # 448 / m = f 2^e, 0.5 <= f < 1
+    return math.ldexp(1.0, e - 1)
+
+
+def fp8_scales(tables_fp16_max: float, weights) -> tuple[list, list]:
+    """Per-layer power-of-two scales of the FP8 network: input scales s_l
+    (s_0 from the largest FP16 table value, which bounds every interpolated
+    feature; s_{l+1} from the magnitude estimate M_{l+1} = max_j
+    (||W_l[j]||_2 M_l + |b_l[j]|), with M_0 the table maximum) and weight
+    scales w_l (from max |W_l|). Values beyond the E4M3 range saturate."""
+    s, w = [], []
+    M = float(tables_fp16_max)
+    for W, b in weights:
+        W = np.asarray(W, np.float64)
+        b = np.asarray(b, np.float64)
+        s.append(pow2_scale(M))
+        w.append(pow2_scale(float(np.max(np.abs(W))) if W.size else 0.0))
+        M = float(np.max(np.sqrt(np.sum(W * W, axis=1)) * M + np.abs(b)))
+    return s, w
+
+
 # --------------------------------------------------------------------------
 # network (Sec. 5.1) and decode (Sec. 5.1, Sec. 5.3)
 # --------------------------------------------------------------------------
@@ -253,18 +293,26 @@ def activation_grad(pre: np.ndarray, kind: int) -> np.ndarray:
     return (pre > 0).astype(np.float64) if kind == 0 else np.where(pre > 0, 1.0, 0.01)
 
 
-def mlp_forward(X: np.ndarray, weights, act: int = 0, precision: str = "f64", keep: bool = False):
+def mlp_forward(X: np.ndarray, weights, act: int = 0, precision: str = "f64", keep: bool = False,
+                fp8=None):
     """Dense layers, hidden activation `act`, linear output. With
     precision='bf16' the matmul operands (inputs, weights, hidden
-    activations) are rounded to bfloat16 first; sums stay float64."""
+    activations) are rounded to bfloat16 first; sums stay float64. With
+    precision='fp8' (fp8 = (s, w) from fp8_scales) every layer multiplies
+    round_e4m3(s_l h) by round_e4m3(w_l W_l) and divides the sum by s_l w_l
+    before the bias."""
     h = np.asarray(X, np.float64)
     if precision == "bf16":
         h = round_bf16(h)
     cache = []
     for i, (W, b) in enumerate(weights):
-        Wq = round_bf16(W) if precision == "bf16" else W
         bq = np.asarray(b, np.float64)
-        z = h @ Wq.T + bq
+        if precision == "fp8":
+            s, w = fp8[0][i], fp8[1][i]
+            z = (round_e4m3(h * s) @ round_e4m3(np.asarray(W, np.float64) * w).T) / (s * w) + bq
+        else:
+            Wq = round_bf16(W) if precision == "bf16" else W
+            z = h @ Wq.T + bq
         cache.append((h, z))
         if i < len(weights) - 1:
             h = activation(z, act)
@@ -314,13 +362,14 @@ def query(obj: OracleObject, rays: np.ndarray, precision: str = "f64", seg: Segm
     seg = ray_segments(obj, rays) if seg is None else seg
     n = seg.k.size
     live = seg.k > 0
-    tables = round_fp16(obj.tables) if precision == "bf16" else obj.tables
+    tables = round_fp16(obj.tables) if precision in ("bf16", "fp8") else obj.tables
+    fp8 = fp8_scales(float(np.max(np.abs(tables))), obj.weights) if precision == "fp8" else None
     out = Hits(np.zeros(n, bool), np.full(n, np.inf), np.zeros((n, 3)), np.full(n, -1, np.int32),
                np.zeros((n, 3)), np.full((n, cfg.n_out), np.nan), live)
     if live.any():
         sub = Segments(seg.k[live], seg.t01[live], seg.pts[live], seg.vox[live], seg.near[live])
         X = features(obj, sub, tables)
-        Z = mlp_forward(X, obj.weights, cfg.activation, precision)
+        Z = mlp_forward(X, obj.weights, cfg.activation, precision, fp8=fp8)
         rr = np.asarray(rays, np.float64)[:, live]
         dec = decode(Z, sub.t01, rr[6], rr[7])
         out.hit[live] = dec["hit"]
