@@ -37,7 +37,7 @@ WORKLOAD = ("noise torus 200k tris; V=128^3; hash grid L=16 F=2 T=2^19 N=16..204
             "MLP 576-64x4-12; 2048x2048 pinhole primary rays")
 PROFILE_MD = os.path.join(ROOT, "profiles", "fused_kernel_torus_4m.md")
 FUSED_SOURCES = ["paper_2504_21627_gb300/csrc/fused.cu", "paper_2504_21627_gb300/csrc/encode.cuh",
-                 "paper_2504_21627_gb300/csrc/device.cuh"]
+                 "paper_2504_21627_gb300/csrc/device.cuh", "paper_2504_21627_gb300/csrc/tc_common.cuh"]
 
 
 def fused_source_hash() -> str:
@@ -387,15 +387,18 @@ def bench_train(args):
 
 def bench_scene(args):
     """Path-tracer-shaped stress: 32 instances of 8 unique objects (50k..1M
-    triangles, V 128, L 16, F 2, T 2^21, 4 x 64 BF16 network) with seeded
-    rigid transforms and scales, 1920 x 1080 x 4 jittered primary rays, 3
-    bounces: each bounce is one lsnif_query_scene (broad phase over the
-    instances, pairs grouped by object, nearest hit) and one
-    lsnif_bounce_rays. Mrays/s counts every submitted ray (dead rays
-    included), as the query's own metric does."""
+    triangles, V 128, L 16, F 4, T 2^21, 4 x 128 network; `--scene-net
+    small` takes F 2 and 4 x 64 instead) with seeded rigid transforms and
+    scales, 1920 x 1080 x 4 jittered primary rays, 3 bounces: each bounce is
+    one lsnif_query_scene (broad phase over the instances' boxes, pairs
+    grouped by object, nearest hit) and one lsnif_bounce_rays. Mrays/s
+    counts every submitted ray (dead rays included), as the query's own
+    metric does. The F 4, 4 x 128 network runs on the FP8 tensor-core path
+    (its BF16 first layer does not fit shared memory) and on the FP32 path."""
     import torch
     from paper_2504_21627_gb300 import lsnif
-    spec = I.scene_objects()
+    stress = args.scene_net == "stress"
+    spec = I.scene_objects(features=4, width=128) if stress else I.scene_objects()
     ctx = lsnif.Context(0)
     handles = []
     for i, (mesh, cfg) in enumerate(spec):
@@ -423,8 +426,10 @@ def bench_scene(args):
 
     out = {"workload": "scene", "metric": "Mrays/s over 3 bounces of an instanced scene (misses included)",
            "instances": len(insts), "unique_objects": len(spec), "rays_per_bounce": n,
-           "deviation": "F=2 features, 4x64 BF16 network (the stress config's F=4, 4x128 FP8 network is not built)"}
-    for name, prec, steps in (("bf16", lsnif.BF16_FUSED, max(3, args.steps // 4)), ("fp32", lsnif.FP32_PLAIN, 2)):
+           "network": "L=16 F=4 T=2^21, 1152-128x4-12" if stress else "L=16 F=2 T=2^21, 576-64x4-12"}
+    fast = (("fp8", lsnif.FP8_FUSED, max(3, args.steps // 4)),) if stress else \
+        (("bf16", lsnif.BF16_FUSED, max(3, args.steps // 4)), ("fp8", lsnif.FP8_FUSED, max(3, args.steps // 4)))
+    for name, prec, steps in fast + (("fp32", lsnif.FP32_PLAIN, 2),):
         stats = []
         frame(prec, stats)
         for _ in range(2):
@@ -463,6 +468,7 @@ def main():
     ap.add_argument("--requests", type=int, default=200)
     ap.add_argument("--scene-width", type=int, default=1920)
     ap.add_argument("--scene-height", type=int, default=1080)
+    ap.add_argument("--scene-net", default="stress", choices=["stress", "small"])
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":

@@ -75,7 +75,16 @@ typedef uint32_t lsnif_obj;         /* object handle; 0 is never a valid handle 
  * FP32 interpolation, BF16 tcgen05 tensor-core MLP with FP32 accumulation,
  * gather + every layer + decode in one kernel (Sec. 5: half precision,
  * fused layers). Traversal is FP32 in both. */
-enum lsnif_precision { LSNIF_FP32_PLAIN = 0, LSNIF_BF16_FUSED = 1 };
+/* FP8_FUSED: as BF16_FUSED with E4M3 network operands (features, weights,
+ * hidden activations) and per-layer power-of-two scales chosen from the
+ * parameters (the input scale from the largest FP16 table value, each
+ * weight scale from the layer's largest weight, each activation scale from
+ * max_j ||W_j||_2 M + |b_j| with M the previous magnitude), rounding to
+ * nearest even and saturating at 448; tcgen05 kind::f8f6f4, FP32
+ * accumulation; the first layer's weights are streamed, so networks too
+ * large for BF16 shared memory (F = 4, L = 16, 4 x 128) run. Needs F in
+ * {2, 4}, width 64 or 128, L * F a multiple of 16. */
+enum lsnif_precision { LSNIF_FP32_PLAIN = 0, LSNIF_BF16_FUSED = 1, LSNIF_FP8_FUSED = 2 };
 
 /* Hidden-layer activation: ReLU, or leaky ReLU with slope 0.01 (Sec. 5.1). */
 enum lsnif_activation { LSNIF_RELU = 0, LSNIF_LEAKY_RELU = 1 };

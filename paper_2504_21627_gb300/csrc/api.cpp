@@ -259,11 +259,157 @@ int lsnif::upload_params(lsnif_ctx *ctx, Object *o, const float *tables, const f
 }
 
 int lsnif::refresh_copies(lsnif_ctx *, Object *o, cudaStream_t st) {
+  o->fp8_stale = true;
   const lsnif_config &c = o->cfg;
   size_t nt = ((size_t)c.L << c.log2_T) * c.F;
   cudaError_t e = launch_tables_to_half(o->d.tab32, const_cast<uint16_t *>(o->d.tab16), (int64_t)nt, st);
   if (e == cudaSuccess) e = launch_build_umma(o->d, const_cast<uint8_t *>(o->d.umma), st);
   if (e != cudaSuccess) return cuda_fail(e, "refresh reduced-precision copies");
+  return LSNIF_OK;
+}
+
+// ---- FP8 network (LSNIF_FP8_FUSED) -------------------------------------------
+
+// The power of two s with 448/2 < s m <= 448 (1 when m is 0).
+static double e4m3_scale(double m) {
+  if (!(m > 0)) return 1.0;
+  int e = 0;
+  std::frexp(448.0 / m, &e);
+  return std::ldexp(1.0, e - 1);
+}
+
+// Nearest FP8 E4M3 code (1 sign, 4 exponent bits with bias 7, 3 mantissa
+// bits; normals from 2^-6, subnormals in steps of 2^-9, largest finite 448),
+// ties to even, saturating.
+static uint8_t to_e4m3(double x) {
+  const uint8_t sign = std::signbit(x) ? 0x80 : 0x00;
+  double a = std::fabs(x);
+  if (!(a == a)) return 0x7F;
+  if (a >= 448.0) return sign | 0x7E;
+  int e = 0;
+  std::frexp(a, &e);  // a = f 2^e, 0.5 <= f < 1
+  const int E = std::max(e - 1, -6);
+  const double q = std::ldexp(1.0, E - 3);
+  double k = std::nearbyint(a / q);  // default rounding: to nearest, ties to even
+  double r = k * q;
+  if (r >= 448.0) return sign | 0x7E;
+  if (r == 0.0) return sign;
+  int er = 0;
+  std::frexp(r, &er);
+  const int Er = er - 1;
+  if (Er < -6) return sign | (uint8_t)(r / std::ldexp(1.0, -9));           // subnormal: m 2^-9
+  const int m = (int)(r / std::ldexp(1.0, Er - 3)) - 8;                      // 1.m x 2^Er
+  return sign | (uint8_t)(((Er + 7) << 3) | m);
+}
+
+// offset of (row n, column k) in a K-major core-matrix tile of E4M3 bytes
+// with K columns
+static size_t core8(int n, int k, int K) {
+  return ((size_t)(n >> 3) * (K / 16) + (k >> 4)) * 128 + (n & 7) * 16 + (k & 15);
+}
+
+int lsnif::ensure_fp8(lsnif_ctx *ctx, Object *o, cudaStream_t st) {
+  DevObject &d = o->d;
+  if (!fused8_supported(d))
+    return fail(LSNIF_ERR_UNSUPPORTED, "FP8 query: object %u has no FP8 kernel shape (F in {2,4}, width 64/128, "
+                                       "L*F a multiple of 16, L <= 16)", o->handle);
+  if (!o->fp8_stale && d.w0_8) return LSNIF_OK;
+  const lsnif_config &c = o->cfg;
+  const int W = c.width, n_in = d.n_in, nh = c.n_hidden, nop = d.n_out_pad, n_out = d.n_out;
+  const int CHK = 2 * c.L * c.F, chunks = c.H / 2;
+  const size_t hid_bytes = (size_t)(nh - 1) * W * W, out_bytes = (size_t)nop * W;
+  const size_t bias_off = (hid_bytes + out_bytes + 15) & ~size_t(15);
+  const size_t n_bias = (size_t)nh * W + nop;
+  const size_t scale_off = bias_off + 4 * n_bias;
+  const size_t blob_bytes = (scale_off + 4 * 2 * (nh + 1) + 15) & ~size_t(15);
+  int rc;
+  if (!d.w0_8) {
+    void *p = nullptr;
+    if ((rc = obj_alloc(ctx, o, (size_t)W * n_in, &p, "FP8 first layer"))) return rc;
+    d.w0_8 = (const uint8_t *)p;
+    if ((rc = obj_alloc(ctx, o, blob_bytes, &p, "FP8 network"))) return rc;
+    d.blob8 = (const uint8_t *)p;
+  }
+  // the parameters as they are now (training may have changed them)
+  std::vector<float> mlp(o->n_params_mlp);
+  uint32_t *dmax = nullptr;
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) e = cudaMalloc(&dmax, 4);
+  if (e == cudaSuccess)
+    e = launch_max_abs_half(d.tab16, ((int64_t)c.L << c.log2_T) * c.F, dmax, st);
+  uint32_t mbits = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&mbits, dmax, 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(mlp.data(), d.mlp32, 4 * mlp.size(), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (dmax) cudaFree(dmax);
+  if (e != cudaSuccess) return cuda_fail(e, "FP8 network: read parameters");
+  float tmax;
+  memcpy(&tmax, &mbits, 4);
+  // layers: (fan_in, fan_out) = n_in -> W (x nh) -> n_out
+  std::vector<int> fi(nh + 1), fo(nh + 1);
+  for (int l = 0; l <= nh; ++l) {
+    fi[l] = l == 0 ? n_in : W;
+    fo[l] = l == nh ? n_out : W;
+  }
+  std::vector<size_t> woff(nh + 1);
+  size_t off = 0;
+  for (int l = 0; l <= nh; ++l) {
+    woff[l] = off;
+    off += (size_t)fi[l] * fo[l] + fo[l];
+  }
+  std::vector<double> s_in(nh + 1), w_sc(nh + 1);
+  double M = tmax;
+  for (int l = 0; l <= nh; ++l) {
+    const float *Wl = mlp.data() + woff[l], *bl = Wl + (size_t)fi[l] * fo[l];
+    double wmax = 0.0, next = 0.0;
+    for (int j = 0; j < fo[l]; ++j) {
+      double ss = 0.0;
+      for (int i = 0; i < fi[l]; ++i) {
+        const double w = Wl[(size_t)j * fi[l] + i];
+        wmax = std::max(wmax, std::fabs(w));
+        ss += w * w;
+      }
+      next = std::max(next, std::sqrt(ss) * M + std::fabs((double)bl[j]));
+    }
+    s_in[l] = e4m3_scale(M);
+    w_sc[l] = e4m3_scale(wmax);
+    M = next;
+  }
+  // first layer, chunk-major: chunk s holds columns [s CHK, (s+1) CHK)
+  std::vector<uint8_t> w0((size_t)W * n_in, 0);
+  for (int s2 = 0; s2 < chunks; ++s2)
+    for (int n = 0; n < W; ++n)
+      for (int k = 0; k < CHK; ++k)
+        w0[(size_t)s2 * W * CHK + core8(n, k, CHK)] =
+            to_e4m3((double)mlp[woff[0] + (size_t)n * n_in + (size_t)s2 * CHK + k] * w_sc[0]);
+  // hidden layers 1.., then the output layer (rows beyond n_out zero), then FP32
+  std::vector<uint8_t> blob(blob_bytes, 0);
+  size_t p8 = 0;
+  for (int l = 1; l <= nh; ++l) {
+    const int rows = l == nh ? nop : W;
+    for (int n = 0; n < rows; ++n)
+      for (int k = 0; k < W; ++k)
+        blob[p8 + core8(n, k, W)] =
+            n < fo[l] ? to_e4m3((double)mlp[woff[l] + (size_t)n * W + k] * w_sc[l]) : (uint8_t)0;
+    p8 += (size_t)rows * W;
+  }
+  float *fb = reinterpret_cast<float *>(blob.data() + bias_off);
+  for (int l = 0; l <= nh; ++l)
+    for (int j = 0; j < (l == nh ? nop : W); ++j)
+      fb[(size_t)l * W + j] = j < fo[l] ? mlp[woff[l] + (size_t)fi[l] * fo[l] + j] : 0.f;
+  float *fs = reinterpret_cast<float *>(blob.data() + scale_off);
+  for (int l = 0; l <= nh; ++l) {
+    fs[l] = (float)(1.0 / (s_in[l] * w_sc[l]));
+    fs[nh + 1 + l] = (float)s_in[l];
+  }
+  e = cudaMemcpy((void *)d.w0_8, w0.data(), w0.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy((void *)d.blob8, blob.data(), blob.size(), cudaMemcpyHostToDevice);
+  d.blob8_bytes = (uint32_t)blob_bytes;
+  d.blob8_bias_off = (uint32_t)bias_off;
+  d.blob8_scale_off = (uint32_t)scale_off;
+  if (e == cudaSuccess) e = cudaMemcpy(ctx->d_objs + o->slot, &d, sizeof d, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(e, "FP8 network: upload");
+  o->fp8_stale = false;
   return LSNIF_OK;
 }
 

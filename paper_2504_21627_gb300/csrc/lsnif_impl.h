@@ -37,6 +37,12 @@ struct DevObject {
   const uint32_t *brick;   // bit (bz*nb + by)*nb + bx: brick holds an occupied voxel
   const uint32_t *brick2;  // the same for bricks twice as wide
   int32_t log2B;           // bricks are 2^log2B voxels wide, nb = V >> log2B per axis
+  // FP8 network (built on the first FP8 query after a parameter change):
+  // first layer chunk-major (W x 2LF E4M3 bytes per chunk, core-matrix
+  // layout); hidden and output layers (E4M3) then FP32 biases and scales
+  const uint8_t *w0_8;
+  const uint8_t *blob8;
+  uint32_t blob8_bytes, blob8_bias_off, blob8_scale_off;
 
   int32_t L, F, log2T;
   uint32_t mask;
@@ -135,6 +141,10 @@ cudaError_t launch_tables_to_half(const float *src, uint16_t *dst, int64_t n, cu
 // ---- fused tensor-core path (fused.cu) ----
 // Returns cudaErrorNotSupported when the object's shape is outside the
 // fused kernel's instantiations.
+bool fused8_supported(const DevObject &host_obj);
+size_t fused8_smem_bytes(const DevObject &host_obj, int H_max);
+cudaError_t launch_fused8(const QueryLaunch &q, const DevObject &host_obj, int *launches);
+cudaError_t launch_max_abs_half(const uint16_t *v, int64_t n, uint32_t *out_bits, cudaStream_t st);
 bool fused_supported(const DevObject &host_obj);
 size_t fused_smem_bytes(const DevObject &host_obj, int H_max);  // smallest ring; H_max: query's largest H
 cudaError_t launch_fused(const QueryLaunch &q, const DevObject &host_obj, int variant, int *launches);

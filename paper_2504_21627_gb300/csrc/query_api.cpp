@@ -137,16 +137,43 @@ static int check_rays(const lsnif_rays *r, const lsnif_hits *h) {
   return LSNIF_OK;
 }
 
+// Build (or refresh) the FP8 networks of every object the rays may name. It
+// synchronises `st` when a network is stale, so it runs before any capture.
+static int ensure_fp8_for(lsnif_ctx *ctx, const lsnif_rays *r, cudaStream_t st) {
+  int rc;
+  if (!r->obj) {
+    Object *o = find_object(ctx, r->single_obj);
+    if (!o) return fail(LSNIF_ERR_BAD_HANDLE, "query: bad object handle %u", r->single_obj);
+    return ensure_fp8(ctx, o, st);
+  }
+  for (int s = 0; s < ctx->n_slots_used; ++s)
+    if (ctx->slots[s] && (rc = ensure_fp8(ctx, ctx->slots[s], st))) return rc;
+  return LSNIF_OK;
+}
+
 int lsnif::run_query(lsnif_ctx *ctx, Workspace *ws, const lsnif_rays *r, lsnif_hits *h, int precision,
                      cudaStream_t st, bool profile) {
   int rc = check_rays(r, h);
   if (rc) return rc;
-  if (precision != LSNIF_FP32_PLAIN && precision != LSNIF_BF16_FUSED)
+  if (precision != LSNIF_FP32_PLAIN && precision != LSNIF_BF16_FUSED && precision != LSNIF_FP8_FUSED)
     return fail(LSNIF_ERR_INVALID_ARG, "query: unknown precision %d", precision);
   if (r->n == 0) return LSNIF_OK;
   Shape sh;
   if ((rc = shape_of(ctx, r, &sh))) return rc;
+  if (precision == LSNIF_FP8_FUSED) {
+    if ((rc = ensure_fp8_for(ctx, r, st))) return rc;
+    if ((rc = shape_of(ctx, r, &(sh = Shape{})))) return rc;
+  }
   DevObject rep = sh.rep->d;
+  if (precision == LSNIF_FP8_FUSED) {
+    uint32_t b8 = 0;
+    for (int s = 0; s < ctx->n_slots_used; ++s)
+      if (ctx->slots[s]) b8 = std::max(b8, ctx->slots[s]->d.blob8_bytes);
+    rep.blob8_bytes = std::max(rep.blob8_bytes, r->obj ? b8 : 0u);
+    if (sh.mixed_fused || !fused8_supported(rep) || fused8_smem_bytes(rep, sh.H) > 232448)
+      return fail(LSNIF_ERR_UNSUPPORTED, "query: the fused FP8 path needs F in {2,4}, width 64/128, L <= 16, "
+                                         "L*F a multiple of 16 and one shape for all objects");
+  }
   if (precision == LSNIF_BF16_FUSED) {
     rep.umma_bytes = sh.umma_max;
     if (sh.mixed_fused || !fused_supported(rep) || fused_smem_bytes(rep, sh.H) > 232448)
@@ -176,6 +203,7 @@ int lsnif::run_query(lsnif_ctx *ctx, Workspace *ws, const lsnif_rays *r, lsnif_h
   if (profile) cudaEventRecord(ctx->ev[2], st);
   if (e == cudaSuccess) {
     if (precision == LSNIF_FP32_PLAIN) e = launch_plain_tail(q, ws->cap_nin, kChunkTiles, &launches);
+    else if (precision == LSNIF_FP8_FUSED) e = launch_fused8(q, rep, &launches);
     else e = launch_fused(q, rep, ctx->fused_variant, &launches);
   }
   if (profile) {
@@ -204,6 +232,7 @@ static int query_graph(lsnif_ctx *ctx, const lsnif_rays *r, lsnif_hits *h, int p
   int rc = check_rays(r, h);
   if (rc) return rc;
   if (r->n == 0) return LSNIF_OK;
+  if (precision == LSNIF_FP8_FUSED && (rc = ensure_fp8_for(ctx, r, st))) return rc;
   Shape sh;
   if ((rc = shape_of(ctx, r, &sh))) return rc;
   const int n_in = precision == LSNIF_FP32_PLAIN ? sh.n_in : 0;

@@ -32,6 +32,7 @@ struct Object {
   int64_t tb_batch = 0;   // rays the buffers are sized for
   int64_t step = 0;
   std::vector<void *> train_allocs;
+  bool fp8_stale = true;   // the FP8 network no longer matches the parameters
 };
 
 // Scratch of one query stream. Grows on demand; freed with the context.
@@ -99,6 +100,7 @@ void free_object(lsnif_ctx *ctx, Object *o);
 size_t blob_size(const Object *o);
 int upload_params(lsnif_ctx *ctx, Object *o, const float *tables, const float *mlp);
 int refresh_copies(lsnif_ctx *ctx, Object *o, cudaStream_t st);
+int ensure_fp8(lsnif_ctx *ctx, Object *o, cudaStream_t st);
 
 // query
 size_t workspace_bytes(int64_t n, int H, int n_slots, int n_in);

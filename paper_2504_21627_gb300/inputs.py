@@ -402,18 +402,27 @@ def batched_objects(n_obj: int = 64, seed: int = 3, total_rays: int = 16 << 20):
     return out
 
 
-def scene_objects(n_unique: int = 8, seed: int = 5):
+def cfg_stress_object(log2_T: int = 21) -> Config:
+    """Per-object configuration of the path-tracing stress scene: 128^3
+    voxels, 16 levels x 4 features, 2^21 entries per level, resolutions
+    16..2048, MLP 4 x 128, 4 materials."""
+    return Config(V=128, H=18, L=16, F=4, log2_T=log2_T, N_min=16, N_max=2048, n_hidden=4,
+                  width=128, n_mat=4)
+
+
+def scene_objects(n_unique: int = 8, seed: int = 5, features: int = 2, width: int = 64):
     """The instanced scene's unique objects: seeded noise icospheres or tori
-    of 50k..1M triangles (log-uniform), V = 128, L = 16, F = 2, T = 2^21,
-    4 x 64 network. Returns [(mesh, cfg)]."""
+    of 50k..1M triangles (log-uniform), V = 128, L = 16, T = 2^21, F
+    features per level and a 4 x width network (F = 4 and width 128 is the
+    stress configuration). Returns [(mesh, cfg)]."""
     g = rng(seed)
     out = []
     for i in range(n_unique):
         tris = int(math.exp(g.uniform(math.log(50000), math.log(1000000))))
         mesh = noise_icosphere(seed + 200 + i, tris, n_mat=4) if i % 2 == 0 else \
             noise_torus_tris(seed + 200 + i, tris, n_mat=4)
-        cfg = Config(V=128, H=18, L=16, F=2, log2_T=21, N_min=16, N_max=2048, n_hidden=4, width=64, n_mat=4,
-                     seed=seed + i)
+        cfg = Config(V=128, H=18, L=16, F=features, log2_T=21, N_min=16, N_max=2048, n_hidden=4, width=width,
+                     n_mat=4, seed=seed + i)
         out.append((mesh, cfg))
     return out
 

@@ -104,11 +104,14 @@ def scene(ctx):
     return dict(objs=objs, handles=handles, boxes=boxes, insts=insts)
 
 
-@pytest.mark.parametrize("prec", [lsnif.FP32_PLAIN, lsnif.BF16_FUSED])
+ORACLE_PRECISION = {lsnif.FP32_PLAIN: "f64", lsnif.BF16_FUSED: "bf16", lsnif.FP8_FUSED: "fp8"}
+
+
+@pytest.mark.parametrize("prec", [lsnif.FP32_PLAIN, lsnif.BF16_FUSED, lsnif.FP8_FUSED])
 def test_instanced_scene_matches_oracle(ctx, scene, prec):
     rays = _aim(scene["insts"], 6000, 5, scene["boxes"])
     got = _gpu_scene(ctx, rays, scene["insts"], scene["handles"], prec)
-    ref = O.scene_query(scene["objs"], scene["insts"], rays, "bf16" if prec == lsnif.BF16_FUSED else "f64")
+    ref = O.scene_query(scene["objs"], scene["insts"], rays, ORACLE_PRECISION[prec])
     ok = ~ref["near"]
     assert ok.mean() > 0.8
     agree = got["hit"][ok] == ref["hit"][ok]

@@ -200,5 +200,20 @@ def test_training_learns_and_beats_voxel_only(ctx):
           f"visibility accuracy: network {acc_net:.4f}, voxel-only {acc_vox:.4f}; losses {losses}")
     assert err_net < err_vox
     assert acc_net > acc_vox
+    # reduced precision on the trained network, against its FP32 evaluation
+    ref = ctx.query_rays(_cuda(test), obj=h, precision=lsnif.FP32_PLAIN)
+    torch.cuda.synchronize()
+    r_hit, r_t, r_mat = ref.hit.cpu().numpy().astype(bool), ref.t.cpu().numpy(), ref.mat.cpu().numpy()
+    diag = float(np.linalg.norm(ext))
+    for name, prec in (("BF16", lsnif.BF16_FUSED), ("FP8", lsnif.FP8_FUSED)):
+        q = ctx.query_rays(_cuda(test), obj=h, precision=prec)
+        torch.cuda.synchronize()
+        q_hit, q_t, q_mat = q.hit.cpu().numpy().astype(bool), q.t.cpu().numpy(), q.mat.cpu().numpy()
+        both = q_hit & r_hit
+        vis = (q_hit != r_hit).mean()
+        t_err = np.quantile(np.abs(q_t[both] - r_t[both]), 0.99) / diag
+        mat_ok = (q_mat[both] == r_mat[both]).mean()
+        print(f"{name} vs FP32 on the trained network: visibility mismatch {vis:.4%}, hit-t error p99 "
+              f"{t_err:.2e} of the diagonal, material agreement {mat_ok:.4%}")
     del orc_occ
     ctx.unload_object(h)
