@@ -542,6 +542,7 @@ def main():
         ms16, prof16, wall16 = timed(lsnif.BF16_FUSED, args.steps, args.warmup, profile=True)
     clocks = clk.summary()
     ms32, prof32, wall32 = timed(lsnif.FP32_PLAIN, max(3, args.steps // 2), 3, profile=True)
+    ms8, prof8, wall8 = timed(lsnif.FP8_FUSED, max(3, args.steps // 2), 3, profile=True)
 
     from paper_2504_21627_gb300 import replicas
 
@@ -550,6 +551,7 @@ def main():
 
     mean16, _, value = replicas.aggregate(float(ms16.mean()), n)
     mean32, _, v32 = replicas.aggregate(float(ms32.mean()), n)
+    mean8, _, v8 = replicas.aggregate(float(ms8.mean()), n)
 
     # ---- end to end through the host-buffer C-ABI call ----
     host_rays = torch.from_numpy(rays_np).pin_memory()
@@ -592,6 +594,8 @@ def main():
         "latency_ms": {"bf16_p50": float(np.percentile(ms16, 50)), "bf16_p99": float(np.percentile(ms16, 99)),
                        "fp32_p50": float(np.percentile(ms32, 50)), "fp32_p99": float(np.percentile(ms32, 99))},
         "fp32_plain": {"value": v32, "unit": "Mrays/s", "ms_per_step": mean32},
+        "fp8_fused": {"value": v8, "unit": "Mrays/s", "ms_per_step": mean8,
+                      "fused_ms": float(np.mean([q.ms_mlp for q in prof8]))},
         "rays": {"live": int(live), "live_frac": live / n, "points": int(pts),
                  "mean_points_per_live_ray": pts / max(live, 1)},
         "stages_ms_bf16": {"trace": float(np.mean([q.ms_trace for q in prof16])),
@@ -610,7 +614,7 @@ def main():
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
-        "wall_s": {"bf16_timed": wall16, "fp32_timed": wall32},
+        "wall_s": {"bf16_timed": wall16, "fp32_timed": wall32, "fp8_timed": wall8},
     }
     if rank == 0 and not args.no_cpu_baseline:
         rate, cores, dt = oracle_rate(cfg, mesh, params, rays_np, args.cpu_sample)

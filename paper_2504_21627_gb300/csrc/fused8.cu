@@ -41,13 +41,26 @@ __device__ __forceinline__ void mma_e4m3(uint32_t tmem, uint64_t a, uint64_t b, 
       : "memory");
 }
 
+// two values -> two E4M3 bytes (lo in the low byte), round to nearest even,
+// saturating to +-448; one cvt instruction converts the pair
+__device__ __forceinline__ uint32_t e4m3x2(float lo, float hi) {
+  uint16_t r;
+  asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(r) : "f"(hi), "f"(lo));
+  return r;
+}
+
 // four values -> four E4M3 bytes, the first in the lowest byte
 __device__ __forceinline__ uint32_t pack_e4m3(float a, float b, float c, float d) {
-  const uint32_t x0 = __nv_cvt_float_to_fp8(a, __NV_SATFINITE, __NV_E4M3);
-  const uint32_t x1 = __nv_cvt_float_to_fp8(b, __NV_SATFINITE, __NV_E4M3);
-  const uint32_t x2 = __nv_cvt_float_to_fp8(c, __NV_SATFINITE, __NV_E4M3);
-  const uint32_t x3 = __nv_cvt_float_to_fp8(d, __NV_SATFINITE, __NV_E4M3);
-  return x0 | (x1 << 8) | (x2 << 16) | (x3 << 24);
+  return e4m3x2(a, b) | (e4m3x2(c, d) << 16);
+}
+
+// 1-D bulk copy global -> shared, completing on an mbarrier (sizes and both
+// addresses multiples of 16 bytes)
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t mbar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(mbar)
+               : "memory");
 }
 
 struct Fused8Args {
@@ -65,8 +78,9 @@ struct Layout8 {
 };
 
 // mbarriers: full[kNBufMax], empty[kNBufMax], tile_ready[2], acc_full[2],
-// acc_empty[2], layer_done, fin[2]
-constexpr int kNumBars8 = 2 * kNBufMax + 2 + 2 + 2 + 1 + 2;
+// acc_empty[2], layer_done, fin[2], wfull[kNBufMax] (first-layer weights
+// of a ring slot landed)
+constexpr int kNumBars8 = 2 * kNBufMax + 2 + 2 + 2 + 1 + 2 + kNBufMax;
 
 __host__ __device__ inline Layout8 make_layout8(uint32_t blob_bytes, int F, int W, int nbuf, int list_chunks) {
   Layout8 o{};
@@ -99,7 +113,7 @@ struct Smem8 {
   uint16_t *list;
   uint32_t *wsum;
   TileInfo *info;
-  uint64_t *full, *empty, *ready, *accf, *acce, *layer, *fin;
+  uint64_t *full, *empty, *ready, *accf, *acce, *layer, *fin, *wfull;
   uint32_t *tmem;
   int32_t *misc;
   volatile int *abort_flag;
@@ -128,6 +142,7 @@ __device__ __forceinline__ Smem8 carve8(const Fused8Args &a, uint8_t *base) {
   S.acce = S.ready + 4;
   S.layer = S.ready + 6;
   S.fin = S.ready + 7;
+  S.wfull = S.ready + 9;
   S.tmem = reinterpret_cast<uint32_t *>(base + l.tmem);
   S.misc = reinterpret_cast<int32_t *>(base + l.misc);
   S.abort_flag = reinterpret_cast<volatile int *>(S.misc + 4);
@@ -186,12 +201,16 @@ __device__ __noinline__ void mma8_role(const Fused8Args *ap, uint8_t *base, uint
         ok = false;
         break;
       }
-      const uint4 *src = reinterpret_cast<const uint4 *>(ob.w0_8 + (size_t)s * slice);
-      uint4 *dst = reinterpret_cast<uint4 *>(slot + S.slot_w);
-      for (uint32_t k = lane; k < slice / 16; k += 32) dst[k] = __ldg(src + k);
-      fence_async_smem();
-      __syncwarp();
-      if (!mbar_wait(su32(&S.full[buf]), (uint32_t)(use & 1), S.abort_flag)) {
+      // the weight slice travels by bulk copy while the gather warps fill
+      // the A tile of the same slot
+      if (lane == 0) bulk_g2s(su32(slot + S.slot_w), ob.w0_8 + (size_t)s * slice, slice, su32(&S.wfull[buf]));
+      const bool got_a = mbar_wait(su32(&S.full[buf]), (uint32_t)(use & 1), S.abort_flag);
+      // the copy is waited for even after an abort: it must land before the
+      // shared memory is released
+      const bool got_w = got_a ? mbar_wait(su32(&S.wfull[buf]), (uint32_t)(use & 1), S.abort_flag)
+                               : mbar_wait_teardown(su32(&S.wfull[buf]), (uint32_t)(use & 1));
+      if (!got_a || !got_w) {
+        if (!got_w) *S.abort_flag = 1;
         ok = false;
         break;
       }
@@ -457,6 +476,7 @@ __global__ void __launch_bounds__((NG + 1 + kEpiWarps) * 32, 1) fused8_kernel(co
     for (int b = 0; b < nbuf; ++b) {
       mbar_init(su32(&S.full[b]), kGatherThreads);
       mbar_init(su32(&S.empty[b]), 1);
+      mbar_init(su32(&S.wfull[b]), 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(su32(&S.ready[b]), 1);
@@ -465,6 +485,8 @@ __global__ void __launch_bounds__((NG + 1 + kEpiWarps) * 32, 1) fused8_kernel(co
       mbar_init(su32(&S.fin[b]), 1);
     }
     mbar_init(su32(S.layer), 1);
+    // make the initialised barriers visible to the bulk-copy unit
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     *S.abort_flag = 0;
   }
   if (warp == 0) {
@@ -536,23 +558,23 @@ __global__ void __launch_bounds__((NG + 1 + kEpiWarps) * 32, 1) fused8_kernel(co
             const float *P = q.s.pts + ((size_t)ray * Hs + 2 * s + j) * 3;
             const float3 p = make_float3(P[0], P[1], P[2]);
             // FP32 interpolation of the FP16 entries: the E4M3 rounding that
-            // follows then sees the feature to FP32 accuracy
-            float x[16];
+            // follows then sees the feature to FP32 accuracy. Each pair of
+            // levels is scaled and packed at once (2F bytes).
+            uint32_t wv[4];
 #pragma unroll
             for (int u0 = 0; u0 < LPG; u0 += 2) {
               const int l = g * LPG + u0;
               float f[2][F];
               encode_levels_f16<F, 2>(reinterpret_cast<const __half *>(tab) + (size_t)l * lstride, lstride * 2, mask,
                                       p, S.res + l, f);
-#pragma unroll
-              for (int u = 0; u < 2; ++u)
-#pragma unroll
-                for (int cc = 0; cc < F; ++cc) x[(u0 + u) * F + cc] = f[u][cc];
+              if constexpr (F == 4) {
+                wv[u0] = pack_e4m3(f[0][0] * s0, f[0][1] * s0, f[0][2] * s0, f[0][3] * s0);
+                wv[u0 + 1] = pack_e4m3(f[1][0] * s0, f[1][1] * s0, f[1][2] * s0, f[1][3] * s0);
+              } else {
+                wv[u0 / 2] = pack_e4m3(f[0][0] * s0, f[0][1] * s0, f[1][0] * s0, f[1][1] * s0);
+              }
             }
-#pragma unroll
-            for (int u = 0; u < 16; ++u) x[u] *= s0;
-            const uint4 outv = make_uint4(pack_e4m3(x[0], x[1], x[2], x[3]), pack_e4m3(x[4], x[5], x[6], x[7]),
-                                          pack_e4m3(x[8], x[9], x[10], x[11]), pack_e4m3(x[12], x[13], x[14], x[15]));
+            const uint4 outv = make_uint4(wv[0], wv[1], wv[2], wv[3]);
             *reinterpret_cast<uint4 *>(A + core_off(r, j * G + g, a_sbo)) = outv;
           }
         }
