@@ -385,6 +385,53 @@ def bench_train(args):
     print(json.dumps(out))
 
 
+def bench_stress1(args):
+    """One object of the stress scene's network shape (L 16, F 4, T 2^21,
+    1152-128x4-12) on the torus workload's mesh and camera: FP8 fused and
+    FP32 plain queries of side x side primary rays, with the FP8 kernel's
+    stage times. A single-object case of the stress network, small enough
+    for full profiler captures at side 1024."""
+    import torch
+    from paper_2504_21627_gb300 import lsnif
+    cfg = I.cfg_stress_object()
+    mesh = I.noise_torus(seed=2)
+    params = I.random_params(cfg, seed=5, table_range=0.05, bias_range=0.1)
+    rays = torch.from_numpy(I.rays_pinhole(I.seeded_camera(2, width=args.side, height=args.side))).cuda()
+    n = rays.shape[1]
+    ctx = lsnif.Context(0)
+    obj = ctx.load_object(mesh, cfg, tables=params.tables, mlp=params.packed_mlp())
+    if args.variant8 is not None:
+        ctx.set_variant8(args.variant8)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    out = {"workload": "stress1", "network": "L=16 F=4 T=2^21, 1152-128x4-12", "rays": n}
+    for name, prec, steps in (("fp8", lsnif.FP8_FUSED, args.steps), ("fp32", lsnif.FP32_PLAIN, 3)):
+        res = ctx.query_rays(rays, obj=obj, precision=prec)
+        for _ in range(args.warmup):
+            ctx.query_rays(rays, obj=obj, precision=prec, out=res)
+        ctx.set_profiling(True)
+        ms, prof = [], []
+        for _ in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.query_rays(rays, obj=obj, precision=prec, out=res)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            prof.append(ctx.last_profile())
+        ctx.set_profiling(False)
+        ctx.check()
+        p = prof[-1]
+        out[name] = {"mrays_s": n / (np.mean(ms) / 1e3) / 1e6, "ms_per_step": float(np.mean(ms)),
+                     "stages_ms": {"trace": float(np.mean([q.ms_trace for q in prof])),
+                                   "group": float(np.mean([q.ms_group for q in prof])),
+                                   "network": float(np.mean([q.ms_mlp for q in prof]))},
+                     "live": int(p.n_live), "points": int(p.n_points)}
+    print(json.dumps(out))
+    ctx.close()
+
+
 def bench_scene(args):
     """Path-tracer-shaped stress: 32 instances of 8 unique objects (50k..1M
     triangles, V 128, L 16, F 4, T 2^21, 4 x 128 network; `--scene-net
@@ -399,15 +446,19 @@ def bench_scene(args):
     from paper_2504_21627_gb300 import lsnif
     stress = args.scene_net == "stress"
     spec = I.scene_objects(features=4, width=128) if stress else I.scene_objects()
+    spec = spec[:args.scene_objects]
     ctx = lsnif.Context(0)
     handles = []
     for i, (mesh, cfg) in enumerate(spec):
         p = I.random_params(cfg, seed=3000 + i, table_range=0.05, bias_range=0.1)
         p.weights[-1][1][0] = 1.0   # occupancy logit biased towards hits, so bounces continue
         handles.append(ctx.load_object(mesh, cfg, tables=p.tables, mlp=p.packed_mlp()))
-    insts = [(handles[o], A, b) for o, A, b in I.seeded_instances(32, len(spec), seed=9, spread=10.0)]
+    if args.variant8 is not None:
+        ctx.set_variant8(args.variant8)
+    insts = [(handles[o], A, b) for o, A, b in I.seeded_instances(args.scene_instances, len(spec), seed=9,
+                                                                   spread=10.0)]
     cam = I.seeded_camera(4, radius=14.0, width=args.scene_width, height=args.scene_height, fov_deg=50.0)
-    rays0 = torch.from_numpy(I.camera_rays_spp(cam, 4, seed=10)).cuda()
+    rays0 = torch.from_numpy(I.camera_rays_spp(cam, args.scene_spp, seed=10)).cuda()
     n = rays0.shape[1]
     gen = torch.Generator("cuda").manual_seed(11)
     us = [torch.rand((n, 2), device="cuda", generator=gen) for _ in range(3)]
@@ -463,12 +514,16 @@ def main():
     ap.add_argument("--variant", type=int, default=None,
                     help="fused-kernel variant to time instead of the autotuner's choice")
     ap.add_argument("--side", type=int, default=2048, help="image side; below 2048 only for profiling captures")
-    ap.add_argument("--workload", default="torus4m", choices=["torus4m", "batched", "serving", "train", "scene"],
+    ap.add_argument("--workload", default="torus4m", choices=["torus4m", "batched", "serving", "train", "scene", "stress1"],
                     help="torus4m is the headline; the others print their own line")
     ap.add_argument("--requests", type=int, default=200)
     ap.add_argument("--scene-width", type=int, default=1920)
     ap.add_argument("--scene-height", type=int, default=1080)
     ap.add_argument("--scene-net", default="stress", choices=["stress", "small"])
+    ap.add_argument("--variant8", type=int, default=None, help="FP8 fused-kernel variant for --workload scene")
+    ap.add_argument("--scene-objects", type=int, default=8, help="unique objects (below 8 only for profiling)")
+    ap.add_argument("--scene-instances", type=int, default=32)
+    ap.add_argument("--scene-spp", type=int, default=4)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -481,6 +536,8 @@ def main():
         return bench_train(args)
     if args.workload == "scene":
         return bench_scene(args)
+    if args.workload == "stress1":
+        return bench_stress1(args)
 
     import torch
     import torch.distributed as dist

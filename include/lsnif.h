@@ -378,6 +378,18 @@ LSNIF_API int lsnif_variant_shape(int v, int *threads, int *levels);
 /* Use variant v for every later BF16 query of the context. */
 LSNIF_API int lsnif_set_variant(lsnif_ctx *ctx, int v);
 
+/* The FP8 fused kernel's shapes (LSNIF_FP8_FUSED with F = 4; F = 2 always
+ * runs variant 0): *threads = gather threads per CTA, *levels = hash levels
+ * whose corner loads one gather item issues together. Fewer levels per
+ * batch need fewer registers, which lets more gather warps share an SM.
+ * Errors: INVALID_ARG for v out of range. All variants compute identical
+ * results. */
+LSNIF_API int lsnif_variant8_count(void);
+LSNIF_API int lsnif_variant8_shape(int v, int *threads, int *levels);
+
+/* Use FP8 variant v for every later LSNIF_FP8_FUSED query of the context. */
+LSNIF_API int lsnif_set_variant8(lsnif_ctx *ctx, int v);
+
 /* Traversal kernel for later queries: 0 = one ray per thread, voxel by
  * voxel; 1 = persistent lanes (a lane whose ray finished takes the next ray
  * from a global counter) that cross bricks without occupied voxels in one

@@ -458,7 +458,7 @@ __device__ __noinline__ void epilogue8_role(const Fused8Args *ap, uint8_t *base,
 // ---------------------------------------------------------------------------
 // the kernel: setup, gather warps inline, the other roles as functions
 // ---------------------------------------------------------------------------
-template <int F, int W, int NG>
+template <int F, int W, int NG, int NL>
 __global__ void __launch_bounds__((NG + 1 + kEpiWarps) * 32, 1) fused8_kernel(const __grid_constant__ Fused8Args a) {
   constexpr int kGatherThreads = NG * 32;
   constexpr int kMmaWarp = NG;
@@ -561,17 +561,20 @@ __global__ void __launch_bounds__((NG + 1 + kEpiWarps) * 32, 1) fused8_kernel(co
             // follows then sees the feature to FP32 accuracy. Each pair of
             // levels is scaled and packed at once (2F bytes).
             uint32_t wv[4];
+            static_assert(F == 4 || NL % 2 == 0, "F = 2 packs levels in pairs");
 #pragma unroll
-            for (int u0 = 0; u0 < LPG; u0 += 2) {
+            for (int u0 = 0; u0 < LPG; u0 += NL) {
               const int l = g * LPG + u0;
-              float f[2][F];
-              encode_levels_f16<F, 2>(reinterpret_cast<const __half *>(tab) + (size_t)l * lstride, lstride * 2, mask,
-                                      p, S.res + l, f);
-              if constexpr (F == 4) {
-                wv[u0] = pack_e4m3(f[0][0] * s0, f[0][1] * s0, f[0][2] * s0, f[0][3] * s0);
-                wv[u0 + 1] = pack_e4m3(f[1][0] * s0, f[1][1] * s0, f[1][2] * s0, f[1][3] * s0);
-              } else {
-                wv[u0 / 2] = pack_e4m3(f[0][0] * s0, f[0][1] * s0, f[1][0] * s0, f[1][1] * s0);
+              float f[NL][F];
+              encode_levels_f16<F, NL>(reinterpret_cast<const __half *>(tab) + (size_t)l * lstride, lstride * 2,
+                                       mask, p, S.res + l, f);
+#pragma unroll
+              for (int u = 0; u < NL; ++u) {
+                if constexpr (F == 4) {
+                  wv[u0 + u] = pack_e4m3(f[u][0] * s0, f[u][1] * s0, f[u][2] * s0, f[u][3] * s0);
+                } else if (u % 2 == 0) {
+                  wv[(u0 + u) / 2] = pack_e4m3(f[u][0] * s0, f[u][1] * s0, f[u + 1][0] * s0, f[u + 1][1] * s0);
+                }
               }
             }
             const uint4 outv = make_uint4(wv[0], wv[1], wv[2], wv[3]);
@@ -663,23 +666,47 @@ size_t fused8_smem_bytes(const DevObject &h, int H_max) {
   return make_layout8((h.blob8_bytes + 15u) & ~15u, h.F, h.width, 2, std::max(H_max, h.H) / 2).total;
 }
 
-template <int F, int W>
-static cudaError_t launch8_one(const Fused8Args &a, size_t smem, cudaStream_t st) {
-  constexpr int NG = 11;
+// kernel shapes: gather warps x levels per corner-load batch (F = 4; F = 2
+// always runs the first)
+struct Variant8 {
+  int ng, nl;
+};
+constexpr Variant8 kVariants8[] = {{11, 2}, {15, 2}, {19, 1}};
+constexpr int kNumVariants8 = (int)(sizeof(kVariants8) / sizeof(kVariants8[0]));
+
+template <int F, int W, int NG, int NL>
+static cudaError_t launch8_shape(const Fused8Args &a, size_t smem, cudaStream_t st) {
   static int attr = 0;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(fused8_kernel<F, W, NG>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
+    cudaError_t e =
+        cudaFuncSetAttribute(fused8_kernel<F, W, NG, NL>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
     if (e != cudaSuccess) return e;
     attr = 1;
   }
   int sms = 0, dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  fused8_kernel<F, W, NG><<<sms, (NG + 1 + kEpiWarps) * 32, smem, st>>>(a);
+  fused8_kernel<F, W, NG, NL><<<sms, (NG + 1 + kEpiWarps) * 32, smem, st>>>(a);
   return cudaGetLastError();
 }
 
-cudaError_t launch_fused8(const QueryLaunch &q, const DevObject &h, int *launches) {
+template <int F, int W>
+static cudaError_t launch8_one(const Fused8Args &a, size_t smem, cudaStream_t st, int variant) {
+  if constexpr (F == 4) {
+    if (variant == 1) return launch8_shape<F, W, 15, 2>(a, smem, st);
+    if (variant == 2) return launch8_shape<F, W, 19, 1>(a, smem, st);
+  }
+  return launch8_shape<F, W, 11, 2>(a, smem, st);
+}
+
+int fused8_variant_count() { return kNumVariants8; }
+
+void fused8_variant_shape(int v, int *threads, int *levels) {
+  *threads = kVariants8[v].ng * 32;
+  *levels = kVariants8[v].nl;
+}
+
+cudaError_t launch_fused8(const QueryLaunch &q, const DevObject &h, int variant, int *launches) {
   if (!fused8_supported(h)) return cudaErrorNotSupported;
   Fused8Args a{};
   a.q = q;
@@ -689,10 +716,10 @@ cudaError_t launch_fused8(const QueryLaunch &q, const DevObject &h, int *launche
   if (!a.nbuf) return cudaErrorNotSupported;
   const size_t smem = make_layout8(a.smem_blob, h.F, h.width, a.nbuf, a.list_chunks).total;
   *launches += 1;
-  if (h.F == 2 && h.width == 64) return launch8_one<2, 64>(a, smem, q.stream);
-  if (h.F == 2 && h.width == 128) return launch8_one<2, 128>(a, smem, q.stream);
-  if (h.F == 4 && h.width == 64) return launch8_one<4, 64>(a, smem, q.stream);
-  if (h.F == 4 && h.width == 128) return launch8_one<4, 128>(a, smem, q.stream);
+  if (h.F == 2 && h.width == 64) return launch8_one<2, 64>(a, smem, q.stream, variant);
+  if (h.F == 2 && h.width == 128) return launch8_one<2, 128>(a, smem, q.stream, variant);
+  if (h.F == 4 && h.width == 64) return launch8_one<4, 64>(a, smem, q.stream, variant);
+  if (h.F == 4 && h.width == 128) return launch8_one<4, 128>(a, smem, q.stream, variant);
   return cudaErrorNotSupported;
 }
 

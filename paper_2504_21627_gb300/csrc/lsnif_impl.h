@@ -143,7 +143,9 @@ cudaError_t launch_tables_to_half(const float *src, uint16_t *dst, int64_t n, cu
 // fused kernel's instantiations.
 bool fused8_supported(const DevObject &host_obj);
 size_t fused8_smem_bytes(const DevObject &host_obj, int H_max);
-cudaError_t launch_fused8(const QueryLaunch &q, const DevObject &host_obj, int *launches);
+cudaError_t launch_fused8(const QueryLaunch &q, const DevObject &host_obj, int variant, int *launches);
+int fused8_variant_count();
+void fused8_variant_shape(int variant, int *threads, int *levels);
 cudaError_t launch_max_abs_half(const uint16_t *v, int64_t n, uint32_t *out_bits, cudaStream_t st);
 bool fused_supported(const DevObject &host_obj);
 size_t fused_smem_bytes(const DevObject &host_obj, int H_max);  // smallest ring; H_max: query's largest H

@@ -203,7 +203,7 @@ int lsnif::run_query(lsnif_ctx *ctx, Workspace *ws, const lsnif_rays *r, lsnif_h
   if (profile) cudaEventRecord(ctx->ev[2], st);
   if (e == cudaSuccess) {
     if (precision == LSNIF_FP32_PLAIN) e = launch_plain_tail(q, ws->cap_nin, kChunkTiles, &launches);
-    else if (precision == LSNIF_FP8_FUSED) e = launch_fused8(q, rep, &launches);
+    else if (precision == LSNIF_FP8_FUSED) e = launch_fused8(q, rep, ctx->fp8_variant, &launches);
     else e = launch_fused(q, rep, ctx->fused_variant, &launches);
   }
   if (profile) {
@@ -238,7 +238,8 @@ static int query_graph(lsnif_ctx *ctx, const lsnif_rays *r, lsnif_hits *h, int p
   const int n_in = precision == LSNIF_FP32_PLAIN ? sh.n_in : 0;
   if ((rc = ensure_workspace(ctx, &ctx->ws, r->n, sh.H, sh.n_slots, n_in))) return rc;
   if (ctx->graphs_ws != ctx->ws.base) clear_graphs(ctx);
-  std::vector<uint64_t> key = {(uint64_t)r->n, (uint64_t)precision, (uint64_t)ctx->fused_variant,
+  std::vector<uint64_t> key = {(uint64_t)r->n, (uint64_t)precision,
+                               (uint64_t)(precision == LSNIF_FP8_FUSED ? 1000 + ctx->fp8_variant : ctx->fused_variant),
                                (uint64_t)ctx->trace_mode, (uint64_t)ctx->group_mode, (uint64_t)sh.n_slots,
                                (uint64_t)r->single_obj};
   for (const void *p : {(const void *)r->ox, (const void *)r->oy, (const void *)r->oz, (const void *)r->dx,
@@ -505,6 +506,22 @@ extern "C" int lsnif_set_variant(lsnif_ctx *ctx, int v) {
   if (!ctx || v < 0 || v >= fused_variant_count())
     return fail(LSNIF_ERR_INVALID_ARG, "lsnif_set_variant: bad variant %d", v);
   ctx->fused_variant = v;
+  return LSNIF_OK;
+}
+
+extern "C" int lsnif_variant8_count(void) { return fused8_variant_count(); }
+
+extern "C" int lsnif_variant8_shape(int v, int *threads, int *levels) {
+  if (v < 0 || v >= fused8_variant_count() || !threads || !levels)
+    return fail(LSNIF_ERR_INVALID_ARG, "lsnif_variant8_shape: bad variant %d", v);
+  fused8_variant_shape(v, threads, levels);
+  return LSNIF_OK;
+}
+
+extern "C" int lsnif_set_variant8(lsnif_ctx *ctx, int v) {
+  if (!ctx || v < 0 || v >= fused8_variant_count())
+    return fail(LSNIF_ERR_INVALID_ARG, "lsnif_set_variant8: bad variant %d", v);
+  ctx->fp8_variant = v;
   return LSNIF_OK;
 }
 

@@ -65,6 +65,7 @@ struct lsnif_ctx {
   int32_t *d_prof_meta = nullptr;
   lsnif::Workspace ws;
   int fused_variant = 0;  // fused-kernel shape (see lsnif_autotune)
+  int fp8_variant = 0;    // FP8 fused-kernel shape (lsnif_set_variant8)
   int trace_mode = 1;     // traversal kernel (see lsnif_autotune)
   int group_mode = 0;     // grouping of live rays (see lsnif_set_group_mode)
   // CUDA-graph cache of queries (see lsnif_set_graph_mode)

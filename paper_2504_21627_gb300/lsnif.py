@@ -131,6 +131,9 @@ SIGNATURES = {
     "lsnif_variant_count": (_I, []),
     "lsnif_variant_shape": (_I, [_I, C.POINTER(_I), C.POINTER(_I)]),
     "lsnif_set_variant": (_I, [_P, _I]),
+    "lsnif_variant8_count": (_I, []),
+    "lsnif_variant8_shape": (_I, [_I, C.POINTER(_I), C.POINTER(_I)]),
+    "lsnif_set_variant8": (_I, [_P, _I]),
     "lsnif_autotune": (_I, [_P, C.POINTER(Rays), _I, _P, C.POINTER(_I)]),
     "lsnif_set_trace_mode": (_I, [_P, _I]),
     "lsnif_get_tuning": (_I, [_P, C.POINTER(_I), C.POINTER(_I), C.POINTER(_I)]),
@@ -432,6 +435,19 @@ class Context:
             _check(lib.lsnif_variant_shape(v, C.byref(t), C.byref(l)))
             out.append((t.value, l.value))
         return out
+
+    @staticmethod
+    def variants8() -> list[tuple[int, int]]:
+        lib = load_library()
+        out = []
+        for v in range(lib.lsnif_variant8_count()):
+            t, l = C.c_int(), C.c_int()
+            _check(lib.lsnif_variant8_shape(v, C.byref(t), C.byref(l)))
+            out.append((t.value, l.value))
+        return out
+
+    def set_variant8(self, v: int):
+        _check(self.lib.lsnif_set_variant8(self.h, v))
 
     def set_graph_mode(self, on: bool):
         _check(self.lib.lsnif_set_graph_mode(self.h, 1 if on else 0))

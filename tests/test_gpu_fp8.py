@@ -243,6 +243,24 @@ def test_fp8_submit_graph_and_query_agree(ctx, torus):
         assert torch.equal(torch.nan_to_num(other.logits, nan=-1e30), torch.nan_to_num(direct.logits, nan=-1e30))
 
 
+def test_fp8_variants_give_identical_results(ctx, stress):
+    o = stress["orc"]
+    rays = _cuda(I.rays_sphere_to_box(20000, 3.0, o.bmin, o.bmax, seed=16))
+    got = []
+    try:
+        for v in range(len(lsnif.Context.variants8())):
+            ctx.set_variant8(v)
+            out = ctx.query_rays(rays, obj=stress["h"], precision=lsnif.FP8_FUSED, logits=True)
+            ctx.check()
+            got.append((out.hit.cpu(), out.t.cpu(), out.mat.cpu(), torch.nan_to_num(out.logits.cpu(), nan=-1e30)))
+    finally:
+        ctx.set_variant8(0)
+    assert len(got) >= 2
+    for other in got[1:]:
+        for a, b in zip(got[0], other):
+            assert torch.equal(torch.nan_to_num(a, posinf=-1.0), torch.nan_to_num(b, posinf=-1.0))
+
+
 def test_fp8_unsupported_shape_is_refused(ctx):
     cfg = I.Config(V=8, H=8, L=2, F=4, log2_T=8, N_min=4, N_max=8, n_hidden=1, width=32, n_mat=2)
     h = ctx.load_object(I.icosphere(1), cfg)
