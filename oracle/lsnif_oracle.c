@@ -476,10 +476,55 @@ ORC_API void orc_encode_backward(const double *pts, int64_t npts, const int32_t 
 
 /* ------------------------------------------------------------------------
  * Geometric judge: nearest Moller-Trumbore hit over all triangles.
- * rays: n x 8 floats (object space). Accepts tmin <= t <= tmax, u >= 0,
- * v >= 0, u + v <= 1 (closed triangle); a zero determinant is a miss.
- * out_t = INFINITY and out_tri = -1 on a miss; ties keep the lowest index.
+ * Accepts tmin <= t <= tmax, u >= 0, v >= 0, u + v <= 1 (closed triangle);
+ * a zero determinant is a miss. t = INFINITY and tri = -1 on a miss; ties
+ * keep the lowest index.
  * ---------------------------------------------------------------------- */
+static void cast_one(const double o[3], const double d[3], double tmin, double tmax, const float *verts,
+                     const int32_t *tris, int64_t nt, double *out_t, int32_t *out_tri, double *out_u,
+                     double *out_v)
+{
+    double best = INFINITY, bu = 0, bv = 0;
+    int32_t bt = -1;
+    for (int64_t t = 0; t < nt; ++t) {
+        const float *a = verts + 3 * (int64_t)tris[3 * t];
+        const float *b = verts + 3 * (int64_t)tris[3 * t + 1];
+        const float *c = verts + 3 * (int64_t)tris[3 * t + 2];
+        double e1[3], e2[3], s[3], p[3], q[3];
+        for (int k = 0; k < 3; ++k) {
+            e1[k] = (double)b[k] - (double)a[k];
+            e2[k] = (double)c[k] - (double)a[k];
+            s[k] = o[k] - (double)a[k];
+        }
+        p[0] = d[1] * e2[2] - d[2] * e2[1];
+        p[1] = d[2] * e2[0] - d[0] * e2[2];
+        p[2] = d[0] * e2[1] - d[1] * e2[0];
+        double det = e1[0] * p[0] + e1[1] * p[1] + e1[2] * p[2];
+        if (det == 0.0) continue;
+        double inv = 1.0 / det;
+        double u = (s[0] * p[0] + s[1] * p[1] + s[2] * p[2]) * inv;
+        if (u < 0.0 || u > 1.0) continue;
+        q[0] = s[1] * e1[2] - s[2] * e1[1];
+        q[1] = s[2] * e1[0] - s[0] * e1[2];
+        q[2] = s[0] * e1[1] - s[1] * e1[0];
+        double v = (d[0] * q[0] + d[1] * q[1] + d[2] * q[2]) * inv;
+        if (v < 0.0 || u + v > 1.0) continue;
+        double tt = (e2[0] * q[0] + e2[1] * q[1] + e2[2] * q[2]) * inv;
+        if (tt < tmin || tt > tmax) continue;
+        if (tt < best) {
+            best = tt;
+            bt = (int32_t)t;
+            bu = u;
+            bv = v;
+        }
+    }
+    *out_t = best;
+    *out_tri = bt;
+    if (out_u) *out_u = bu;
+    if (out_v) *out_v = bv;
+}
+
+/* rays: n x 8 floats (object space) */
 ORC_API void orc_judge(const float *rays, int64_t n, const float *verts, const int32_t *tris,
                        int64_t nt, double *out_t, int32_t *out_tri, double *out_u, double *out_v)
 {
@@ -487,44 +532,17 @@ ORC_API void orc_judge(const float *rays, int64_t n, const float *verts, const i
     for (int64_t i = 0; i < n; ++i) {
         const float *r = rays + 8 * i;
         double o[3] = {r[0], r[1], r[2]}, d[3] = {r[3], r[4], r[5]};
-        double tmin = r[6], tmax = r[7];
-        double best = INFINITY, bu = 0, bv = 0;
-        int32_t bt = -1;
-        for (int64_t t = 0; t < nt; ++t) {
-            const float *a = verts + 3 * (int64_t)tris[3 * t];
-            const float *b = verts + 3 * (int64_t)tris[3 * t + 1];
-            const float *c = verts + 3 * (int64_t)tris[3 * t + 2];
-            double e1[3], e2[3], s[3], p[3], q[3];
-            for (int k = 0; k < 3; ++k) {
-                e1[k] = (double)b[k] - (double)a[k];
-                e2[k] = (double)c[k] - (double)a[k];
-                s[k] = o[k] - (double)a[k];
-            }
-            p[0] = d[1] * e2[2] - d[2] * e2[1];
-            p[1] = d[2] * e2[0] - d[0] * e2[2];
-            p[2] = d[0] * e2[1] - d[1] * e2[0];
-            double det = e1[0] * p[0] + e1[1] * p[1] + e1[2] * p[2];
-            if (det == 0.0) continue;
-            double inv = 1.0 / det;
-            double u = (s[0] * p[0] + s[1] * p[1] + s[2] * p[2]) * inv;
-            if (u < 0.0 || u > 1.0) continue;
-            q[0] = s[1] * e1[2] - s[2] * e1[1];
-            q[1] = s[2] * e1[0] - s[0] * e1[2];
-            q[2] = s[0] * e1[1] - s[1] * e1[0];
-            double v = (d[0] * q[0] + d[1] * q[1] + d[2] * q[2]) * inv;
-            if (v < 0.0 || u + v > 1.0) continue;
-            double tt = (e2[0] * q[0] + e2[1] * q[1] + e2[2] * q[2]) * inv;
-            if (tt < tmin || tt > tmax) continue;
-            if (tt < best) {
-                best = tt;
-                bt = (int32_t)t;
-                bu = u;
-                bv = v;
-            }
-        }
-        out_t[i] = best;
-        out_tri[i] = bt;
-        if (out_u) out_u[i] = bu;
-        if (out_v) out_v[i] = bv;
+        cast_one(o, d, r[6], r[7], verts, tris, nt, out_t + i, out_tri + i, out_u ? out_u + i : 0,
+                 out_v ? out_v + i : 0);
     }
+}
+
+/* FP64 rays: o, d n x 3 doubles; every t >= 0 accepted */
+ORC_API void orc_cast64(const double *o, const double *d, int64_t n, const float *verts, const int32_t *tris,
+                        int64_t nt, double *out_t, int32_t *out_tri, double *out_u, double *out_v)
+{
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < n; ++i)
+        cast_one(o + 3 * i, d + 3 * i, 0.0, INFINITY, verts, tris, nt, out_t + i, out_tri + i, out_u + i,
+                 out_v + i);
 }

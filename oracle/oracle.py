@@ -62,6 +62,7 @@ def lib():
         L.orc_encode.argtypes = [P, i64, P, i32, i32, i32, P, P, P, P]
         L.orc_encode_backward.argtypes = [P, i64, P, i32, i32, i32, P, P]
         L.orc_judge.argtypes = [P, i64, P, P, i64, P, P, P, P]
+        L.orc_cast64.argtypes = [P, P, i64, P, P, i64, P, P, P, P]
         _lib = L
     return _lib
 
@@ -400,6 +401,54 @@ def to_object_frame(rays: np.ndarray, inst: Instance) -> np.ndarray:
     out[0:3] = inst.A @ r[0:3] + inst.b[:, None]
     out[3:6] = inst.A @ r[3:6]
     out[6:8] = r[6:8]
+    return out
+
+
+def pixel_rays(eye, forward, right, up, tan_half_fov: float, width: int, height: int):
+    """Primary rays of a pinhole camera through the pixel centres, row-major
+    (y outer), in FP64: d = forward + x tan a right + y tan up with x = 2 (px
+    + 1/2) / width - 1, y = 1 - 2 (py + 1/2) / height, a = width / height,
+    normalised (so t is the distance from the eye). The camera vectors are
+    taken as given (FP32 values widened to FP64)."""
+    e, f, r, u = (np.asarray(v, np.float64) for v in (eye, forward, right, up))
+    py, px = np.meshgrid(np.arange(height), np.arange(width), indexing="ij")
+    x = (2.0 * (px.reshape(-1) + 0.5) / width - 1.0) * tan_half_fov * (width / height)
+    y = (1.0 - 2.0 * (py.reshape(-1) + 0.5) / height) * tan_half_fov
+    d = f[None, :] + x[:, None] * r[None, :] + y[:, None] * u[None, :]
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    return np.broadcast_to(e, d.shape).copy(), d
+
+
+def gbuffer(meshes, instances, eye, forward, right, up, tan_half_fov: float, width: int, height: int) -> dict:
+    """The primary-ray G-buffer of the hybrid pipeline (Sec. 4, Fig. 4a):
+    for every pixel, the nearest triangle that the ray through the pixel
+    centre hits over all instances -- shape index (the instance), primitive
+    index (the triangle), barycentric coordinates (u, v) of the hit (p = (1
+    - u - v) a + u b + v c) and camera distance. Each instance's triangles
+    are met in its object frame (the ray mapped by o' = A o + b, d' = A d;
+    t unchanged), by brute force over every triangle. Ties: the lowest
+    instance, then the lowest triangle. A pixel with no hit: shape -1,
+    prim -1, u = v = 0, distance +inf."""
+    o, d = pixel_rays(eye, forward, right, up, tan_half_fov, width, height)
+    n = o.shape[0]
+    out = dict(shape=np.full(n, -1, np.int32), prim=np.full(n, -1, np.int32), u=np.zeros(n), v=np.zeros(n),
+               dist=np.full(n, np.inf))
+    for k, inst in enumerate(instances):
+        mesh = meshes[inst.obj]
+        oo = _c(o @ inst.A.T + inst.b[None, :], np.float64)
+        dd = _c(d @ inst.A.T, np.float64)
+        t = np.zeros(n)
+        tri = np.zeros(n, np.int32)
+        uu = np.zeros(n)
+        vv = np.zeros(n)
+        lib().orc_cast64(_p(oo), _p(dd), n, _p(_c(mesh.verts, np.float32)), _p(_c(mesh.tris, np.int32)), mesh.nt,
+                         _p(t), _p(tri), _p(uu), _p(vv))
+        take = (tri >= 0) & (t < out["dist"])
+        out["shape"][take] = k
+        out["prim"][take] = tri[take]
+        out["u"][take] = uu[take]
+        out["v"][take] = vv[take]
+        out["dist"][take] = t[take]
     return out
 
 
