@@ -304,6 +304,45 @@ typedef struct lsnif_instance {
 LSNIF_API int lsnif_query_scene(lsnif_ctx *ctx, const lsnif_rays *rays, const lsnif_instance *inst, int n_inst,
                                 lsnif_hits *hits, int32_t *inst_hit, int precision, void *stream);
 
+/* ---- primary-ray G-buffer (Sec. 4, Fig. 4a) ----------------------------- */
+
+/* Pinhole camera: the ray of pixel (px, py) (row py from the top) starts at
+ * eye with direction forward + x right + y up, normalised, where x = (2 (px
+ * + 1/2) / width - 1) tan_half_fov width / height and y = (1 - 2 (py +
+ * 1/2) / height) tan_half_fov. forward, right, up must be orthonormal. */
+typedef struct lsnif_camera {
+    float eye[3], forward[3], right[3], up[3];
+    float tan_half_fov;   /* tangent of half the vertical field of view */
+    int32_t width, height;
+} lsnif_camera;
+
+/* G-buffer planes, width x height each, row-major (DEVICE; any pointer may
+ * be NULL; nx, ny, nz all or none). */
+typedef struct lsnif_gbuffer {
+    uint8_t *hit;         /* 1 where a triangle is hit, else 0 (the lsnif_hits convention) */
+    int32_t *shape;       /* instance index; -1 where no triangle is hit */
+    int32_t *prim;        /* triangle index in the instance's mesh; -1 */
+    float *u, *v;         /* barycentric coordinates: p = (1-u-v) a + u b + v c; 0 */
+    float *dist;          /* camera distance (t of the unit-direction ray); +inf */
+    float *nx, *ny, *nz;  /* shading normal: vertex normals interpolated at (u, v),
+                             mapped to world by A^T and normalised; 0 */
+} lsnif_gbuffer;
+
+/* Rasterise the primary visibility of n_inst instances (HOST array, as for
+ * lsnif_query_scene; their objects must have been loaded with keep_mesh) into
+ * a G-buffer: for every pixel, the nearest triangle that the pixel-centre ray
+ * hits (closed triangles, Moller-Trumbore in FP32 on the triangle mapped to
+ * world space, distance >= 0); equal distances keep the lowest instance,
+ * then the lowest triangle (Sec. 4: primary visibility by rasterisation, so
+ * that LSNIF answers only the later rays). Asynchronous on `stream`.
+ * Scratch (8 bytes per pixel + 4 per triangle over the instances) is owned
+ * by the context and reused. Errors: INVALID_ARG (NULL arguments, image
+ * outside 1..16384 a side, camera not orthonormal, singular transform, more
+ * than 2^31 - 1 triangles), BAD_HANDLE, UNSUPPORTED (object without its
+ * mesh), OUT_OF_MEMORY, CUDA. */
+LSNIF_API int lsnif_raster_gbuffer(lsnif_ctx *ctx, const lsnif_camera *cam, const lsnif_instance *inst, int n_inst,
+                                   lsnif_gbuffer *out, void *stream);
+
 /* Next-bounce rays of a path tracer from query results (all DEVICE): for a
  * ray with hit != 0 and a non-zero normal, origin = o + t d + eps n_f and a
  * cosine-weighted direction about n_f, where n_f is the normal turned to

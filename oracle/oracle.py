@@ -432,7 +432,7 @@ def gbuffer(meshes, instances, eye, forward, right, up, tan_half_fov: float, wid
     o, d = pixel_rays(eye, forward, right, up, tan_half_fov, width, height)
     n = o.shape[0]
     out = dict(shape=np.full(n, -1, np.int32), prim=np.full(n, -1, np.int32), u=np.zeros(n), v=np.zeros(n),
-               dist=np.full(n, np.inf))
+               dist=np.full(n, np.inf), normal=np.zeros((n, 3)))
     for k, inst in enumerate(instances):
         mesh = meshes[inst.obj]
         oo = _c(o @ inst.A.T + inst.b[None, :], np.float64)
@@ -449,7 +449,41 @@ def gbuffer(meshes, instances, eye, forward, right, up, tan_half_fov: float, wid
         out["u"][take] = uu[take]
         out["v"][take] = vv[take]
         out["dist"][take] = t[take]
+    # shading normal of the winner: its vertex normals interpolated at (u, v)
+    # (Sec. 5.3 convention), mapped to world by A^T and normalised
+    for k, inst in enumerate(instances):
+        m = out["shape"] == k
+        if not m.any():
+            continue
+        mesh = meshes[inst.obj]
+        tri = mesh.tris[out["prim"][m]]
+        vn = mesh.vnormals.astype(np.float64)
+        u, v = out["u"][m], out["v"][m]
+        nrm = (1 - u - v)[:, None] * vn[tri[:, 0]] + u[:, None] * vn[tri[:, 1]] + v[:, None] * vn[tri[:, 2]]
+        nrm = nrm @ inst.A
+        ln = np.linalg.norm(nrm, axis=1, keepdims=True)
+        out["normal"][m] = nrm / np.where(ln > 0, ln, 1.0)
     return out
+
+
+def ray_triangle(mesh, inst, tri: np.ndarray, o: np.ndarray, d: np.ndarray):
+    """(t, u, v) of rays (o, d; n x 3, world) against triangles `tri` of an
+    instance's mesh, one per ray, WITHOUT the inside test: the Moller-Trumbore
+    solution of o' + t d' = (1 - u - v) a + u b + v c in the object frame.
+    For judging pixels that lie on a triangle's edge within rounding."""
+    oo = o @ inst.A.T + inst.b[None, :]
+    dd = d @ inst.A.T
+    v3 = mesh.verts.astype(np.float64)
+    a, b, c = (v3[mesh.tris[tri, j]] for j in range(3))
+    e1, e2, s = b - a, c - a, oo - a
+    p = np.cross(dd, e2)
+    det = np.einsum("ij,ij->i", e1, p)
+    q = np.cross(s, e1)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        u = np.einsum("ij,ij->i", s, p) / det
+        v = np.einsum("ij,ij->i", dd, q) / det
+        t = np.einsum("ij,ij->i", e2, q) / det
+    return t, u, v
 
 
 def scene_query(objs, instances, rays: np.ndarray, precision: str = "f64") -> dict:

@@ -133,6 +133,7 @@ extern "C" int lsnif_destroy(lsnif_ctx *ctx) {
   free_workspace(ctx, &ctx->ws);
   if (ctx->scene_buf) dev_free(ctx, ctx->scene_buf);
   if (ctx->pair_buf) dev_free(ctx, ctx->pair_buf);
+  if (ctx->raster_buf) dev_free(ctx, ctx->raster_buf);
   dev_free(ctx, ctx->d_objs);
   dev_free(ctx, ctx->d_err);
   dev_free(ctx, ctx->d_prof_meta);

@@ -81,8 +81,8 @@ struct lsnif_ctx {
   // serving
   lsnif::Server *server = nullptr;
   // instanced-scene queries: instances, per-ray pair counts and offsets; pairs
-  void *scene_buf = nullptr, *pair_buf = nullptr;
-  size_t scene_bytes = 0, pair_bytes = 0;
+  void *scene_buf = nullptr, *pair_buf = nullptr, *raster_buf = nullptr;
+  size_t scene_bytes = 0, pair_bytes = 0, raster_bytes = 0;
   // host-buffer queries: copy streams and per-chunk events (created on first use)
   cudaStream_t copy_in = nullptr, copy_out = nullptr;
   cudaEvent_t hev[16]{};

@@ -68,6 +68,17 @@ class Instance(C.Structure):
     _fields_ = [("obj", C.c_uint32), ("world_to_obj", C.c_float * 12)]
 
 
+class Camera(C.Structure):
+    _fields_ = [("eye", C.c_float * 3), ("forward", C.c_float * 3), ("right", C.c_float * 3), ("up", C.c_float * 3),
+                ("tan_half_fov", C.c_float), ("width", C.c_int32), ("height", C.c_int32)]
+
+
+class GBufferS(C.Structure):
+    _fields_ = [("hit", C.c_void_p), ("shape", C.c_void_p), ("prim", C.c_void_p), ("u", C.c_void_p),
+                ("v", C.c_void_p), ("dist", C.c_void_p), ("nx", C.c_void_p), ("ny", C.c_void_p),
+                ("nz", C.c_void_p)]
+
+
 class Hits(C.Structure):
     _fields_ = [("hit", C.c_void_p), ("t", C.c_void_p), ("nx", C.c_void_p), ("ny", C.c_void_p),
                 ("nz", C.c_void_p), ("mat", C.c_void_p), ("ar", C.c_void_p), ("ag", C.c_void_p),
@@ -123,6 +134,7 @@ SIGNATURES = {
     "lsnif_query_rays_noalloc": (_I, [_P, C.POINTER(Rays), C.POINTER(Hits), _P]),
     "lsnif_query_scene": (_I, [_P, C.POINTER(Rays), C.POINTER(Instance), _I, C.POINTER(Hits), _P, _I, _P]),
     "lsnif_bounce_rays": (_I, [_P, C.POINTER(Rays), C.POINTER(Hits), _P, C.c_float, _P, _P]),
+    "lsnif_raster_gbuffer": (_I, [_P, C.POINTER(Camera), C.POINTER(Instance), _I, C.POINTER(GBufferS), _P]),
     "lsnif_trace": (_I, [_P, C.POINTER(Rays), C.POINTER(TraceOut), _P]),
     "lsnif_encode": (_I, [_P, _U32, _P, _I64, _P, _I, _P]),
     "lsnif_corner_indices": (_I, [_P, _U32, _P, _I64, _P, _P]),
@@ -217,6 +229,17 @@ class QueryResult:
     mat: object
     albedo: object     # (3, n)
     logits: object | None
+
+
+@dataclass
+class GBuffer:
+    hit: object        # (h, w) uint8
+    shape: object      # (h, w) int32 instance index, -1 background
+    prim: object       # (h, w) int32 triangle index, -1 background
+    u: object
+    v: object
+    dist: object       # (h, w) camera distance, inf background
+    normal: object | None   # (3, h, w)
 
 
 class Context:
@@ -364,16 +387,50 @@ class Context:
         n = int(rays.shape[1])
         res = self._alloc_hits(n, 0, False)
         inst = torch.full((n,), -1, dtype=torch.int32, device=rays.device)
-        arr = (Instance * len(instances))()
-        for k, (h, A, b) in enumerate(instances):
-            m = np.concatenate([np.asarray(A, np.float64), np.asarray(b, np.float64)[:, None]], 1)
-            arr[k].obj = int(h)
-            arr[k].world_to_obj[:] = [float(x) for x in m.astype(np.float32).reshape(-1)]
+        arr = self._instances(instances)
         rs = rays_struct(rays)
         hs = self.hits_struct(res)
         _check(self.lib.lsnif_query_scene(self.h, C.byref(rs), arr, len(instances), C.byref(hs), _ptr(inst),
                                           precision, _stream(stream)))
         return res, inst
+
+    @staticmethod
+    def _instances(instances):
+        arr = (Instance * len(instances))()
+        for k, (h, A, b) in enumerate(instances):
+            m = np.concatenate([np.asarray(A, np.float64), np.asarray(b, np.float64)[:, None]], 1)
+            arr[k].obj = int(h)
+            arr[k].world_to_obj[:] = [float(x) for x in m.astype(np.float32).reshape(-1)]
+        return arr
+
+    def raster_gbuffer(self, eye, forward, right, up, tan_half_fov: float, width: int, height: int, instances,
+                       normals: bool = True, out: GBuffer | None = None, stream=None) -> GBuffer:
+        """Primary-ray G-buffer of instances [(handle, A, b), ...] (objects
+        loaded with keep_mesh) seen by a pinhole camera; CUDA tensors of
+        height x width (normal: 3 x height x width)."""
+        import torch
+        if out is None:
+            kw = dict(device=f"cuda:{self.device}")
+            n = (height, width)
+            out = GBuffer(torch.zeros(n, dtype=torch.uint8, **kw), torch.zeros(n, dtype=torch.int32, **kw),
+                          torch.zeros(n, dtype=torch.int32, **kw), torch.zeros(n, dtype=torch.float32, **kw),
+                          torch.zeros(n, dtype=torch.float32, **kw), torch.zeros(n, dtype=torch.float32, **kw),
+                          torch.zeros((3,) + n, dtype=torch.float32, **kw) if normals else None)
+        cam = Camera()
+        cam.eye[:] = [float(x) for x in np.asarray(eye, np.float32)]
+        cam.forward[:] = [float(x) for x in np.asarray(forward, np.float32)]
+        cam.right[:] = [float(x) for x in np.asarray(right, np.float32)]
+        cam.up[:] = [float(x) for x in np.asarray(up, np.float32)]
+        cam.tan_half_fov = float(np.float32(tan_half_fov))
+        cam.width, cam.height = int(width), int(height)
+        npx = width * height
+        nrm = _ptr(out.normal) if out.normal is not None else None
+        g = GBufferS(_ptr(out.hit), _ptr(out.shape), _ptr(out.prim), _ptr(out.u), _ptr(out.v), _ptr(out.dist),
+                     nrm, nrm + 4 * npx if nrm else None, nrm + 8 * npx if nrm else None)
+        arr = self._instances(instances)
+        _check(self.lib.lsnif_raster_gbuffer(self.h, C.byref(cam), arr, len(instances), C.byref(g),
+                                             _stream(stream)))
+        return out
 
     def bounce_rays(self, rays, res: QueryResult, u, eps: float, stream=None):
         """Next-bounce rays (8, n) from world rays and their query results;

@@ -165,3 +165,24 @@ def test_instance_equals_the_pretransformed_mesh():
     assert np.array_equal(gw["prim"][firm], gi["prim"][firm])
     assert np.allclose(gw["dist"][firm], gi["dist"][firm], rtol=1e-6)
     assert np.allclose(gw["u"][firm], gi["u"][firm], atol=1e-5) and np.allclose(gw["v"][firm], gi["v"][firm], atol=1e-5)
+
+
+def test_normals_and_unclipped_triangle_solution():
+    """A flat quad whose vertex normals are +z, seen through a rotated and
+    scaled instance: every hit's world normal is A^T e_z normalised (R e_z
+    for A = R^T / s); and the unclipped ray-triangle solution of the winning
+    triangle reproduces each hit's (t, u, v)."""
+    quad = _quad(0.0)
+    R = I.rotation([0.2, 1.0, 0.3], 0.6)
+    inst = O.Instance(0, R.T / 1.5, np.array([0.1, -0.2, 0.3]))
+    eye, f, r, u = _cam([0.5, -1.0, -4.0], [0.0, 0.0, 0.0])
+    W, H, tan = 40, 30, 0.35
+    g = O.gbuffer([quad], [inst], eye, f, r, u, tan, W, H)
+    hit = g["shape"] == 0
+    assert hit.sum() > 100
+    assert np.allclose(g["normal"][hit], R[:, 2][None, :], atol=1e-12)
+    assert np.all(g["normal"][~hit] == 0)
+    o, d = O.pixel_rays(eye, f, r, u, tan, W, H)
+    t, uu, vv = O.ray_triangle(quad, inst, g["prim"][hit], o[hit], d[hit])
+    assert np.allclose(t, g["dist"][hit], rtol=1e-12)
+    assert np.allclose(uu, g["u"][hit], atol=1e-12) and np.allclose(vv, g["v"][hit], atol=1e-12)
