@@ -432,6 +432,77 @@ def bench_stress1(args):
     ctx.close()
 
 
+def _scene_raster(args, ctx, spec, handles, insts, stress):
+    """The paper's hybrid frame (Sec. 4, Fig. 4): primary visibility by
+    rasterising the meshes into a G-buffer (lsnif_raster_gbuffer; spp
+    samples per pixel as a sqrt(spp)-times supersampled G-buffer), first
+    bounce rays from the G-buffer, then 2 bounces of LSNIF queries."""
+    import torch
+    from paper_2504_21627_gb300 import lsnif
+    s = int(round(math.sqrt(args.scene_spp)))
+    W, H = args.scene_width * s, args.scene_height * s
+    cam = I.seeded_camera(4, radius=14.0, width=W, height=H, fov_deg=50.0)
+    tan = math.tan(math.radians(cam.fov_deg) / 2.0)
+    prim = torch.from_numpy(I.rays_pinhole(cam)).cuda()
+    n = prim.shape[1]
+    gen = torch.Generator("cuda").manual_seed(11)
+    us = [torch.rand((n, 2), device="cuda", generator=gen) for _ in range(3)]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    gbuf = ctx.raster_gbuffer(cam.eye, cam.forward, cam.right, cam.up, tan, W, H, insts)
+
+    def raster():
+        return ctx.raster_gbuffer(cam.eye, cam.forward, cam.right, cam.up, tan, W, H, insts, out=gbuf)
+
+    def frame(prec, stats=None):
+        g = raster()
+        res = lsnif.QueryResult(g.hit.view(-1), g.dist.view(-1), g.normal.view(3, -1), None, None, None)
+        if stats is not None:
+            stats.append((int(g.hit.sum().item()), n))
+        rays = ctx.bounce_rays(prim, res, us[0], 1e-3)
+        for b in range(2):
+            res, _ = ctx.query_scene(rays, insts, precision=prec)
+            if stats is not None:
+                stats.append((int(res.hit.sum().item()), int((rays[3:6].abs().sum(0) > 0).sum().item())))
+            if b < 1:
+                rays = ctx.bounce_rays(rays, res, us[b + 1], 1e-3)
+        return res
+
+    def timed(fn, steps):
+        ms = []
+        for _ in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return np.array(ms)
+
+    nt_of = {h: int(spec[i][0].nt) for i, h in enumerate(handles)}
+    n_tri = sum(nt_of[h] for h, _, _ in insts)
+    for _ in range(3):
+        raster()
+    ms_r = timed(raster, max(5, args.steps))
+    out = {"workload": "scene-raster", "metric": "hybrid frame: raster G-buffer + 2 LSNIF bounces",
+           "instances": len(insts), "unique_objects": len(spec), "gbuffer": [W, H], "triangles": n_tri,
+           "network": "L=16 F=4 T=2^21, 1152-128x4-12" if stress else "L=16 F=2 T=2^21, 576-64x4-12",
+           "raster": {"ms": float(ms_r.mean()), "mpixels_s": W * H / (ms_r.mean() / 1e3) / 1e6,
+                      "gtris_s": n_tri / (ms_r.mean() / 1e3) / 1e9}}
+    prec, name = (lsnif.FP8_FUSED, "fp8") if stress else (lsnif.BF16_FUSED, "bf16")
+    stats = []
+    frame(prec, stats)
+    for _ in range(2):
+        frame(prec)
+    ms = timed(lambda: frame(prec), max(3, args.steps // 4))
+    out[name] = {"ms_per_frame": float(ms.mean()), "lsnif_mrays_s": 2 * n / ((ms.mean() - ms_r.mean()) / 1e3) / 1e6,
+                 "hits": [h for h, _ in stats], "live_rays": [l for _, l in stats]}
+    out["device_gb"] = ctx.device_bytes() / 1e9
+    print(json.dumps(out))
+    ctx.close()
+
+
 def bench_scene(args):
     """Path-tracer-shaped stress: 32 instances of 8 unique objects (50k..1M
     triangles, V 128, L 16, F 4, T 2^21, 4 x 128 network; `--scene-net
@@ -452,11 +523,14 @@ def bench_scene(args):
     for i, (mesh, cfg) in enumerate(spec):
         p = I.random_params(cfg, seed=3000 + i, table_range=0.05, bias_range=0.1)
         p.weights[-1][1][0] = 1.0   # occupancy logit biased towards hits, so bounces continue
-        handles.append(ctx.load_object(mesh, cfg, tables=p.tables, mlp=p.packed_mlp()))
+        handles.append(ctx.load_object(mesh, cfg, tables=p.tables, mlp=p.packed_mlp(),
+                                       keep_mesh=args.primary == "raster"))
     if args.variant8 is not None:
         ctx.set_variant8(args.variant8)
     insts = [(handles[o], A, b) for o, A, b in I.seeded_instances(args.scene_instances, len(spec), seed=9,
                                                                    spread=10.0)]
+    if args.primary == "raster":
+        return _scene_raster(args, ctx, spec, handles, insts, stress)
     cam = I.seeded_camera(4, radius=14.0, width=args.scene_width, height=args.scene_height, fov_deg=50.0)
     rays0 = torch.from_numpy(I.camera_rays_spp(cam, args.scene_spp, seed=10)).cuda()
     n = rays0.shape[1]
@@ -524,6 +598,8 @@ def main():
     ap.add_argument("--scene-objects", type=int, default=8, help="unique objects (below 8 only for profiling)")
     ap.add_argument("--scene-instances", type=int, default=32)
     ap.add_argument("--scene-spp", type=int, default=4)
+    ap.add_argument("--primary", default="lsnif", choices=["lsnif", "raster"],
+                    help="scene workload: primary rays by LSNIF, or by the rasterised G-buffer (Sec. 4)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":

@@ -13,7 +13,7 @@
 // patterns, so the minimum is the nearest hit, and equal distances keep the
 // lowest instance, then the lowest triangle. Triangles whose box holds more
 // than a few pixel centres, or that cross the camera plane, are queued for a
-// second kernel where a whole block sweeps their pixels. A resolve pass
+// second kernel where a whole warp sweeps their pixels. A resolve pass
 // re-tests the winning triangle to recover (u, v) and writes the buffers.
 #include <cuda_runtime.h>
 #include <math_constants.h>
@@ -29,7 +29,7 @@ using namespace lsnif;
 
 namespace {
 
-constexpr int kSmallPixels = 16;        // pixel centres a setup thread tests itself
+constexpr int kSmallPixels = 64;        // larger boxes go to the warp-per-triangle queue
 constexpr unsigned long long kEmpty = ~0ull;
 
 struct RInstance {
@@ -44,6 +44,7 @@ struct RInstance {
 struct RCam {
   float e[3], f[3], r[3], u[3];
   float tx, ty;  // tan(half fov) * aspect, tan(half fov)
+  float rw, rh;  // 2 / width, 2 / height
   int w, h;
 };
 
@@ -55,15 +56,15 @@ struct WorldTri {
 };
 
 __device__ __forceinline__ void pixel_dir(const RCam &cam, int px, int py, float d[3]) {
-  const float x = (2.f * ((float)px + 0.5f) / (float)cam.w - 1.f) * cam.tx;
-  const float y = (1.f - 2.f * ((float)py + 0.5f) / (float)cam.h) * cam.ty;
+  const float x = fmaf((float)px + 0.5f, cam.rw, -1.f) * cam.tx;
+  const float y = fmaf(-((float)py + 0.5f), cam.rh, 1.f) * cam.ty;
   float n2 = 0.f;
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     d[k] = cam.f[k] + x * cam.r[k] + y * cam.u[k];
     n2 += d[k] * d[k];
   }
-  const float inv = 1.f / sqrtf(n2);
+  const float inv = rsqrtf(n2);
 #pragma unroll
   for (int k = 0; k < 3; ++k) d[k] *= inv;
 }
@@ -121,6 +122,17 @@ __device__ __forceinline__ int find_instance(const RInstance *inst, int n_inst, 
   return lo;
 }
 
+// the same search over a copy of the instances' first ids
+__device__ __forceinline__ int find_first(const uint32_t *first, int n_inst, uint32_t gid) {
+  int lo = 0, hi = n_inst - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (first[mid] <= gid) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
 __device__ __forceinline__ void load_world_tri(const RInstance &in, const DevObject &ob, uint32_t tri, const RCam &cam,
                                                WorldTri &T, float zc[3], float sx[3], float sy[3]) {
   const int32_t *ix = ob.tris + 3 * (int64_t)tri;
@@ -133,8 +145,9 @@ __device__ __forceinline__ void load_world_tri(const RInstance &in, const DevObj
     const float q[3] = {w[k][0] - cam.e[0], w[k][1] - cam.e[1], w[k][2] - cam.e[2]};
     zc[k] = dot3(q, cam.f);
     const float xc = dot3(q, cam.r), yc = dot3(q, cam.u);
-    sx[k] = (xc / (zc[k] * cam.tx) + 1.f) * 0.5f * (float)cam.w;
-    sy[k] = (1.f - yc / (zc[k] * cam.ty)) * 0.5f * (float)cam.h;
+    // approximate division: the box is widened and the ray test decides
+    sx[k] = (__fdividef(xc, zc[k] * cam.tx) + 1.f) * 0.5f * (float)cam.w;
+    sy[k] = (1.f - __fdividef(yc, zc[k] * cam.ty)) * 0.5f * (float)cam.h;
   }
   make_tri(cam, w[0], w[1], w[2], T);
 }
@@ -145,7 +158,7 @@ __device__ __forceinline__ bool pixel_box(const RCam &cam, const float sx[3], co
                                           int &y0, int &y1) {
   float lx = fminf(sx[0], fminf(sx[1], sx[2])), hx = fmaxf(sx[0], fmaxf(sx[1], sx[2]));
   float ly = fminf(sy[0], fminf(sy[1], sy[2])), hy = fmaxf(sy[0], fmaxf(sy[1], sy[2]));
-  const float slack = 1e-2f;
+  const float slack = 5e-2f;
   if (!(hx >= -1.f && lx <= (float)cam.w + 1.f && hy >= -1.f && ly <= (float)cam.h + 1.f)) return false;
   // clamp before the integer conversions (vertices near the camera plane
   // project far outside the image)
@@ -170,73 +183,111 @@ __device__ __forceinline__ void test_pixel(const RCam &cam, const WorldTri &T, u
   }
 }
 
-__global__ void raster_setup_kernel(RCam cam, const RInstance *inst, int n_inst, const DevObject *objs,
-                                    uint32_t total, unsigned long long *keys, uint32_t *large, uint32_t *n_large) {
-  for (uint32_t gid = blockIdx.x * blockDim.x + threadIdx.x; gid < total; gid += gridDim.x * blockDim.x) {
-    const int k = find_instance(inst, n_inst, gid);
-    const RInstance &in = inst[k];
-    const DevObject &ob = objs[in.slot];
-    WorldTri T;
-    float zc[3], sx[3], sy[3];
-    load_world_tri(in, ob, gid - in.first, cam, T, zc, sx, sy);
-    if (zc[0] <= 0.f && zc[1] <= 0.f && zc[2] <= 0.f) continue;  // behind the camera
-    if (zc[0] <= 0.f || zc[1] <= 0.f || zc[2] <= 0.f) {          // crosses the camera plane: whole screen
-      large[atomicAdd(n_large, 1u)] = gid;
-      continue;
+// Setup: one thread per (instance, triangle). A warp then tests the pixel
+// centres of its 32 triangles' boxes together: the lanes' pixel counts are
+// scanned, and the warp walks the concatenated (triangle, pixel) list 32
+// items at a time, each item finding its triangle in the warp's shared
+// memory -- so one triangle with a large box does not idle the other lanes.
+constexpr int kSetupThreads = 256;
+constexpr int kMaxSharedInstances = 2048;
+
+__global__ void __launch_bounds__(kSetupThreads) raster_setup_kernel(RCam cam, const RInstance *inst, int n_inst,
+                                                                     const DevObject *objs, uint32_t total,
+                                                                     unsigned long long *keys, uint32_t *large,
+                                                                     uint32_t *n_large) {
+  __shared__ WorldTri s_tri[kSetupThreads];
+  __shared__ int s_box[kSetupThreads][2];  // x0 | y0 << 16, width
+  __shared__ uint32_t s_gid[kSetupThreads];
+  __shared__ int s_end[kSetupThreads];     // inclusive prefix of the pixel counts, per warp
+  __shared__ uint32_t s_first[kMaxSharedInstances];
+  const int lane = threadIdx.x & 31, wbase = threadIdx.x & ~31;
+  const bool shared_first = n_inst <= kMaxSharedInstances;
+  if (shared_first)
+    for (int k = threadIdx.x; k < n_inst; k += blockDim.x) s_first[k] = inst[k].first;
+  __syncthreads();
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t base = blockIdx.x * blockDim.x; base < total; base += stride) {
+    const uint32_t gid = base + threadIdx.x;
+    int count = 0;
+    if (gid < total) {
+      const int k = shared_first ? find_first(s_first, n_inst, gid) : find_instance(inst, n_inst, gid);
+      const RInstance &in = inst[k];
+      WorldTri T;
+      float zc[3], sx[3], sy[3];
+      load_world_tri(in, objs[in.slot], gid - in.first, cam, T, zc, sx, sy);
+      const bool behind = zc[0] <= 0.f && zc[1] <= 0.f && zc[2] <= 0.f;
+      const bool straddles = zc[0] <= 0.f || zc[1] <= 0.f || zc[2] <= 0.f || !isfinite(sx[0]) ||
+                             !isfinite(sx[1]) || !isfinite(sx[2]) || !isfinite(sy[0]) || !isfinite(sy[1]) ||
+                             !isfinite(sy[2]);
+      int x0, x1, y0, y1;
+      if (behind) {
+      } else if (straddles) {  // crosses the camera plane: the whole screen, in the queue
+        large[atomicAdd(n_large, 1u)] = gid;
+      } else if (pixel_box(cam, sx, sy, x0, x1, y0, y1)) {
+        const int bw = x1 - x0 + 1, n = bw * (y1 - y0 + 1);
+        if (n > kSmallPixels) {
+          large[atomicAdd(n_large, 1u)] = gid;
+        } else {
+          count = n;
+          s_tri[threadIdx.x] = T;
+          s_box[threadIdx.x][0] = x0 | (y0 << 16);
+          s_box[threadIdx.x][1] = bw;
+          s_gid[threadIdx.x] = gid;
+        }
+      }
     }
-    if (!(isfinite(sx[0]) && isfinite(sx[1]) && isfinite(sx[2]) && isfinite(sy[0]) && isfinite(sy[1]) &&
-          isfinite(sy[2]))) {
-      large[atomicAdd(n_large, 1u)] = gid;
-      continue;
+    int incl = count;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
     }
-    int x0, x1, y0, y1;
-    if (!pixel_box(cam, sx, sy, x0, x1, y0, y1)) continue;
-    if ((x1 - x0 + 1) * (y1 - y0 + 1) > kSmallPixels) {
-      large[atomicAdd(n_large, 1u)] = gid;
-      continue;
+    s_end[threadIdx.x] = incl;
+    const int n_items = __shfl_sync(0xffffffffu, incl, 31);
+    __syncwarp();
+    for (int j = lane; j < n_items; j += 32) {
+      // owner: the first lane whose inclusive prefix exceeds j
+      int lo = 0, hi = 31;
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (s_end[wbase + mid] > j) hi = mid;
+        else lo = mid + 1;
+      }
+      const int t = wbase + lo;
+      const int first = lo ? s_end[t - 1] : 0;
+      const int idx = j - first;
+      const int bw = s_box[t][1];
+      const int px = (s_box[t][0] & 0xffff) + idx % bw, py = (s_box[t][0] >> 16) + idx / bw;
+      test_pixel(cam, s_tri[t], s_gid[t], px, py, keys);
     }
-    for (int py = y0; py <= y1; ++py)
-      for (int px = x0; px <= x1; ++px) test_pixel(cam, T, gid, px, py, keys);
+    __syncwarp();
   }
 }
 
-// one block per queued triangle at a time; its threads sweep the box
+// one warp per queued triangle at a time: every lane forms the triangle
+// (the loads are shared through L1), then the lanes sweep its box
 __global__ void raster_large_kernel(RCam cam, const RInstance *inst, int n_inst, const DevObject *objs,
                                     unsigned long long *keys, const uint32_t *large, const uint32_t *n_large,
                                     uint32_t *next) {
-  __shared__ uint32_t s_item;
-  __shared__ int s_box[4];
-  __shared__ WorldTri s_tri;
+  const int lane = threadIdx.x & 31;
   const uint32_t n = *n_large;
   while (true) {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      s_item = atomicAdd(next, 1u);
-      if (s_item < n) {
-        const uint32_t gid = large[s_item];
-        const int k = find_instance(inst, n_inst, gid);
-        const RInstance &in = inst[k];
-        float zc[3], sx[3], sy[3];
-        load_world_tri(in, objs[in.slot], gid - in.first, cam, s_tri, zc, sx, sy);
-        int x0 = 0, x1 = cam.w - 1, y0 = 0, y1 = cam.h - 1;
-        const bool straddles = zc[0] <= 0.f || zc[1] <= 0.f || zc[2] <= 0.f || !isfinite(sx[0]) ||
-                               !isfinite(sx[1]) || !isfinite(sx[2]) || !isfinite(sy[0]) || !isfinite(sy[1]) ||
-                               !isfinite(sy[2]);
-        if (!straddles && !pixel_box(cam, sx, sy, x0, x1, y0, y1)) x1 = x0 - 1;
-        s_box[0] = x0;
-        s_box[1] = x1;
-        s_box[2] = y0;
-        s_box[3] = y1;
-      }
-    }
-    __syncthreads();
-    const uint32_t item = s_item;
+    uint32_t item = 0;
+    if (lane == 0) item = atomicAdd(next, 1u);
+    item = __shfl_sync(0xffffffffu, item, 0);
     if (item >= n) break;
     const uint32_t gid = large[item];
-    const int x0 = s_box[0], bw = s_box[1] - s_box[0] + 1, y0 = s_box[2], bh = s_box[3] - s_box[2] + 1;
-    if (bw <= 0 || bh <= 0) continue;
-    const WorldTri T = s_tri;
-    for (int64_t j = threadIdx.x; j < (int64_t)bw * bh; j += blockDim.x)
+    const int k = find_instance(inst, n_inst, gid);
+    const RInstance &in = inst[k];
+    WorldTri T;
+    float zc[3], sx[3], sy[3];
+    load_world_tri(in, objs[in.slot], gid - in.first, cam, T, zc, sx, sy);
+    int x0 = 0, x1 = cam.w - 1, y0 = 0, y1 = cam.h - 1;
+    const bool straddles = zc[0] <= 0.f || zc[1] <= 0.f || zc[2] <= 0.f || !isfinite(sx[0]) || !isfinite(sx[1]) ||
+                           !isfinite(sx[2]) || !isfinite(sy[0]) || !isfinite(sy[1]) || !isfinite(sy[2]);
+    if (!straddles && !pixel_box(cam, sx, sy, x0, x1, y0, y1)) continue;
+    const int bw = x1 - x0 + 1, bh = y1 - y0 + 1;
+    for (int64_t j = lane; j < (int64_t)bw * bh; j += 32)
       test_pixel(cam, T, gid, x0 + (int)(j % bw), y0 + (int)(j / bw), keys);
   }
 }
@@ -371,6 +422,8 @@ extern "C" int lsnif_raster_gbuffer(lsnif_ctx *ctx, const lsnif_camera *cam, con
   }
   rc.ty = cam->tan_half_fov;
   rc.tx = (float)((double)cam->tan_half_fov * cam->width / cam->height);
+  rc.rw = 2.f / (float)cam->width;
+  rc.rh = 2.f / (float)cam->height;
   rc.w = cam->width;
   rc.h = cam->height;
   cudaSetDevice(ctx->device);
@@ -406,7 +459,7 @@ extern "C" int lsnif_raster_gbuffer(lsnif_ctx *ctx, const lsnif_camera *cam, con
     const uint32_t t32 = (uint32_t)total;
     const int grid = (int)std::min<uint64_t>((total + 255) / 256, (uint64_t)sms * 16);
     raster_setup_kernel<<<grid, 256, 0, st>>>(rc, dinst, n_inst, ctx->d_objs, t32, keys, large, counters);
-    raster_large_kernel<<<sms * 4, 256, 0, st>>>(rc, dinst, n_inst, ctx->d_objs, keys, large, counters,
+    raster_large_kernel<<<sms * 8, 256, 0, st>>>(rc, dinst, n_inst, ctx->d_objs, keys, large, counters,
                                                  counters + 1);
     e = cudaGetLastError();
   }

@@ -347,8 +347,9 @@ class Context:
     @staticmethod
     def hits_struct(r: QueryResult) -> Hits:
         n = r.t.shape[0]
-        return Hits(_ptr(r.hit), _ptr(r.t), _ptr(r.normal), _ptr(r.normal) + 4 * n, _ptr(r.normal) + 8 * n,
-                    _ptr(r.mat), _ptr(r.albedo), _ptr(r.albedo) + 4 * n, _ptr(r.albedo) + 8 * n, _ptr(r.logits))
+        nrm, alb = _ptr(r.normal), _ptr(r.albedo)
+        return Hits(_ptr(r.hit), _ptr(r.t), nrm, nrm and nrm + 4 * n, nrm and nrm + 8 * n,
+                    _ptr(r.mat), alb, alb and alb + 4 * n, alb and alb + 8 * n, _ptr(r.logits))
 
     def query_rays(self, rays, obj: int = 0, obj_per_ray=None, precision: int = BF16_FUSED,
                    logits: bool = False, out: QueryResult | None = None, stream=None) -> QueryResult:
