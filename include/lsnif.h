@@ -131,6 +131,12 @@ typedef struct lsnif_object_desc {
     int32_t keep_mesh;       /* nonzero: keep the mesh on the device for training labels */
     const void *blob;        /* host, from lsnif_save_object, or NULL */
     size_t blob_len;
+    /* Face-count switch of the hybrid pipeline (Sec. 4): a mesh with fewer
+     * than this many triangles is not turned into an LSNIF object but kept
+     * as a mesh object -- its triangles and a BVH, answered exactly by every
+     * query (lsnif_query_rays, lsnif_query_scene, lsnif_raster_gbuffer).
+     * Only cfg.n_mat of the config is used then. 0: never. */
+    int64_t bvh_below_faces;
 } lsnif_object_desc;
 
 /* Read-only facts about a loaded object. */
@@ -142,6 +148,9 @@ typedef struct lsnif_object_info {
     int64_t n_params_mlp;                /* weights + biases */
     size_t device_bytes;                 /* device memory charged to the budget */
     size_t footprint_fp16_bytes;         /* paper's storage model: bits + FP16 tables + FP16 network */
+    int32_t kind;                        /* 0 = LSNIF object, 1 = mesh object (triangles + BVH) */
+    int64_t n_triangles;                 /* mesh objects: triangles */
+    int64_t bvh_nodes;                   /* mesh objects: BVH nodes (32 bytes each) */
 } lsnif_object_info;
 
 /* Rays, structure of arrays, DEVICE pointers (host pointers for
@@ -303,6 +312,19 @@ typedef struct lsnif_instance {
  * shapes), CUDA, DEVICE_CHECK. */
 LSNIF_API int lsnif_query_scene(lsnif_ctx *ctx, const lsnif_rays *rays, const lsnif_instance *inst, int n_inst,
                                 lsnif_hits *hits, int32_t *inst_hit, int precision, void *stream);
+
+/* ---- mesh objects ------------------------------------------------------- */
+
+/* The BVH builder of mesh objects (see bvh_below_faces), on the host only
+ * (no GPU, no context): binned-SAH binary BVH over nt triangles. nodes_out
+ * (room for 2 nt - 1 nodes) receives *n_nodes nodes of 32 bytes: float lo[3],
+ * int32 a, float hi[3], int32 n -- an internal node has n = 0 and children
+ * a and a + 1; a leaf has n > 0 triangles at order_out[a .. a + n). order_out
+ * (nt entries) maps stored positions to mesh triangles; *depth (may be NULL)
+ * receives the deepest leaf's depth. For checking the structure. Errors:
+ * INVALID_ARG (NULL pointers, empty mesh, index out of range). */
+LSNIF_API int lsnif_bvh_build_host(const float *verts, int64_t nv, const int32_t *tris, int64_t nt,
+                                   void *nodes_out, int64_t *n_nodes, int32_t *order_out, int32_t *depth);
 
 /* ---- primary-ray G-buffer (Sec. 4, Fig. 4a) ----------------------------- */
 

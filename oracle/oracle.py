@@ -486,6 +486,39 @@ def ray_triangle(mesh, inst, tri: np.ndarray, o: np.ndarray, d: np.ndarray):
     return t, u, v
 
 
+@dataclass
+class MeshObject:
+    """A scene object kept as triangles (the hybrid pipeline's non-LSNIF
+    objects, Sec. 4): queries are answered exactly."""
+    mesh: object
+    bmin: np.ndarray
+    bmax: np.ndarray
+
+
+def mesh_object(mesh) -> MeshObject:
+    lo, hi = bbox(mesh.verts)
+    return MeshObject(mesh, lo, hi)
+
+
+def mesh_query(mobj: MeshObject, rays: np.ndarray):
+    """Exact answer for a mesh object: the nearest triangle by brute force
+    (the judge, tmin <= t <= tmax, lowest index on ties), its shading normal
+    (vertex normals interpolated at the hit, Sec. 5.3 convention),
+    material and the material's albedo. Returns (Hits, Segments) shaped like
+    query()'s, with no network outputs and no near-face rays."""
+    mesh = mobj.mesh
+    j = judge(mesh, rays)
+    n = j.t.size
+    hit = j.tri >= 0
+    h = Hits(hit.copy(), np.where(hit, j.t, np.inf), shading_normal(mesh, j), np.full(n, -1, np.int32),
+             np.zeros((n, 3)), np.full((n, 0), np.nan), np.zeros(n, bool))
+    h.mat[hit] = mesh.tri_mat[j.tri[hit]]
+    h.albedo[hit] = mesh.albedo[h.mat[hit]].astype(np.float64)
+    seg = Segments(np.zeros(n, np.int32), np.full((n, 2), np.nan), np.zeros((n, 0, 3)), np.zeros((n, 0), np.int32),
+                   np.zeros(n, bool))
+    return h, seg
+
+
 def scene_query(objs, instances, rays: np.ndarray, precision: str = "f64") -> dict:
     """The wavefront integration of Sec. 4 over instanced objects (Sec. 6):
     every (ray, instance) pair is queried in the instance's object frame (the
@@ -494,7 +527,8 @@ def scene_query(objs, instances, rays: np.ndarray, precision: str = "f64") -> di
     t. The normal returns to world space as A^T n, normalised (normals map
     with the inverse transpose of the object-to-world map, which is A^T). A
     ray no pair hits gets the miss values: hit 0, t inf, normal 0, mat -1,
-    albedo 0, instance -1. `near` marks rays with a near-face pair."""
+    albedo 0, instance -1. `near` marks rays with a near-face pair. Objects
+    may be LSNIF objects or mesh objects (answered exactly, mesh_query)."""
     r = np.asarray(rays, np.float64)
     n = r.shape[1]
     res = dict(hit=np.zeros(n, bool), t=np.full(n, np.inf), normal=np.zeros((n, 3)),
@@ -502,7 +536,8 @@ def scene_query(objs, instances, rays: np.ndarray, precision: str = "f64") -> di
                near=np.zeros(n, bool))
     for i, inst in enumerate(instances):
         local = to_object_frame(r, inst).astype(np.float32)
-        h, seg = query(objs[inst.obj], local, precision)
+        ob = objs[inst.obj]
+        h, seg = mesh_query(ob, local) if isinstance(ob, MeshObject) else query(ob, local, precision)
         res["near"] |= seg.near
         take = h.hit & (h.t < res["t"])
         if not take.any():

@@ -12,6 +12,7 @@
 #include <string>
 #include <vector>
 
+#include "bvh.h"
 #include "lsnif_impl.h"
 #include "runtime.h"
 
@@ -414,10 +415,103 @@ int lsnif::ensure_fp8(lsnif_ctx *ctx, Object *o, cudaStream_t st) {
   return LSNIF_OK;
 }
 
+// A mesh object: the triangles, shading normals, materials and a BVH built
+// on the host; no voxels, tables or network.
+static int load_mesh_object(lsnif_ctx *ctx, const lsnif_object_desc *desc, lsnif_obj *out) {
+  const lsnif_mesh &m = desc->mesh;
+  const int n_mat = desc->cfg.n_mat;
+  if (n_mat < 1 || n_mat > 64) return fail(LSNIF_ERR_INVALID_ARG, "lsnif_load_object: n_mat = %d", n_mat);
+  if (!m.verts || !m.tris || m.nv <= 0 || m.nt <= 0)
+    return fail(LSNIF_ERR_INVALID_ARG, "lsnif_load_object: mesh needs vertices and triangles");
+  if (m.nt >= ((int64_t)1 << 30)) return fail(LSNIF_ERR_INVALID_ARG, "lsnif_load_object: too many triangles");
+  for (int64_t i = 0; i < 3 * m.nt; ++i)
+    if (m.tris[i] < 0 || m.tris[i] >= m.nv) return fail(LSNIF_ERR_INVALID_ARG, "lsnif_load_object: triangle index out of range");
+  for (int64_t i = 0; i < 3 * m.nv; ++i)
+    if (!std::isfinite(m.verts[i])) return fail(LSNIF_ERR_INVALID_ARG, "lsnif_load_object: non-finite vertex");
+  if (m.tri_mat)
+    for (int64_t i = 0; i < m.nt; ++i)
+      if (m.tri_mat[i] < 0 || m.tri_mat[i] >= n_mat) return fail(LSNIF_ERR_INVALID_ARG, "lsnif_load_object: material index out of range");
+  float bmin[3], bmax[3];
+  mesh_bbox(m.verts, m.nv, bmin, bmax);
+  std::vector<BvhNode> nodes;
+  std::vector<int32_t> order;
+  bvh_build(m.verts, m.tris, m.nt, nodes, order);
+  std::vector<float> tdata(12 * (size_t)m.nt, 0.f);  // v0, e1, e2 as float4
+  for (int64_t i = 0; i < m.nt; ++i) {
+    const int32_t *ix = m.tris + 3 * (int64_t)order[i];
+    const float *a = m.verts + 3 * (int64_t)ix[0], *b = m.verts + 3 * (int64_t)ix[1], *c = m.verts + 3 * (int64_t)ix[2];
+    float *w = tdata.data() + 12 * i;
+    for (int k = 0; k < 3; ++k) {
+      w[k] = a[k];
+      w[4 + k] = b[k] - a[k];
+      w[8 + k] = c[k] - a[k];
+    }
+  }
+  int slot = -1;
+  for (int s = 0; s < kMaxSlots; ++s)
+    if (!ctx->slots[s]) { slot = s; break; }
+  if (slot < 0) return fail(LSNIF_ERR_OUT_OF_MEMORY, "lsnif_load_object: object table full (%d)", kMaxSlots);
+  Object *o = new Object();
+  o->cfg = lsnif_config{};
+  o->cfg.n_mat = n_mat;
+  o->slot = slot;
+  ctx->gen[slot] = (uint16_t)(ctx->gen[slot] + 1);
+  if (ctx->gen[slot] == 0) ctx->gen[slot] = 1;
+  o->handle = ((uint32_t)ctx->gen[slot] << 16) | (uint32_t)(slot + 1);
+  memcpy(o->bmin, bmin, 12);
+  memcpy(o->bmax, bmax, 12);
+  o->bvh_nodes = (int64_t)nodes.size();
+  ctx->slots[slot] = o;
+  DevObject &d = o->d;
+  memset(&d, 0, sizeof d);
+  for (int a = 0; a < 3; ++a) {
+    d.bmin[a] = bmin[a];
+    d.inv_ext[a] = 1.0f / (bmax[a] - bmin[a]);
+  }
+  d.kind = 1;
+  d.n_mat = n_mat;
+  d.nt = m.nt;
+  std::vector<float> vn(3 * m.nv, 0.f), alb(3 * n_mat, 0.5f);
+  std::vector<int32_t> tm(m.nt, 0);
+  if (m.vnormals) memcpy(vn.data(), m.vnormals, 12 * m.nv);
+  if (m.tri_mat) memcpy(tm.data(), m.tri_mat, 4 * m.nt);
+  if (m.mat_albedo) memcpy(alb.data(), m.mat_albedo, 12 * n_mat);
+  int rc;
+  void *p;
+  cudaError_t e = cudaSuccess;
+  auto put = [&](const void **field, const void *src, size_t bytes, const char *what) -> bool {
+    if ((rc = obj_alloc(ctx, o, bytes, &p, what)) != LSNIF_OK) return false;
+    *field = p;
+    if (e == cudaSuccess) e = cudaMemcpy(p, src, bytes, cudaMemcpyHostToDevice);
+    return true;
+  };
+  if (!put((const void **)&d.verts, m.verts, 12 * m.nv, "mesh vertices") ||
+      !put((const void **)&d.tris, m.tris, 12 * m.nt, "mesh triangles") ||
+      !put((const void **)&d.vnormals, vn.data(), 12 * m.nv, "mesh normals") ||
+      !put((const void **)&d.tri_mat, tm.data(), 4 * m.nt, "mesh materials") ||
+      !put((const void **)&d.albedo, alb.data(), 12 * n_mat, "material albedo") ||
+      !put((const void **)&d.bvh_nodes, nodes.data(), sizeof(BvhNode) * nodes.size(), "BVH nodes") ||
+      !put((const void **)&d.bvh_tris, tdata.data(), 4 * tdata.size(), "BVH triangles") ||
+      !put((const void **)&d.bvh_order, order.data(), 4 * order.size(), "BVH order")) {
+    free_object(ctx, o);
+    return rc;
+  }
+  d.handle = o->handle;
+  d.valid = 1;
+  if (e == cudaSuccess) e = cudaMemcpy(ctx->d_objs + slot, &d, sizeof d, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) { free_object(ctx, o); return cuda_fail(e, "lsnif_load_object: upload mesh object"); }
+  ctx->n_slots_used = std::max(ctx->n_slots_used, slot + 1);
+  *out = o->handle;
+  return LSNIF_OK;
+}
+
 extern "C" int lsnif_load_object(lsnif_ctx *ctx, const lsnif_object_desc *desc, lsnif_obj *out) {
   if (!ctx || !desc || !out) return fail(LSNIF_ERR_INVALID_ARG, "lsnif_load_object: NULL argument");
   *out = 0;
   cudaSetDevice(ctx->device);
+  if (!desc->blob && desc->bvh_below_faces > 0 && desc->mesh.nt < desc->bvh_below_faces)
+    return load_mesh_object(ctx, desc, out);
   lsnif_config cfg;
   float bmin[3], bmax[3];
   std::vector<int32_t> res;
@@ -665,12 +759,17 @@ extern "C" int lsnif_get_object_info(lsnif_ctx *ctx, lsnif_obj h, lsnif_object_i
   const lsnif_config &c = o->cfg;
   out->footprint_fp16_bytes = ((size_t)c.V * c.V * c.V) / 8 + 2 * (((size_t)c.L << c.log2_T) * c.F) +
                               2 * (size_t)o->n_params_mlp;
+  out->kind = o->d.kind;
+  out->n_triangles = o->d.nt;
+  out->bvh_nodes = o->bvh_nodes;
+  if (o->d.kind != 0) out->footprint_fp16_bytes = 0;
   return LSNIF_OK;
 }
 
 extern "C" int lsnif_save_object(lsnif_ctx *ctx, lsnif_obj h, void *buf, size_t *inout_len) {
   Object *o = find_object(ctx, h);
   if (!o) return fail(LSNIF_ERR_BAD_HANDLE, "lsnif_save_object: bad handle %u", h);
+  if (o->d.kind != 0) return fail(LSNIF_ERR_UNSUPPORTED, "lsnif_save_object: object %u is a mesh object (no LSNIF state)", o->handle);
   if (!inout_len) return fail(LSNIF_ERR_INVALID_ARG, "lsnif_save_object: inout_len is NULL");
   size_t need = blob_size(o);
   if (!buf) { *inout_len = need; return LSNIF_OK; }
@@ -709,6 +808,7 @@ extern "C" int lsnif_save_object(lsnif_ctx *ctx, lsnif_obj h, void *buf, size_t 
 extern "C" int lsnif_read_params(lsnif_ctx *ctx, lsnif_obj h, int which, void *dst, size_t bytes) {
   Object *o = find_object(ctx, h);
   if (!o) return fail(LSNIF_ERR_BAD_HANDLE, "lsnif_read_params: bad handle %u", h);
+  if (o->d.kind != 0) return fail(LSNIF_ERR_UNSUPPORTED, "lsnif_read_params: object %u is a mesh object (no LSNIF state)", o->handle);
   if (!dst) return fail(LSNIF_ERR_INVALID_ARG, "lsnif_read_params: dst is NULL");
   cudaSetDevice(ctx->device);
   const lsnif_config &c = o->cfg;
@@ -734,6 +834,7 @@ extern "C" int lsnif_read_params(lsnif_ctx *ctx, lsnif_obj h, int which, void *d
 extern "C" int lsnif_write_params(lsnif_ctx *ctx, lsnif_obj h, int which, const void *src, size_t bytes) {
   Object *o = find_object(ctx, h);
   if (!o) return fail(LSNIF_ERR_BAD_HANDLE, "lsnif_write_params: bad handle %u", h);
+  if (o->d.kind != 0) return fail(LSNIF_ERR_UNSUPPORTED, "lsnif_write_params: object %u is a mesh object (no LSNIF state)", o->handle);
   if (!src) return fail(LSNIF_ERR_INVALID_ARG, "lsnif_write_params: src is NULL");
   cudaSetDevice(ctx->device);
   const lsnif_config &c = o->cfg;

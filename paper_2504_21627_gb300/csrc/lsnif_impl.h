@@ -67,6 +67,14 @@ struct DevObject {
   const int32_t *vox_tris;
   int64_t nt;
 
+  // object kind: 0 = LSNIF (voxels, hash grid, network); 1 = a triangle mesh
+  // answered exactly through its BVH (the hybrid pipeline's non-LSNIF
+  // objects, Sec. 4)
+  int32_t kind;
+  const float4 *bvh_nodes;   // 2 float4 per node (BvhNode)
+  const float4 *bvh_tris;    // 3 float4 per stored triangle: v0, e1 = v1 - v0, e2 = v2 - v0
+  const int32_t *bvh_order;  // stored position -> mesh triangle
+
   uint32_t handle;  // handle the slot currently holds (0 = free)
   int32_t valid;
 };
@@ -144,6 +152,8 @@ cudaError_t launch_tables_to_half(const float *src, uint16_t *dst, int64_t n, cu
 bool fused8_supported(const DevObject &host_obj);
 size_t fused8_smem_bytes(const DevObject &host_obj, int H_max);
 cudaError_t launch_fused8(const QueryLaunch &q, const DevObject &host_obj, int variant, int *launches);
+// exact nearest-triangle query of the rays whose object is a mesh object
+cudaError_t launch_mesh_query(const QueryLaunch &q, int *launches);
 int fused8_variant_count();
 void fused8_variant_shape(int variant, int *threads, int *levels);
 cudaError_t launch_max_abs_half(const uint16_t *v, int64_t n, uint32_t *out_bits, cudaStream_t st);

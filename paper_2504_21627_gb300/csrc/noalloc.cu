@@ -68,7 +68,12 @@ extern "C" int lsnif_query_rays_noalloc(lsnif_ctx *ctx, const lsnif_rays *r, lsn
   const Object *rep = nullptr;
   uint32_t umma_max = 0;
   bool mixed = false;
+  bool mesh = false;
   auto add = [&](const Object *o) {
+    if (o->d.kind != 0) {
+      mesh = true;
+      return;
+    }
     H = std::max(H, o->cfg.H);
     umma_max = std::max(umma_max, o->d.umma_bytes);
     if (!rep) rep = o;
@@ -81,8 +86,10 @@ extern "C" int lsnif_query_rays_noalloc(lsnif_ctx *ctx, const lsnif_rays *r, lsn
   } else {
     for (int s = 0; s < ctx->n_slots_used; ++s)
       if (ctx->slots[s]) add(ctx->slots[s]);
-    if (!rep) return fail(LSNIF_ERR_BAD_HANDLE, "lsnif_query_rays_noalloc: no objects are loaded");
+    if (!rep && !mesh) return fail(LSNIF_ERR_BAD_HANDLE, "lsnif_query_rays_noalloc: no objects are loaded");
   }
+  if (mesh || !rep)
+    return fail(LSNIF_ERR_UNSUPPORTED, "lsnif_query_rays_noalloc: mesh objects are answered by lsnif_query_rays");
   DevObject hobj = rep->d;
   hobj.umma_bytes = umma_max;
   if (mixed || !fused_supported(hobj) || fused_smem_bytes(hobj, H) > 232448)

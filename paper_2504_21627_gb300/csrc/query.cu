@@ -41,7 +41,8 @@ __global__ void __launch_bounds__(256) trace_kernel(QueryLaunch q, int smem_hist
     int ea;
     uint32_t dupm = 0u;
     float tmin = q.rays.tmin[i];
-    bool live = to_unit(ob, q.rays.ox[i], q.rays.oy[i], q.rays.oz[i], q.rays.dx[i], q.rays.dy[i], q.rays.dz[i], o,
+    bool live = ob.kind == 0 &&
+                to_unit(ob, q.rays.ox[i], q.rays.oy[i], q.rays.oz[i], q.rays.dx[i], q.rays.dy[i], q.rays.dz[i], o,
                         d) &&
                 unit_slab(o, d, tmin, t0, t1, ea);
     if (live) {
@@ -202,7 +203,8 @@ __global__ void __launch_bounds__(256) trace_pool_kernel(QueryLaunch q, int smem
             const DevObject &ob = q.objs[R.s];
             int ea;
             float t0, t1;
-            bool live = to_unit(ob, q.rays.ox[my], q.rays.oy[my], q.rays.oz[my], q.rays.dx[my], q.rays.dy[my],
+            bool live = ob.kind == 0 &&
+                        to_unit(ob, q.rays.ox[my], q.rays.oy[my], q.rays.oz[my], q.rays.dx[my], q.rays.dy[my],
                                 q.rays.dz[my], R.o, R.d) &&
                         unit_slab(R.o, R.d, q.rays.tmin[my], t0, t1, ea);
             if (!live) {

@@ -104,10 +104,15 @@ struct Shape {
   const Object *rep = nullptr;   // representative object (fused: F/width)
   uint32_t umma_max = 0;
   bool mixed_fused = false;      // objects differ in F or width
+  bool has_mesh = false;         // some object of the batch is a mesh object
 };
 
 static int shape_of(lsnif_ctx *ctx, const lsnif_rays *r, Shape *sh) {
   auto add = [&](const Object *o) {
+    if (o->d.kind != 0) {  // mesh objects take no part in the LSNIF launches
+      sh->has_mesh = true;
+      return;
+    }
     sh->H = std::max(sh->H, o->cfg.H);
     sh->n_in = std::max(sh->n_in, o->d.n_in);
     sh->wmax = std::max(sh->wmax, std::max(o->d.width, o->d.n_out_pad));
@@ -122,7 +127,7 @@ static int shape_of(lsnif_ctx *ctx, const lsnif_rays *r, Shape *sh) {
   } else {
     for (int s = 0; s < ctx->n_slots_used; ++s)
       if (ctx->slots[s]) add(ctx->slots[s]);
-    if (!sh->rep) return fail(LSNIF_ERR_BAD_HANDLE, "query: no objects are loaded");
+    if (!sh->rep && !sh->has_mesh) return fail(LSNIF_ERR_BAD_HANDLE, "query: no objects are loaded");
   }
   sh->n_slots = std::max(ctx->n_slots_used, 1);
   return LSNIF_OK;
@@ -144,10 +149,10 @@ static int ensure_fp8_for(lsnif_ctx *ctx, const lsnif_rays *r, cudaStream_t st) 
   if (!r->obj) {
     Object *o = find_object(ctx, r->single_obj);
     if (!o) return fail(LSNIF_ERR_BAD_HANDLE, "query: bad object handle %u", r->single_obj);
-    return ensure_fp8(ctx, o, st);
+    return o->d.kind != 0 ? LSNIF_OK : ensure_fp8(ctx, o, st);
   }
   for (int s = 0; s < ctx->n_slots_used; ++s)
-    if (ctx->slots[s] && (rc = ensure_fp8(ctx, ctx->slots[s], st))) return rc;
+    if (ctx->slots[s] && ctx->slots[s]->d.kind == 0 && (rc = ensure_fp8(ctx, ctx->slots[s], st))) return rc;
   return LSNIF_OK;
 }
 
@@ -160,6 +165,25 @@ int lsnif::run_query(lsnif_ctx *ctx, Workspace *ws, const lsnif_rays *r, lsnif_h
   if (r->n == 0) return LSNIF_OK;
   Shape sh;
   if ((rc = shape_of(ctx, r, &sh))) return rc;
+  if (!sh.rep) {  // mesh objects only: the BVH query alone
+    QueryLaunch q{};
+    q.objs = ctx->d_objs;
+    q.n_slots = sh.n_slots;
+    q.rays = RaysArg{r->ox, r->oy, r->oz, r->dx, r->dy, r->dz, r->tmin, r->tmax, r->obj, r->single_obj, r->n};
+    q.hits = HitsArg{h->hit, h->t, h->nx, h->ny, h->nz, h->mat, h->ar, h->ag, h->ab, h->logits};
+    q.err = ctx->d_err;
+    q.stream = st;
+    int launches = 0;
+    cudaError_t e = launch_mesh_query(q, &launches);
+    if (profile) {
+      ctx->prof = lsnif_profile{};
+      ctx->prof.n_rays = r->n;
+      ctx->prof.launches = launches;
+      ctx->prof_valid = false;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "mesh query launch");
+    return LSNIF_OK;
+  }
   if (precision == LSNIF_FP8_FUSED) {
     if ((rc = ensure_fp8_for(ctx, r, st))) return rc;
     if ((rc = shape_of(ctx, r, &(sh = Shape{})))) return rc;
@@ -206,6 +230,9 @@ int lsnif::run_query(lsnif_ctx *ctx, Workspace *ws, const lsnif_rays *r, lsnif_h
     else if (precision == LSNIF_FP8_FUSED) e = launch_fused8(q, rep, ctx->fp8_variant, &launches);
     else e = launch_fused(q, rep, ctx->fused_variant, &launches);
   }
+  // rays on mesh objects were answered as misses by the traversal (no
+  // voxels); their BVH query overwrites them
+  if (e == cudaSuccess && sh.has_mesh) e = launch_mesh_query(q, &launches);
   if (profile) {
     cudaEventRecord(ctx->ev[3], st);
     cudaMemcpyAsync(ctx->d_prof_meta, q.s.meta, 16, cudaMemcpyDeviceToDevice, st);
@@ -235,6 +262,7 @@ static int query_graph(lsnif_ctx *ctx, const lsnif_rays *r, lsnif_hits *h, int p
   if (precision == LSNIF_FP8_FUSED && (rc = ensure_fp8_for(ctx, r, st))) return rc;
   Shape sh;
   if ((rc = shape_of(ctx, r, &sh))) return rc;
+  if (!sh.rep) return run_query(ctx, &ctx->ws, r, h, precision, st, false);
   const int n_in = precision == LSNIF_FP32_PLAIN ? sh.n_in : 0;
   if ((rc = ensure_workspace(ctx, &ctx->ws, r->n, sh.H, sh.n_slots, n_in))) return rc;
   if (ctx->graphs_ws != ctx->ws.base) clear_graphs(ctx);
@@ -409,6 +437,7 @@ extern "C" int lsnif_trace(lsnif_ctx *ctx, const lsnif_rays *rays, lsnif_trace_o
   if (!ctx || !rays || !out) return fail(LSNIF_ERR_INVALID_ARG, "lsnif_trace: NULL argument");
   Object *o = find_object(ctx, rays->single_obj);
   if (!o) return fail(LSNIF_ERR_BAD_HANDLE, "lsnif_trace: bad handle %u", rays->single_obj);
+  if (o->d.kind != 0) return fail(LSNIF_ERR_UNSUPPORTED, "lsnif_trace: object %u is a mesh object (no LSNIF state)", o->handle);
   lsnif_hits dummy{};
   int rc = check_rays(rays, &dummy);
   if (rc) return rc;
@@ -425,6 +454,7 @@ extern "C" int lsnif_encode(lsnif_ctx *ctx, lsnif_obj h, const float *pts, int64
                             void *stream) {
   Object *o = find_object(ctx, h);
   if (!o) return fail(LSNIF_ERR_BAD_HANDLE, "lsnif_encode: bad handle %u", h);
+  if (o->d.kind != 0) return fail(LSNIF_ERR_UNSUPPORTED, "lsnif_encode: object %u is a mesh object (no LSNIF state)", o->handle);
   if (n < 0 || (n > 0 && (!pts || !feats))) return fail(LSNIF_ERR_INVALID_ARG, "lsnif_encode: bad arguments");
   if (n == 0) return LSNIF_OK;
   cudaSetDevice(ctx->device);
@@ -436,6 +466,7 @@ extern "C" int lsnif_corner_indices(lsnif_ctx *ctx, lsnif_obj h, const float *pt
                                     void *stream) {
   Object *o = find_object(ctx, h);
   if (!o) return fail(LSNIF_ERR_BAD_HANDLE, "lsnif_corner_indices: bad handle %u", h);
+  if (o->d.kind != 0) return fail(LSNIF_ERR_UNSUPPORTED, "lsnif_corner_indices: object %u is a mesh object (no LSNIF state)", o->handle);
   if (n < 0 || (n > 0 && (!pts || !out))) return fail(LSNIF_ERR_INVALID_ARG, "lsnif_corner_indices: bad arguments");
   if (n == 0) return LSNIF_OK;
   cudaSetDevice(ctx->device);
@@ -447,6 +478,7 @@ extern "C" int lsnif_mlp(lsnif_ctx *ctx, lsnif_obj h, const float *X, int64_t n,
                          void *stream) {
   Object *o = find_object(ctx, h);
   if (!o) return fail(LSNIF_ERR_BAD_HANDLE, "lsnif_mlp: bad handle %u", h);
+  if (o->d.kind != 0) return fail(LSNIF_ERR_UNSUPPORTED, "lsnif_mlp: object %u is a mesh object (no LSNIF state)", o->handle);
   if (n < 0 || (n > 0 && (!X || !Z))) return fail(LSNIF_ERR_INVALID_ARG, "lsnif_mlp: bad arguments");
   if (n == 0) return LSNIF_OK;
   cudaSetDevice(ctx->device);

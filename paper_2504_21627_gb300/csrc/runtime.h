@@ -33,6 +33,7 @@ struct Object {
   int64_t step = 0;
   std::vector<void *> train_allocs;
   bool fp8_stale = true;   // the FP8 network no longer matches the parameters
+  int64_t bvh_nodes = 0;   // mesh objects: nodes of the BVH
 };
 
 // Scratch of one query stream. Grows on demand; freed with the context.

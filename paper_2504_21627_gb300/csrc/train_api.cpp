@@ -101,6 +101,7 @@ extern "C" int lsnif_make_training_rays(lsnif_ctx *ctx, lsnif_obj h, const float
                                         float *rays_out, uint8_t *surface, void *stream) {
   Object *o = find_object(ctx, h);
   if (!o) return fail(LSNIF_ERR_BAD_HANDLE, "lsnif_make_training_rays: bad handle %u", h);
+  if (o->d.kind != 0) return fail(LSNIF_ERR_UNSUPPORTED, "lsnif_make_training_rays: object %u is a mesh object (no LSNIF state)", o->handle);
   if (n < 0 || n_outside < 0 || n_outside > n || (n > 0 && (!u || !rays_out)))
     return fail(LSNIF_ERR_INVALID_ARG, "lsnif_make_training_rays: bad arguments");
   if (!o->d.vox_start)
@@ -116,6 +117,7 @@ extern "C" int lsnif_label_rays(lsnif_ctx *ctx, const lsnif_rays *rays, lsnif_la
   if (!ctx || !rays || !out) return fail(LSNIF_ERR_INVALID_ARG, "lsnif_label_rays: NULL argument");
   Object *o = find_object(ctx, rays->single_obj);
   if (!o) return fail(LSNIF_ERR_BAD_HANDLE, "lsnif_label_rays: bad handle %u", rays->single_obj);
+  if (o->d.kind != 0) return fail(LSNIF_ERR_UNSUPPORTED, "lsnif_label_rays: object %u is a mesh object (no LSNIF state)", o->handle);
   if (!o->d.vox_start) return fail(LSNIF_ERR_INVALID_ARG, "lsnif_label_rays: load the object with keep_mesh = 1");
   if (rays->n < 0) return fail(LSNIF_ERR_INVALID_ARG, "lsnif_label_rays: n < 0");
   if (rays->n == 0) return LSNIF_OK;
@@ -133,6 +135,7 @@ extern "C" int lsnif_train_step(lsnif_ctx *ctx, const lsnif_rays *rays, const ls
   if (!ctx || !rays || !labels || !opts) return fail(LSNIF_ERR_INVALID_ARG, "lsnif_train_step: NULL argument");
   Object *o = find_object(ctx, rays->single_obj);
   if (!o) return fail(LSNIF_ERR_BAD_HANDLE, "lsnif_train_step: bad handle %u", rays->single_obj);
+  if (o->d.kind != 0) return fail(LSNIF_ERR_UNSUPPORTED, "lsnif_train_step: object %u is a mesh object (no LSNIF state)", o->handle);
   if (rays->n <= 0 || rays->n > (1 << 24)) return fail(LSNIF_ERR_INVALID_ARG, "lsnif_train_step: batch of %lld rays", (long long)rays->n);
   if (!labels->occ || !labels->t_local || !labels->normal || !labels->albedo || !labels->mat)
     return fail(LSNIF_ERR_INVALID_ARG, "lsnif_train_step: labels need occ, t_local, normal, albedo and mat");

@@ -49,13 +49,15 @@ class Mesh(C.Structure):
 
 class ObjectDesc(C.Structure):
     _fields_ = [("cfg", Config), ("mesh", Mesh), ("tables", C.c_void_p), ("mlp", C.c_void_p),
-                ("keep_mesh", C.c_int32), ("blob", C.c_void_p), ("blob_len", C.c_size_t)]
+                ("keep_mesh", C.c_int32), ("blob", C.c_void_p), ("blob_len", C.c_size_t),
+                ("bvh_below_faces", C.c_int64)]
 
 
 class ObjectInfo(C.Structure):
     _fields_ = [("cfg", Config), ("bmin", C.c_float * 3), ("bmax", C.c_float * 3),
                 ("res", C.c_int32 * MAX_LEVELS), ("n_occupied", C.c_int64), ("n_params_mlp", C.c_int64),
-                ("device_bytes", C.c_size_t), ("footprint_fp16_bytes", C.c_size_t)]
+                ("device_bytes", C.c_size_t), ("footprint_fp16_bytes", C.c_size_t), ("kind", C.c_int32),
+                ("n_triangles", C.c_int64), ("bvh_nodes", C.c_int64)]
 
 
 class Rays(C.Structure):
@@ -135,6 +137,7 @@ SIGNATURES = {
     "lsnif_query_scene": (_I, [_P, C.POINTER(Rays), C.POINTER(Instance), _I, C.POINTER(Hits), _P, _I, _P]),
     "lsnif_bounce_rays": (_I, [_P, C.POINTER(Rays), C.POINTER(Hits), _P, C.c_float, _P, _P]),
     "lsnif_raster_gbuffer": (_I, [_P, C.POINTER(Camera), C.POINTER(Instance), _I, C.POINTER(GBufferS), _P]),
+    "lsnif_bvh_build_host": (_I, [_P, C.c_int64, _P, C.c_int64, _P, C.POINTER(C.c_int64), _P, C.POINTER(_I)]),
     "lsnif_trace": (_I, [_P, C.POINTER(Rays), C.POINTER(TraceOut), _P]),
     "lsnif_encode": (_I, [_P, _U32, _P, _I64, _P, _I, _P]),
     "lsnif_corner_indices": (_I, [_P, _U32, _P, _I64, _P, _P]),
@@ -207,6 +210,24 @@ def _stream(stream=None):
     return C.c_void_p(s.cuda_stream)
 
 
+BVH_NODE = np.dtype([("lo", np.float32, 3), ("a", np.int32), ("hi", np.float32, 3), ("n", np.int32)])
+
+
+def bvh_build_host(verts, tris):
+    """The mesh objects' BVH builder run on the host (no GPU): returns
+    (nodes as a BVH_NODE array, order, depth)."""
+    lib = load_library()
+    v = np.ascontiguousarray(verts, np.float32)
+    t = np.ascontiguousarray(tris, np.int32)
+    nt = t.shape[0]
+    nodes = np.zeros(max(2 * nt - 1, 1), BVH_NODE)
+    order = np.zeros(nt, np.int32)
+    nn, depth = C.c_int64(), _I()
+    _check(lib.lsnif_bvh_build_host(_ptr(v), v.shape[0], _ptr(t), nt, nodes.ctypes.data, C.byref(nn), _ptr(order),
+                                    C.byref(depth)))
+    return nodes[:nn.value], order, depth.value
+
+
 def cfg_struct(cfg) -> Config:
     """An inputs.Config (or any object with the same fields) -> Config."""
     return Config(cfg.V, cfg.H, cfg.L, cfg.F, cfg.log2_T, cfg.N_min, cfg.N_max, cfg.n_hidden, cfg.width, cfg.n_mat,
@@ -271,8 +292,11 @@ class Context:
 
     # ---- objects -------------------------------------------------------------
     def load_object(self, mesh=None, cfg=None, tables=None, mlp=None, keep_mesh: bool = False,
-                    blob: bytes | None = None) -> int:
+                    blob: bytes | None = None, bvh_below_faces: int = 0) -> int:
+        """bvh_below_faces: meshes with fewer triangles stay mesh objects
+        (triangles + BVH, exact answers) instead of becoming LSNIF objects."""
         d = ObjectDesc()
+        d.bvh_below_faces = int(bvh_below_faces)
         keep = []
         if blob is not None:
             buf = C.create_string_buffer(blob, len(blob))
@@ -300,6 +324,14 @@ class Context:
         out = C.c_uint32()
         _check(self.lib.lsnif_load_object(self.h, C.byref(d), C.byref(out)))
         return out.value
+
+    def load_mesh(self, mesh, n_mat: int | None = None) -> int:
+        """A mesh object: the triangles and a BVH, answered exactly."""
+        from types import SimpleNamespace
+        cfg = SimpleNamespace(V=0, H=0, L=0, F=0, log2_T=0, N_min=0, N_max=0, n_hidden=0, width=0,
+                              n_mat=int(mesh.n_mat if n_mat is None else n_mat), activation=0, table_init=0.0,
+                              seed=0)
+        return self.load_object(mesh, cfg, bvh_below_faces=int(mesh.tris.shape[0]) + 1)
 
     def unload_object(self, obj: int):
         _check(self.lib.lsnif_unload_object(self.h, obj))

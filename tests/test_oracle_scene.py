@@ -169,3 +169,47 @@ def test_bounce_rays():
     out0 = O.bounce_rays(rays[:, :5], np.ones(5, bool), t[:5], normal[50:55], np.zeros((5, 2)), eps=0.0)
     nf0 = np.where((np.einsum("ij,ij->i", normal[50:55], d[:5]) > 0)[:, None], -normal[50:55], normal[50:55])
     assert np.allclose(out0[3:6].T, nf0, atol=1e-12)
+
+
+def test_mesh_object_in_a_scene_is_exact():
+    """A mesh object (a flat quad, vertex normals +z, two materials) through a
+    rotated, scaled, translated instance beside an LSNIF cube: hits on the
+    quad are the plane intersection in closed form, with the world normal
+    A^T e_z normalised and the triangle's material; a ray hitting both keeps
+    the nearer."""
+    v = np.array([[-1, -1, 0], [1, -1, 0], [-1, 1, 0], [1, 1, 0]], np.float32)
+    quad = I.Mesh(v, np.array([[0, 1, 2], [1, 3, 2]], np.int32), np.tile(np.array([[0, 0, 1.0]], np.float32), (4, 1)),
+                  np.array([0, 1], np.int32), np.array([[0.2, 0.3, 0.4], [0.6, 0.5, 0.1]], np.float32), 2)
+    cube_obj, _, _ = _cube_object()
+    R = I.rotation([0.3, 0.4, 1.0], 0.8)
+    A = R.T / 1.5
+    c = np.array([0.5, -2.0, 0.7])
+    insts = [O.Instance(1, A, -A @ c), O.Instance(0, np.eye(3), np.zeros(3))]
+    objs = [cube_obj, O.mesh_object(quad)]
+    g = np.random.default_rng(7)
+    n = 4000
+    # rays from above the quad's plane towards random points of the quad
+    nrm_w = R @ np.array([0.0, 0.0, 1.0])
+    tgt_local = np.c_[g.uniform(-1.2, 1.2, (n, 2)), np.zeros(n)]
+    tgt = (R @ (1.5 * tgt_local).T).T + c
+    eye = tgt + 4.0 * nrm_w + g.normal(size=(n, 3))
+    rays = np.zeros((8, n), np.float32)
+    rays[0:3] = eye.T
+    rays[3:6] = (tgt - eye).T
+    rays[7] = np.inf
+    res = O.scene_query(objs, insts, rays)
+    r = rays.astype(np.float64)
+    local = O.to_object_frame(r, insts[0]).astype(np.float32).astype(np.float64)
+    t_plane = -local[2] / local[5]
+    p = local[0:3] + t_plane * local[3:6]
+    on_quad = (np.abs(p[0]) < 1 - 1e-6) & (np.abs(p[1]) < 1 - 1e-6) & (np.abs(p[0] + p[1]) > 1e-6)
+    only_quad = on_quad & (res["inst"] != 1)
+    assert only_quad.sum() > 1000
+    assert np.all(res["inst"][only_quad] == 0) and np.all(res["hit"][only_quad])
+    assert np.allclose(res["t"][only_quad], t_plane[only_quad], rtol=1e-12)
+    want_n = A.T @ np.array([0, 0, 1.0])
+    assert np.allclose(res["normal"][only_quad], want_n / np.linalg.norm(want_n), atol=1e-12)
+    tri = np.where(p[0] + p[1] < 0, 0, 1)
+    assert np.array_equal(res["mat"][only_quad], tri[only_quad])
+    assert np.allclose(res["albedo"][only_quad], quad.albedo[tri[only_quad]])
+    assert np.all(~res["hit"][~on_quad & (res["inst"] != 1)])
