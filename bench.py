@@ -503,6 +503,45 @@ def _scene_raster(args, ctx, spec, handles, insts, stress):
     ctx.close()
 
 
+def bench_mesh1(args):
+    """The torus workload's mesh (200k triangles) kept as a mesh object --
+    triangles and a BVH, the hybrid pipeline's non-LSNIF objects (Sec. 4) --
+    queried with the same 2048 x 2048 primary rays: exact nearest hits by
+    BVH traversal, beside the LSNIF query of the same mesh."""
+    import torch
+    from paper_2504_21627_gb300 import lsnif
+    cfg, mesh, params, rays_np = workload(args.side)
+    n = rays_np.shape[1]
+    ctx = lsnif.Context(0)
+    hm = ctx.load_mesh(mesh)
+    hl = ctx.load_object(mesh, cfg, tables=params.tables, mlp=params.packed_mlp())
+    rays = torch.from_numpy(rays_np).cuda()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    out = {"workload": "mesh1", "triangles": int(mesh.tris.shape[0]), "rays": n}
+    for name, h, prec in (("bvh", hm, lsnif.FP32_PLAIN), ("lsnif_bf16", hl, lsnif.BF16_FUSED)):
+        res = ctx.query_rays(rays, obj=h, precision=prec)
+        for _ in range(args.warmup):
+            ctx.query_rays(rays, obj=h, precision=prec, out=res)
+        ms = []
+        for _ in range(args.steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.query_rays(rays, obj=h, precision=prec, out=res)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        ctx.check()
+        info = ctx.object_info(h)
+        out[name] = {"mrays_s": n / (np.mean(ms) / 1e3) / 1e6, "ms_per_step": float(np.mean(ms)),
+                     "hits": int(res.hit.sum().item()), "device_mb": info.device_bytes / 2 ** 20}
+        if name == "bvh":
+            out[name]["bvh_nodes"] = int(info.bvh_nodes)
+    print(json.dumps(out))
+    ctx.close()
+
+
 def bench_scene(args):
     """Path-tracer-shaped stress: 32 instances of 8 unique objects (50k..1M
     triangles, V 128, L 16, F 4, T 2^21, 4 x 128 network; `--scene-net
@@ -524,7 +563,7 @@ def bench_scene(args):
         p = I.random_params(cfg, seed=3000 + i, table_range=0.05, bias_range=0.1)
         p.weights[-1][1][0] = 1.0   # occupancy logit biased towards hits, so bounces continue
         handles.append(ctx.load_object(mesh, cfg, tables=p.tables, mlp=p.packed_mlp(),
-                                       keep_mesh=args.primary == "raster"))
+                                       keep_mesh=args.primary == "raster", bvh_below_faces=args.bvh_below_faces))
     if args.variant8 is not None:
         ctx.set_variant8(args.variant8)
     insts = [(handles[o], A, b) for o, A, b in I.seeded_instances(args.scene_instances, len(spec), seed=9,
@@ -551,6 +590,7 @@ def bench_scene(args):
 
     out = {"workload": "scene", "metric": "Mrays/s over 3 bounces of an instanced scene (misses included)",
            "instances": len(insts), "unique_objects": len(spec), "rays_per_bounce": n,
+           "mesh_objects": int(sum(ctx.object_info(h).kind == 1 for h in handles)),
            "network": "L=16 F=4 T=2^21, 1152-128x4-12" if stress else "L=16 F=2 T=2^21, 576-64x4-12"}
     fast = (("fp8", lsnif.FP8_FUSED, max(3, args.steps // 4)),) if stress else \
         (("bf16", lsnif.BF16_FUSED, max(3, args.steps // 4)), ("fp8", lsnif.FP8_FUSED, max(3, args.steps // 4)))
@@ -588,7 +628,7 @@ def main():
     ap.add_argument("--variant", type=int, default=None,
                     help="fused-kernel variant to time instead of the autotuner's choice")
     ap.add_argument("--side", type=int, default=2048, help="image side; below 2048 only for profiling captures")
-    ap.add_argument("--workload", default="torus4m", choices=["torus4m", "batched", "serving", "train", "scene", "stress1"],
+    ap.add_argument("--workload", default="torus4m", choices=["torus4m", "batched", "serving", "train", "scene", "stress1", "mesh1"],
                     help="torus4m is the headline; the others print their own line")
     ap.add_argument("--requests", type=int, default=200)
     ap.add_argument("--scene-width", type=int, default=1920)
@@ -598,6 +638,8 @@ def main():
     ap.add_argument("--scene-objects", type=int, default=8, help="unique objects (below 8 only for profiling)")
     ap.add_argument("--scene-instances", type=int, default=32)
     ap.add_argument("--scene-spp", type=int, default=4)
+    ap.add_argument("--bvh-below-faces", type=int, default=0,
+                    help="scene workload: objects with fewer triangles stay mesh objects (BVH), Sec. 4")
     ap.add_argument("--primary", default="lsnif", choices=["lsnif", "raster"],
                     help="scene workload: primary rays by LSNIF, or by the rasterised G-buffer (Sec. 4)")
     args = ap.parse_args()
@@ -614,6 +656,8 @@ def main():
         return bench_scene(args)
     if args.workload == "stress1":
         return bench_stress1(args)
+    if args.workload == "mesh1":
+        return bench_mesh1(args)
 
     import torch
     import torch.distributed as dist
