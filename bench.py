@@ -385,6 +385,78 @@ def bench_train(args):
     print(json.dumps(out))
 
 
+def bench_sweep(args):
+    """Parameter and quality sweeps (Sec. 6.1 parameter study; Table 1 low /
+    high quality) on a synthetic mesh: each configuration is trained on the
+    GPU from its seeded initialisation (balanced rays, labels by ray casting,
+    2000 steps of batch 2^14 unless swept) and evaluated on held-out rays
+    against the exact answers of the same mesh kept as a mesh object (BVH):
+    visibility accuracy, hit-distance error (median and 90th percentile, in
+    units of the box diagonal), normal angle (median, degrees) and material
+    accuracy. Memory from the storage model (bits + FP16 tables + FP16
+    network). Geometric error stands in for the paper's FLIP image error."""
+    import torch
+    from paper_2504_21627_gb300 import lsnif
+    mesh = I.noise_torus_tris(11, 50000, amplitude=0.08, n_mat=4)
+    base = dict(V=32, H=18, L=2, F=4, log2_T=17, N_min=64, N_max=128, n_hidden=2, width=128, n_mat=4)
+    runs = [("base (paper's V 32, H 18, T 2^17, 2 x 128)", {}, 2000)]
+    runs += [(f"V {v}", {"V": v}, 2000) for v in (8, 16, 64)]
+    runs += [(f"H {h}", {"H": h}, 2000) for h in (6, 10, 26)]
+    runs += [(f"T 2^{t}", {"log2_T": t}, 2000) for t in (11, 13, 15, 19)]
+    runs += [(f"{st} training steps", {}, st) for st in (100, 700)]
+    runs += [("low quality (width 64, H 10)", {"width": 64, "H": 10}, 2000)]
+    if args.steps < 20:   # a shortened sweep for smoke runs
+        runs = runs[:2]
+    ctx = lsnif.Context(0)
+    hm = ctx.load_mesh(mesh)
+    lo, hi = mesh.verts.min(0), mesh.verts.max(0)
+    diag = float(np.linalg.norm(hi.astype(np.float64) - lo))
+    test = torch.from_numpy(I.rays_sphere_to_box(200000, 2.5 * diag / 2, lo, hi, seed=77)).cuda()
+    ref = ctx.query_rays(test, obj=hm, precision=lsnif.FP32_PLAIN)
+    torch.cuda.synchronize()
+    r_hit = ref.hit.bool()
+    rows = []
+    for name, over, steps in runs:
+        c = dict(base, **over)
+        cfg = I.Config(**c)
+        h = ctx.load_object(mesh, cfg, keep_mesh=True)
+        n_pool, B = 1 << 20, 1 << 14
+        u = torch.rand((n_pool, lsnif.TRAIN_UNIFORMS), device="cuda", generator=torch.Generator("cuda").manual_seed(3))
+        pool, _ = ctx.make_training_rays(h, u, n_outside=n_pool // 2)
+        lab = ctx.label_rays(pool, h)
+        keep = lab["k"] > 0
+        pool = pool[:, keep].contiguous()
+        lab = {k: v[keep].contiguous() for k, v in lab.items()}
+        gen = torch.Generator("cuda").manual_seed(5)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for s in range(steps):
+            idx = torch.randint(0, pool.shape[1], (B,), device="cuda", generator=gen)
+            ctx.train_step(pool[:, idx].contiguous(), {k: v[idx].contiguous() for k, v in lab.items()}, h,
+                           lr=0.01, stats=False)
+        torch.cuda.synchronize()
+        t_train = time.perf_counter() - t0
+        q = ctx.query_rays(test, obj=h, precision=lsnif.FP32_PLAIN)
+        torch.cuda.synchronize()
+        q_hit = q.hit.bool()
+        both = q_hit & r_hit
+        terr = ((q.t - ref.t).abs()[both] / diag).cpu().numpy()
+        cosang = (q.normal[:, both] * ref.normal[:, both]).sum(0).clamp(-1, 1).cpu().numpy()
+        info = ctx.object_info(h)
+        rows.append({"run": name, "V": c["V"], "H": c["H"], "log2_T": c["log2_T"], "width": c["width"],
+                     "train_steps": steps, "train_s": t_train,
+                     "visibility_acc": float((q_hit == r_hit).float().mean().item()),
+                     "t_err_p50": float(np.median(terr)), "t_err_p90": float(np.quantile(terr, 0.9)),
+                     "normal_deg_p50": float(np.degrees(np.median(np.arccos(cosang)))),
+                     "material_acc": float((q.mat[both] == ref.mat[both]).float().mean().item()),
+                     "memory_fp16_kb": info.footprint_fp16_bytes / 1024})
+        ctx.unload_object(h)
+    out = {"workload": "sweep", "mesh_triangles": int(mesh.tris.shape[0]), "test_rays": int(test.shape[1]),
+           "reference_hits": int(r_hit.sum().item()), "base": base, "rows": rows}
+    print(json.dumps(out))
+    ctx.close()
+
+
 def bench_stress1(args):
     """One object of the stress scene's network shape (L 16, F 4, T 2^21,
     1152-128x4-12) on the torus workload's mesh and camera: FP8 fused and
@@ -628,7 +700,7 @@ def main():
     ap.add_argument("--variant", type=int, default=None,
                     help="fused-kernel variant to time instead of the autotuner's choice")
     ap.add_argument("--side", type=int, default=2048, help="image side; below 2048 only for profiling captures")
-    ap.add_argument("--workload", default="torus4m", choices=["torus4m", "batched", "serving", "train", "scene", "stress1", "mesh1"],
+    ap.add_argument("--workload", default="torus4m", choices=["torus4m", "batched", "serving", "train", "scene", "stress1", "mesh1", "sweep"],
                     help="torus4m is the headline; the others print their own line")
     ap.add_argument("--requests", type=int, default=200)
     ap.add_argument("--scene-width", type=int, default=1920)
@@ -658,6 +730,8 @@ def main():
         return bench_stress1(args)
     if args.workload == "mesh1":
         return bench_mesh1(args)
+    if args.workload == "sweep":
+        return bench_sweep(args)
 
     import torch
     import torch.distributed as dist
