@@ -415,6 +415,46 @@ int lsnif::ensure_fp8(lsnif_ctx *ctx, Object *o, cudaStream_t st) {
   return LSNIF_OK;
 }
 
+// Chebyshev (L-infinity) distance, in voxels, from every voxel to the
+// nearest occupied one, capped at `cap` -- separable: the distance along x
+// within each row, then D(x,y,z) = min over |j| <= cap of max(|j|,
+// D_x(x,y+j,z)), then the same along z (the maximum norm splits into
+// per-axis maxima, so the minimum over all occupied voxels can be taken one
+// axis at a time).
+static std::vector<uint8_t> occupancy_distance(const std::vector<uint32_t> &occ, int V, int cap) {
+  const size_t n = (size_t)V * V * V;
+  std::vector<uint8_t> a(n), b(n);
+  for (size_t row = 0; row < (size_t)V * V; ++row) {
+    uint8_t *r = a.data() + row * V;
+    int last = -1000000;
+    for (int x = 0; x < V; ++x) {
+      const size_t id = row * V + x;
+      if ((occ[id >> 5] >> (id & 31)) & 1u) last = x;
+      r[x] = (uint8_t)std::min(cap, x - last);
+    }
+    last = 1000000;
+    for (int x = V - 1; x >= 0; --x) {
+      const size_t id = row * V + x;
+      if ((occ[id >> 5] >> (id & 31)) & 1u) last = x;
+      r[x] = (uint8_t)std::min<int>(r[x], std::min(cap, last - x));
+    }
+  }
+  auto pass = [&](const std::vector<uint8_t> &src, std::vector<uint8_t> &dst, size_t stride) {
+    for (size_t id = 0; id < n; ++id) {
+      const int c = (int)((id / stride) % (size_t)V);
+      int best = src[id];
+      for (int j = 1; j < best && j <= cap; ++j) {
+        if (c - j >= 0) best = std::min(best, std::max(j, (int)src[id - j * stride]));
+        if (c + j < V) best = std::min(best, std::max(j, (int)src[id + j * stride]));
+      }
+      dst[id] = (uint8_t)best;
+    }
+  };
+  pass(a, b, (size_t)V);
+  pass(b, a, (size_t)V * V);
+  return a;
+}
+
 // A mesh object: the triangles, shading normals, materials and a BVH built
 // on the host; no voxels, tables or network.
 static int load_mesh_object(lsnif_ctx *ctx, const lsnif_object_desc *desc, lsnif_obj *out) {
@@ -649,24 +689,9 @@ extern "C" int lsnif_load_object(lsnif_ctx *ctx, const lsnif_object_desc *desc, 
   }                                                                        \
   d.field = (type)p;
   OALLOC(occ, const uint32_t *, 4 * occ.size(), "occupancy");
-  // brick masks for empty-space skipping in the traversal: 32 bricks per
-  // axis (bricks of at least 2 voxels, so fewer for V < 64) and 16 bricks
-  // per axis, twice as wide
-  d.log2B = std::max(1, d.log2V - 5);
-  const int nbk = cfg.V >> d.log2B, nbk2 = cfg.V >> (d.log2B + 1);
-  std::vector<uint32_t> brick(((size_t)nbk * nbk * nbk + 31) / 32, 0u);
-  std::vector<uint32_t> brick2(((size_t)nbk2 * nbk2 * nbk2 + 31) / 32, 0u);
-  for (size_t id = 0; id < (size_t)cfg.V * cfg.V * cfg.V; ++id) {
-    if (!((occ[id >> 5] >> (id & 31)) & 1u)) continue;
-    const size_t x = id % cfg.V, y = (id / cfg.V) % cfg.V, z = id / ((size_t)cfg.V * cfg.V);
-    const size_t b = ((z >> d.log2B) * nbk + (y >> d.log2B)) * nbk + (x >> d.log2B);
-    brick[b >> 5] |= 1u << (b & 31);
-    const int l2 = d.log2B + 1;
-    const size_t b2 = ((z >> l2) * nbk2 + (y >> l2)) * nbk2 + (x >> l2);
-    brick2[b2 >> 5] |= 1u << (b2 & 31);
-  }
-  OALLOC(brick, const uint32_t *, 4 * brick.size(), "brick mask");
-  OALLOC(brick2, const uint32_t *, 4 * brick2.size(), "brick mask");
+  // occupancy distance field for empty-space skipping in the traversal
+  const std::vector<uint8_t> dist = occupancy_distance(occ, cfg.V, kDistCap);
+  OALLOC(dist, const uint8_t *, dist.size(), "occupancy distance");
   OALLOC(tab32, const float *, 4 * nt, "tables");
   OALLOC(tab16, const uint16_t *, 2 * nt, "FP16 tables");
   OALLOC(mlp32, const float *, 4 * (size_t)o->n_params_mlp, "network");
@@ -679,8 +704,7 @@ extern "C" int lsnif_load_object(lsnif_ctx *ctx, const lsnif_object_desc *desc, 
   OALLOC(umma, const uint8_t *, d.umma_bytes, "tensor-core weights");
   OALLOC(plain_out, const float *, 4 * ((size_t)d.n_out_pad * cfg.width + d.n_out_pad), "padded output layer");
   cudaError_t e = cudaMemcpy((void *)d.occ, occ.data(), 4 * occ.size(), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy((void *)d.brick, brick.data(), 4 * brick.size(), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy((void *)d.brick2, brick2.data(), 4 * brick2.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy((void *)d.dist, dist.data(), dist.size(), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) { free_object(ctx, o); return cuda_fail(e, "upload occupancy"); }
   cudaMemset((void *)d.umma, 0, d.umma_bytes);
   if ((rc = upload_params(ctx, o, tab_src, mlp_src)) != LSNIF_OK) { free_object(ctx, o); return rc; }

@@ -17,6 +17,7 @@ constexpr uint32_t kPi3 = 805459861u;
 constexpr int kMaxCap = 32;          // H/2 <= 32
 constexpr int kBuckets = kMaxCap + 1;  // per object: k = 0..32
 constexpr int kTileM = 128;          // rays per tensor-core tile (tcgen05 M)
+constexpr int kDistCap = 32;         // largest stored occupancy distance
 
 // error word bits written by kernels (never trap, never hang)
 enum DeviceError : int {
@@ -34,9 +35,10 @@ struct DevObject {
   int32_t log2V;
   float invV;
   const uint32_t *occ;  // ceil(V^3/32) words
-  const uint32_t *brick;   // bit (bz*nb + by)*nb + bx: brick holds an occupied voxel
-  const uint32_t *brick2;  // the same for bricks twice as wide
-  int32_t log2B;           // bricks are 2^log2B voxels wide, nb = V >> log2B per axis
+  // per voxel, the Chebyshev distance (in voxels) to the nearest occupied
+  // voxel, capped at kDistCap: 0 = occupied; D >= 1 = every voxel within
+  // D - 1 of this one is empty (V^3 bytes, voxel order of occ)
+  const uint8_t *dist;
   // FP8 network (built on the first FP8 query after a parameter change):
   // first layer chunk-major (W x 2LF E4M3 bytes per chunk, core-matrix
   // layout); hidden and output layers (E4M3) then FP32 biases and scales

@@ -96,17 +96,17 @@ __global__ void __launch_bounds__(256) trace_kernel(QueryLaunch q, int smem_hist
 // Rays need anywhere from 0 to 3V DDA steps; with one ray per thread a warp
 // runs as long as its longest ray.
 //
-// Empty-space skipping: every iteration crosses one cell: a voxel, or, when
-// the ray is inside a brick (2^log2B voxels a side, or one twice as wide)
-// that holds no occupied voxel, the largest such brick. All are the same
-// instruction sequence (exit plane
-// per axis at the cell's granularity, earliest axis with the lowest axis on
-// ties, cross it), so lanes of a warp do not split between a voxel path and
-// a brick path. Crossing times are the same expression of the plane index as
-// in the voxel-by-voxel walk (dda_walk), and when a brick is crossed the
-// other axes first step over every plane the walk would cross before it, so
-// the voxels visited, the boundary points and the shared-point marks are
-// exactly those of the voxel-by-voxel walk (trace_kernel).
+// Empty-space skipping: every iteration crosses one cell: the cube of
+// voxels within Chebyshev distance r of the current voxel, where r + 1 is
+// the voxel's distance to the nearest occupied voxel (so the whole cube is
+// empty; r = 0 is the voxel itself). All cells are crossed by the same
+// instruction sequence (exit plane per axis, earliest axis with the lowest
+// axis on ties, cross it), so lanes of a warp do not split between a voxel
+// path and a skipping path. Crossing times are the same expression of the
+// plane index as in the voxel-by-voxel walk (dda_walk), and when a cube is
+// crossed the other axes first step over every plane the walk would cross
+// before it, so the voxels visited, the boundary points and the shared-point
+// marks are exactly those of the voxel-by-voxel walk (trace_kernel).
 // ---------------------------------------------------------------------------
 struct LaneRay {
   int64_t i;
@@ -118,7 +118,8 @@ struct LaneRay {
   int ain;
   float fin;
   int k, cap;
-  int lg;          // log2 of the current cell's width: 0 (voxel) or an empty brick's
+  int r;           // the current cell: voxels within r of (ix0, ix1, ix2), all empty when r > 0
+  bool occ;        // the current voxel is occupied (its distance is 0)
   uint32_t dup;    // bit k: entry point of segment k equals the exit of segment k-1
   uint32_t lt, lf; // exit (t, face) of the last segment, as bits
   int la;          // and its axis
@@ -130,17 +131,10 @@ __device__ __forceinline__ int sel3i(int a, int x, int y, int z) { return a == 0
 // crossing time of plane index P on one axis (the expression dda_walk uses)
 __device__ __forceinline__ float plane_t(int P, float invV, float o, float inv) { return ((float)P * invV - o) * inv; }
 
-__device__ __forceinline__ bool bit_clear(const uint32_t *mask, int lb, int nbk, int x, int y, int z) {
-  const uint32_t bid = ((uint32_t)(z >> lb) * nbk + (uint32_t)(y >> lb)) * nbk + (uint32_t)(x >> lb);
-  return !((__ldg(mask + (bid >> 5)) >> (bid & 31)) & 1u);
-}
-
-// width (log2) of the largest empty brick holding voxel (x, y, z), 0 if none
-__device__ __forceinline__ int cell_level(const DevObject &ob, int x, int y, int z) {
-  const int lb = ob.log2B, V = ob.V;
-  if (bit_clear(ob.brick2, lb + 1, V >> (lb + 1), x, y, z)) return lb + 1;
-  if (bit_clear(ob.brick, lb, V >> lb, x, y, z)) return lb;
-  return 0;
+// occupancy distance of voxel (x, y, z): 0 when occupied, else the radius
+// of the empty cube around it is D - 1
+__device__ __forceinline__ int voxel_distance(const DevObject &ob, int x, int y, int z) {
+  return __ldg(ob.dist + ((uint32_t)z * ob.V + (uint32_t)y) * ob.V + (uint32_t)x);
 }
 
 __global__ void __launch_bounds__(256) trace_pool_kernel(QueryLaunch q, int smem_hist, int steps_per_round) {
@@ -234,7 +228,9 @@ __global__ void __launch_bounds__(256) trace_pool_kernel(QueryLaunch q, int smem
               R.tcur = t0;
               R.ain = ea;
               R.fin = ea >= 0 ? (dd[ea] > 0.f ? 0.f : 1.f) : 0.f;
-              R.lg = cell_level(ob, c[0], c[1], c[2]);
+              const int D = voxel_distance(ob, c[0], c[1], c[2]);
+              R.r = D > 0 ? D - 1 : 0;
+              R.occ = D == 0;
             }
           }
         }
@@ -246,16 +242,14 @@ __global__ void __launch_bounds__(256) trace_pool_kernel(QueryLaunch q, int smem
     const DevObject &ob = q.objs[R.s];
     const int V = ob.V;
     const float invV = ob.invV;
-    const uint32_t *occ = ob.occ;
-    const int LB = ob.log2B;
     float *P = q.s.pts + (size_t)R.i * Hs * 3;
     for (int it = 0; it < steps_per_round; ++it) {
       bool done = false;
-      const int lg = R.lg;  // cell granularity: voxel or empty brick
+      const int rr = R.r;  // cell: the voxel, or the empty cube of radius rr around it
       // exit plane of the cell on each axis, and its crossing time
-      const int P0 = R.st0 > 0 ? ((R.ix0 >> lg) + 1) << lg : (R.ix0 >> lg) << lg;
-      const int P1 = R.st1 > 0 ? ((R.ix1 >> lg) + 1) << lg : (R.ix1 >> lg) << lg;
-      const int P2 = R.st2 > 0 ? ((R.ix2 >> lg) + 1) << lg : (R.ix2 >> lg) << lg;
+      const int P0 = R.st0 > 0 ? R.ix0 + rr + 1 : R.ix0 - rr;
+      const int P1 = R.st1 > 0 ? R.ix1 + rr + 1 : R.ix1 - rr;
+      const int P2 = R.st2 > 0 ? R.ix2 + rr + 1 : R.ix2 - rr;
       const float e0 = R.st0 != 0 ? plane_t(P0, invV, R.o.x, R.inv0) : CUDART_INF_F;
       const float e1 = R.st1 != 0 ? plane_t(P1, invV, R.o.y, R.inv1) : CUDART_INF_F;
       const float e2 = R.st2 != 0 ? plane_t(P2, invV, R.o.z, R.inv2) : CUDART_INF_F;
@@ -263,7 +257,7 @@ __global__ void __launch_bounds__(256) trace_pool_kernel(QueryLaunch q, int smem
       const float ea = sel3(a, e0, e1, e2);
       const int Pa = sel3i(a, P0, P1, P2);
       const float tx = fminf(ea, R.t1);
-      if (lg == 0 && tx > R.tcur && occupied(occ, ((uint32_t)R.ix2 * V + R.ix1) * V + R.ix0)) {
+      if (R.occ && tx > R.tcur) {
         const float fx = (float)Pa * invV;
         if (R.k > 0 && __float_as_uint(R.tcur) == R.lt && R.ain == R.la && __float_as_uint(R.fin) == R.lf)
           R.dup |= 1u << R.k;
@@ -280,31 +274,59 @@ __global__ void __launch_bounds__(256) trace_pool_kernel(QueryLaunch q, int smem
       }
       if (!done && ea >= R.t1) done = true;
       if (!done) {
-        // when a brick is crossed, the other axes first cross the planes the
-        // voxel walk crosses before (ea, a); for a voxel there are none
-        if (lg) {
-          for (int g = 0; g < (1 << lg); ++g) {
+        // when a cube is crossed, the other axes first cross the planes the
+        // voxel walk crosses before (ea, a) -- at most 2 rr each; for a voxel
+        // there are none
+        // A cube may reach past the grid: an axis whose next plane is the
+        // grid's own boundary leaves the grid there, and the voxel walk
+        // ends at that crossing (the slab's exit time and the plane's
+        // crossing time may round differently), so the ray ends here too
+        // -- the cube holds no occupied voxel, so nothing is lost.
+        bool out = false;
+        if (rr) {
+          for (int g = 0; g < 2 * rr; ++g) {
             const int nx = R.ix0 + (R.st0 > 0);
-            if (a != 0 && R.st0 != 0 && plane_t(nx, invV, R.o.x, R.inv0) <= ea) R.ix0 += R.st0;  // 0 < a
-            else break;
+            if (a != 0 && R.st0 != 0 && plane_t(nx, invV, R.o.x, R.inv0) <= ea) {  // 0 < a
+              if ((unsigned)(R.ix0 + R.st0) >= (unsigned)V) {
+                out = true;
+                break;
+              }
+              R.ix0 += R.st0;
+            } else {
+              break;
+            }
           }
-          for (int g = 0; g < (1 << lg); ++g) {
+          for (int g = 0; g < 2 * rr && !out; ++g) {
             const int ny = R.ix1 + (R.st1 > 0);
             const float ty = plane_t(ny, invV, R.o.y, R.inv1);
-            if (a != 1 && R.st1 != 0 && (ty < ea || (ty == ea && a == 2))) R.ix1 += R.st1;
-            else break;
+            if (a != 1 && R.st1 != 0 && (ty < ea || (ty == ea && a == 2))) {
+              if ((unsigned)(R.ix1 + R.st1) >= (unsigned)V) {
+                out = true;
+                break;
+              }
+              R.ix1 += R.st1;
+            } else {
+              break;
+            }
           }
-          for (int g = 0; g < (1 << lg); ++g) {
+          for (int g = 0; g < 2 * rr && !out; ++g) {
             const int nz = R.ix2 + (R.st2 > 0);
             const float tz = plane_t(nz, invV, R.o.z, R.inv2);
-            if (a != 2 && R.st2 != 0 && tz < ea) R.ix2 += R.st2;
-            else break;
+            if (a != 2 && R.st2 != 0 && tz < ea) {
+              if ((unsigned)(R.ix2 + R.st2) >= (unsigned)V) {
+                out = true;
+                break;
+              }
+              R.ix2 += R.st2;
+            } else {
+              break;
+            }
           }
         }
         // then axis a crosses its plane
         const int sa = sel3i(a, R.st0, R.st1, R.st2);
         const int ia = sa > 0 ? Pa : Pa - 1;
-        if (ia < 0 || ia >= V) {
+        if (out || ia < 0 || ia >= V) {
           done = true;
         } else {
           R.tcur = ea;
@@ -313,8 +335,16 @@ __global__ void __launch_bounds__(256) trace_pool_kernel(QueryLaunch q, int smem
           if (a == 0) R.ix0 = ia;
           else if (a == 1) R.ix1 = ia;
           else R.ix2 = ia;
-          // a brick plane was crossed: look up the new brick
-          if ((Pa & ((1 << LB) - 1)) == 0) R.lg = cell_level(ob, R.ix0, R.ix1, R.ix2);
+          // the next cell is centred on the voxel just entered (indices
+          // are checked: a violation is reported, never read)
+          if ((unsigned)R.ix0 >= (unsigned)V || (unsigned)R.ix1 >= (unsigned)V || (unsigned)R.ix2 >= (unsigned)V) {
+            atomicOr(q.err, kErrCheck);
+            done = true;
+          } else {
+            const int D = voxel_distance(ob, R.ix0, R.ix1, R.ix2);
+            R.r = D > 0 ? D - 1 : 0;
+            R.occ = D == 0;
+          }
         }
       }
       if (done) {
