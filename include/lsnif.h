@@ -326,6 +326,13 @@ LSNIF_API int lsnif_query_scene(lsnif_ctx *ctx, const lsnif_rays *rays, const ls
 LSNIF_API int lsnif_bvh_build_host(const float *verts, int64_t nv, const int32_t *tris, int64_t nt,
                                    void *nodes_out, int64_t *n_nodes, int32_t *order_out, int32_t *depth);
 
+/* The occupancy distance field the traversal skips empty space with, on the
+ * host only (no GPU, no context): for every voxel of the V^3 bitset `occ`
+ * (layout of lsnif_read_params' occupancy), the Chebyshev distance in voxels
+ * to the nearest occupied voxel, capped at `cap` (0 = occupied), into out[V^3]
+ * in the same voxel order. For checking the transform. Errors: INVALID_ARG. */
+LSNIF_API int lsnif_occupancy_distance_host(const uint32_t *occ, int32_t V, int32_t cap, uint8_t *out);
+
 /* ---- primary-ray G-buffer (Sec. 4, Fig. 4a) ----------------------------- */
 
 /* Pinhole camera: the ray of pixel (px, py) (row py from the top) starts at

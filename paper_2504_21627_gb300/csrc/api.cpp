@@ -455,6 +455,16 @@ static std::vector<uint8_t> occupancy_distance(const std::vector<uint32_t> &occ,
   return a;
 }
 
+// Host-only entry point of the distance transform (no GPU), for tests.
+extern "C" int lsnif_occupancy_distance_host(const uint32_t *occ, int32_t V, int32_t cap, uint8_t *out) {
+  if (!occ || !out || V < 1 || V > 1024 || cap < 1 || cap > 255) return LSNIF_ERR_INVALID_ARG;
+  const size_t words = ((size_t)V * V * V + 31) / 32;
+  std::vector<uint32_t> o(occ, occ + words);
+  const std::vector<uint8_t> d = occupancy_distance(o, V, cap);
+  memcpy(out, d.data(), d.size());
+  return LSNIF_OK;
+}
+
 // A mesh object: the triangles, shading normals, materials and a BVH built
 // on the host; no voxels, tables or network.
 static int load_mesh_object(lsnif_ctx *ctx, const lsnif_object_desc *desc, lsnif_obj *out) {

@@ -138,6 +138,7 @@ SIGNATURES = {
     "lsnif_bounce_rays": (_I, [_P, C.POINTER(Rays), C.POINTER(Hits), _P, C.c_float, _P, _P]),
     "lsnif_raster_gbuffer": (_I, [_P, C.POINTER(Camera), C.POINTER(Instance), _I, C.POINTER(GBufferS), _P]),
     "lsnif_bvh_build_host": (_I, [_P, C.c_int64, _P, C.c_int64, _P, C.POINTER(C.c_int64), _P, C.POINTER(_I)]),
+    "lsnif_occupancy_distance_host": (_I, [_P, _I, _I, _P]),
     "lsnif_trace": (_I, [_P, C.POINTER(Rays), C.POINTER(TraceOut), _P]),
     "lsnif_encode": (_I, [_P, _U32, _P, _I64, _P, _I, _P]),
     "lsnif_corner_indices": (_I, [_P, _U32, _P, _I64, _P, _P]),
@@ -226,6 +227,16 @@ def bvh_build_host(verts, tris):
     _check(lib.lsnif_bvh_build_host(_ptr(v), v.shape[0], _ptr(t), nt, nodes.ctypes.data, C.byref(nn), _ptr(order),
                                     C.byref(depth)))
     return nodes[:nn.value], order, depth.value
+
+
+def occupancy_distance_host(occ_words, V: int, cap: int) -> np.ndarray:
+    """The traversal's occupancy distance field computed on the host (no
+    GPU): uint8 array of V^3 in voxel order."""
+    lib = load_library()
+    w = np.ascontiguousarray(occ_words, np.uint32)
+    out = np.zeros(V ** 3, np.uint8)
+    _check(lib.lsnif_occupancy_distance_host(_ptr(w), V, cap, _ptr(out)))
+    return out
 
 
 def cfg_struct(cfg) -> Config:
