@@ -474,9 +474,12 @@ def bench_stress1(args):
     obj = ctx.load_object(mesh, cfg, tables=params.tables, mlp=params.packed_mlp())
     if args.variant8 is not None:
         ctx.set_variant8(args.variant8)
+    if args.group_mode is not None:
+        ctx.set_group_mode(args.group_mode)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
-    out = {"workload": "stress1", "network": "L=16 F=4 T=2^21, 1152-128x4-12", "rays": n}
+    out = {"workload": "stress1", "network": "L=16 F=4 T=2^21, 1152-128x4-12", "rays": n,
+           "group_mode": ctx.tuning()[2]}
     for name, prec, steps in (("fp8", lsnif.FP8_FUSED, args.steps), ("fp32", lsnif.FP32_PLAIN, 3)):
         res = ctx.query_rays(rays, obj=obj, precision=prec)
         for _ in range(args.warmup):
@@ -638,6 +641,8 @@ def bench_scene(args):
                                        keep_mesh=args.primary == "raster", bvh_below_faces=args.bvh_below_faces))
     if args.variant8 is not None:
         ctx.set_variant8(args.variant8)
+    if args.group_mode is not None:
+        ctx.set_group_mode(args.group_mode)
     insts = [(handles[o], A, b) for o, A, b in I.seeded_instances(args.scene_instances, len(spec), seed=9,
                                                                    spread=10.0)]
     if args.primary == "raster":
@@ -707,6 +712,8 @@ def main():
     ap.add_argument("--scene-height", type=int, default=1080)
     ap.add_argument("--scene-net", default="stress", choices=["stress", "small"])
     ap.add_argument("--variant8", type=int, default=None, help="FP8 fused-kernel variant for --workload scene")
+    ap.add_argument("--group-mode", type=int, default=None,
+                    help="stress1 / scene: live rays grouped by (object, point count) (0) or kept in ray order (1)")
     ap.add_argument("--scene-objects", type=int, default=8, help="unique objects (below 8 only for profiling)")
     ap.add_argument("--scene-instances", type=int, default=32)
     ap.add_argument("--scene-spp", type=int, default=4)

@@ -473,10 +473,12 @@ LSNIF_API int lsnif_set_trace_mode(lsnif_ctx *ctx, int mode);
 LSNIF_API int lsnif_autotune(lsnif_ctx *ctx, const lsnif_rays *rays, int reps, void *stream, int *chosen);
 
 /* How live rays are grouped into 128-ray tiles: 0 = by object, then by
- * number of occupied voxels (descending); 1 = single-object queries keep the
- * rays' original order (neighbouring primary rays share voxels and lattice
- * cells, which the gather's L1 cache exploits); multi-object queries always
- * use 0. Both compute identical results. */
+ * number of occupied voxels (descending); 1 = in the rays' own order within
+ * each object: single-object queries keep the original order exactly,
+ * multi-object queries (and instanced scenes) group by object only and keep
+ * each warp's run of consecutive rays together (neighbouring primary rays
+ * share voxels and lattice cells, which the gather's caches exploit). Both
+ * compute identical results. */
 LSNIF_API int lsnif_set_group_mode(lsnif_ctx *ctx, int mode);
 
 /* The context's current fused-kernel variant, traversal kernel and

@@ -126,7 +126,8 @@ struct QueryLaunch {
   int *err;               // device error word
   cudaStream_t stream;
   int trace_mode;         // traversal kernel: 0 one ray per thread, 1 persistent lanes
-  int group_mode;         // 0: live rays grouped by (object, k desc); 1: one object, original order kept
+  int group_mode;         // 0: live rays grouped by (object, k desc); 1: one object, original order kept;
+                          // 2: grouped by object only, warps of consecutive rays kept together
   int single_slot;        // object slot of a single-object query (group_mode 1)
 };
 

@@ -372,7 +372,8 @@ __global__ void __launch_bounds__(1024) scan_kernel(QueryLaunch q) {
       int start = run;
       for (int k = kMaxCap; k >= 1; --k) {
         int c = q.s.counts[s * kBuckets + k];
-        q.s.offsets[s * kBuckets + k] = run;
+        // group mode 2: one bucket per object (bucket k = 1 takes all)
+        q.s.offsets[s * kBuckets + k] = q.group_mode == 2 ? start : run;
         q.s.cursor[s * kBuckets + k] = 0;
         run += c;
         pts += 2 * k * c;
@@ -416,7 +417,9 @@ __global__ void __launch_bounds__(1024) scan_kernel(QueryLaunch q) {
 }
 
 // Scatter live rays into their bucket ranges; warp-aggregated atomics keep
-// rays of one warp contiguous (spatially coherent rays stay together).
+// rays of one warp contiguous (spatially coherent rays stay together). In
+// group mode 2 a bucket is a whole object (point counts mixed), so
+// consecutive rays of an object stay close in the tile order.
 __global__ void __launch_bounds__(256) scatter_kernel(QueryLaunch q) {
   const int64_t n = q.rays.n;
   const int lane = threadIdx.x & 31;
@@ -426,7 +429,7 @@ __global__ void __launch_bounds__(256) scatter_kernel(QueryLaunch q) {
     if (i < n) {
       int k = q.s.k[i];
       int s = q.s.slot[i];
-      if (k > 0 && s >= 0) bucket = s * kBuckets + k;
+      if (k > 0 && s >= 0) bucket = s * kBuckets + (q.group_mode == 2 ? 1 : k);
     }
     unsigned active = __ballot_sync(0xffffffffu, bucket >= 0);
     if (bucket >= 0) {

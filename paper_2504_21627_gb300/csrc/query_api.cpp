@@ -217,7 +217,7 @@ int lsnif::run_query(lsnif_ctx *ctx, Workspace *ws, const lsnif_rays *r, lsnif_h
   q.err = ctx->d_err;
   q.stream = st;
   q.trace_mode = ctx->trace_mode;
-  q.group_mode = (ctx->group_mode == 1 && !r->obj) ? 1 : 0;
+  q.group_mode = ctx->group_mode == 1 ? (r->obj ? 2 : 1) : 0;
   q.single_slot = r->obj ? 0 : sh.rep->slot;
   int launches = 0;
   if (profile) cudaEventRecord(ctx->ev[0], st);
@@ -597,8 +597,9 @@ extern "C" int lsnif_autotune(lsnif_ctx *ctx, const lsnif_rays *rays, int reps, 
       if (ms < best_ms) { best_t = t; best_ms = ms; }
     }
     ctx->trace_mode = best_t;
-    // grouping: only single-object queries can keep the original order
-    if (rc == LSNIF_OK && !rays->obj) {
+    // grouping: by (object, point count), or rays kept in order within
+    // their object
+    if (rc == LSNIF_OK) {
       for (int g = 0; g < 2 && rc == LSNIF_OK; ++g) {
         if (g == best_g) continue;
         ctx->group_mode = g;

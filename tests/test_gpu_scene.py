@@ -128,6 +128,25 @@ def test_instanced_scene_matches_oracle(ctx, scene, prec):
     assert (got["mat"][same] == ref["mat"][same]).mean() > 0.99
 
 
+@pytest.mark.parametrize("prec", [lsnif.FP32_PLAIN, lsnif.BF16_FUSED, lsnif.FP8_FUSED])
+def test_grouping_modes_give_identical_scene_results(ctx, scene, prec):
+    """Pairs grouped by (object, point count) or by object in ray order:
+    the same bits."""
+    rays = _cuda(_aim(scene["insts"], 6000, 13, scene["boxes"]))
+    insts = [(scene["handles"][i.obj], i.A, i.b) for i in scene["insts"]]
+    got = []
+    try:
+        for g in (0, 1):
+            ctx.set_group_mode(g)
+            res, inst = ctx.query_scene(rays, insts, precision=prec)
+            ctx.check()
+            got.append([x.cpu() for x in (res.hit, res.t, res.normal, res.mat, inst)])
+    finally:
+        ctx.set_group_mode(0)
+    for a, b in zip(*got):
+        assert torch.equal(torch.nan_to_num(a, posinf=-1.0), torch.nan_to_num(b, posinf=-1.0))
+
+
 def test_identity_instance_equals_plain_query(ctx, scene):
     h = scene["handles"][0]
     obj = scene["objs"][0]
