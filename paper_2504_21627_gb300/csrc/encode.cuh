@@ -490,7 +490,15 @@ __device__ __forceinline__ void encode_level_backward(float *__restrict__ gtab, 
     const float w = (dx ? c.wx : 1.f - c.wx) * (dy ? c.wy : 1.f - c.wy) * (dz ? c.wz : 1.f - c.wz);
     if (w == 0.f) continue;
     const uint32_t idx = hash3(c.cx + dx, c.cy + dy, c.cz + dz) & mask;
-    for (int f = 0; f < F; ++f) atomicAdd(gtab + (size_t)idx * F + f, w * g[f]);
+    float *dst = gtab + (size_t)idx * F;
+    // one vector reduction per entry where the entry is 8 or 16 bytes
+    if (F == 2) {
+      atomicAdd(reinterpret_cast<float2 *>(dst), make_float2(w * g[0], w * g[1]));
+    } else if (F == 4) {
+      atomicAdd(reinterpret_cast<float4 *>(dst), make_float4(w * g[0], w * g[1], w * g[2], w * g[3]));
+    } else {
+      for (int f = 0; f < F; ++f) atomicAdd(dst + f, w * g[f]);
+    }
   }
 }
 

@@ -334,15 +334,24 @@ void gemm(cudaStream_t st, int M, int N, int K, const float *A, int lda, int tA,
   gemm_kernel<<<grid, 256, 0, st>>>(M, N, K, A, lda, tA, B, ldb, tB, C, ldc, mode, bias, post, aux, act, k_split);
 }
 
-// column sums of G (rows x cols) added into out (bias gradients)
+// column sums of G (rows x cols, cols <= 256) added into out (bias
+// gradients). The block is a whole number of rows wide (blockDim = cols x
+// rows per sweep), so a thread keeps one column and the block's reads of a
+// sweep are one contiguous run; per-thread sums, then per-column sums of
+// the block, then one atomic per column and block.
 __global__ void colsum_kernel(const float *G, int64_t rows, int cols, float *out) {
   extern __shared__ float part[];
-  for (int c = threadIdx.x; c < cols; c += blockDim.x) part[c] = 0.f;
+  const int per = blockDim.x / cols;
+  const int c = threadIdx.x % cols, rr = threadIdx.x / cols;
+  float acc = 0.f;
+  for (int64_t r = (int64_t)blockIdx.x * per + rr; r < rows; r += (int64_t)gridDim.x * per) acc += G[r * cols + c];
+  part[threadIdx.x] = acc;
   __syncthreads();
-  for (int64_t r = blockIdx.x; r < rows; r += gridDim.x)
-    for (int c = threadIdx.x; c < cols; c += blockDim.x) part[c] += G[r * cols + c];
-  __syncthreads();
-  for (int c = threadIdx.x; c < cols; c += blockDim.x) atomicAdd(out + c, part[c]);
+  if (threadIdx.x < cols) {
+    float s = 0.f;
+    for (int j = 0; j < per; ++j) s += part[j * cols + threadIdx.x];
+    atomicAdd(out + threadIdx.x, s);
+  }
 }
 
 // loss terms and dLoss/dZ for the batch mean over rays that reach the
@@ -502,7 +511,10 @@ cudaError_t launch_train_step(const DevObject *dobj, const DevObject &h, const R
     const float *hin = l == 0 ? tb.feats : tb.acts + (size_t)(l - 1) * B * W;
     // dW = d^T . hin  (dcols x fi), split over the batch
     gemm(st, dcols, fi, (int)B, d, dcols, 1, hin, fi, 0, gW[l], fi, 1, nullptr, nullptr, nullptr, 0, ks);
-    colsum_kernel<<<152, 256, dcols * sizeof(float), st>>>(d, B, dcols, gb[l]);
+    {
+      const int threads = dcols * std::max(1, 256 / dcols);
+      colsum_kernel<<<152 * 8, threads, threads * sizeof(float), st>>>(d, B, dcols, gb[l]);
+    }
     // gradient w.r.t. the layer input: d . W_l (B x fi); for hidden inputs
     // multiply by act'(pre of layer l-1)
     float *dn = (l % 2 == 0) ? tb.dA : tb.dB;
