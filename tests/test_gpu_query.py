@@ -1,6 +1,6 @@
 """GPU parity of the query path against the FP64 oracle, through the C ABI.
 
-Tolerances (stated per test, derived in the design doc):
+Tolerances (stated per test, with the arithmetic behind each):
   occupancy, lattice-corner indices: bit-exact
   voxel lists: exact except near-face rays (counted)
   FP32 path: logits within 1e-4 of the oracle, relative to the batch's max |logit|
