@@ -801,6 +801,7 @@ def main():
     clocks = clk.summary()
     ms32, prof32, wall32 = timed(lsnif.FP32_PLAIN, max(3, args.steps // 2), 3, profile=True)
     ms8, prof8, wall8 = timed(lsnif.FP8_FUSED, max(3, args.steps // 2), 3, profile=True)
+    msh, profh, wallh = timed(lsnif.FP16_FUSED, max(3, args.steps // 2), 3, profile=True)
 
     from paper_2504_21627_gb300 import replicas
 
@@ -810,6 +811,7 @@ def main():
     mean16, _, value = replicas.aggregate(float(ms16.mean()), n)
     mean32, _, v32 = replicas.aggregate(float(ms32.mean()), n)
     mean8, _, v8 = replicas.aggregate(float(ms8.mean()), n)
+    meanh, _, vh = replicas.aggregate(float(msh.mean()), n)
 
     # ---- end to end through the host-buffer C-ABI call ----
     host_rays = torch.from_numpy(rays_np).pin_memory()
@@ -854,6 +856,9 @@ def main():
         "fp32_plain": {"value": v32, "unit": "Mrays/s", "ms_per_step": mean32},
         "fp8_fused": {"value": v8, "unit": "Mrays/s", "ms_per_step": mean8,
                       "fused_ms": float(np.mean([q.ms_mlp for q in prof8]))},
+        "fp16_fused": {"value": vh, "unit": "Mrays/s", "ms_per_step": meanh,
+                       "fused_ms": float(np.mean([q.ms_mlp for q in profh])),
+                       "note": "the BF16 kernel with FP16 operands (three more significand bits)"},
         "rays": {"live": int(live), "live_frac": live / n, "points": int(pts),
                  "mean_points_per_live_ray": pts / max(live, 1)},
         "stages_ms_bf16": {"trace": float(np.mean([q.ms_trace for q in prof16])),

@@ -84,7 +84,12 @@ typedef uint32_t lsnif_obj;         /* object handle; 0 is never a valid handle 
  * accumulation; the first layer's weights are streamed, so networks too
  * large for BF16 shared memory (F = 4, L = 16, 4 x 128) run. Needs F in
  * {2, 4}, width 64 or 128, L * F a multiple of 16. */
-enum lsnif_precision { LSNIF_FP32_PLAIN = 0, LSNIF_BF16_FUSED = 1, LSNIF_FP8_FUSED = 2 };
+/* FP16_FUSED: BF16_FUSED's kernel with FP16 network operands instead of
+ * BF16 (tcgen05 kind::f16 with both A and B FP16): features as gathered from
+ * the FP16 tables, FP16 weights, hidden activations rounded to FP16 (nearest
+ * even, saturating at +-65504), FP32 accumulation. Three more significand
+ * bits than BF16 at the same cost; same shapes as BF16_FUSED. */
+enum lsnif_precision { LSNIF_FP32_PLAIN = 0, LSNIF_BF16_FUSED = 1, LSNIF_FP8_FUSED = 2, LSNIF_FP16_FUSED = 3 };
 
 /* Hidden-layer activation: ReLU, or leaky ReLU with slope 0.01 (Sec. 5.1). */
 enum lsnif_activation { LSNIF_RELU = 0, LSNIF_LEAKY_RELU = 1 };
@@ -404,8 +409,8 @@ LSNIF_API int lsnif_trace(lsnif_ctx *ctx, const lsnif_rays *rays, lsnif_trace_ou
 
 /* Hash-grid encoding of n unit-cube points (Sec. 3.2): pts DEVICE n x 3 FP32
  * -> feats DEVICE n x L x F FP32. precision FP32_PLAIN reads the FP32
- * tables; BF16_FUSED reads the FP16 copies (interpolation in FP32 either
- * way). Zero-weight corners are skipped. */
+ * tables; every other precision reads the FP16 copies (interpolation in FP32
+ * either way). Zero-weight corners are skipped. */
 LSNIF_API int lsnif_encode(lsnif_ctx *ctx, lsnif_obj obj, const float *pts, int64_t n, float *feats,
                  int precision, void *stream);
 
@@ -417,8 +422,9 @@ LSNIF_API int lsnif_corner_indices(lsnif_ctx *ctx, lsnif_obj obj, const float *p
                          void *stream);
 
 /* The object's network alone (Sec. 5.1) on n given input rows: X DEVICE
- * n x (H*L*F) FP32 -> Z DEVICE n x (8+n_mat) FP32 logits. BF16_FUSED runs
- * the tcgen05 tensor-core layers (inputs rounded to BF16). */
+ * n x (H*L*F) FP32 -> Z DEVICE n x (8+n_mat) FP32 logits. BF16_FUSED and
+ * FP16_FUSED run the tcgen05 tensor-core layers (inputs rounded to the
+ * operand type); FP8_FUSED is not offered here. */
 LSNIF_API int lsnif_mlp(lsnif_ctx *ctx, lsnif_obj obj, const float *X, int64_t n, float *Z, int precision,
               void *stream);
 

@@ -242,6 +242,15 @@ def round_fp16(x: np.ndarray) -> np.ndarray:
     return np.asarray(x, np.float64).astype(np.float32).astype(np.float16).astype(np.float64)
 
 
+FP16_MAX = 65504.0
+
+
+def round_fp16_sat(x: np.ndarray) -> np.ndarray:
+    """Round to the nearest IEEE binary16 value (ties to even) through
+    float32, saturating at +-65504 instead of overflowing to infinity."""
+    return round_fp16(np.clip(np.asarray(x, np.float64), -FP16_MAX, FP16_MAX))
+
+
 E4M3_MAX = 448.0
 
 
@@ -298,13 +307,15 @@ def mlp_forward(X: np.ndarray, weights, act: int = 0, precision: str = "f64", ke
                 fp8=None):
     """Dense layers, hidden activation `act`, linear output. With
     precision='bf16' the matmul operands (inputs, weights, hidden
-    activations) are rounded to bfloat16 first; sums stay float64. With
+    activations) are rounded to bfloat16 first; sums stay float64;
+    precision='fp16' does the same with saturating binary16 rounding. With
     precision='fp8' (fp8 = (s, w) from fp8_scales) every layer multiplies
     round_e4m3(s_l h) by round_e4m3(w_l W_l) and divides the sum by s_l w_l
     before the bias."""
     h = np.asarray(X, np.float64)
-    if precision == "bf16":
-        h = round_bf16(h)
+    rnd = {"bf16": round_bf16, "fp16": round_fp16_sat}.get(precision)
+    if rnd is not None:
+        h = rnd(h)
     cache = []
     for i, (W, b) in enumerate(weights):
         bq = np.asarray(b, np.float64)
@@ -312,13 +323,13 @@ def mlp_forward(X: np.ndarray, weights, act: int = 0, precision: str = "f64", ke
             s, w = fp8[0][i], fp8[1][i]
             z = (round_e4m3(h * s) @ round_e4m3(np.asarray(W, np.float64) * w).T) / (s * w) + bq
         else:
-            Wq = round_bf16(W) if precision == "bf16" else W
+            Wq = rnd(W) if rnd is not None else W
             z = h @ Wq.T + bq
         cache.append((h, z))
         if i < len(weights) - 1:
             h = activation(z, act)
-            if precision == "bf16":
-                h = round_bf16(h)
+            if rnd is not None:
+                h = rnd(h)
         else:
             h = z
     return (h, cache) if keep else h
@@ -363,7 +374,7 @@ def query(obj: OracleObject, rays: np.ndarray, precision: str = "f64", seg: Segm
     seg = ray_segments(obj, rays) if seg is None else seg
     n = seg.k.size
     live = seg.k > 0
-    tables = round_fp16(obj.tables) if precision in ("bf16", "fp8") else obj.tables
+    tables = round_fp16(obj.tables) if precision in ("bf16", "fp16", "fp8") else obj.tables
     fp8 = fp8_scales(float(np.max(np.abs(tables))), obj.weights) if precision == "fp8" else None
     out = Hits(np.zeros(n, bool), np.full(n, np.inf), np.zeros((n, 3)), np.full(n, -1, np.int32),
                np.zeros((n, 3)), np.full((n, cfg.n_out), np.nan), live)

@@ -265,7 +265,7 @@ int lsnif::refresh_copies(lsnif_ctx *, Object *o, cudaStream_t st) {
   const lsnif_config &c = o->cfg;
   size_t nt = ((size_t)c.L << c.log2_T) * c.F;
   cudaError_t e = launch_tables_to_half(o->d.tab32, const_cast<uint16_t *>(o->d.tab16), (int64_t)nt, st);
-  if (e == cudaSuccess) e = launch_build_umma(o->d, const_cast<uint8_t *>(o->d.umma), st);
+  if (e == cudaSuccess) e = launch_build_umma(o->d, st);
   if (e != cudaSuccess) return cuda_fail(e, "refresh reduced-precision copies");
   return LSNIF_OK;
 }
@@ -705,18 +705,20 @@ extern "C" int lsnif_load_object(lsnif_ctx *ctx, const lsnif_object_desc *desc, 
   OALLOC(tab32, const float *, 4 * nt, "tables");
   OALLOC(tab16, const uint16_t *, 2 * nt, "FP16 tables");
   OALLOC(mlp32, const float *, 4 * (size_t)o->n_params_mlp, "network");
-  // tcgen05 weight blob: BF16 layers (output padded to n_out_pad rows) + FP32 biases
+  // tcgen05 weight blobs (BF16 and FP16 copies): layers (output padded to n_out_pad rows) + FP32 biases
   size_t wbytes = (size_t)cfg.width * d.n_in * 2 + (size_t)(cfg.n_hidden - 1) * cfg.width * cfg.width * 2 +
                   (size_t)d.n_out_pad * cfg.width * 2;
   d.umma_bias_off = (uint32_t)((wbytes + 15) & ~size_t(15));
   d.umma_bytes = (uint32_t)(d.umma_bias_off + 4 * ((size_t)cfg.n_hidden * cfg.width + d.n_out_pad));
   d.umma_bytes = (d.umma_bytes + 15) & ~15u;
   OALLOC(umma, const uint8_t *, d.umma_bytes, "tensor-core weights");
+  OALLOC(umma_h, const uint8_t *, d.umma_bytes, "FP16 tensor-core weights");
   OALLOC(plain_out, const float *, 4 * ((size_t)d.n_out_pad * cfg.width + d.n_out_pad), "padded output layer");
   cudaError_t e = cudaMemcpy((void *)d.occ, occ.data(), 4 * occ.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy((void *)d.dist, dist.data(), dist.size(), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) { free_object(ctx, o); return cuda_fail(e, "upload occupancy"); }
   cudaMemset((void *)d.umma, 0, d.umma_bytes);
+  cudaMemset((void *)d.umma_h, 0, d.umma_bytes);
   if ((rc = upload_params(ctx, o, tab_src, mlp_src)) != LSNIF_OK) { free_object(ctx, o); return rc; }
   // kept mesh for training labels
   if (!desc->blob && desc->keep_mesh) {

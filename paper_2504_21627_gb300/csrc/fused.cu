@@ -46,12 +46,14 @@ namespace {
 constexpr int kNBufMax = 4;
 constexpr int kEpiWarps = 4;
 
-// kind::f16 instruction descriptor: BF16 A and B (K-major), FP32 D, M = 128.
-__device__ __forceinline__ uint32_t idesc_bf16(int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(kTileM >> 4) << 24);
+// kind::f16 instruction descriptor: A and B both BF16 (fp16 = 0) or both
+// FP16 (fp16 = 1), K-major, FP32 D, M = 128.
+__device__ __forceinline__ uint32_t idesc_f16(int N, int fp16) {
+  const uint32_t ab = fp16 ? 0u : (1u << 7) | (1u << 10);
+  return (1u << 4) | ab | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(kTileM >> 4) << 24);
 }
 
-__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+__device__ __forceinline__ void mma_f16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
   asm volatile(
       "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
@@ -64,6 +66,28 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
   return *reinterpret_cast<uint32_t *>(&v);
 }
 
+// FP16 operands saturate at the largest finite half (65504) instead of
+// overflowing to infinity; rounding to nearest even below that.
+__device__ __forceinline__ uint32_t pack_h2_sat(float a, float b) {
+  a = fminf(fmaxf(a, -65504.f), 65504.f);
+  b = fminf(fmaxf(b, -65504.f), 65504.f);
+  __half2 v = __floats2half2_rn(a, b);
+  return *reinterpret_cast<uint32_t *>(&v);
+}
+
+__device__ __forceinline__ uint32_t pack_op(float a, float b, int fp16) {
+  return fp16 ? pack_h2_sat(a, b) : pack_bf16(a, b);
+}
+
+__device__ __forceinline__ uint32_t h2_bits(__half2 h) { return *reinterpret_cast<uint32_t *>(&h); }
+
+// Two FP16 features (one half2 word) rounded to BF16 through their exact
+// FP32 values.
+__device__ __forceinline__ uint32_t h2_bits_to_bf16(uint32_t w) {
+  const float2 f = __half22float2(*reinterpret_cast<const __half2 *>(&w));
+  return pack_bf16(f.x, f.y);
+}
+
 struct FusedArgs {
   QueryLaunch q;
   // X-rows mode (lsnif_mlp): X n x n_in FP32 in, Z n x n_out FP32 out
@@ -73,6 +97,8 @@ struct FusedArgs {
   uint32_t smem_blob;  // bytes of the weight blob
   int nbuf;            // ring buffers (2..kNBufMax)
   int list_chunks;     // work-list capacity in chunks (H_max / 2)
+  int fp16;            // operand type: 0 BF16 (weights from umma), 1 FP16 (weights from umma_h);
+                       // selects the kernel instantiation
 };
 
 // Shared-memory layout (byte offsets from a 1024-aligned base), the same on
@@ -109,7 +135,7 @@ __host__ __device__ inline Layout make_layout(uint32_t blob_bytes, int F, int W,
 }  // namespace
 
 // The MMA warp's work (see epilogue_role for why it is a function).
-template <int F, int W, bool XROWS, int NG>
+template <int F, int W, bool XROWS, int NG, bool H16>
 __device__ __noinline__ void mma_role(const FusedArgs *ap, uint8_t *base, uint32_t tmem) {
   const FusedArgs &a = *ap;
   const int lane = threadIdx.x & 31;
@@ -128,7 +154,7 @@ __device__ __noinline__ void mma_role(const FusedArgs *ap, uint8_t *base, uint32
   {
     // =================== MMA warp ===================
     int chunk_ctr = 0;
-    const uint32_t idesc0 = idesc_bf16(W);
+    const uint32_t idesc0 = idesc_f16(W, H16);
     for (int i = 0;; ++i) {
       const int tb = i & 1;
       if (!mbar_wait(su32(&b_ready[tb]), (uint32_t)((i >> 1) & 1), abort_flag)) break;
@@ -154,7 +180,7 @@ __device__ __noinline__ void mma_role(const FusedArgs *ap, uint8_t *base, uint32
           for (int ks = 0; ks < CHK / 16; ++ks) {
             const uint64_t ad = umma_desc(a0 + ks * 256, 128, a_sbo);
             const uint64_t bd = umma_desc(b0 + (uint32_t)((s * CHK) / 8 + 2 * ks) * 128u, 128, w0_sbo);
-            mma_bf16(dacc, ad, bd, idesc0, (s > 0 || ks > 0) ? 1u : 0u);
+            mma_f16(dacc, ad, bd, idesc0, (s > 0 || ks > 0) ? 1u : 0u);
           }
           mma_commit(su32(&b_empty[buf]));
         }
@@ -175,9 +201,10 @@ __device__ __noinline__ void mma_role(const FusedArgs *ap, uint8_t *base, uint32
 
 // The epilogue warps' work, compiled as its own function so that its
 // registers do not add to the gather warps' allocation.
-template <int F, int W, bool XROWS, int NG>
+template <int F, int W, bool XROWS, int NG, bool H16>
 __device__ __noinline__ void epilogue_role(const FusedArgs *ap, uint8_t *base, uint32_t tmem) {
   const FusedArgs &a = *ap;
+  constexpr int fp16 = H16;
   constexpr int kEpiWarp0 = NG + 1;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const QueryLaunch &q = a.q;
@@ -244,7 +271,7 @@ __device__ __noinline__ void epilogue_role(const FusedArgs *ap, uint8_t *base, u
       }
       const DevObject &ob = objs[slot];
       if (slot != su_slot) {
-        const uint4 *src = reinterpret_cast<const uint4 *>(ob.umma);
+        const uint4 *src = reinterpret_cast<const uint4 *>(H16 ? ob.umma_h : ob.umma);
         uint4 *dst = reinterpret_cast<uint4 *>(s_blob);
         const int nvec = (int)(ob.umma_bytes / 16);
         for (int k = etid; k < nvec; k += kEpiThreads) dst[k] = __ldg(src + k);
@@ -374,8 +401,8 @@ __device__ __noinline__ void epilogue_role(const FusedArgs *ap, uint8_t *base, u
                 float h8[8];
 #pragma unroll
                 for (int u = 0; u < 8; ++u) h8[u] = act_fn(__uint_as_float(v[c + u]) + bl[c0 + c + u], act);
-                const uint4 pk = make_uint4(pack_bf16(h8[0], h8[1]), pack_bf16(h8[2], h8[3]),
-                                            pack_bf16(h8[4], h8[5]), pack_bf16(h8[6], h8[7]));
+                const uint4 pk = make_uint4(pack_op(h8[0], h8[1], fp16), pack_op(h8[2], h8[3], fp16),
+                                            pack_op(h8[4], h8[5], fp16), pack_op(h8[6], h8[7], fp16));
                 *reinterpret_cast<uint4 *>(s_act + core_off(r, (c0 + c) / 8, act_sbo)) = pk;
               }
             }
@@ -386,11 +413,11 @@ __device__ __noinline__ void epilogue_role(const FusedArgs *ap, uint8_t *base, u
             if (etid == 0) {
               tc_after();
               const uint32_t a0 = su32(s_act), b0 = su32(s_blob) + wl_off;
-              const uint32_t idesc = idesc_bf16(N);
+              const uint32_t idesc = idesc_f16(N, fp16);
               for (int ks = 0; ks < W / 16; ++ks) {
                 const uint64_t ad = umma_desc(a0 + ks * 256, 128, act_sbo);
                 const uint64_t bd = umma_desc(b0 + ks * 256, 128, act_sbo);
-                mma_bf16(dacc, ad, bd, idesc, ks > 0 ? 1u : 0u);
+                mma_f16(dacc, ad, bd, idesc, ks > 0 ? 1u : 0u);
               }
               mma_commit(su32(b_layer));
               mbar_wait(su32(b_layer), (uint32_t)(layer_ctr & 1), abort_flag);
@@ -441,7 +468,9 @@ __device__ __noinline__ void epilogue_role(const FusedArgs *ap, uint8_t *base, u
 // whose corner loads are in flight together per gather item; GS (F = 2):
 // 0 = 16-byte corner groups, 1 = the same with the next level's loads in
 // flight during interpolation, 2 = 8-byte corner pairs (fewer registers).
-template <int F, int W, bool XROWS, int NG, int NLB, int GS>
+// H16: FP16 operands (else BF16) -- features, weights and hidden
+// activations; a template parameter so that no loop branches on it.
+template <int F, int W, bool XROWS, int NG, int NLB, int GS, bool H16>
 __global__ void __launch_bounds__((NG + 1 + kEpiWarps) * 32, 1) fused_kernel(const __grid_constant__ FusedArgs a) {
   constexpr int kGatherThreads = NG * 32;
   constexpr int kMmaWarp = NG;
@@ -562,24 +591,22 @@ __global__ void __launch_bounds__((NG + 1 + kEpiWarps) * 32, 1) fused_kernel(con
               const float *xr = a.X + (int64_t)ray * n_in + (size_t)(2 * s + j) * L * F + g * 8;
               const float4 x0 = *reinterpret_cast<const float4 *>(xr);
               const float4 x1 = *reinterpret_cast<const float4 *>(xr + 4);
-              outv = make_uint4(pack_bf16(x0.x, x0.y), pack_bf16(x0.z, x0.w), pack_bf16(x1.x, x1.y),
-                                pack_bf16(x1.z, x1.w));
+              outv = make_uint4(pack_op(x0.x, x0.y, H16), pack_op(x0.z, x0.w, H16), pack_op(x1.x, x1.y, H16),
+                                pack_op(x1.z, x1.w, H16));
             } else {
               const float *P = q.s.pts + ((size_t)ray * Hs + 2 * s + j) * 3;
               const float3 p = make_float3(P[0], P[1], P[2]);
               constexpr int LPG = 8 / F;  // levels per 16-byte group
-              float flat[8];
+              // the group's 8 features as operand words: F = 2 gathers give
+              // one half2 per level, F = 4 gathers FP32 values
+              uint32_t ow[4];
               if constexpr (F == 2 && GS == 1) {
                 // all LPG levels of the group, the next level's loads in flight
                 __half2 h[LPG];
                 encode_levels_h2_pipelined<LPG>(reinterpret_cast<const __half *>(tab) + (size_t)(g * LPG) * lstride,
                                                 lstride * 2, mask, p, s_res + g * LPG, h);
 #pragma unroll
-                for (int u = 0; u < LPG; ++u) {
-                  const float2 f2 = __half22float2(h[u]);
-                  flat[u * 2] = f2.x;
-                  flat[u * 2 + 1] = f2.y;
-                }
+                for (int u = 0; u < LPG; ++u) ow[u] = h2_bits(h[u]);
               } else
 #pragma unroll
               for (int u0 = 0; u0 < LPG; u0 += NLB) {
@@ -593,11 +620,7 @@ __global__ void __launch_bounds__((NG + 1 + kEpiWarps) * 32, 1) fused_kernel(con
                     encode_levels_h2<NLB>(reinterpret_cast<const __half *>(tab) + (size_t)l * lstride, lstride * 2,
                                           mask, p, s_res + l, h);
 #pragma unroll
-                  for (int u = 0; u < NLB; ++u) {
-                    const float2 f2 = __half22float2(h[u]);
-                    flat[(u0 + u) * 2] = f2.x;
-                    flat[(u0 + u) * 2 + 1] = f2.y;
-                  }
+                  for (int u = 0; u < NLB; ++u) ow[u0 + u] = h2_bits(h[u]);
                 } else {
                   float f[NLB][F];
                   encode_levels_f16<F, NLB>(reinterpret_cast<const __half *>(tab) + (size_t)l * lstride,
@@ -605,11 +628,14 @@ __global__ void __launch_bounds__((NG + 1 + kEpiWarps) * 32, 1) fused_kernel(con
 #pragma unroll
                   for (int u = 0; u < NLB; ++u)
 #pragma unroll
-                    for (int cc = 0; cc < F; ++cc) flat[(u0 + u) * F + cc] = f[u][cc];
+                    for (int cc = 0; cc < F; cc += 2) ow[((u0 + u) * F + cc) / 2] = pack_op(f[u][cc], f[u][cc + 1], H16);
                 }
               }
-              outv = make_uint4(pack_bf16(flat[0], flat[1]), pack_bf16(flat[2], flat[3]),
-                                pack_bf16(flat[4], flat[5]), pack_bf16(flat[6], flat[7]));
+              if constexpr (F == 2 && !H16) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) ow[k] = h2_bits_to_bf16(ow[k]);
+              }
+              outv = make_uint4(ow[0], ow[1], ow[2], ow[3]);
             }
             *reinterpret_cast<uint4 *>(A + core_off(r, j * G + g, a_sbo)) = outv;
           }
@@ -644,9 +670,9 @@ __global__ void __launch_bounds__((NG + 1 + kEpiWarps) * 32, 1) fused_kernel(con
       chunk_ctr += kmax;
     }
   } else if (warp == kMmaWarp) {
-    mma_role<F, W, XROWS, NG>(&a, base, tmem);
+    mma_role<F, W, XROWS, NG, H16>(&a, base, tmem);
   } else {
-    epilogue_role<F, W, XROWS, NG>(&a, base, tmem);
+    epilogue_role<F, W, XROWS, NG, H16>(&a, base, tmem);
   }
 
   tc_before();
@@ -683,11 +709,11 @@ static int pick_nbuf(const DevObject &h, int list_chunks) {
   return 0;
 }
 
-template <int F, int W, bool XR, int NG, int NLB, int GS>
-static cudaError_t launch_one(const FusedArgs &a, size_t smem, cudaStream_t st) {
+template <int F, int W, bool XR, int NG, int NLB, int GS, bool H16>
+static cudaError_t launch_op(const FusedArgs &a, size_t smem, cudaStream_t st) {
   static int attr = 0;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(fused_kernel<F, W, XR, NG, NLB, GS>,
+    cudaError_t e = cudaFuncSetAttribute(fused_kernel<F, W, XR, NG, NLB, GS, H16>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
     if (e != cudaSuccess) return e;
     attr = 1;
@@ -695,8 +721,14 @@ static cudaError_t launch_one(const FusedArgs &a, size_t smem, cudaStream_t st) 
   int sms = 0, dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  fused_kernel<F, W, XR, NG, NLB, GS><<<sms, (NG + 1 + kEpiWarps) * 32, smem, st>>>(a);
+  fused_kernel<F, W, XR, NG, NLB, GS, H16><<<sms, (NG + 1 + kEpiWarps) * 32, smem, st>>>(a);
   return cudaGetLastError();
+}
+
+template <int F, int W, bool XR, int NG, int NLB, int GS>
+static cudaError_t launch_one(const FusedArgs &a, size_t smem, cudaStream_t st) {
+  return a.fp16 ? launch_op<F, W, XR, NG, NLB, GS, true>(a, smem, st)
+                : launch_op<F, W, XR, NG, NLB, GS, false>(a, smem, st);
 }
 
 // Shapes the autotuner chooses between: gather warps per CTA (with the MMA
@@ -717,13 +749,18 @@ static cudaError_t dispatch_variant(const FusedArgs &a, int v, size_t smem, cuda
   constexpr int LPG = 8 / F;
   constexpr int NL2 = 2 < LPG ? 2 : LPG;
   constexpr int PAIRS = F == 2 ? 2 : 0;
-  switch (v) {
-    case 0: return launch_one<F, W, XR, 11, LPG, PAIRS>(a, smem, st);
-    case 1: return launch_one<F, W, XR, 11, NL2, F == 2 ? 1 : 0>(a, smem, st);
-    case 2: return launch_one<F, W, XR, 15, 1, PAIRS>(a, smem, st);
-    case 3: return launch_one<F, W, XR, 19, 1, PAIRS>(a, smem, st);
-    case 4: return launch_one<F, W, XR, 15, LPG, PAIRS>(a, smem, st);
-    default: return cudaErrorInvalidValue;
+  // rows given as input (lsnif_mlp) gather nothing: one shape serves them
+  if constexpr (XR) {
+    return v == 1 ? launch_one<F, W, XR, 11, NL2, F == 2 ? 1 : 0>(a, smem, st) : cudaErrorInvalidValue;
+  } else {
+    switch (v) {
+      case 0: return launch_one<F, W, XR, 11, LPG, PAIRS>(a, smem, st);
+      case 1: return launch_one<F, W, XR, 11, NL2, F == 2 ? 1 : 0>(a, smem, st);
+      case 2: return launch_one<F, W, XR, 15, 1, PAIRS>(a, smem, st);
+      case 3: return launch_one<F, W, XR, 19, 1, PAIRS>(a, smem, st);
+      case 4: return launch_one<F, W, XR, 15, LPG, PAIRS>(a, smem, st);
+      default: return cudaErrorInvalidValue;
+    }
   }
 }
 
@@ -743,11 +780,12 @@ void fused_variant_shape(int v, int *threads, int *levels) {
   *levels = kVariants[v].levels;
 }
 
-cudaError_t launch_fused(const QueryLaunch &q, const DevObject &h, int variant, int *launches) {
+cudaError_t launch_fused(const QueryLaunch &q, const DevObject &h, int variant, bool fp16, int *launches) {
   if (!fused_supported(h)) return cudaErrorNotSupported;
   if (variant < 0 || variant >= kNumVariants) return cudaErrorInvalidValue;
   FusedArgs a{};
   a.q = q;
+  a.fp16 = fp16 ? 1 : 0;
   a.smem_blob = blob_bytes(h);
   a.list_chunks = std::max(q.H_max, h.H) / 2;
   a.nbuf = pick_nbuf(h, a.list_chunks);
@@ -758,9 +796,10 @@ cudaError_t launch_fused(const QueryLaunch &q, const DevObject &h, int variant, 
 }
 
 cudaError_t launch_mlp_fused(const DevObject *dobj, const DevObject &h, const float *X, int64_t n, float *Z,
-                             int *err, cudaStream_t st) {
+                             bool fp16, int *err, cudaStream_t st) {
   if (!fused_supported(h)) return cudaErrorNotSupported;
   FusedArgs a{};
+  a.fp16 = fp16 ? 1 : 0;
   a.smem_blob = blob_bytes(h);
   a.list_chunks = h.H / 2;
   a.nbuf = pick_nbuf(h, a.list_chunks);

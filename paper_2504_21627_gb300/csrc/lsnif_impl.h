@@ -19,6 +19,12 @@ constexpr int kBuckets = kMaxCap + 1;  // per object: k = 0..32
 constexpr int kTileM = 128;          // rays per tensor-core tile (tcgen05 M)
 constexpr int kDistCap = 32;         // largest stored occupancy distance
 
+inline bool valid_precision(int p) {
+  return p == LSNIF_FP32_PLAIN || p == LSNIF_BF16_FUSED || p == LSNIF_FP8_FUSED || p == LSNIF_FP16_FUSED;
+}
+// the BF16 and FP16 paths share the fused kernel (only the operand type differs)
+inline bool fused16_precision(int p) { return p == LSNIF_BF16_FUSED || p == LSNIF_FP16_FUSED; }
+
 // error word bits written by kernels (never trap, never hang)
 enum DeviceError : int {
   kErrBadHandle = 1,
@@ -55,7 +61,8 @@ struct DevObject {
   int32_t H, n_in, n_hidden, width, n_out, n_out_pad, n_mat, act;
   const float *mlp32;   // packed FP32 [W0 b0 W1 b1 ...]
   const uint8_t *umma;  // BF16 weights in tcgen05 core-matrix layout + FP32 biases
-  uint32_t umma_bytes;  // total bytes of the umma blob
+  const uint8_t *umma_h;  // the same blob with FP16 weights (saturated at 65504)
+  uint32_t umma_bytes;  // total bytes of the umma blob (each of the two)
   uint32_t umma_bias_off;  // byte offset of the FP32 biases inside it
   const float *plain_out;  // FP32 output layer padded to n_out_pad rows, then its bias
 
@@ -146,7 +153,8 @@ cudaError_t launch_corners(const DevObject *dobj, const DevObject &host_obj, con
                            int64_t n, uint32_t *out, cudaStream_t st);
 cudaError_t launch_mlp_plain(const DevObject *dobj, const DevObject &host_obj, const float *X,
                              int64_t n, float *Z, cudaStream_t st);
-cudaError_t launch_build_umma(const DevObject &host_obj, uint8_t *dst, cudaStream_t st);
+// builds both tensor-core blobs (umma: BF16, umma_h: FP16) and the padded FP32 output layer
+cudaError_t launch_build_umma(const DevObject &host_obj, cudaStream_t st);
 cudaError_t launch_tables_to_half(const float *src, uint16_t *dst, int64_t n, cudaStream_t st);
 
 // ---- fused tensor-core path (fused.cu) ----
@@ -162,11 +170,12 @@ void fused8_variant_shape(int variant, int *threads, int *levels);
 cudaError_t launch_max_abs_half(const uint16_t *v, int64_t n, uint32_t *out_bits, cudaStream_t st);
 bool fused_supported(const DevObject &host_obj);
 size_t fused_smem_bytes(const DevObject &host_obj, int H_max);  // smallest ring; H_max: query's largest H
-cudaError_t launch_fused(const QueryLaunch &q, const DevObject &host_obj, int variant, int *launches);
+// fp16: FP16 operands (weights from umma_h) instead of BF16
+cudaError_t launch_fused(const QueryLaunch &q, const DevObject &host_obj, int variant, bool fp16, int *launches);
 int fused_variant_count();
 void fused_variant_shape(int variant, int *threads, int *levels);
 cudaError_t launch_mlp_fused(const DevObject *dobj, const DevObject &host_obj, const float *X,
-                             int64_t n, float *Z, int *err, cudaStream_t st);
+                             int64_t n, float *Z, bool fp16, int *err, cudaStream_t st);
 
 // ---- training (train.cu) ----
 struct TrainBuffers {

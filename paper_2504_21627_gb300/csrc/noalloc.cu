@@ -146,7 +146,7 @@ extern "C" int lsnif_query_rays_noalloc(lsnif_ctx *ctx, const lsnif_rays *r, lsn
   int launches = 0;
   cudaError_t e = launch_trace(q, &launches);
   if (e == cudaSuccess) e = launch_group(q, &launches);
-  if (e == cudaSuccess) e = launch_fused(q, hobj, ctx->fused_variant, &launches);
+  if (e == cudaSuccess) e = launch_fused(q, hobj, ctx->fused_variant, false, &launches);
   if (e != cudaSuccess) return cuda_fail(e, "lsnif_query_rays_noalloc");
   return LSNIF_OK;
 }

@@ -928,11 +928,12 @@ cudaError_t launch_tables_to_half(const float *src, uint16_t *dst, int64_t n, cu
   return cudaGetLastError();
 }
 
-// BF16 weights in the tcgen05 no-swizzle K-major core-matrix layout:
-// element (n, k) of a layer with K inputs sits at byte
+// BF16 (dst) and FP16 (dst16) weights in the tcgen05 no-swizzle K-major
+// core-matrix layout: element (n, k) of a layer with K inputs sits at byte
 //   ((n/8)*(K/8) + k/8)*128 + (n%8)*16 + (k%8)*2
-// Rows past the real output count are zero. Biases follow as FP32.
-__global__ void build_umma_kernel(DevObject h, uint8_t *dst) {
+// Rows past the real output count are zero. Biases follow as FP32 in both.
+// FP16 weights saturate at +-65504.
+__global__ void build_umma_kernel(DevObject h, uint8_t *dst, uint8_t *dst16) {
   const float *p = h.mlp32;
   uint32_t off = 0;
   int n_layers = h.n_hidden + 1;
@@ -946,11 +947,13 @@ __global__ void build_umma_kernel(DevObject h, uint8_t *dst) {
       float v = nn < Nr ? p[(int64_t)nn * K + kk] : 0.f;
       size_t o = off + ((size_t)(nn / 8) * (K / 8) + kk / 8) * 128 + (nn % 8) * 16 + (kk % 8) * 2;
       *reinterpret_cast<__nv_bfloat16 *>(dst + o) = __float2bfloat16_rn(v);
+      *reinterpret_cast<__half *>(dst16 + o) = __float2half_rn(fminf(fmaxf(v, -65504.f), 65504.f));
     }
     const float *b = p + (size_t)Nr * K;
     float *bd = reinterpret_cast<float *>(dst + h.umma_bias_off) + (size_t)l * h.width;
+    float *bd16 = reinterpret_cast<float *>(dst16 + h.umma_bias_off) + (size_t)l * h.width;
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < Np; j += gridDim.x * blockDim.x)
-      bd[j] = j < Nr ? b[j] : 0.f;
+      bd[j] = bd16[j] = j < Nr ? b[j] : 0.f;
     off += (uint32_t)Np * K * 2;
     p += (size_t)Nr * K + Nr;
   }
@@ -977,8 +980,8 @@ __global__ void build_plain_out_kernel(DevObject h, float *dst) {
   }
 }
 
-cudaError_t launch_build_umma(const DevObject &h, uint8_t *dst, cudaStream_t st) {
-  build_umma_kernel<<<152, 256, 0, st>>>(h, dst);
+cudaError_t launch_build_umma(const DevObject &h, cudaStream_t st) {
+  build_umma_kernel<<<152, 256, 0, st>>>(h, const_cast<uint8_t *>(h.umma), const_cast<uint8_t *>(h.umma_h));
   build_plain_out_kernel<<<16, 256, 0, st>>>(h, const_cast<float *>(h.plain_out));
   return cudaGetLastError();
 }

@@ -160,8 +160,7 @@ int lsnif::run_query(lsnif_ctx *ctx, Workspace *ws, const lsnif_rays *r, lsnif_h
                      cudaStream_t st, bool profile) {
   int rc = check_rays(r, h);
   if (rc) return rc;
-  if (precision != LSNIF_FP32_PLAIN && precision != LSNIF_BF16_FUSED && precision != LSNIF_FP8_FUSED)
-    return fail(LSNIF_ERR_INVALID_ARG, "query: unknown precision %d", precision);
+  if (!valid_precision(precision)) return fail(LSNIF_ERR_INVALID_ARG, "query: unknown precision %d", precision);
   if (r->n == 0) return LSNIF_OK;
   Shape sh;
   if ((rc = shape_of(ctx, r, &sh))) return rc;
@@ -198,10 +197,10 @@ int lsnif::run_query(lsnif_ctx *ctx, Workspace *ws, const lsnif_rays *r, lsnif_h
       return fail(LSNIF_ERR_UNSUPPORTED, "query: the fused FP8 path needs F in {2,4}, width 64/128, L <= 16, "
                                          "L*F a multiple of 16 and one shape for all objects");
   }
-  if (precision == LSNIF_BF16_FUSED) {
+  if (fused16_precision(precision)) {
     rep.umma_bytes = sh.umma_max;
     if (sh.mixed_fused || !fused_supported(rep) || fused_smem_bytes(rep, sh.H) > 232448)
-      return fail(LSNIF_ERR_UNSUPPORTED, "query: the fused BF16 path needs F in {2,4}, width 64/128, L <= 16, "
+      return fail(LSNIF_ERR_UNSUPPORTED, "query: the fused BF16/FP16 path needs F in {2,4}, width 64/128, L <= 16, "
                                          "one shape for all objects and weights that fit shared memory");
   }
   const int n_in = precision == LSNIF_FP32_PLAIN ? sh.n_in : 0;
@@ -228,7 +227,7 @@ int lsnif::run_query(lsnif_ctx *ctx, Workspace *ws, const lsnif_rays *r, lsnif_h
   if (e == cudaSuccess) {
     if (precision == LSNIF_FP32_PLAIN) e = launch_plain_tail(q, ws->cap_nin, kChunkTiles, &launches);
     else if (precision == LSNIF_FP8_FUSED) e = launch_fused8(q, rep, ctx->fp8_variant, &launches);
-    else e = launch_fused(q, rep, ctx->fused_variant, &launches);
+    else e = launch_fused(q, rep, ctx->fused_variant, precision == LSNIF_FP16_FUSED, &launches);
   }
   // rays on mesh objects were answered as misses by the traversal (no
   // voxels); their BVH query overwrites them
@@ -485,10 +484,11 @@ extern "C" int lsnif_mlp(lsnif_ctx *ctx, lsnif_obj h, const float *X, int64_t n,
   cudaError_t e;
   if (precision == LSNIF_FP32_PLAIN) {
     e = launch_mlp_plain(ctx->d_objs + o->slot, o->d, X, n, Z, (cudaStream_t)stream);
-  } else if (precision == LSNIF_BF16_FUSED) {
+  } else if (fused16_precision(precision)) {
     if (!fused_supported(o->d) || fused_smem_bytes(o->d, o->d.H) > 232448)
       return fail(LSNIF_ERR_UNSUPPORTED, "lsnif_mlp: shape not covered by the tensor-core kernel");
-    e = launch_mlp_fused(ctx->d_objs + o->slot, o->d, X, n, Z, ctx->d_err, (cudaStream_t)stream);
+    e = launch_mlp_fused(ctx->d_objs + o->slot, o->d, X, n, Z, precision == LSNIF_FP16_FUSED, ctx->d_err,
+                         (cudaStream_t)stream);
   } else {
     return fail(LSNIF_ERR_INVALID_ARG, "lsnif_mlp: unknown precision %d", precision);
   }

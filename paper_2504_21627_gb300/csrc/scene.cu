@@ -258,8 +258,7 @@ extern "C" int lsnif_query_scene(lsnif_ctx *ctx, const lsnif_rays *rays, const l
   if (n_inst < 1) return fail(LSNIF_ERR_INVALID_ARG, "lsnif_query_scene: n_inst < 1");
   if (hits->logits) return fail(LSNIF_ERR_INVALID_ARG, "lsnif_query_scene: logits are not supported");
   if (rays->n < 0) return fail(LSNIF_ERR_INVALID_ARG, "lsnif_query_scene: n < 0");
-  if (precision != LSNIF_FP32_PLAIN && precision != LSNIF_BF16_FUSED && precision != LSNIF_FP8_FUSED)
-    return fail(LSNIF_ERR_INVALID_ARG, "lsnif_query_scene: unknown precision %d", precision);
+  if (!valid_precision(precision)) return fail(LSNIF_ERR_INVALID_ARG, "lsnif_query_scene: unknown precision %d", precision);
   if (rays->n == 0) return LSNIF_OK;
   if (!rays->ox || !rays->oy || !rays->oz || !rays->dx || !rays->dy || !rays->dz || !rays->tmin || !rays->tmax)
     return fail(LSNIF_ERR_INVALID_ARG, "lsnif_query_scene: every ray array must be given");

@@ -175,8 +175,7 @@ static void advance(lsnif_ctx *ctx, Server *sv) {
 extern "C" int lsnif_submit(lsnif_ctx *ctx, const lsnif_rays *rays, lsnif_hits *hits, int precision,
                             void *stream, uint64_t *ticket) {
   if (!ctx || !rays || !hits || !ticket) return fail(LSNIF_ERR_INVALID_ARG, "lsnif_submit: NULL argument");
-  if (precision != LSNIF_FP32_PLAIN && precision != LSNIF_BF16_FUSED && precision != LSNIF_FP8_FUSED)
-    return fail(LSNIF_ERR_INVALID_ARG, "lsnif_submit: unknown precision %d", precision);
+  if (!valid_precision(precision)) return fail(LSNIF_ERR_INVALID_ARG, "lsnif_submit: unknown precision %d", precision);
   if (rays->n < 0) return fail(LSNIF_ERR_INVALID_ARG, "lsnif_submit: n < 0");
   cudaSetDevice(ctx->device);
   Server *sv;

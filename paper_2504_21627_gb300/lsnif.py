@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "liblsnif.so")
 OK, PENDING = 0, 1
 ERR = {-1: "INVALID_ARG", -2: "BAD_HANDLE", -3: "OUT_OF_MEMORY", -4: "OVER_BUDGET", -5: "CORRUPT", -6: "TIMEOUT",
        -7: "CUDA", -8: "DEVICE_CHECK", -9: "BUSY", -10: "UNSUPPORTED"}
-FP32_PLAIN, BF16_FUSED, FP8_FUSED = 0, 1, 2
+FP32_PLAIN, BF16_FUSED, FP8_FUSED, FP16_FUSED = 0, 1, 2, 3
 PARAM_OCCUPANCY, PARAM_TABLES, PARAM_MLP, PARAM_GRAD_TABLES, PARAM_GRAD_MLP = 0, 1, 2, 3, 4
 TRAIN_UNIFORMS = 40
 MAX_LEVELS = 32

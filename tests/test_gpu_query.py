@@ -7,6 +7,7 @@ Tolerances (stated per test, with the arithmetic behind each):
   BF16 path: logits against the oracle run with the same BF16/FP16 rounding of
   operands, decisions identical except where |logit| is within the rounding
   noise; against the pure FP64 oracle the error is reported
+  FP16 path: the same against the oracle run with FP16 operand rounding
 """
 import numpy as np
 import pytest
@@ -65,6 +66,14 @@ def fp32_tol(cfg):
 # same BF16-rounded operands) can round a hidden activation to neighbouring
 # BF16 values; one such step is 2^-8 of that activation.
 BF16_TOL = 2.0 ** -7
+
+# FP16 operands: the same argument with FP16 steps (2^-11 of an activation)
+# gives 2^-10 for the network alone. In a whole query the F = 2 gather also
+# interpolates in half2 arithmetic (a few FP16 rounding steps of the table
+# range per feature, against the oracle's one rounding of the exact value):
+# 2^-9 of the largest logit.
+FP16_NET_TOL = 2.0 ** -10
+FP16_TOL = 2.0 ** -9
 
 
 # ---------------------------------------------------------------------------
@@ -195,6 +204,24 @@ def test_mlp_tensor_core_matches_oracle(ctx, torus, n):
     assert e64 < 3e-2, f"vs FP64 oracle: {e64}"
 
 
+@pytest.mark.parametrize("n", [1, 129, 5001])
+def test_mlp_tensor_core_fp16_matches_oracle(ctx, torus, n):
+    g = np.random.default_rng(200 + n)
+    X = g.normal(scale=0.05, size=(n, torus["cfg"].n_in)).astype(np.float32)
+    got = ctx.mlp(torus["h"], _cuda(X), lsnif.FP16_FUSED).cpu().numpy()
+    ctx.check()
+    want16 = O.mlp_forward(X.astype(np.float64), torus["orc"].weights, torus["cfg"].activation, precision="fp16")
+    want64 = O.mlp_forward(X.astype(np.float64), torus["orc"].weights, torus["cfg"].activation)
+    wantb = O.mlp_forward(X.astype(np.float64), torus["orc"].weights, torus["cfg"].activation, precision="bf16")
+    scale = np.abs(want64).max()
+    e16 = np.abs(got - want16).max() / scale
+    print(f"FP16 network, n={n}: {e16:.2e} against the FP16 oracle, {np.abs(got - want64).max() / scale:.2e} "
+          f"against FP64 (BF16 oracle against FP64: {np.abs(wantb - want64).max() / scale:.2e})")
+    assert e16 < FP16_NET_TOL, f"vs FP16-rounded oracle: {e16}"
+    # FP16 keeps three more significand bits than BF16: closer to FP64
+    assert np.abs(got - want64).max() < np.abs(wantb - want64).max()
+
+
 # ---------------------------------------------------------------------------
 # end to end
 # ---------------------------------------------------------------------------
@@ -202,12 +229,13 @@ def test_mlp_tensor_core_matches_oracle(ctx, torus, n):
 def _query_compare(ctx, o, rays, prec, tol_logit):
     out = ctx.query_rays(_cuda(rays), obj=o["h"], precision=prec, logits=True)
     ctx.check()
-    ref, seg = O.query(o["orc"], rays, precision="bf16" if prec == lsnif.BF16_FUSED else "f64")
+    ref, seg = O.query(o["orc"], rays, precision={lsnif.BF16_FUSED: "bf16", lsnif.FP16_FUSED: "fp16"}.get(prec, "f64"))
     ok = ~seg.near
     live = ref.live & ok
     lg = out.logits.cpu().numpy()
     scale = np.abs(ref.logits[live]).max()
     err = np.abs(lg[live] - ref.logits[live]).max() / scale
+    print(f"precision {prec}: logit error {err:.3g} of the largest (bound {tol_logit:.3g})")
     assert err < tol_logit, f"logit error {err:.3g}"
     # rays that never reach the network: exact miss record
     miss = ~ref.live & ok
@@ -248,6 +276,18 @@ def test_query_bf16_torus_sample(ctx, torus):
     g = np.random.default_rng(4)
     rays = np.ascontiguousarray(I.rays_pinhole(cam)[:, g.choice(2048 * 2048, 768, replace=False)])
     _query_compare(ctx, torus, rays, lsnif.BF16_FUSED, BF16_TOL + fp32_tol(torus["cfg"]))
+
+
+def test_query_fp16_torus_sample(ctx, torus):
+    cam = I.seeded_camera(2)
+    g = np.random.default_rng(4)
+    rays = np.ascontiguousarray(I.rays_pinhole(cam)[:, g.choice(2048 * 2048, 768, replace=False)])
+    _query_compare(ctx, torus, rays, lsnif.FP16_FUSED, FP16_TOL + fp32_tol(torus["cfg"]))
+
+
+def test_query_fp16_sphere(ctx, sphere):
+    rays = I.rays_sphere_to_box(1000, 3.0, sphere["orc"].bmin, sphere["orc"].bmax, seed=32)
+    _query_compare(ctx, sphere, rays, lsnif.FP16_FUSED, FP16_TOL + fp32_tol(sphere["cfg"]))
 
 
 def test_query_bf16_sphere_unsupported_shape_is_refused(ctx, sphere):
@@ -301,7 +341,7 @@ def test_full_size_torus_4m_rays(ctx, torus, prec):
 
 def test_host_buffer_query_equals_device_query(ctx, sphere):
     rays = I.rays_sphere_to_box(3000, 3.0, sphere["orc"].bmin, sphere["orc"].bmax, seed=41)
-    for prec in (lsnif.FP32_PLAIN, lsnif.BF16_FUSED):
+    for prec in (lsnif.FP32_PLAIN, lsnif.BF16_FUSED, lsnif.FP16_FUSED):
         dev = ctx.query_rays(_cuda(rays), obj=sphere["h"], precision=prec)
         torch.cuda.synchronize()
         host = ctx.query_rays_host(torch.from_numpy(rays).pin_memory(), obj=sphere["h"], precision=prec)
@@ -436,7 +476,7 @@ def test_graph_mode_replays_the_query(ctx, sphere, torus):
     handles = _cuda(np.concatenate([np.full(ra.shape[1], sphere["h"]),
                                     np.full(rb.shape[1], torus["h"])]).astype(np.uint32).view(np.int32))
     side = torch.cuda.Stream()
-    for prec in (lsnif.FP32_PLAIN, lsnif.BF16_FUSED):
+    for prec in (lsnif.FP32_PLAIN, lsnif.BF16_FUSED, lsnif.FP16_FUSED):
         direct = ctx.query_rays(both, obj_per_ray=handles, precision=prec)
         torch.cuda.synchronize()
         ctx.set_graph_mode(True)
@@ -476,10 +516,10 @@ def test_tuning_choices_give_identical_results(ctx, torus):
     rays = _cuda(np.ascontiguousarray(I.rays_pinhole(cam, px0=500, py0=700, w=512, h=256)))
     ref = {}
     keep = ctx.tuning()
-    for prec in (lsnif.FP32_PLAIN, lsnif.BF16_FUSED):
+    for prec in (lsnif.FP32_PLAIN, lsnif.BF16_FUSED, lsnif.FP16_FUSED):
         for tm in (0, 1):
             for gm in (0, 1):
-                for v in (range(len(lsnif.Context.variants())) if prec == lsnif.BF16_FUSED else [0]):
+                for v in (range(len(lsnif.Context.variants())) if prec != lsnif.FP32_PLAIN else [0]):
                     ctx.set_trace_mode(tm)
                     ctx.set_group_mode(gm)
                     ctx.set_variant(v)

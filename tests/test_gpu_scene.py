@@ -104,10 +104,11 @@ def scene(ctx):
     return dict(objs=objs, handles=handles, boxes=boxes, insts=insts)
 
 
-ORACLE_PRECISION = {lsnif.FP32_PLAIN: "f64", lsnif.BF16_FUSED: "bf16", lsnif.FP8_FUSED: "fp8"}
+ORACLE_PRECISION = {lsnif.FP32_PLAIN: "f64", lsnif.BF16_FUSED: "bf16", lsnif.FP8_FUSED: "fp8",
+                    lsnif.FP16_FUSED: "fp16"}
 
 
-@pytest.mark.parametrize("prec", [lsnif.FP32_PLAIN, lsnif.BF16_FUSED, lsnif.FP8_FUSED])
+@pytest.mark.parametrize("prec", [lsnif.FP32_PLAIN, lsnif.BF16_FUSED, lsnif.FP8_FUSED, lsnif.FP16_FUSED])
 def test_instanced_scene_matches_oracle(ctx, scene, prec):
     rays = _aim(scene["insts"], 6000, 5, scene["boxes"])
     got = _gpu_scene(ctx, rays, scene["insts"], scene["handles"], prec)

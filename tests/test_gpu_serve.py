@@ -51,7 +51,7 @@ def _requests(objs, seed, n_req=24):
     return out
 
 
-@pytest.mark.parametrize("prec", [lsnif.FP32_PLAIN, lsnif.BF16_FUSED])
+@pytest.mark.parametrize("prec", [lsnif.FP32_PLAIN, lsnif.BF16_FUSED, lsnif.FP16_FUSED])
 def test_results_alone_and_in_the_mix_are_identical(prec):
     with lsnif.Context(0) as ctx:
         objs = _objects(ctx)
