@@ -131,6 +131,30 @@ __device__ __forceinline__ int sel3i(int a, int x, int y, int z) { return a == 0
 // crossing time of plane index P on one axis (the expression dda_walk uses)
 __device__ __forceinline__ float plane_t(int P, float invV, float o, float inv) { return ((float)P * invV - o) * inv; }
 
+// Planes that one axis crosses before the current cell's exit time ea, as
+// the voxel walk counts them: plane m of the axis (m = 0, 1, ...) is
+// ix + 1 + m for st > 0 and ix - m for st < 0, crossed when its time is
+// below ea, or equal to it when the axis wins the tie (`tie`). Plane times
+// are monotone in m (each operation of plane_t is), so the crossed planes
+// are a prefix: the count is guessed from the position at ea and then
+// corrected with the exact comparisons until plane n is the first one not
+// crossed. At most `cap` planes; 0 when the axis does not move.
+__device__ __forceinline__ int planes_before(int ix, int st, float o, float d, float inv, float invV, int V,
+                                             float ea, bool tie, int cap) {
+  if (st == 0 || cap <= 0) return 0;
+  auto crosses = [&](int m) {
+    const float t = plane_t(st > 0 ? ix + 1 + m : ix - m, invV, o, inv);
+    return t < ea || (tie && t == ea);
+  };
+  const float xe = fmaf(ea, d, o) * (float)V;  // position at ea, in voxels
+  float g = st > 0 ? floorf(xe) - (float)ix : (float)ix - ceilf(xe) + 1.f;
+  g = fminf(fmaxf(g, 0.f), (float)cap);          // also maps NaN to 0
+  int n = (int)g;
+  while (n > 0 && !crosses(n - 1)) --n;
+  while (n < cap && crosses(n)) ++n;
+  return n;
+}
+
 // occupancy distance of voxel (x, y, z): 0 when occupied, else the radius
 // of the empty cube around it is D - 1
 __device__ __forceinline__ int voxel_distance(const DevObject &ob, int x, int y, int z) {
@@ -284,44 +308,16 @@ __global__ void __launch_bounds__(256) trace_pool_kernel(QueryLaunch q, int smem
         // -- the cube holds no occupied voxel, so nothing is lost.
         bool out = false;
         if (rr) {
-          for (int g = 0; g < 2 * rr; ++g) {
-            const int nx = R.ix0 + (R.st0 > 0);
-            if (a != 0 && R.st0 != 0 && plane_t(nx, invV, R.o.x, R.inv0) <= ea) {  // 0 < a
-              if ((unsigned)(R.ix0 + R.st0) >= (unsigned)V) {
-                out = true;
-                break;
-              }
-              R.ix0 += R.st0;
-            } else {
-              break;
-            }
-          }
-          for (int g = 0; g < 2 * rr && !out; ++g) {
-            const int ny = R.ix1 + (R.st1 > 0);
-            const float ty = plane_t(ny, invV, R.o.y, R.inv1);
-            if (a != 1 && R.st1 != 0 && (ty < ea || (ty == ea && a == 2))) {
-              if ((unsigned)(R.ix1 + R.st1) >= (unsigned)V) {
-                out = true;
-                break;
-              }
-              R.ix1 += R.st1;
-            } else {
-              break;
-            }
-          }
-          for (int g = 0; g < 2 * rr && !out; ++g) {
-            const int nz = R.ix2 + (R.st2 > 0);
-            const float tz = plane_t(nz, invV, R.o.z, R.inv2);
-            if (a != 2 && R.st2 != 0 && tz < ea) {
-              if ((unsigned)(R.ix2 + R.st2) >= (unsigned)V) {
-                out = true;
-                break;
-              }
-              R.ix2 += R.st2;
-            } else {
-              break;
-            }
-          }
+          // axis b moves n_b voxels; stepping onto voxel -1 or V (more steps
+          // than the grid leaves, m_b) means the ray leaves the grid first
+          const int n0 = a == 0 ? 0 : planes_before(R.ix0, R.st0, R.o.x, R.d.x, R.inv0, invV, V, ea, true, 2 * rr);
+          const int n1 = a == 1 ? 0 : planes_before(R.ix1, R.st1, R.o.y, R.d.y, R.inv1, invV, V, ea, a == 2, 2 * rr);
+          const int n2 = a == 2 ? 0 : planes_before(R.ix2, R.st2, R.o.z, R.d.z, R.inv2, invV, V, ea, false, 2 * rr);
+          out = n0 > (R.st0 > 0 ? V - 1 - R.ix0 : R.ix0) || n1 > (R.st1 > 0 ? V - 1 - R.ix1 : R.ix1) ||
+                n2 > (R.st2 > 0 ? V - 1 - R.ix2 : R.ix2);
+          R.ix0 += R.st0 * n0;
+          R.ix1 += R.st1 * n1;
+          R.ix2 += R.st2 * n2;
         }
         // then axis a crosses its plane
         const int sa = sel3i(a, R.st0, R.st1, R.st2);
