@@ -840,7 +840,8 @@ def main():
     fused_ms = float(np.mean([q.ms_mlp for q in prof16]))
     achieved = alg_bytes / (fused_ms / 1e3) / 1e9
     peak, peak_src = measured_peaks()
-    traffic = recorded_traffic()
+    # the committed capture is of the 2048 x 2048 workload
+    traffic = recorded_traffic() if args.side == 2048 else None
     launches_per_step = int(prof16[-1].launches)
     l2_requests = pts * L * 5.0  # ~1.25 16-byte requests per x-pair, 4 pairs per point and level
 
