@@ -190,9 +190,13 @@ __global__ void __launch_bounds__(256) trace_pool_kernel(QueryLaunch q, int smem
   };
 
   for (;;) {
-    const bool need = R.i < 0 && !exhausted;
-    const unsigned m = __ballot_sync(FULL, need);
-    if (m) {
+    // refill: a lane without a ray takes rays until one enters its object's
+    // box (a ray that misses it is answered at once, so no lane spends the
+    // round idle on it) or the pool is empty
+    for (;;) {
+      const bool need = R.i < 0 && !exhausted;
+      const unsigned m = __ballot_sync(FULL, need);
+      if (!m) break;
       const int leader = __ffs(m) - 1;
       int base = 0;
       if (lane == leader) base = atomicAdd(counter, __popc(m));
