@@ -145,8 +145,19 @@ def oracle_rate(cfg, mesh, params, rays, n_sample: int, seed: int = 0):
     t0 = time.perf_counter()
     O.query(orc, sub)
     dt = time.perf_counter() - t0
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    cores = O.threads()
     return n_sample / dt / 1e6, cores, dt
+
+
+def oracle_rate_single_thread(cfg, mesh, params, rays, n_sample: int, seed: int = 1):
+    """oracle_rate with the oracle's loops on one host thread."""
+    from oracle import oracle as O
+    before = O.threads(1)
+    try:
+        rate, _, dt = oracle_rate(cfg, mesh, params, rays, n_sample, seed)
+    finally:
+        O.threads(before)
+    return rate, dt
 
 
 def run_reference(args):
@@ -884,6 +895,11 @@ def main():
         rate, cores, dt = oracle_rate(cfg, mesh, params, rays_np, args.cpu_sample)
         line["cpu_baseline"] = {"value": rate, "unit": "Mrays/s", "cores": cores, "kind": "oracle",
                                 "sample": f"{args.cpu_sample} seeded rays of the workload ({dt:.1f} s)"}
+        n1 = max(256, args.cpu_sample // 16)
+        rate1, dt1 = oracle_rate_single_thread(cfg, mesh, params, rays_np, n1)
+        line["cpu_baseline"]["single_thread"] = {
+            "value": rate1, "unit": "Mrays/s", "cores": 1,
+            "sample": f"{n1} seeded rays of the workload ({dt1:.1f} s)"}
     if rank == 0:
         print(json.dumps(line))
     ctx.close()

@@ -29,6 +29,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_API __attribute__((visibility("default")))
 
@@ -545,4 +548,19 @@ ORC_API void orc_cast64(const double *o, const double *d, int64_t n, const float
     for (int64_t i = 0; i < n; ++i)
         cast_one(o + 3 * i, d + 3 * i, 0.0, INFINITY, verts, tris, nt, out_t + i, out_tri + i, out_u + i,
                  out_v + i);
+}
+
+/* Host threads of the parallel loops above (timing only; no result depends
+ * on it: every loop writes each output from one iteration). Returns the
+ * count in effect before the call; n <= 0 only queries it. */
+ORC_API int orc_threads(int n)
+{
+#ifdef _OPENMP
+    const int before = omp_get_max_threads();
+    if (n > 0) omp_set_num_threads(n);
+    return before;
+#else
+    (void)n;
+    return 1;
+#endif
 }

@@ -63,8 +63,16 @@ def lib():
         L.orc_encode_backward.argtypes = [P, i64, P, i32, i32, i32, P, P]
         L.orc_judge.argtypes = [P, i64, P, P, i64, P, P, P, P]
         L.orc_cast64.argtypes = [P, P, i64, P, P, i64, P, P, P, P]
+        L.orc_threads.argtypes = [i32]
+        L.orc_threads.restype = i32
         _lib = L
     return _lib
+
+
+def threads(n: int = 0) -> int:
+    """Host threads of the C loops (n > 0 sets them); returns the previous
+    count. Timing only: every output comes from one loop iteration."""
+    return int(lib().orc_threads(n))
 
 
 def _p(a: np.ndarray):
