@@ -1,12 +1,15 @@
-// Fused BF16 tensor-core query kernel for sm_103a: hash-grid gather ->
-// every MLP layer on tcgen05 (TMEM accumulators) -> decode, one persistent
-// CTA per SM. The paper fuses all layers of its FP16 network into one kernel
-// on its own hardware (Sec. 5); here the gather is fused in as well, so the
-// concatenated input vector (Sec. 3.2) never leaves shared memory.
+// Fused half-precision tensor-core query kernel for sm_103a: hash-grid
+// gather -> every MLP layer on tcgen05 (TMEM accumulators) -> decode, one
+// persistent CTA per SM. The paper fuses all layers of its FP16 network into
+// one kernel on its own hardware (Sec. 5); here the gather is fused in as
+// well, so the concatenated input vector (Sec. 3.2) never leaves shared
+// memory. The network's operands are BF16 or, in the H16 instantiations,
+// FP16 (kind::f16 takes either, A and B always of the same type); FP32
+// accumulation in both.
 //
 // Work unit: a tile of 128 rays (the tcgen05 M). The first layer's K runs
 // over the tile's occupied-voxel segments: chunk s holds the features of
-// points 2s and 2s+1 (2*L*F BF16 columns, no-swizzle K-major core-matrix
+// points 2s and 2s+1 (2*L*F 16-bit columns, no-swizzle K-major core-matrix
 // layout). Chunks no ray of the tile reaches are skipped (tiles are sorted
 // by point count).
 //
@@ -16,7 +19,7 @@
 //   one MMA warp: issues each filled chunk's MMAs against the resident
 //     first-layer weights into the tile's TMEM accumulator;
 //   four epilogue warps (TMEM lane = ray): hidden and output layers (bias,
-//     activation, BF16 activations back to shared memory, next MMA) and the
+//     activation, 16-bit activations back to shared memory, next MMA) and the
 //     decode, while the gather warps fill the next tile. Two TMEM
 //     accumulators alternate between tiles.
 //
