@@ -257,8 +257,9 @@ LSNIF_API int lsnif_write_params(lsnif_ctx *ctx, lsnif_obj obj, int which, const
  * context-owned scratch memory (grown on demand and charged to the budget).
  * Results do not depend on which other rays share the call.
  * Errors: INVALID_ARG, BAD_HANDLE (a ray names an unknown object: checked
- * on the device, reported as DEVICE_CHECK), UNSUPPORTED (BF16 path with a
- * config it does not cover), OVER_BUDGET, CUDA. */
+ * on the device, reported as DEVICE_CHECK), UNSUPPORTED (a fused path --
+ * BF16, FP16 or FP8 -- with a config it does not cover), OVER_BUDGET, CUDA.
+ * precision: one of enum lsnif_precision. */
 LSNIF_API int lsnif_query_rays(lsnif_ctx *ctx, const lsnif_rays *rays, lsnif_hits *hits, int precision,
                      void *stream);
 
