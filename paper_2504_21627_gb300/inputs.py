@@ -231,6 +231,15 @@ def cube(n_mat: int = 1) -> Mesh:
     return Mesh(v, f, _vertex_normals(v, f), np.zeros(12, np.int32), _albedo_table(n_mat, 0), n_mat)
 
 
+def tetrahedron(n_mat: int = 2) -> Mesh:
+    """Regular tetrahedron inscribed in the unit sphere (alternate corners of
+    a cube), outward winding; triangle i has material i mod n_mat."""
+    v = np.array([[1, 1, 1], [1, -1, -1], [-1, 1, -1], [-1, -1, 1]], dtype=np.float32) / np.float32(math.sqrt(3.0))
+    f = np.array([[0, 1, 2], [0, 3, 1], [0, 2, 3], [1, 3, 2]], dtype=np.int32)
+    mat = (np.arange(4) % n_mat).astype(np.int32)
+    return Mesh(v, f, _vertex_normals(v, f), mat, _albedo_table(n_mat, 0), n_mat)
+
+
 def single_triangle(a, b, c, n_mat: int = 1) -> Mesh:
     v = np.array([a, b, c], dtype=np.float32)
     f = np.array([[0, 1, 2]], dtype=np.int32)
