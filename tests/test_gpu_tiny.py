@@ -1,6 +1,7 @@
 """Every stage on tiny meshes -- a tetrahedron, a single tilted triangle and
-icospheres at subdivision 0 and 1 -- against the oracle: occupancy, box and level resolutions bit-exact, voxel
-counts exact away from voxel faces, and the query's logits and decisions in
+icospheres at subdivision 0 and 1 -- against the oracle: occupancy, box and
+level resolutions bit-exact, voxel counts exact away from voxel faces, and
+the query's logits and decisions in
 the FP32, BF16 and FP16 paths at the tolerances of the query tests (FP32:
 1e-4 of the largest logit at these lattice resolutions; BF16 2^-7 and FP16
 2^-9 on top, against the oracle run with the same operand rounding)."""
