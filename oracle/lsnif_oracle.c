@@ -37,9 +37,12 @@
 
 /* ------------------------------------------------------------------------
  * Bounding box (Sec. 3.1: the object's AABB is its local frame).
- * The box of FP32 vertices is exact in FP32. An axis thinner than 1e-6 of
+ * The box of FP32 vertices is exact in FP32. An axis thinner than 1/8 of
  * the diagonal is widened symmetrically to that thickness, rounded outward
- * to FP32, so that the unit-cube map stays finite.
+ * to FP32. The unit-cube map multiplies an axis by 1/extent, so a very thin
+ * axis would magnify the rounding of FP32 ray origins along it into whole
+ * voxels; at 1/8 of the diagonal it magnifies them at most 8 times as much
+ * as the diagonal does.
  * ---------------------------------------------------------------------- */
 ORC_API void orc_bbox(const float *verts, int64_t nv, float bmin[3], float bmax[3])
 {
@@ -52,7 +55,7 @@ ORC_API void orc_bbox(const float *verts, int64_t nv, float bmin[3], float bmax[
         }
     double diag = sqrt((hi[0] - lo[0]) * (hi[0] - lo[0]) + (hi[1] - lo[1]) * (hi[1] - lo[1]) +
                        (hi[2] - lo[2]) * (hi[2] - lo[2]));
-    double emin = 1e-6 * diag;
+    double emin = diag / 8.0;
     if (emin == 0.0) emin = 1e-6;
     for (int a = 0; a < 3; ++a) {
         if (hi[a] - lo[a] < emin) {

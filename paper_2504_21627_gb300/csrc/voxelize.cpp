@@ -27,10 +27,13 @@ void mesh_bbox(const float *verts, int64_t nv, float bmin[3], float bmax[3]) {
   }
   double d2 = 0;
   for (int a = 0; a < 3; ++a) d2 += (hi[a] - lo[a]) * (hi[a] - lo[a]);
-  double thin = 1e-6 * std::sqrt(d2);
+  // An axis thinner than 1/8 of the diagonal is widened to that: the unit-cube
+  // map scales an axis by 1/extent, so a thinner axis would magnify the FP32
+  // rounding of ray origins along it into a large part of a voxel.
+  double thin = std::sqrt(d2) / 8.0;
   if (thin == 0.0) thin = 1e-6;
   for (int a = 0; a < 3; ++a) {
-    if (hi[a] - lo[a] < thin) {  // widen a flat axis symmetrically
+    if (hi[a] - lo[a] < thin) {  // widen a flat or thin axis symmetrically
       const double mid = 0.5 * (lo[a] + hi[a]);
       lo[a] = mid - 0.5 * thin;
       hi[a] = mid + 0.5 * thin;

@@ -1,4 +1,5 @@
-"""Every stage on tiny meshes -- a tetrahedron, a single tilted triangle and
+"""Every stage on tiny meshes -- a tetrahedron, a single tilted triangle, an
+axis-aligned (flat) triangle whose box is widened along its normal, and
 icospheres at subdivision 0 and 1 -- against the oracle: occupancy, box and
 level resolutions bit-exact, voxel counts exact away from voxel faces, and
 the query's logits and decisions in
@@ -18,6 +19,7 @@ from paper_2504_21627_gb300 import lsnif  # noqa: E402
 MESHES = {
     "tetrahedron": lambda: I.tetrahedron(n_mat=2),
     "triangle": lambda: I.single_triangle((-0.8, -0.5, -0.3), (0.9, -0.2, 0.4), (0.1, 0.8, -0.6), n_mat=2),
+    "flat_triangle": lambda: I.single_triangle((-0.8, -0.5, 0.2), (0.9, -0.2, 0.2), (0.1, 0.8, 0.2), n_mat=2),
     "icosphere0": lambda: I.icosphere(0),
     "icosphere1": lambda: I.icosphere(1),
 }

@@ -13,14 +13,34 @@ from paper_2504_21627_gb300 import inputs as I
 
 
 def test_bbox_exact_and_widened():
+    """The box is the exact FP32 box of the vertices; an axis thinner than 1/8
+    of the diagonal is widened to 1/8 of it, symmetrically about its centre,
+    and rounded outward to FP32 (at most one FP32 step beyond the exact
+    bounds)."""
     m = I.icosphere(2)
     lo, hi = O.bbox(m.verts)
     assert np.array_equal(lo, m.verts.min(0)) and np.array_equal(hi, m.verts.max(0))
+
+    def widened(lo_a, hi_a, c, e):
+        want_lo, want_hi = c - e / 2, c + e / 2    # compared in float64
+        up = float(np.nextafter(lo_a, np.float32(np.inf)))
+        down = float(np.nextafter(hi_a, np.float32(-np.inf)))
+        return float(lo_a) <= want_lo < up and down < want_hi <= float(hi_a)
+
+    # flat along z: diagonal sqrt(2), widened to sqrt(2)/8 about z = 0.5
     flat = I.single_triangle((0, 0, 0.5), (1, 0, 0.5), (0, 1, 0.5))
     lo, hi = O.bbox(flat.verts)
-    assert lo[2] < 0.5 < hi[2]
-    diag = math.sqrt(2.0)
-    assert hi[2] - lo[2] >= 1e-6 * diag and hi[2] - lo[2] < 1.1e-6 * diag + 1e-7
+    assert widened(lo[2], hi[2], 0.5, math.sqrt(2.0) / 8)
+    assert lo[0] == 0 and hi[0] == 1 and lo[1] == 0 and hi[1] == 1
+    # thin but not flat: z extent 0.1 < sqrt(2.01)/8 = 0.1772..., centre 0.05
+    thin = I.single_triangle((0, 0, 0), (1, 0, 0.1), (0, 1, 0))
+    lo, hi = O.bbox(thin.verts)
+    assert widened(lo[2], hi[2], float(np.float32(0.1)) / 2, math.sqrt(2 + float(np.float32(0.1)) ** 2) / 8)
+    # z extent 0.2 > sqrt(2.04)/8 = 0.1785...: kept exact
+    kept = I.single_triangle((0, 0, 0), (1, 0, 0.2), (0, 1, 0))
+    lo, hi = O.bbox(kept.verts)
+    assert lo[2] == 0 and hi[2] == np.float32(0.2)
+    assert float(np.float32(0.2)) > math.sqrt(2 + float(np.float32(0.2)) ** 2) / 8
 
 
 def _grid_tri(V, a, b, c):
