@@ -246,6 +246,15 @@ def round_bf16(x: np.ndarray) -> np.ndarray:
     return out
 
 
+def split_bf16(x: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
+    """Two-term bfloat16 form of x: hi = BF16(x), lo = BF16(x - hi), so that
+    hi + lo carries about 16 significant bits of x (each rounding as in
+    round_bf16, through float32)."""
+    x = np.asarray(x, np.float64)
+    hi = round_bf16(x)
+    return hi, round_bf16(x - hi)
+
+
 def round_fp16(x: np.ndarray) -> np.ndarray:
     return np.asarray(x, np.float64).astype(np.float32).astype(np.float16).astype(np.float64)
 
@@ -313,30 +322,42 @@ def activation_grad(pre: np.ndarray, kind: int) -> np.ndarray:
 
 def mlp_forward(X: np.ndarray, weights, act: int = 0, precision: str = "f64", keep: bool = False,
                 fp8=None):
-    """Dense layers, hidden activation `act`, linear output. With
-    precision='bf16' the matmul operands (inputs, weights, hidden
-    activations) are rounded to bfloat16 first; sums stay float64;
-    precision='fp16' does the same with saturating binary16 rounding. With
-    precision='fp8' (fp8 = (s, w) from fp8_scales) every layer multiplies
-    round_e4m3(s_l h) by round_e4m3(w_l W_l) and divides the sum by s_l w_l
-    before the bias."""
+    """Dense layers, hidden activation `act`, linear output; sums in float64.
+
+    precision='bf16_plain': every matmul operand (inputs, weights, hidden
+    activations) is rounded once to bfloat16. precision='bf16': the first
+    layer is the same, and every later layer takes its input activations
+    and its weights in the two-term form of split_bf16 and forms
+    hi_a.hi_w + hi_a.lo_w + lo_a.hi_w (the lo_a.lo_w product, about 2^-16
+    of the rest, is left out). precision='fp16' rounds every operand once
+    to binary16 with saturation. precision='fp8' (fp8 = (s, w) from
+    fp8_scales): every layer multiplies round_e4m3(s_l h) by
+    round_e4m3(w_l W_l) and divides the sum by s_l w_l before the bias."""
     h = np.asarray(X, np.float64)
-    rnd = {"bf16": round_bf16, "fp16": round_fp16_sat}.get(precision)
+    rnd = {"bf16": round_bf16, "bf16_plain": round_bf16, "fp16": round_fp16_sat}.get(precision)
     if rnd is not None:
         h = rnd(h)
     cache = []
     for i, (W, b) in enumerate(weights):
         bq = np.asarray(b, np.float64)
+        W = np.asarray(W, np.float64)
         if precision == "fp8":
             s, w = fp8[0][i], fp8[1][i]
-            z = (round_e4m3(h * s) @ round_e4m3(np.asarray(W, np.float64) * w).T) / (s * w) + bq
+            z = (round_e4m3(h * s) @ round_e4m3(W * w).T) / (s * w) + bq
+        elif precision == "bf16" and i > 0:
+            h_hi, h_lo = h
+            W_hi, W_lo = split_bf16(W)
+            z = h_hi @ W_hi.T + h_hi @ W_lo.T + h_lo @ W_hi.T + bq
+            h = h_hi + h_lo
         else:
             Wq = rnd(W) if rnd is not None else W
             z = h @ Wq.T + bq
         cache.append((h, z))
         if i < len(weights) - 1:
             h = activation(z, act)
-            if rnd is not None:
+            if precision == "bf16":
+                h = split_bf16(h)
+            elif rnd is not None:
                 h = rnd(h)
         else:
             h = z
@@ -382,7 +403,7 @@ def query(obj: OracleObject, rays: np.ndarray, precision: str = "f64", seg: Segm
     seg = ray_segments(obj, rays) if seg is None else seg
     n = seg.k.size
     live = seg.k > 0
-    tables = round_fp16(obj.tables) if precision in ("bf16", "fp16", "fp8") else obj.tables
+    tables = round_fp16(obj.tables) if precision in ("bf16", "bf16_plain", "fp16", "fp8") else obj.tables
     fp8 = fp8_scales(float(np.max(np.abs(tables))), obj.weights) if precision == "fp8" else None
     out = Hits(np.zeros(n, bool), np.full(n, np.inf), np.zeros((n, 3)), np.full(n, -1, np.int32),
                np.zeros((n, 3)), np.full((n, cfg.n_out), np.nan), live)

@@ -43,7 +43,7 @@ def _net():
     #   b0 = 2^-12 (bias, FP32, not rounded)
     #   z0 = x W0 + b0         FP16: 1 + 2^-9 + 2^-12 -> activation rounds to 1 + 2^-9
     #                          BF16: 1 + 2^-12        -> 1
-    #   out = 2 h              FP16: 2 + 2^-8            BF16: 2
+    #   out = 2 h              FP16: 2 + 2^-8            BF16 (single rounding): 2
     return [(np.array([[1.0 + 2**-9]]), np.array([2**-12])), (np.array([[2.0]]), np.array([0.0]))]
 
 
@@ -51,7 +51,9 @@ def test_fp16_network_rounds_inputs_weights_and_activations():
     X = np.array([[1.0 + 2**-12]])
     w = _net()
     assert O.mlp_forward(X, w, 0, "fp16")[0, 0] == 2.0 + 2**-8
-    assert O.mlp_forward(X, w, 0, "bf16")[0, 0] == 2.0
+    assert O.mlp_forward(X, w, 0, "bf16_plain")[0, 0] == 2.0
+    # two-term BF16 after the first layer: the activation 1 + 2^-12 survives as hi 1, lo 2^-12
+    assert O.mlp_forward(X, w, 0, "bf16")[0, 0] == 2.0 + 2**-11
     exact = 2.0 * ((1.0 + 2**-12) * (1.0 + 2**-9) + 2**-12)
     assert O.mlp_forward(X, w, 0, "f64")[0, 0] == exact
 
