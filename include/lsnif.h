@@ -276,7 +276,10 @@ LSNIF_API int lsnif_query_rays_host(lsnif_ctx *ctx, const lsnif_rays *rays, lsni
  * an integration convenience of this library.
  *
  * Runs the BF16 fused query (precision LSNIF_BF16_FUSED) on DEVICE ray and
- * hit buffers like lsnif_query_rays, but its scratch lives in one static
+ * hit buffers like lsnif_query_rays -- the same kernels, with the context's
+ * traversal and grouping choices (lsnif_set_trace_mode, lsnif_set_group_mode,
+ * lsnif_autotune), so the results are those of lsnif_query_rays at
+ * LSNIF_BF16_FUSED bit for bit -- but its scratch lives in one static
  * device array of 32 MiB compiled into the library (every GPU that loads the
  * library holds it until the process exits) and it calls no cudaMalloc,
  * cudaFree or other allocating routine. The first call on a device looks up
@@ -577,7 +580,13 @@ LSNIF_API int lsnif_submit(lsnif_ctx *ctx, const lsnif_rays *rays, lsnif_hits *h
 /* Advance the queue and report a request: OK (done; *st filled if not
  * NULL), PENDING (not done and timeout_us == 0), TIMEOUT (not done within
  * timeout_us microseconds), BAD_HANDLE, or the request's own error. Never
- * blocks longer than timeout_us (plus one admission step). */
+ * blocks longer than timeout_us (plus one admission step). A failed device
+ * check in a request's kernels (for example a ray naming an unknown object
+ * handle) is reported as DEVICE_CHECK on that request's ticket only: each of
+ * the context's serving streams has its own device error word, copied to
+ * host memory behind the request's kernels, so no read blocks and other
+ * requests are not charged. The queue advances only inside lsnif_submit and
+ * lsnif_poll. */
 LSNIF_API int lsnif_poll(lsnif_ctx *ctx, uint64_t ticket, int64_t timeout_us, lsnif_req_stats *st);
 
 /* Number of submitted requests not yet reported done by lsnif_poll. */
@@ -601,6 +610,20 @@ LSNIF_API int lsnif_set_profiling(lsnif_ctx *ctx, int on);
 /* Stage times and counts of the last query run with profiling on
  * (synchronises the stream it ran on). */
 LSNIF_API int lsnif_last_profile(lsnif_ctx *ctx, lsnif_profile *out);
+
+/* Measurement: the request ceiling of the hash-grid gather on this GPU. The
+ * paper has no counterpart; it supplies the roof against which the fused
+ * query's corner loads are reported. Runs `loads` (0: about 1.6e9)
+ * independent 8-byte loads at uniformly random positions of object obj's
+ * FP16 table copy (L x 2^log2_T x F x 2 bytes, the tables the fused query
+ * gathers from), 16 in flight per thread and every SM fully occupied, after
+ * an untimed warm-up launch, and writes the loads completed per second to
+ * *requests_per_s (each load touches one 32-byte sector). Tables that fit
+ * L2 (129 MB) give L2's random-request rate; larger ones HBM's. Timed with
+ * CUDA events on `stream`; returns when done. Allocates 4 bytes for the
+ * duration of the call. Errors: INVALID_ARG, BAD_HANDLE, UNSUPPORTED (a mesh
+ * object, or a table of 2^32 or more 8-byte words), OVER_BUDGET, CUDA. */
+LSNIF_API int lsnif_gather_rate(lsnif_ctx *ctx, lsnif_obj obj, int64_t loads, void *stream, double *requests_per_s);
 
 /* Device memory the context currently holds (objects + scratch). */
 LSNIF_API size_t lsnif_device_bytes(lsnif_ctx *ctx);

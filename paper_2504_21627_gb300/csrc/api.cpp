@@ -713,12 +713,15 @@ extern "C" int lsnif_load_object(lsnif_ctx *ctx, const lsnif_object_desc *desc, 
   d.umma_bytes = (d.umma_bytes + 15) & ~15u;
   OALLOC(umma, const uint8_t *, d.umma_bytes, "tensor-core weights");
   OALLOC(umma_h, const uint8_t *, d.umma_bytes, "FP16 tensor-core weights");
+  d.umma_lo_bytes = (uint32_t)(((wbytes - (size_t)cfg.width * d.n_in * 2) + 15) & ~size_t(15));
+  OALLOC(umma_lo, const uint8_t *, d.umma_lo_bytes, "BF16 residual weights");
   OALLOC(plain_out, const float *, 4 * ((size_t)d.n_out_pad * cfg.width + d.n_out_pad), "padded output layer");
   cudaError_t e = cudaMemcpy((void *)d.occ, occ.data(), 4 * occ.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy((void *)d.dist, dist.data(), dist.size(), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) { free_object(ctx, o); return cuda_fail(e, "upload occupancy"); }
   cudaMemset((void *)d.umma, 0, d.umma_bytes);
   cudaMemset((void *)d.umma_h, 0, d.umma_bytes);
+  cudaMemset((void *)d.umma_lo, 0, d.umma_lo_bytes);
   if ((rc = upload_params(ctx, o, tab_src, mlp_src)) != LSNIF_OK) { free_object(ctx, o); return rc; }
   // kept mesh for training labels
   if (!desc->blob && desc->keep_mesh) {

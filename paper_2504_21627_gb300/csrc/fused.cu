@@ -35,6 +35,7 @@
 // Every mbarrier wait is bounded by a clock limit; on expiry the kernel flags
 // an abort, every role stops, the device error word is set, in-flight MMAs
 // are waited for (again bounded), TMEM is freed and the kernel returns.
+#include <algorithm>
 #include <climits>
 #include <cstdio>
 
@@ -63,6 +64,22 @@ __device__ __forceinline__ void mma_f16(uint32_t tmem, uint64_t a, uint64_t b, u
       "l"(a), "l"(b), "r"(idesc), "r"(acc)
       : "memory");
 }
+
+// The same with the A operand read from tensor memory (a_tmem: lane 0 and
+// the first column of a 128-lane x K/2-column tile, row i in lane i, two
+// 16-bit values per column).
+__device__ __forceinline__ void mma_f16_ts(uint32_t tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(tmem),
+      "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+// TMEM columns a CTA allocates: two W-column accumulators and a W-column
+// activation tile (W/2 columns of hi words, W/2 of lo words), rounded up to
+// the power of two the allocator takes
+__host__ __device__ constexpr int tmem_cols(int W) { return 3 * W <= 256 ? 256 : 512; }
 
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
   __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
@@ -98,6 +115,7 @@ struct FusedArgs {
   float *Z;
   int64_t xrows;
   uint32_t smem_blob;  // bytes of the weight blob
+  uint32_t smem_lo;    // bytes of the BF16 residual weights of the later layers (0 with FP16 operands)
   int nbuf;            // ring buffers (2..kNBufMax)
   int list_chunks;     // work-list capacity in chunks (H_max / 2)
   int fp16;            // operand type: 0 BF16 (weights from umma), 1 FP16 (weights from umma_h);
@@ -107,20 +125,23 @@ struct FusedArgs {
 // Shared-memory layout (byte offsets from a 1024-aligned base), the same on
 // host (sizing) and device (carving).
 struct Layout {
-  uint32_t blob, ring, ring_stride, act, ray, t0, t1, list, wsum, info, bars, tmem, misc, res, total;
+  uint32_t blob, blob_lo, ring, ring_stride, ray, t0, t1, list, wsum, info, bars, tmem, misc, res, total;
 };
 
 // mbarriers: full[kNBufMax], empty[kNBufMax], tile_ready[2], acc_full[2],
 // acc_empty[2], layer_done, fin[2]
 constexpr int kNumBars = 2 * kNBufMax + 2 + 2 + 2 + 1 + 2;
 
-__host__ __device__ inline Layout make_layout(uint32_t blob_bytes, int F, int W, int nbuf, int list_chunks) {
+// lo_bytes > 0 (BF16 operands): the later layers' residual weights, the lo
+// terms of their two-term products.
+__host__ __device__ inline Layout make_layout(uint32_t blob_bytes, uint32_t lo_bytes, int F, int W, int nbuf,
+                                              int list_chunks) {
   Layout o{};
   uint32_t off = 0;
   o.ring_stride = (uint32_t)kTileM * (uint32_t)(2 * 16 * F) * 2u;  // one chunk for L <= 16
   o.blob = lay_take(off, blob_bytes, 1024);
+  o.blob_lo = lay_take(off, lo_bytes, 1024);
   o.ring = lay_take(off, (uint32_t)nbuf * o.ring_stride, 1024);
-  o.act = lay_take(off, (uint32_t)kTileM * W * 2u, 1024);
   o.ray = lay_take(off, 2 * kTileM * 4, 16);
   o.t0 = lay_take(off, 2 * kTileM * 4, 16);
   o.t1 = lay_take(off, 2 * kTileM * 4, 16);
@@ -144,7 +165,7 @@ __device__ __noinline__ void mma_role(const FusedArgs *ap, uint8_t *base, uint32
   const int lane = threadIdx.x & 31;
   const DevObject *objs = a.q.objs;
   const int nbuf = a.nbuf;
-  const Layout lay = make_layout(a.smem_blob, F, W, nbuf, a.list_chunks);
+  const Layout lay = make_layout(a.smem_blob, a.smem_lo, F, W, nbuf, a.list_chunks);
   uint8_t *s_blob = base + lay.blob;
   uint8_t *s_ring = base + lay.ring;
   TileInfo *s_info = reinterpret_cast<TileInfo *>(base + lay.info);
@@ -212,9 +233,9 @@ __device__ __noinline__ void epilogue_role(const FusedArgs *ap, uint8_t *base, u
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const QueryLaunch &q = a.q;
   const DevObject *objs = q.objs;
-  const Layout lay = make_layout(a.smem_blob, F, W, a.nbuf, a.list_chunks);
+  const Layout lay = make_layout(a.smem_blob, a.smem_lo, F, W, a.nbuf, a.list_chunks);
   uint8_t *s_blob = base + lay.blob;
-  uint8_t *s_act = base + lay.act;
+  uint8_t *s_blob_lo = base + lay.blob_lo;
   int32_t *s_ray = reinterpret_cast<int32_t *>(base + lay.ray);
   float *s_t0 = reinterpret_cast<float *>(base + lay.t0);
   float *s_t1 = reinterpret_cast<float *>(base + lay.t1);
@@ -278,6 +299,12 @@ __device__ __noinline__ void epilogue_role(const FusedArgs *ap, uint8_t *base, u
         uint4 *dst = reinterpret_cast<uint4 *>(s_blob);
         const int nvec = (int)(ob.umma_bytes / 16);
         for (int k = etid; k < nvec; k += kEpiThreads) dst[k] = __ldg(src + k);
+        if constexpr (!H16) {
+          const uint4 *src_lo = reinterpret_cast<const uint4 *>(ob.umma_lo);
+          uint4 *dst_lo = reinterpret_cast<uint4 *>(s_blob_lo);
+          const int nlo = (int)(ob.umma_lo_bytes / 16);
+          for (int k = etid; k < nlo; k += kEpiThreads) dst_lo[k] = __ldg(src_lo + k);
+        }
         if (etid < LSNIF_MAX_LEVELS) s_res[etid] = (float)ob.res[etid];
         fence_async_smem();
         su_slot = slot;
@@ -387,40 +414,62 @@ __device__ __noinline__ void epilogue_role(const FusedArgs *ap, uint8_t *base, u
         const int n_hidden = ob.n_hidden, n_out = ob.n_out, n_out_pad = ob.n_out_pad, n_mat = ob.n_mat,
                   act = ob.act;
         const float *bias = reinterpret_cast<const float *>(s_blob + ob.umma_bias_off);
-        uint32_t wl_off = (uint32_t)W * ob.n_in * 2u;  // byte offset of W1 in the blob
+        const uint32_t wl_off0 = (uint32_t)W * ob.n_in * 2u;  // byte offset of W1 in the blob
+        uint32_t wl_off = wl_off0;
         const uint32_t dacc = tmem + (uint32_t)(tb * W);
         const uint32_t trow = dacc + ((uint32_t)(quarter * 32) << 16);
+        const uint32_t act_col = tmem + (uint32_t)(2 * W);  // activation tile (A operand), lane 0
+        const uint32_t tact = act_col + ((uint32_t)(quarter * 32) << 16), tact_lo = tact + (uint32_t)(W / 2);
         for (int layer = 0; layer <= n_hidden; ++layer) {
           const bool out_layer = layer == n_hidden;
           const float *bl = bias + layer * W;
           if (!out_layer) {
-#pragma unroll 1
+            const int N = (layer + 1 < n_hidden) ? W : n_out_pad;
+            const uint32_t idesc = idesc_f16(N, fp16);
+            // The activations go to tensor memory, row r in lane r, two 16-bit
+            // values per 32-bit column (the A operand of tcgen05.mma read from
+            // TMEM): hi at columns [2W, 2W + W/2), lo (two-term BF16) after it.
+#pragma unroll
             for (int c0 = 0; c0 < W; c0 += 16) {
               uint32_t v[16];
               TMEM_LD16(trow + c0, (&v[0]));
               tmem_wait_ld();
+              uint32_t hw[8];
+              if constexpr (H16) {
 #pragma unroll
-              for (int c = 0; c < 16; c += 8) {
-                float h8[8];
+                for (int u = 0; u < 8; ++u)
+                  hw[u] = pack_op(act_fn(__uint_as_float(v[2 * u]) + bl[c0 + 2 * u], act),
+                                  act_fn(__uint_as_float(v[2 * u + 1]) + bl[c0 + 2 * u + 1], act), fp16);
+              } else {
+                // two-term BF16: hi = BF16(h), lo = BF16(h - hi) (the difference is exact in FP32)
+                uint32_t lw[8];
 #pragma unroll
-                for (int u = 0; u < 8; ++u) h8[u] = act_fn(__uint_as_float(v[c + u]) + bl[c0 + c + u], act);
-                const uint4 pk = make_uint4(pack_op(h8[0], h8[1], fp16), pack_op(h8[2], h8[3], fp16),
-                                            pack_op(h8[4], h8[5], fp16), pack_op(h8[6], h8[7], fp16));
-                *reinterpret_cast<uint4 *>(s_act + core_off(r, (c0 + c) / 8, act_sbo)) = pk;
+                for (int u = 0; u < 8; ++u) {
+                  const float x0 = act_fn(__uint_as_float(v[2 * u]) + bl[c0 + 2 * u], act);
+                  const float x1 = act_fn(__uint_as_float(v[2 * u + 1]) + bl[c0 + 2 * u + 1], act);
+                  const __nv_bfloat162 hb = __floats2bfloat162_rn(x0, x1);
+                  const float2 hf = __bfloat1622float2(hb);
+                  hw[u] = *reinterpret_cast<const uint32_t *>(&hb);
+                  lw[u] = pack_bf16(x0 - hf.x, x1 - hf.y);
+                }
+                TMEM_ST8(tact_lo + (uint32_t)(c0 / 2), lw);
               }
+              TMEM_ST8(tact + (uint32_t)(c0 / 2), hw);
             }
-            fence_async_smem();
+            tmem_wait_st();
             tc_before();
             named_sync(2, kEpiThreads);
-            const int N = (layer + 1 < n_hidden) ? W : n_out_pad;
             if (etid == 0) {
               tc_after();
-              const uint32_t a0 = su32(s_act), b0 = su32(s_blob) + wl_off;
-              const uint32_t idesc = idesc_f16(N, fp16);
+              const uint32_t b0 = su32(s_blob) + wl_off, b0l = su32(s_blob_lo) + (wl_off - wl_off0);
               for (int ks = 0; ks < W / 16; ++ks) {
-                const uint64_t ad = umma_desc(a0 + ks * 256, 128, act_sbo);
                 const uint64_t bd = umma_desc(b0 + ks * 256, 128, act_sbo);
-                mma_f16(dacc, ad, bd, idesc, ks > 0 ? 1u : 0u);
+                mma_f16_ts(dacc, act_col + (uint32_t)(ks * 8), bd, idesc, ks > 0 ? 1u : 0u);
+                if constexpr (!H16) {
+                  // the lo terms: hi_a . lo_w + lo_a . hi_w (lo_a . lo_w is left out)
+                  mma_f16_ts(dacc, act_col + (uint32_t)(ks * 8), umma_desc(b0l + ks * 256, 128, act_sbo), idesc, 1u);
+                  mma_f16_ts(dacc, act_col + (uint32_t)(W / 2 + ks * 8), bd, idesc, 1u);
+                }
               }
               mma_commit(su32(b_layer));
               mbar_wait(su32(b_layer), (uint32_t)(layer_ctr & 1), abort_flag);
@@ -477,7 +526,7 @@ template <int F, int W, bool XROWS, int NG, int NLB, int GS, bool H16>
 __global__ void __launch_bounds__((NG + 1 + kEpiWarps) * 32, 1) fused_kernel(const __grid_constant__ FusedArgs a) {
   constexpr int kGatherThreads = NG * 32;
   constexpr int kMmaWarp = NG;
-  constexpr int kTmemCols = 2 * W;  // two accumulators
+  constexpr int kTmemCols = tmem_cols(W);  // two accumulators, the activation tile (hi and lo)
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const QueryLaunch &q = a.q;
@@ -485,7 +534,7 @@ __global__ void __launch_bounds__((NG + 1 + kEpiWarps) * 32, 1) fused_kernel(con
   const int nbuf = a.nbuf;
 
   uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  const Layout lay = make_layout(a.smem_blob, F, W, nbuf, a.list_chunks);
+  const Layout lay = make_layout(a.smem_blob, a.smem_lo, F, W, nbuf, a.list_chunks);
   uint8_t *s_ring = base + lay.ring;
   int32_t *s_ray = reinterpret_cast<int32_t *>(base + lay.ray);
   uint16_t *s_list = reinterpret_cast<uint16_t *>(base + lay.list);
@@ -700,15 +749,28 @@ bool fused_supported(const DevObject &h) {
 }
 
 static uint32_t blob_bytes(const DevObject &h) { return (h.umma_bytes + 15u) & ~15u; }
+static uint32_t lo_bytes(const DevObject &h, bool fp16) { return fp16 ? 0u : (h.umma_lo_bytes + 15u) & ~15u; }
 
 // with the smallest ring (2 buffers); launches use up to kNBufMax that fit
-size_t fused_smem_bytes(const DevObject &h, int H_max) {
-  return make_layout(blob_bytes(h), h.F, h.width, 2, std::max(H_max, h.H) / 2).total;
+size_t fused_smem_bytes(const DevObject &h, int H_max, bool fp16) {
+  return make_layout(blob_bytes(h), lo_bytes(h, fp16), h.F, h.width, 2, std::max(H_max, h.H) / 2).total;
 }
 
-static int pick_nbuf(const DevObject &h, int list_chunks) {
+// Shared memory and L1 share one array per SM. A CTA that needs more than
+// the 196 KB configuration (less the 1 KB the system keeps per CTA) gets the
+// 228 KB one, which leaves L1 28 KB instead of 60 KB; the gather's coarse
+// levels live in L1, and on the torus workload that alone took the fused
+// kernel from 2.79 to 3.93 ms. A ring of 3 buffers ran as fast as 4, one of
+// 2 about 13% slower. So: the largest ring of at least 3 buffers that stays
+// within the 196 KB configuration, else the largest that fits at all.
+constexpr uint32_t kSmemL1Friendly = 195u * 1024u;
+
+static int pick_nbuf(const DevObject &h, int list_chunks, bool fp16) {
+  auto total = [&](int nb) { return make_layout(blob_bytes(h), lo_bytes(h, fp16), h.F, h.width, nb, list_chunks).total; };
+  for (int nb = kNBufMax; nb >= 3; --nb)
+    if (total(nb) <= kSmemL1Friendly) return nb;
   for (int nb = kNBufMax; nb >= 2; --nb)
-    if (make_layout(blob_bytes(h), h.F, h.width, nb, list_chunks).total <= 232448) return nb;
+    if (total(nb) <= 232448) return nb;
   return 0;
 }
 
@@ -724,7 +786,11 @@ static cudaError_t launch_op(const FusedArgs &a, size_t smem, cudaStream_t st) {
   int sms = 0, dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  fused_kernel<F, W, XR, NG, NLB, GS, H16><<<sms, (NG + 1 + kEpiWarps) * 32, smem, st>>>(a);
+  // one persistent CTA per SM, but no more CTAs than the batch can have
+  // tiles: a small request leaves the other SMs to concurrent work
+  const int64_t tiles = XR ? (a.xrows + kTileM - 1) / kTileM : (int64_t)a.q.s.max_tiles;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(sms, tiles));
+  fused_kernel<F, W, XR, NG, NLB, GS, H16><<<grid, (NG + 1 + kEpiWarps) * 32, smem, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -790,10 +856,11 @@ cudaError_t launch_fused(const QueryLaunch &q, const DevObject &h, int variant, 
   a.q = q;
   a.fp16 = fp16 ? 1 : 0;
   a.smem_blob = blob_bytes(h);
+  a.smem_lo = lo_bytes(h, fp16);
   a.list_chunks = std::max(q.H_max, h.H) / 2;
-  a.nbuf = pick_nbuf(h, a.list_chunks);
+  a.nbuf = pick_nbuf(h, a.list_chunks, fp16);
   if (!a.nbuf) return cudaErrorNotSupported;
-  const size_t smem = make_layout(a.smem_blob, h.F, h.width, a.nbuf, a.list_chunks).total;
+  const size_t smem = make_layout(a.smem_blob, a.smem_lo, h.F, h.width, a.nbuf, a.list_chunks).total;
   *launches += 1;
   return dispatch<false>(a, h, variant, smem, q.stream);
 }
@@ -804,10 +871,11 @@ cudaError_t launch_mlp_fused(const DevObject *dobj, const DevObject &h, const fl
   FusedArgs a{};
   a.fp16 = fp16 ? 1 : 0;
   a.smem_blob = blob_bytes(h);
+  a.smem_lo = lo_bytes(h, fp16);
   a.list_chunks = h.H / 2;
-  a.nbuf = pick_nbuf(h, a.list_chunks);
+  a.nbuf = pick_nbuf(h, a.list_chunks, fp16);
   if (!a.nbuf) return cudaErrorNotSupported;
-  const size_t smem = make_layout(a.smem_blob, h.F, h.width, a.nbuf, a.list_chunks).total;
+  const size_t smem = make_layout(a.smem_blob, a.smem_lo, h.F, h.width, a.nbuf, a.list_chunks).total;
   int32_t *meta = nullptr;
   cudaError_t e = cudaMallocAsync(&meta, 16 * sizeof(int32_t), st);
   if (e != cudaSuccess) return e;

@@ -12,6 +12,7 @@
 //     hidden and output layers stay resident.
 // One 16-byte column group of a point holds 16 E4M3 features (16 / F
 // levels).
+#include <algorithm>
 #include <climits>
 #include <cstdio>
 
@@ -686,7 +687,9 @@ static cudaError_t launch8_shape(const Fused8Args &a, size_t smem, cudaStream_t 
   int sms = 0, dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  fused8_kernel<F, W, NG, NL><<<sms, (NG + 1 + kEpiWarps) * 32, smem, st>>>(a);
+  // one persistent CTA per SM, but no more CTAs than the batch can have tiles
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(sms, (int64_t)a.q.s.max_tiles));
+  fused8_kernel<F, W, NG, NL><<<grid, (NG + 1 + kEpiWarps) * 32, smem, st>>>(a);
   return cudaGetLastError();
 }
 

@@ -64,6 +64,11 @@ struct DevObject {
   const uint8_t *umma_h;  // the same blob with FP16 weights (saturated at 65504)
   uint32_t umma_bytes;  // total bytes of the umma blob (each of the two)
   uint32_t umma_bias_off;  // byte offset of the FP32 biases inside it
+  // BF16 residuals W - BF16(W) of the layers after the first, in the layout of
+  // those layers' part of umma (no biases): the BF16 path runs those layers
+  // with two-term operands (hi.hi + hi.lo + lo.hi)
+  const uint8_t *umma_lo;
+  uint32_t umma_lo_bytes;
   const float *plain_out;  // FP32 output layer padded to n_out_pad rows, then its bias
 
   // kept mesh (training labels): per-voxel triangle lists in CSR form
@@ -169,7 +174,9 @@ int fused8_variant_count();
 void fused8_variant_shape(int variant, int *threads, int *levels);
 cudaError_t launch_max_abs_half(const uint16_t *v, int64_t n, uint32_t *out_bits, cudaStream_t st);
 bool fused_supported(const DevObject &host_obj);
-size_t fused_smem_bytes(const DevObject &host_obj, int H_max);  // smallest ring; H_max: query's largest H
+// smallest ring; H_max: the query's largest H; fp16: FP16 operands (the BF16
+// path also holds the two-term residual weights and activations)
+size_t fused_smem_bytes(const DevObject &host_obj, int H_max, bool fp16);
 // fp16: FP16 operands (weights from umma_h) instead of BF16
 cudaError_t launch_fused(const QueryLaunch &q, const DevObject &host_obj, int variant, bool fp16, int *launches);
 int fused_variant_count();

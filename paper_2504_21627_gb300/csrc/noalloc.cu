@@ -6,9 +6,10 @@
 // whole device and stall the frame), a plug-in inside a host engine that owns
 // every allocation, or a service that fixes its memory at start-up. This
 // entry point runs the same traversal, grouping and fused kernels as
-// lsnif_query_rays, but points their scratch (boundary points, ray
-// intervals, grouping and tile tables) at the array below. It calls no
-// cudaMalloc, cudaFree or other allocating routine.
+// lsnif_query_rays at BF16 (with the context's traversal and grouping
+// choices), but points their scratch (boundary points, ray intervals,
+// grouping and tile tables) at the array below. It calls no cudaMalloc,
+// cudaFree or other allocating routine.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -58,6 +59,9 @@ size_t al256(size_t b) { return (b + 255) & ~size_t(255); }
 extern "C" int lsnif_query_rays_noalloc(lsnif_ctx *ctx, const lsnif_rays *r, lsnif_hits *h, void *stream) {
   if (!ctx || !r || !h) return fail(LSNIF_ERR_INVALID_ARG, "lsnif_query_rays_noalloc: NULL argument");
   if (r->n < 0) return fail(LSNIF_ERR_INVALID_ARG, "lsnif_query_rays_noalloc: n < 0");
+  // sizes below are computed in size_t from n; bound n first, as the regular query does
+  if (r->n > ((int64_t)1 << 31) - 1)
+    return fail(LSNIF_ERR_INVALID_ARG, "lsnif_query_rays_noalloc: n = %lld exceeds 2^31-1", (long long)r->n);
   if (r->n == 0) return LSNIF_OK;
   if (!r->ox || !r->oy || !r->oz || !r->dx || !r->dy || !r->dz || !r->tmin || !r->tmax)
     return fail(LSNIF_ERR_INVALID_ARG, "lsnif_query_rays_noalloc: every ray array must be given");
@@ -66,7 +70,7 @@ extern "C" int lsnif_query_rays_noalloc(lsnif_ctx *ctx, const lsnif_rays *r, lsn
   // the objects the rays may name, and the shape the kernels need
   int H = 0, n_slots = std::max(ctx->n_slots_used, 1);
   const Object *rep = nullptr;
-  uint32_t umma_max = 0;
+  uint32_t umma_max = 0, umma_lo_max = 0;
   bool mixed = false;
   bool mesh = false;
   auto add = [&](const Object *o) {
@@ -76,6 +80,7 @@ extern "C" int lsnif_query_rays_noalloc(lsnif_ctx *ctx, const lsnif_rays *r, lsn
     }
     H = std::max(H, o->cfg.H);
     umma_max = std::max(umma_max, o->d.umma_bytes);
+    umma_lo_max = std::max(umma_lo_max, o->d.umma_lo_bytes);
     if (!rep) rep = o;
     else if (rep->d.F != o->d.F || rep->d.width != o->d.width || o->d.L > 16) mixed = true;
   };
@@ -92,7 +97,8 @@ extern "C" int lsnif_query_rays_noalloc(lsnif_ctx *ctx, const lsnif_rays *r, lsn
     return fail(LSNIF_ERR_UNSUPPORTED, "lsnif_query_rays_noalloc: mesh objects are answered by lsnif_query_rays");
   DevObject hobj = rep->d;
   hobj.umma_bytes = umma_max;
-  if (mixed || !fused_supported(hobj) || fused_smem_bytes(hobj, H) > 232448)
+  hobj.umma_lo_bytes = umma_lo_max;
+  if (mixed || !fused_supported(hobj) || fused_smem_bytes(hobj, H, false) > 232448)
     return fail(LSNIF_ERR_UNSUPPORTED, "lsnif_query_rays_noalloc: objects outside the fused BF16 kernel's shapes");
 
   // carve the static scratch; reject what does not fit
@@ -101,7 +107,7 @@ extern "C" int lsnif_query_rays_noalloc(lsnif_ctx *ctx, const lsnif_rays *r, lsn
   const size_t need = al256((size_t)n * H * 12) + al256((size_t)n * 8) + al256((size_t)n) + al256((size_t)n * 4) +
                       al256((size_t)n * 2) +
                       al256((size_t)n * 4) + 3 * al256((size_t)n_slots * kBuckets * 4) +
-                      al256((size_t)max_tiles * 12) + al256(64 * 4);
+                      al256((size_t)max_tiles * 12) + al256(64 * 4) + al256((size_t)(n / kGroupBlock + 2) * 8);
   if (need > kNoAllocBytes)
     return fail(LSNIF_ERR_INVALID_ARG,
                 "lsnif_query_rays_noalloc: %lld rays need %zu bytes of scratch but the static scratch holds %zu "
@@ -128,6 +134,7 @@ extern "C" int lsnif_query_rays_noalloc(lsnif_ctx *ctx, const lsnif_rays *r, lsn
   s.cursor = reinterpret_cast<int32_t *>(take((size_t)n_slots * kBuckets * 4));
   s.tiles = reinterpret_cast<int32_t *>(take((size_t)max_tiles * 12));
   s.meta = reinterpret_cast<int32_t *>(take(64 * 4));
+  s.blk = reinterpret_cast<int32_t *>(take((size_t)(n / kGroupBlock + 2) * 8));
   s.X = nullptr;
   s.max_tiles = max_tiles;
   s.wmax = 0;
@@ -141,6 +148,9 @@ extern "C" int lsnif_query_rays_noalloc(lsnif_ctx *ctx, const lsnif_rays *r, lsn
   q.s = s;
   q.err = ctx->d_err;
   q.stream = (cudaStream_t)stream;
+  q.trace_mode = ctx->trace_mode;
+  q.group_mode = ctx->group_mode == 1 ? (r->obj ? 2 : 1) : 0;
+  q.single_slot = r->obj ? 0 : rep->slot;
   // The bucket counts must start at zero: launch_trace clears them on the
   // stream; the grouping kernel resets the cursors and the tile counter.
   int launches = 0;

@@ -102,7 +102,7 @@ static QueryScratch carve(Workspace *ws, int64_t n, int H, int n_slots, int n_in
 struct Shape {
   int H = 0, n_in = 0, wmax = 0, n_slots = 0;
   const Object *rep = nullptr;   // representative object (fused: F/width)
-  uint32_t umma_max = 0;
+  uint32_t umma_max = 0, umma_lo_max = 0;
   bool mixed_fused = false;      // objects differ in F or width
   bool has_mesh = false;         // some object of the batch is a mesh object
 };
@@ -117,6 +117,7 @@ static int shape_of(lsnif_ctx *ctx, const lsnif_rays *r, Shape *sh) {
     sh->n_in = std::max(sh->n_in, o->d.n_in);
     sh->wmax = std::max(sh->wmax, std::max(o->d.width, o->d.n_out_pad));
     sh->umma_max = std::max(sh->umma_max, o->d.umma_bytes);
+    sh->umma_lo_max = std::max(sh->umma_lo_max, o->d.umma_lo_bytes);
     if (!sh->rep) sh->rep = o;
     else if (sh->rep->d.F != o->d.F || sh->rep->d.width != o->d.width || o->d.L > 16) sh->mixed_fused = true;
   };
@@ -157,7 +158,8 @@ static int ensure_fp8_for(lsnif_ctx *ctx, const lsnif_rays *r, cudaStream_t st) 
 }
 
 int lsnif::run_query(lsnif_ctx *ctx, Workspace *ws, const lsnif_rays *r, lsnif_hits *h, int precision,
-                     cudaStream_t st, bool profile) {
+                     cudaStream_t st, bool profile, int *err) {
+  if (!err) err = ctx->d_err;
   int rc = check_rays(r, h);
   if (rc) return rc;
   if (!valid_precision(precision)) return fail(LSNIF_ERR_INVALID_ARG, "query: unknown precision %d", precision);
@@ -170,7 +172,7 @@ int lsnif::run_query(lsnif_ctx *ctx, Workspace *ws, const lsnif_rays *r, lsnif_h
     q.n_slots = sh.n_slots;
     q.rays = RaysArg{r->ox, r->oy, r->oz, r->dx, r->dy, r->dz, r->tmin, r->tmax, r->obj, r->single_obj, r->n};
     q.hits = HitsArg{h->hit, h->t, h->nx, h->ny, h->nz, h->mat, h->ar, h->ag, h->ab, h->logits};
-    q.err = ctx->d_err;
+    q.err = err;
     q.stream = st;
     int launches = 0;
     cudaError_t e = launch_mesh_query(q, &launches);
@@ -199,7 +201,8 @@ int lsnif::run_query(lsnif_ctx *ctx, Workspace *ws, const lsnif_rays *r, lsnif_h
   }
   if (fused16_precision(precision)) {
     rep.umma_bytes = sh.umma_max;
-    if (sh.mixed_fused || !fused_supported(rep) || fused_smem_bytes(rep, sh.H) > 232448)
+    rep.umma_lo_bytes = sh.umma_lo_max;
+    if (sh.mixed_fused || !fused_supported(rep) || fused_smem_bytes(rep, sh.H, precision == LSNIF_FP16_FUSED) > 232448)
       return fail(LSNIF_ERR_UNSUPPORTED, "query: the fused BF16/FP16 path needs F in {2,4}, width 64/128, L <= 16, "
                                          "one shape for all objects and weights that fit shared memory");
   }
@@ -213,7 +216,7 @@ int lsnif::run_query(lsnif_ctx *ctx, Workspace *ws, const lsnif_rays *r, lsnif_h
   q.hits = HitsArg{h->hit, h->t, h->nx, h->ny, h->nz, h->mat, h->ar, h->ag, h->ab, h->logits};
   q.s = carve(ws, r->n, sh.H, sh.n_slots, n_in);
   q.s.wmax = sh.wmax;
-  q.err = ctx->d_err;
+  q.err = err;
   q.stream = st;
   q.trace_mode = ctx->trace_mode;
   q.group_mode = ctx->group_mode == 1 ? (r->obj ? 2 : 1) : 0;
@@ -485,7 +488,7 @@ extern "C" int lsnif_mlp(lsnif_ctx *ctx, lsnif_obj h, const float *X, int64_t n,
   if (precision == LSNIF_FP32_PLAIN) {
     e = launch_mlp_plain(ctx->d_objs + o->slot, o->d, X, n, Z, (cudaStream_t)stream);
   } else if (fused16_precision(precision)) {
-    if (!fused_supported(o->d) || fused_smem_bytes(o->d, o->d.H) > 232448)
+    if (!fused_supported(o->d) || fused_smem_bytes(o->d, o->d.H, precision == LSNIF_FP16_FUSED) > 232448)
       return fail(LSNIF_ERR_UNSUPPORTED, "lsnif_mlp: shape not covered by the tensor-core kernel");
     e = launch_mlp_fused(ctx->d_objs + o->slot, o->d, X, n, Z, precision == LSNIF_FP16_FUSED, ctx->d_err,
                          (cudaStream_t)stream);

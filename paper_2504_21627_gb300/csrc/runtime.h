@@ -108,8 +108,9 @@ int ensure_fp8(lsnif_ctx *ctx, Object *o, cudaStream_t st);
 size_t workspace_bytes(int64_t n, int H, int n_slots, int n_in);
 int ensure_workspace(lsnif_ctx *ctx, Workspace *ws, int64_t n, int H, int n_slots, int n_in);
 void free_workspace(lsnif_ctx *ctx, Workspace *ws);
+// err: the device error word the kernels report to (NULL: the context's)
 int run_query(lsnif_ctx *ctx, Workspace *ws, const lsnif_rays *rays, lsnif_hits *hits, int precision,
-              cudaStream_t st, bool profile);
+              cudaStream_t st, bool profile, int *err = nullptr);
 int query_shape(lsnif_ctx *ctx, const lsnif_rays *rays, int precision, int *H, int *n_in);
 void clear_graphs(lsnif_ctx *ctx);
 

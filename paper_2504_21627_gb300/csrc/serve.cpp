@@ -3,7 +3,10 @@
 // scratch fits the context's memory budget; it is then launched on that
 // stream, so requests admitted later overlap on the device with those
 // already running. Completion is observed through CUDA events; lsnif_poll
-// never blocks past its timeout.
+// never blocks past its timeout. Each stream has its own device error word:
+// a failed device-side check (an unknown object handle, a bounded wait that
+// gave up) is copied to page-locked host memory behind the request's kernels
+// and charged to that request alone, without a blocking read.
 #include <cuda_runtime.h>
 
 #include <chrono>
@@ -38,6 +41,8 @@ struct StreamSlot {
   cudaStream_t s = nullptr;
   Workspace ws;
   Request *cur = nullptr;
+  int *d_err = nullptr;           // this stream's device error word (kept at 0 between requests)
+  volatile int *h_err = nullptr;  // page-locked copy of it, written behind each request's kernels
 };
 
 struct Server {
@@ -60,6 +65,8 @@ void server_shutdown(lsnif_ctx *ctx) {
       cudaStreamDestroy(sl.s);
     }
     free_workspace(ctx, &sl.ws);
+    if (sl.d_err) dev_free(ctx, sl.d_err);
+    if (sl.h_err) cudaFreeHost((void *)sl.h_err);
   }
   for (auto &kv : sv->all) {
     if (kv.second->ev_ready) cudaEventDestroy(kv.second->ev_ready);
@@ -75,11 +82,26 @@ static int server_get(lsnif_ctx *ctx, Server **out) {
   if (!ctx->server) {
     Server *sv = new Server();
     for (auto &sl : sv->slots) {
+      void *d = nullptr, *h = nullptr;
+      int rc = LSNIF_OK;
       if (cudaStreamCreateWithFlags(&sl.s, cudaStreamNonBlocking) != cudaSuccess) {
         cudaGetLastError();
+        rc = fail(LSNIF_ERR_CUDA, "serving: cannot create streams");
+      } else if ((rc = dev_alloc(ctx, sizeof(int), &d, "serving error word")) == LSNIF_OK) {
+        sl.d_err = static_cast<int *>(d);
+        if (cudaMemset(sl.d_err, 0, sizeof(int)) != cudaSuccess ||
+            cudaHostAlloc(&h, sizeof(int), cudaHostAllocDefault) != cudaSuccess) {
+          cudaGetLastError();
+          rc = fail(LSNIF_ERR_CUDA, "serving: cannot set up the error words");
+        } else {
+          sl.h_err = static_cast<volatile int *>(h);
+          *sl.h_err = 0;
+        }
+      }
+      if (rc != LSNIF_OK) {
         ctx->server = sv;
         server_shutdown(ctx);
-        return fail(LSNIF_ERR_CUDA, "serving: cannot create streams");
+        return rc;
       }
     }
     ctx->server = sv;
@@ -101,11 +123,12 @@ static void advance(lsnif_ctx *ctx, Server *sv) {
       r->rc = fail(LSNIF_ERR_CUDA, "serving: request %llu failed on the device", (unsigned long long)r->ticket);
     } else {
       cudaEventElapsedTime(&r->gpu_ms, r->ev_start, r->ev_done);
-      int h = 0;
-      cudaMemcpy(&h, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+      // the stream's error word, copied behind the request's kernels (ev_done follows the copy)
+      const int h = *sl.h_err;
       if (h) {
-        cudaMemset(ctx->d_err, 0, sizeof(int));
-        r->rc = fail(LSNIF_ERR_DEVICE_CHECK, "serving: a kernel reported a failed check (0x%x)", h);
+        *sl.h_err = 0;
+        r->rc = fail(LSNIF_ERR_DEVICE_CHECK, "serving: request %llu: a kernel reported a failed check (0x%x)",
+                     (unsigned long long)r->ticket, h);
       }
     }
     r->state = kDone;
@@ -155,7 +178,13 @@ static void advance(lsnif_ctx *ctx, Server *sv) {
     if (rc == LSNIF_OK) {
       cudaStreamWaitEvent(sl.s, r->ev_ready, 0);   // after the caller's writes to the buffers
       cudaEventRecord(r->ev_start, sl.s);
-      rc = run_query(ctx, &sl.ws, &r->rays, &r->hits, r->precision, sl.s, false);
+      rc = run_query(ctx, &sl.ws, &r->rays, &r->hits, r->precision, sl.s, false, sl.d_err);
+      if (rc == LSNIF_OK) {
+        // hand the error word to the host and clear it for the stream's next request
+        cudaError_t e = cudaMemcpyAsync((void *)sl.h_err, sl.d_err, sizeof(int), cudaMemcpyDeviceToHost, sl.s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(sl.d_err, 0, sizeof(int), sl.s);
+        if (e != cudaSuccess) rc = cuda_fail(e, "serving: error word");
+      }
       cudaEventRecord(r->ev_done, sl.s);
     }
     if (rc != LSNIF_OK) {

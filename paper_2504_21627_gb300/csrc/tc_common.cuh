@@ -90,6 +90,15 @@ __device__ __forceinline__ void named_sync(int id, int count) {
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+// 8 consecutive 32-bit TMEM columns of the warp's 32 lanes from registers
+// (thread i writes lane i of the warp's lane quarter)
+#define TMEM_ST8(taddr, r)                                                                                   \
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr),    \
+               "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])  \
+               : "memory")
+
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
 // byte offset of the 16-byte row piece (row r, core K-group kg of 16 bytes)
 // in a tile of 8-row core matrices with row-group stride sbo
 __device__ __forceinline__ uint32_t core_off(int r, int kg, uint32_t sbo) {

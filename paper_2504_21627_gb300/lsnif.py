@@ -163,6 +163,7 @@ SIGNATURES = {
     "lsnif_pending": (_I64, [_P]),
     "lsnif_set_profiling": (_I, [_P, _I]),
     "lsnif_last_profile": (_I, [_P, C.POINTER(Profile)]),
+    "lsnif_gather_rate": (_I, [_P, _U32, _I64, _P, C.POINTER(C.c_double)]),
     "lsnif_device_bytes": (_SZ, [_P]),
     "lsnif_debug_fail_alloc_after": (_I, [_P, _I64]),
 }
@@ -641,6 +642,13 @@ class Context:
         p = Profile()
         _check(self.lib.lsnif_last_profile(self.h, C.byref(p)))
         return p
+
+    def gather_rate(self, obj: int, loads: int = 0, stream=None) -> float:
+        """Random 8-byte loads per second over the object's FP16 tables (the
+        gather's request ceiling; see lsnif_gather_rate)."""
+        r = C.c_double()
+        _check(self.lib.lsnif_gather_rate(self.h, obj, loads, _stream(stream), C.byref(r)))
+        return r.value
 
     def check(self, stream=None):
         _check(self.lib.lsnif_check(self.h, _stream(stream)))

@@ -271,6 +271,40 @@ def test_query_fp32_torus_sample(ctx, torus):
     _query_compare(ctx, torus, rays, lsnif.FP32_PLAIN, fp32_tol(torus["cfg"]))
 
 
+@pytest.mark.parametrize("which", ["sphere", "torus"])
+def test_fp32_query_on_its_own_points_within_1e4_per_element(ctx, which, request):
+    """The whole FP32 query at the 1e-4 relative bound, element by element:
+    the kernel's logits against the oracle's FP64 encoding and network
+    evaluated on the kernel's own FP32 boundary points (lsnif_trace), so
+    what is tested is the encoding and network arithmetic, not the rounding
+    of the points (which the end-to-end tests above bound separately). An
+    element is held to 1e-4 of its own magnitude when that magnitude is at
+    least 1% of its output's largest; smaller elements to 1e-4 of that 1%."""
+    o = request.getfixturevalue(which)
+    if which == "sphere":
+        rays = I.rays_sphere_to_box(4096, 3.0, o["orc"].bmin, o["orc"].bmax, seed=33)
+    else:
+        g = np.random.default_rng(9)
+        cam = np.ascontiguousarray(I.rays_pinhole(I.seeded_camera(2))[:, g.choice(2048 * 2048, 3000, replace=False)])
+        rays = np.concatenate([cam, I.rays_sphere_to_box(1500, 3.0, o["orc"].bmin, o["orc"].bmax, seed=34)], axis=1)
+    rays = np.ascontiguousarray(rays)
+    out = ctx.query_rays(_cuda(rays), obj=o["h"], precision=lsnif.FP32_PLAIN, logits=True)
+    k, t01, pts, vox = ctx.trace(_cuda(rays), o["h"])
+    ctx.check()
+    k, t01, pts, vox = (x.cpu().numpy() for x in (k, t01, pts, vox))
+    live = k > 0
+    assert live.sum() > 1000
+    seg = O.Segments(k[live], t01[live].astype(np.float64), pts[live].astype(np.float64), vox[live],
+                     np.zeros(int(live.sum()), bool))
+    want = O.mlp_forward(O.features(o["orc"], seg), o["orc"].weights, o["cfg"].activation)
+    got = out.logits.cpu().numpy()[live].astype(np.float64)
+    floor = 1e-2 * np.abs(want).max(axis=0, keepdims=True)
+    rel = np.abs(got - want) / np.maximum(np.abs(want), floor)
+    print(f"{which}: FP32 logits on the kernel's points, worst relative error {rel.max():.2e} "
+          f"(median {np.median(rel):.2e}) over {live.sum()} rays x {want.shape[1]} outputs")
+    assert rel.max() <= 1e-4, rel.max()
+
+
 def test_query_bf16_torus_sample(ctx, torus):
     cam = I.seeded_camera(2)
     g = np.random.default_rng(4)

@@ -138,3 +138,41 @@ def test_admission_respects_the_memory_budget():
         ref = free.query_rays(small, obj=free.load_object(mesh, cfg), precision=lsnif.BF16_FUSED)
         for o in outs:
             assert torch.equal(o.t, ref.t)
+
+
+def test_a_failed_request_is_charged_to_its_own_ticket():
+    """One request in a mix names an object handle that was never loaded (a
+    failure made on the host and caught by the kernels' own check, with no
+    fault): it alone gets LSNIF_ERR_DEVICE_CHECK, and every other request
+    still equals its result alone."""
+    with lsnif.Context(0) as ctx:
+        objs = _objects(ctx)
+        reqs = _requests(objs, seed=7, n_req=12)
+        alone = [ctx.query_rays(r, obj=o, precision=lsnif.BF16_FUSED) for o, r in reqs]
+        torch.cuda.synchronize()
+        bad_at = 5
+        unknown = max(objs) + 977
+        outs, tickets = [], []
+        for i, (o, r) in enumerate(reqs):
+            res = ctx._alloc_hits(r.shape[1], 0, False)
+            outs.append(res)
+            if i == bad_at:
+                ids = torch.full((r.shape[1],), unknown, dtype=torch.int32, device="cuda")
+                ids[::2] = o
+                tickets.append(ctx.submit(r, res, obj_per_ray=ids, precision=lsnif.BF16_FUSED))
+            else:
+                tickets.append(ctx.submit(r, res, obj=o, precision=lsnif.BF16_FUSED))
+        for i, t in enumerate(tickets):
+            if i == bad_at:
+                with pytest.raises(lsnif.LsnifError) as e:
+                    ctx.poll(t, timeout_us=20_000_000)
+                assert e.value.code == -8, e.value
+            else:
+                assert ctx.poll(t, timeout_us=20_000_000) is not None
+                for f in ("hit", "t", "mat", "normal", "albedo"):
+                    assert torch.equal(getattr(alone[i], f), getattr(outs[i], f)), (i, f)
+        assert ctx.pending() == 0
+        # the context stays usable and the error was not left for later calls
+        again = ctx.query_rays(reqs[0][1], obj=reqs[0][0], precision=lsnif.BF16_FUSED)
+        ctx.check()
+        assert torch.equal(again.t, alone[0].t)
