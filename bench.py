@@ -133,8 +133,9 @@ class ClockSampler:
 _ORC = {}
 
 
-def oracle_rate(cfg, mesh, params, rays, n_sample: int, seed: int = 0):
-    """The FP64 oracle, as it stands, on a seeded sample of the workload's rays."""
+def oracle_rate(cfg, mesh, params, rays, n_sample: int, seed: int = 0, keep: bool = False):
+    """The FP64 oracle, as it stands, on a seeded sample of the workload's rays.
+    keep: also return the sample, the oracle's results and the box diagonal."""
     from oracle import oracle as O
     if "obj" not in _ORC:
         _ORC["obj"] = O.build_object(mesh, cfg, params)
@@ -143,10 +144,97 @@ def oracle_rate(cfg, mesh, params, rays, n_sample: int, seed: int = 0):
     idx = np.sort(g.choice(rays.shape[1], n_sample, replace=False))
     sub = np.ascontiguousarray(rays[:, idx])
     t0 = time.perf_counter()
-    O.query(orc, sub)
+    ref, seg = O.query(orc, sub)
     dt = time.perf_counter() - t0
     cores = O.threads()
+    if keep:
+        diag = float(np.linalg.norm(orc.bmax.astype(np.float64) - orc.bmin))
+        return n_sample / dt / 1e6, cores, dt, (sub, ref, seg, diag)
     return n_sample / dt / 1e6, cores, dt
+
+
+# the query's acceptance bounds for the half-precision paths (against the FP64
+# oracle): visibility mismatch, hit distance (of the box diagonal, 99th
+# percentile of the rays both call a hit), material agreement
+BOUNDS = {"visibility_mismatch_max": 1e-3, "hit_t_p99_max": 1e-3, "material_min": 0.999}
+
+
+def precision_errors(ctx, obj, sample, precisions):
+    """Each precision's results on the oracle's sample rays against the
+    oracle's FP64 results (near-face rays left out), and whether the bounds
+    hold."""
+    import torch
+    sub, ref, seg, diag = sample
+    rays = torch.from_numpy(sub).cuda()
+    ok = ~seg.near
+    out = {}
+    for name, prec in precisions:
+        q = ctx.query_rays(rays, obj=obj, precision=prec)
+        ctx.check()
+        hit = q.hit.cpu().numpy().astype(bool)
+        t = q.t.cpu().numpy().astype(np.float64)
+        mat = q.mat.cpu().numpy()
+        both = ok & hit & ref.hit
+        dt = np.abs(t[both] - ref.t[both]) / diag
+        e = {"visibility_mismatch": float((hit[ok] != ref.hit[ok]).mean()),
+             "hit_t_p50": float(np.median(dt)) if both.any() else None,
+             "hit_t_p99": float(np.quantile(dt, 0.99)) if both.any() else None,
+             "material": float((mat[both] == ref.mat[both]).mean()) if both.any() else None,
+             "rays": int(ok.sum()), "hits": int(both.sum()), "near_face_left_out": int(seg.near.sum())}
+        e["meets_bounds"] = bool(both.any() and e["visibility_mismatch"] <= BOUNDS["visibility_mismatch_max"]
+                                 and e["hit_t_p99"] <= BOUNDS["hit_t_p99_max"]
+                                 and e["material"] >= BOUNDS["material_min"])
+        out[name] = e
+    return out
+
+
+def train_object(ctx, obj, steps: int, batch: int, n_pool: int, seed: int):
+    """Train an object from its seeded initialisation on GPU-generated
+    balanced rays and ray-cast labels (Sec. 5.2): Adam, lr 0.01."""
+    import torch
+    from paper_2504_21627_gb300 import lsnif
+    t0 = time.perf_counter()
+    u = torch.rand((n_pool, lsnif.TRAIN_UNIFORMS), device="cuda", generator=torch.Generator("cuda").manual_seed(seed))
+    pool, _ = ctx.make_training_rays(obj, u, n_outside=n_pool // 2)
+    lab = ctx.label_rays(pool, obj)
+    keep = lab["k"] > 0
+    pool = pool[:, keep].contiguous()
+    lab = {k: v[keep].contiguous() for k, v in lab.items()}
+    gen = torch.Generator("cuda").manual_seed(seed + 1)
+    losses = []
+    for s in range(steps):
+        idx = torch.randint(0, pool.shape[1], (batch,), device="cuda", generator=gen)
+        st = ctx.train_step(pool[:, idx].contiguous(), {k: v[idx].contiguous() for k, v in lab.items()}, obj,
+                            lr=0.01, stats=(s == 0 or s == steps - 1))
+        if st is not None:
+            losses.append(st.total)
+    torch.cuda.synchronize()
+    return {"steps": steps, "batch": batch, "pool_rays": int(pool.shape[1]), "loss_first": losses[0],
+            "loss_last": losses[-1], "seconds": time.perf_counter() - t0}
+
+
+def corner_loads(ctx, obj, rays, cfg, res):
+    """Corner loads the fused kernel's default gather issues for these rays:
+    per gathered point and level one 8-byte load per (y, z) row of the cell
+    (the aligned pair that holds corner x0, and x1 when the cell's x index is
+    even), plus a 4-byte load per row for x1 when the x index is odd and the
+    x weight is not 0. Points shared with the previous segment's exit are
+    copied, not gathered. Counted from the traversal's own points."""
+    import torch
+    k, _, pts, _ = ctx.trace(rays, obj)
+    H = cfg.H
+    slot = torch.arange(H, device=pts.device)[None, :] < 2 * k[:, None].long()
+    shared = torch.zeros_like(slot)
+    shared[:, 2::2] = (pts[:, 2::2, :] == pts[:, 1:-1:2, :]).all(-1)
+    x = pts[slot & ~shared][:, 0]
+    del pts
+    loads = 0
+    for N in res:
+        xs = x * float(N)
+        cx = torch.floor(xs)
+        odd = ((cx.to(torch.int64) & 1) == 1) & (xs != cx)
+        loads += 4 * (x.numel() + int(odd.sum()))
+    return loads, int(x.numel())
 
 
 def oracle_rate_single_thread(cfg, mesh, params, rays, n_sample: int, seed: int = 1):
@@ -208,12 +296,17 @@ def _timed_graph(ctx, torch, rays, handles, precision, steps, warmup, stream, fl
 
 
 def bench_batched(args):
+    print(json.dumps(batched_run(args.steps, args.warmup, 16 << 20)))
+
+
+def batched_run(steps: int, warmup: int, total_rays: int):
     """64 objects (5k..500k triangles, V 64..256, T 2^16..2^20, 4 x 64 BF16
-    network), power-law rays per object, ~16M rays shuffled together, queried
-    by one grouped launch sequence replayed as a CUDA graph."""
+    network), power-law rays per object, about total_rays shuffled together,
+    queried by one grouped launch sequence replayed as a CUDA graph."""
     import torch
     from paper_2504_21627_gb300 import lsnif
-    spec = I.batched_objects()
+    t_setup = time.perf_counter()
+    spec = I.batched_objects(total_rays=total_rays)
     ctx = lsnif.Context(0)
     rays_l, hand_l = [], []
     for i, (mesh, cfg, n) in enumerate(spec):
@@ -234,17 +327,19 @@ def bench_batched(args):
     prof = ctx.last_profile()
     ctx.set_profiling(False)
     ctx.set_graph_mode(True)
-    ms16 = _timed_graph(ctx, torch, rays, handles, lsnif.BF16_FUSED, args.steps, args.warmup, stream, flush)
-    ms32 = _timed_graph(ctx, torch, rays, handles, lsnif.FP32_PLAIN, max(3, args.steps // 2), 3, stream, flush)
-    print(json.dumps({
+    t_setup = time.perf_counter() - t_setup
+    ms16 = _timed_graph(ctx, torch, rays, handles, lsnif.BF16_FUSED, steps, warmup, stream, flush)
+    ms32 = _timed_graph(ctx, torch, rays, handles, lsnif.FP32_PLAIN, max(3, steps // 2), 3, stream, flush)
+    out = {
         "workload": "batched", "metric": "Mrays/s, 64 objects in one grouped launch sequence (CUDA graph)",
-        "objects": len(spec), "rays_per_step": n, "value_bf16": n / (ms16.mean() / 1e3) / 1e6,
+        "objects": len(spec), "rays_per_step": n, "value": n / (ms16.mean() / 1e3) / 1e6, "unit": "Mrays/s",
         "value_fp32": n / (ms32.mean() / 1e3) / 1e6, "ms_bf16": float(ms16.mean()), "ms_fp32": float(ms32.mean()),
         "p50_ms_bf16": float(np.percentile(ms16, 50)), "p99_ms_bf16": float(np.percentile(ms16, 99)),
         "live_frac": prof.n_live / n, "mean_points_per_live_ray": prof.n_points / max(prof.n_live, 1),
         "fused_variant": lsnif.Context.variants()[variant], "device_gb": ctx.device_bytes() / 1e9,
-        "l2": "flushed before every timed step", "graph": True}))
+        "l2": "flushed before every timed step", "graph": True, "setup_s": t_setup}
     ctx.close()
+    return out
 
 
 def _serving_requests(ctx, torch, objs, n_req, seed):
@@ -324,20 +419,26 @@ def _serve(ctx, reqs, precision, rate_rps, seed):
 
 
 def bench_serving(args):
+    print(json.dumps(serving_run(args.requests)))
+
+
+def serving_run(n_requests: int):
     """16 resident objects, requests of uneven size and kind, admission under
     an 8 GB budget; p50/p99 latency at 0.5x and 0.9x of the saturation rate."""
     import torch
     from paper_2504_21627_gb300 import lsnif
+    t_setup = time.perf_counter()
     spec = I.batched_objects()[:16]
     ctx = lsnif.Context(0, budget_bytes=8 << 30)
     objs = []
     for i, (mesh, cfg, _) in enumerate(spec):
         p = I.random_params(cfg, seed=1000 + i, table_range=0.05, bias_range=0.1)
         objs.append((ctx.load_object(mesh, cfg, tables=p.tables, mlp=p.packed_mlp(), keep_mesh=True), mesh))
-    reqs = _serving_requests(ctx, torch, objs, args.requests, seed=11)
+    reqs = _serving_requests(ctx, torch, objs, n_requests, seed=11)
     torch.cuda.synchronize()
     res = {"workload": "serving", "metric": "request latency (submit -> done) and Mrays/s, 16 resident objects",
-           "requests": len(reqs), "rays": int(sum(r[1].shape[1] for r in reqs)), "budget_gb": 8}
+           "requests": len(reqs), "rays": int(sum(r[1].shape[1] for r in reqs)), "budget_gb": 8,
+           "setup_s": time.perf_counter() - t_setup}
     for name, prec in (("bf16", lsnif.BF16_FUSED), ("fp32", lsnif.FP32_PLAIN)):
         _serve(ctx, reqs[:8], prec, None, 0)                      # warm the streams
         lat, thr, wall = _serve(ctx, reqs, prec, None, 1)          # saturation (closed loop)
@@ -348,8 +449,11 @@ def bench_serving(args):
             res[name][f"at_{frac}x"] = {"p50_ms": float(np.percentile(lat, 50)) / 1e3,
                                         "p99_ms": float(np.percentile(lat, 99)) / 1e3, "mrays_s": thr}
     res["device_gb"] = ctx.device_bytes() / 1e9
-    print(json.dumps(res))
+    # the serving path's headline: BF16 at 0.9x of its saturation rate
+    res["p50_ms"] = res["bf16"]["at_0.9x"]["p50_ms"]
+    res["p99_ms"] = res["bf16"]["at_0.9x"]["p99_ms"]
     ctx.close()
+    return res
 
 
 def bench_train(args):
@@ -719,6 +823,12 @@ def main():
     ap.add_argument("--workload", default="torus4m", choices=["torus4m", "batched", "serving", "train", "scene", "stress1", "mesh1", "sweep"],
                     help="torus4m is the headline; the others print their own line")
     ap.add_argument("--requests", type=int, default=200)
+    ap.add_argument("--no-train", action="store_true",
+                    help="time random-init weights (profiling captures: no training kernels before the query)")
+    ap.add_argument("--train-steps", type=int, default=2000)
+    ap.add_argument("--no-extras", action="store_true", help="leave the serving and batched entries out")
+    ap.add_argument("--serving-requests", type=int, default=60)
+    ap.add_argument("--batched-rays", type=int, default=4 << 20)
     ap.add_argument("--scene-width", type=int, default=1920)
     ap.add_argument("--scene-height", type=int, default=1080)
     ap.add_argument("--scene-net", default="stress", choices=["stress", "small"])
@@ -770,7 +880,17 @@ def main():
     cfg, mesh, params, rays_np = workload(args.side)
     n = rays_np.shape[1]
     ctx = lsnif.Context(local)
-    obj = ctx.load_object(mesh, cfg, tables=params.tables, mlp=params.packed_mlp())
+    train_info = None
+    if args.no_train:   # random-init weights of the architecture (profiling captures)
+        obj = ctx.load_object(mesh, cfg, tables=params.tables, mlp=params.packed_mlp())
+    else:
+        # the network trained by the library's own training step from its seeded
+        # initialisation (the query's cost does not depend on the weights; the
+        # precision figures below need a trained network)
+        obj = ctx.load_object(mesh, cfg, keep_mesh=True)
+        train_info = train_object(ctx, obj, steps=args.train_steps, batch=1 << 16, n_pool=1 << 21, seed=5)
+        params = I.Params(ctx.read_params(obj, lsnif.PARAM_TABLES),
+                          I.unpack_mlp(cfg, ctx.read_params(obj, lsnif.PARAM_MLP)))
     rays = torch.from_numpy(rays_np).cuda()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > L2 (129 MB)
     # pick the fused kernel's tile shape on this workload (outside the timed region)
@@ -854,7 +974,15 @@ def main():
     # the committed capture is of the 2048 x 2048 workload
     traffic = recorded_traffic() if args.side == 2048 else None
     launches_per_step = int(prof16[-1].launches)
-    l2_requests = pts * L * 5.0  # ~1.25 16-byte requests per x-pair, 4 pairs per point and level
+    # The tables (32 MB) stay in L2, so the gather's roof is the rate at which
+    # L2 answers small random loads: measured here by the library's own
+    # kernel on this object's tables (untimed), against the corner loads the
+    # fused kernel must issue for these rays; both in 32-byte sectors.
+    gather_rate = ctx.gather_rate(obj)
+    info = ctx.object_info(obj)
+    loads, gathered_points = corner_loads(ctx, obj, rays, cfg, list(info.res[:L]))
+    l2_achieved = loads * 32 / (fused_ms / 1e3) / 1e9
+    l2_peak = gather_rate * 32 / 1e9
 
     line = {
         "metric": METRIC, "value": value, "unit": "Mrays/s", "n_gpus": world, "steps": args.steps,
@@ -878,10 +1006,16 @@ def main():
         "stages_ms_fp32": {"trace": float(np.mean([q.ms_trace for q in prof32])),
                            "group": float(np.mean([q.ms_group for q in prof32])),
                            "gather+mlp": float(np.mean([q.ms_mlp for q in prof32]))},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": traffic, "kernel": "fused gather+MLP+decode (BF16 tcgen05)",
-                     "peak_source": peak_src,
-                     "l2_request_rate_gps": l2_requests / (fused_ms / 1e3) / 1e9,
+        "roofline": {"bound": "l2", "achieved": l2_achieved, "peak": l2_peak, "unit": "GB/s",
+                     "frac": l2_achieved / l2_peak, "l2_frac": l2_achieved / l2_peak, "traffic": traffic,
+                     "kernel": "fused gather+MLP+decode (BF16 tcgen05)",
+                     "peak_source": "measured in this run: lsnif_gather_rate, random 8-byte loads over the "
+                                    "object's FP16 tables (L2-resident), 32 B sectors",
+                     "corner_loads_per_launch": loads, "gathered_points": gathered_points,
+                     "l2_requests_per_s": loads / (fused_ms / 1e3), "l2_peak_requests_per_s": gather_rate,
+                     "hbm": {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                             "peak_source": peak_src,
+                             "bytes": "every corner of every point as if from HBM (the tables are L2-resident)"},
                      # the query's memory ceiling: every corner of every point from HBM, plus
                      # 32 B of ray in and 33 B of results per submitted ray
                      "memory_ceiling_mrays_s": peak * 1e9 / ((alg_bytes - live * 54) / n + 65) / 1e6},
@@ -891,18 +1025,32 @@ def main():
         "clocks": clocks,
         "wall_s": {"bf16_timed": wall16, "fp32_timed": wall32, "fp8_timed": wall8},
     }
+    if train_info is not None:
+        line["config"]["weights"] = f"trained {train_info['steps']} steps on the GPU from the seeded initialisation"
+        line["training"] = train_info
     if rank == 0 and not args.no_cpu_baseline:
-        rate, cores, dt = oracle_rate(cfg, mesh, params, rays_np, args.cpu_sample)
+        rate, cores, dt, sample = oracle_rate(cfg, mesh, params, rays_np, args.cpu_sample, keep=True)
         line["cpu_baseline"] = {"value": rate, "unit": "Mrays/s", "cores": cores, "kind": "oracle",
                                 "sample": f"{args.cpu_sample} seeded rays of the workload ({dt:.1f} s)"}
+        # every path's results on the same sample rays against the oracle's
+        errs = precision_errors(ctx, obj, sample, (("bf16", lsnif.BF16_FUSED), ("fp16", lsnif.FP16_FUSED),
+                                                   ("fp32", lsnif.FP32_PLAIN), ("fp8", lsnif.FP8_FUSED)))
+        line["precision"] = {"against": "FP64 oracle on the cpu_baseline sample, near-face rays left out",
+                             "weights": "trained" if train_info is not None else "random-init",
+                             "bounds": BOUNDS, **errs}
+        line["accepted_precision"] = [k for k in ("bf16", "fp16", "fp8") if errs[k]["meets_bounds"]]
         n1 = max(256, args.cpu_sample // 16)
         rate1, dt1 = oracle_rate_single_thread(cfg, mesh, params, rays_np, n1)
         line["cpu_baseline"]["single_thread"] = {
             "value": rate1, "unit": "Mrays/s", "cores": 1,
             "sample": f"{n1} seeded rays of the workload ({dt1:.1f} s)"}
+    ctx.close()
+    if rank == 0 and not args.no_extras:
+        # the serving loop and the many-object graph launch, compact
+        line["serving"] = serving_run(args.serving_requests)
+        line["batched"] = batched_run(5, 3, args.batched_rays)
     if rank == 0:
         print(json.dumps(line))
-    ctx.close()
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
