@@ -47,9 +47,10 @@ def fused_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic():
-    """DRAM bytes per fused-kernel launch from the committed ncu summary, or
-    None when the kernel sources changed after the capture."""
+def recorded_profile(key: str):
+    """A figure of the committed ncu summary of the fused kernel (DRAM bytes
+    per launch, L2 sectors per gathered point), or None when the kernel
+    sources changed after the capture."""
     if not os.path.exists(PROFILE_MD):
         return None
     txt = open(PROFILE_MD).read()
@@ -61,7 +62,7 @@ def recorded_traffic():
     if vals.get("source_hash") != fused_source_hash():
         return None
     try:
-        return float(vals["dram_bytes_per_launch"])
+        return float(vals[key])
     except (KeyError, ValueError):
         return None
 
@@ -827,6 +828,8 @@ def main():
                     help="time random-init weights (profiling captures: no training kernels before the query)")
     ap.add_argument("--train-steps", type=int, default=2000)
     ap.add_argument("--no-extras", action="store_true", help="leave the serving and batched entries out")
+    ap.add_argument("--profile-step", action="store_true",
+                    help="profiling captures: run one BF16 query step inside cudaProfilerStart/Stop and exit")
     ap.add_argument("--serving-requests", type=int, default=60)
     ap.add_argument("--batched-rays", type=int, default=4 << 20)
     ap.add_argument("--scene-width", type=int, default=1920)
@@ -894,12 +897,31 @@ def main():
     rays = torch.from_numpy(rays_np).cuda()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > L2 (129 MB)
     # pick the fused kernel's tile shape on this workload (outside the timed region)
-    variant = ctx.autotune(rays, obj=obj, reps=3)
+    if args.profile_step and args.variant is not None:
+        variant = args.variant
+    else:
+        variant = ctx.autotune(rays, obj=obj, reps=3)
     if args.variant is not None:   # fixed shape (profiling runs, whose timings differ)
         variant = args.variant
-        ctx.set_variant(variant)
+    ctx.set_variant(variant)
     vshape = lsnif.Context.variants()[variant]
     stream = torch.cuda.current_stream()
+    if args.profile_step:
+        # one BF16 step inside a profiler range (ncu --profile-from-start off):
+        # the kernels of exactly one query, after warm-up, L2 flushed before it
+        out = ctx.query_rays(rays, obj=obj, precision=lsnif.BF16_FUSED)
+        for _ in range(3):
+            ctx.query_rays(rays, obj=obj, precision=lsnif.BF16_FUSED, out=out)
+        flush.zero_()
+        torch.cuda.synchronize()
+        torch.cuda.cudart().cudaProfilerStart()
+        ctx.query_rays(rays, obj=obj, precision=lsnif.BF16_FUSED, out=out)
+        torch.cuda.synchronize()
+        torch.cuda.cudart().cudaProfilerStop()
+        ctx.check()
+        print(json.dumps({"profile_step": "BF16 query", "rays": n, "variant": vshape}))
+        ctx.close()
+        return
 
     def timed(precision, steps, warmup, profile=False):
         out = ctx.query_rays(rays, obj=obj, precision=precision)
@@ -972,16 +994,21 @@ def main():
     achieved = alg_bytes / (fused_ms / 1e3) / 1e9
     peak, peak_src = measured_peaks()
     # the committed capture is of the 2048 x 2048 workload
-    traffic = recorded_traffic() if args.side == 2048 else None
+    traffic = recorded_profile("dram_bytes_per_launch") if args.side == 2048 else None
     launches_per_step = int(prof16[-1].launches)
     # The tables (32 MB) stay in L2, so the gather's roof is the rate at which
-    # L2 answers small random loads: measured here by the library's own
-    # kernel on this object's tables (untimed), against the corner loads the
-    # fused kernel must issue for these rays; both in 32-byte sectors.
+    # L2 answers small random requests: measured here by the library's own
+    # kernel on this object's tables (untimed), in 32-byte sectors. The fused
+    # kernel's L2 sectors per launch: ncu's L2 <- L1 read sectors per gathered
+    # point (committed capture of the same kernel sources) times this run's
+    # gathered points. Its corner loads hit L1 too, so loads issued per second
+    # (also reported) exceed what reaches L2.
     gather_rate = ctx.gather_rate(obj)
     info = ctx.object_info(obj)
     loads, gathered_points = corner_loads(ctx, obj, rays, cfg, list(info.res[:L]))
-    l2_achieved = loads * 32 / (fused_ms / 1e3) / 1e9
+    sectors_per_point = recorded_profile("l2_sectors_per_gathered_point")
+    l2_sectors = sectors_per_point * gathered_points if sectors_per_point else None
+    l2_achieved = l2_sectors * 32 / (fused_ms / 1e3) / 1e9 if l2_sectors else None
     l2_peak = gather_rate * 32 / 1e9
 
     line = {
@@ -1007,12 +1034,14 @@ def main():
                            "group": float(np.mean([q.ms_group for q in prof32])),
                            "gather+mlp": float(np.mean([q.ms_mlp for q in prof32]))},
         "roofline": {"bound": "l2", "achieved": l2_achieved, "peak": l2_peak, "unit": "GB/s",
-                     "frac": l2_achieved / l2_peak, "l2_frac": l2_achieved / l2_peak, "traffic": traffic,
+                     "frac": l2_achieved / l2_peak if l2_achieved else None,
+                     "l2_frac": l2_achieved / l2_peak if l2_achieved else None, "traffic": traffic,
                      "kernel": "fused gather+MLP+decode (BF16 tcgen05)",
                      "peak_source": "measured in this run: lsnif_gather_rate, random 8-byte loads over the "
                                     "object's FP16 tables (L2-resident), 32 B sectors",
-                     "corner_loads_per_launch": loads, "gathered_points": gathered_points,
-                     "l2_requests_per_s": loads / (fused_ms / 1e3), "l2_peak_requests_per_s": gather_rate,
+                     "l2_sectors_per_launch": l2_sectors, "gathered_points": gathered_points,
+                     "l2_peak_requests_per_s": gather_rate, "corner_loads_per_launch": loads,
+                     "corner_loads_per_s": loads / (fused_ms / 1e3),
                      "hbm": {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                              "peak_source": peak_src,
                              "bytes": "every corner of every point as if from HBM (the tables are L2-resident)"},

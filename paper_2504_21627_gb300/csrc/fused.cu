@@ -757,12 +757,12 @@ size_t fused_smem_bytes(const DevObject &h, int H_max, bool fp16) {
 }
 
 // Shared memory and L1 share one array per SM. A CTA that needs more than
-// the 196 KB configuration (less the 1 KB the system keeps per CTA) gets the
-// 228 KB one, which leaves L1 28 KB instead of 60 KB; the gather's coarse
-// levels live in L1, and on the torus workload that alone took the fused
-// kernel from 2.79 to 3.93 ms. A ring of 3 buffers ran as fast as 4, one of
-// 2 about 13% slower. So: the largest ring of at least 3 buffers that stays
-// within the 196 KB configuration, else the largest that fits at all.
+// the 196 KiB configuration (less the 1 KiB the system keeps per CTA) gets
+// the 228 KiB one, which leaves L1 28 KiB instead of 60 KiB; the gather's
+// coarse levels live in L1, and on the torus workload that alone took the
+// fused kernel from 2.79 to 3.93 ms. A ring of 3 buffers ran as fast as 4,
+// one of 2 about 13% slower. So: the largest ring of at least 3 buffers that
+// stays within the 196 KiB configuration, else the largest that fits at all.
 constexpr uint32_t kSmemL1Friendly = 195u * 1024u;
 
 static int pick_nbuf(const DevObject &h, int list_chunks, bool fp16) {
