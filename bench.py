@@ -463,7 +463,8 @@ def bench_train(args):
     objects, from GPU-generated balanced rays and labels."""
     import torch
     from paper_2504_21627_gb300 import lsnif
-    out = {"workload": "train", "metric": "training steps/s at batch 2^18 (forward, loss, backward, Adam)"}
+    out = {"workload": "train", "metric": "training steps/s at batch 2^18 (forward, loss, backward, Adam); "
+                                          "network products on the tensor cores and, for reference, FP32 SIMT"}
     for name, cfg, mesh in (("icosphere", I.cfg_icosphere_small(), I.icosphere(3)),
                             ("torus", I.cfg_torus_4m(), I.noise_torus(seed=2))):
         ctx = lsnif.Context(0)
@@ -484,19 +485,20 @@ def bench_train(args):
             idx = torch.randint(0, pool.shape[1], (B,), device="cuda", generator=gen)
             batches.append((pool[:, idx].contiguous(), {k: v[idx].contiguous() for k, v in lab.items()}))
         first = ctx.train_step(*batches[0], h).total
-        for s in range(3):
-            ctx.train_step(*batches[s % 8], h, stats=False)
-        torch.cuda.synchronize()
+        out[name] = {"data_generation_s": t_data, "pool_rays": int(pool.shape[1]), "loss_first": first}
         steps = max(20, args.steps)
-        t0 = time.perf_counter()
-        for s in range(steps):
-            ctx.train_step(*batches[s % 8], h, stats=False)
-        torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        last = ctx.train_step(*batches[0], h).total
-        out[name] = {"steps_per_s": steps / dt, "ms_per_step": dt / steps * 1e3,
-                     "seconds_for_2000_steps": 2000 * dt / steps, "data_generation_s": t_data,
-                     "pool_rays": int(pool.shape[1]), "loss_first": first, "loss_after": last}
+        for label, products in (("tensor_cores", lsnif.TRAIN_TENSOR_CORES), ("fp32_simt", lsnif.TRAIN_FP32_SIMT)):
+            for s in range(3):
+                ctx.train_step(*batches[s % 8], h, stats=False, products=products)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for s in range(steps):
+                ctx.train_step(*batches[s % 8], h, stats=False, products=products)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            out[name][label] = {"steps_per_s": steps / dt, "ms_per_step": dt / steps * 1e3,
+                                "seconds_for_2000_steps": 2000 * dt / steps}
+        out[name]["loss_after"] = ctx.train_step(*batches[0], h).total
         ctx.close()
     print(json.dumps(out))
 

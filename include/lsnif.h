@@ -45,7 +45,7 @@
 extern "C" {
 #endif
 
-#define LSNIF_API_VERSION 1
+#define LSNIF_API_VERSION 2
 
 #if defined(__GNUC__)
 #define LSNIF_API __attribute__((visibility("default")))
@@ -87,8 +87,11 @@ typedef uint32_t lsnif_obj;         /* object handle; 0 is never a valid handle 
 /* FP16_FUSED: BF16_FUSED's kernel with FP16 network operands instead of
  * BF16 (tcgen05 kind::f16 with both A and B FP16): features as gathered from
  * the FP16 tables, FP16 weights, hidden activations rounded to FP16 (nearest
- * even, saturating at +-65504), FP32 accumulation. Three more significand
- * bits than BF16 at the same cost; same shapes as BF16_FUSED. */
+ * even, saturating at +-65504), FP32 accumulation. Networks whose weights do
+ * not fit shared memory (such as F = 4, L = 16, 4 x 128) run on a second
+ * FP16 kernel that streams the first layer's weights chunk by chunk and the
+ * later layers' layer by layer; its features are interpolated in FP32 from
+ * the FP16 tables and rounded once to FP16. */
 enum lsnif_precision { LSNIF_FP32_PLAIN = 0, LSNIF_BF16_FUSED = 1, LSNIF_FP8_FUSED = 2, LSNIF_FP16_FUSED = 3 };
 
 /* Hidden-layer activation: ReLU, or leaky ReLU with slope 0.01 (Sec. 5.1). */
@@ -538,7 +541,17 @@ typedef struct lsnif_train_opts {
     float beta1, beta2;  /* Adam moments (0.9, 0.999) */
     float eps;           /* Adam epsilon (1e-8) */
     int32_t apply_update;/* 0: only compute the loss and gradients (kept for lsnif_read_params) */
+    int32_t products;    /* the network's dense products: LSNIF_TRAIN_TENSOR_CORES (default) or
+                            LSNIF_TRAIN_FP32_SIMT */
 } lsnif_train_opts;
+
+/* How the training step forms the network's dense products (forward, input
+ * gradients, weight gradients). TENSOR_CORES: tcgen05 kind::f16 with BF16
+ * operands in two-term form (hi = BF16(x), lo = BF16(x - hi); hi.hi + hi.lo
+ * + lo.hi) and FP32 accumulation -- the paper's reduced-precision products
+ * with FP32 gradient accumulation (Sec. 5), at FP32-level accuracy and range.
+ * FP32_SIMT: FP32 fused multiply-adds on the CUDA cores (the reference). */
+enum lsnif_train_products { LSNIF_TRAIN_TENSOR_CORES = 0, LSNIF_TRAIN_FP32_SIMT = 1 };
 
 typedef struct lsnif_train_stats {
     float total, occ, t, normal, albedo, mat; /* batch-mean loss terms (Sec. 5.3) */

@@ -47,6 +47,9 @@ int lsnif::cuda_fail(cudaError_t e, const char *what) {
 }
 
 extern "C" const char *lsnif_last_error(void) { return g_err.c_str(); }
+// format version of serialized objects (lsnif_save_object), independent of the API's
+constexpr uint64_t kBlobVersion = 1;
+
 extern "C" int lsnif_version(void) { return LSNIF_API_VERSION; }
 
 // ---------------------------------------------------------------------------
@@ -577,7 +580,7 @@ extern "C" int lsnif_load_object(lsnif_ctx *ctx, const lsnif_object_desc *desc, 
       return fail(LSNIF_ERR_CORRUPT, "lsnif_load_object: not an LSNIF blob");
     uint64_t ver;
     memcpy(&ver, b + 8, 8);
-    if (ver != LSNIF_API_VERSION) return fail(LSNIF_ERR_CORRUPT, "lsnif_load_object: blob version %llu", (unsigned long long)ver);
+    if (ver != kBlobVersion) return fail(LSNIF_ERR_CORRUPT, "lsnif_load_object: blob version %llu", (unsigned long long)ver);
     uint64_t stored;
     memcpy(&stored, b + n - 8, 8);
     if (fnv1a(b, n - 8) != stored) return fail(LSNIF_ERR_CORRUPT, "lsnif_load_object: checksum mismatch");
@@ -715,6 +718,7 @@ extern "C" int lsnif_load_object(lsnif_ctx *ctx, const lsnif_object_desc *desc, 
   OALLOC(umma_h, const uint8_t *, d.umma_bytes, "FP16 tensor-core weights");
   d.umma_lo_bytes = (uint32_t)(((wbytes - (size_t)cfg.width * d.n_in * 2) + 15) & ~size_t(15));
   OALLOC(umma_lo, const uint8_t *, d.umma_lo_bytes, "BF16 residual weights");
+  OALLOC(w0_16c, const uint8_t *, (size_t)cfg.width * d.n_in * 2, "chunk-major FP16 first layer");
   OALLOC(plain_out, const float *, 4 * ((size_t)d.n_out_pad * cfg.width + d.n_out_pad), "padded output layer");
   cudaError_t e = cudaMemcpy((void *)d.occ, occ.data(), 4 * occ.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy((void *)d.dist, dist.data(), dist.size(), cudaMemcpyHostToDevice);
@@ -821,7 +825,7 @@ extern "C" int lsnif_save_object(lsnif_ctx *ctx, lsnif_obj h, void *buf, size_t 
   const lsnif_config &c = o->cfg;
   uint8_t *b = (uint8_t *)buf;
   memcpy(b, kMagic, 8);
-  uint64_t ver = LSNIF_API_VERSION;
+  uint64_t ver = kBlobVersion;
   memcpy(b + 8, &ver, 8);
   memcpy(b + 16, &c, sizeof c);
   uint8_t *p = b + 16 + sizeof c;

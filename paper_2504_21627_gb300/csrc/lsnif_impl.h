@@ -69,6 +69,10 @@ struct DevObject {
   // with two-term operands (hi.hi + hi.lo + lo.hi)
   const uint8_t *umma_lo;
   uint32_t umma_lo_bytes;
+  // the first layer's FP16 weights chunk-major for the streamed FP16 kernel:
+  // chunk s (network inputs [s CHK, (s+1) CHK), CHK = 2 L F: two points) is a
+  // contiguous W x CHK core-matrix slice, so one bulk copy moves it
+  const uint8_t *w0_16c;
   const float *plain_out;  // FP32 output layer padded to n_out_pad rows, then its bias
 
   // kept mesh (training labels): per-voxel triangle lists in CSR form
@@ -181,6 +185,11 @@ size_t fused_smem_bytes(const DevObject &host_obj, int H_max, bool fp16);
 cudaError_t launch_fused(const QueryLaunch &q, const DevObject &host_obj, int variant, bool fp16, int *launches);
 int fused_variant_count();
 void fused_variant_shape(int variant, int *threads, int *levels);
+// FP16 fused query for networks whose weights do not fit shared memory (the
+// first layer streamed per chunk, later layers per layer; fused16s.cu)
+bool fused16s_supported(const DevObject &host_obj);
+size_t fused16s_smem_bytes(const DevObject &host_obj, int H_max);
+cudaError_t launch_fused16s(const QueryLaunch &q, const DevObject &host_obj, int *launches);
 cudaError_t launch_mlp_fused(const DevObject *dobj, const DevObject &host_obj, const float *X,
                              int64_t n, float *Z, bool fp16, int *err, cudaStream_t st);
 
@@ -209,6 +218,13 @@ cudaError_t launch_label_rays(const DevObject *dobj, const DevObject &h, const R
                               const lsnif_labels &out, cudaStream_t st);
 cudaError_t launch_train_step(const DevObject *dobj, const DevObject &h, const RaysArg &rays,
                               const lsnif_labels &lab, const lsnif_train_opts &opts, int64_t step,
-                              TrainBuffers &tb, int64_t n_params_mlp, cudaStream_t st);
+                              TrainBuffers &tb, int64_t n_params_mlp, int *err, cudaStream_t st);
+// C[M x N] = op(A) . op(B) on the tensor cores (two-term BF16, FP32
+// accumulation), op(A)[m][k] = tA ? A[k lda + m] : A[m lda + k], op(B)[k][n] =
+// tB ? B[n ldb + k] : B[k ldb + n]; mode 0 store, 1 atomic add (k_split > 1
+// allowed), 2 + bias[n] -> C, act -> post, 3 + bias[n], 4 times act'(aux) (train_gemm.cu)
+cudaError_t launch_tc_gemm(cudaStream_t st, int M, int N, int K, const float *A, int lda, int tA, const float *B,
+                           int ldb, int tB, float *C, int ldc, int mode, const float *bias, float *post,
+                           const float *aux, int act, int k_split, int *err);
 
 }  // namespace lsnif

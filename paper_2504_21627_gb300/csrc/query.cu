@@ -938,7 +938,7 @@ cudaError_t launch_tables_to_half(const float *src, uint16_t *dst, int64_t n, cu
 //   ((n/8)*(K/8) + k/8)*128 + (n%8)*16 + (k%8)*2
 // Rows past the real output count are zero. Biases follow as FP32 in both.
 // FP16 weights saturate at +-65504.
-__global__ void build_umma_kernel(DevObject h, uint8_t *dst, uint8_t *dst16, uint8_t *dst_lo) {
+__global__ void build_umma_kernel(DevObject h, uint8_t *dst, uint8_t *dst16, uint8_t *dst_lo, uint8_t *dst_w0c) {
   const float *p = h.mlp32;
   uint32_t off = 0;
   const uint32_t off1 = (uint32_t)h.width * h.n_in * 2;  // where the layers after the first start
@@ -956,6 +956,12 @@ __global__ void build_umma_kernel(DevObject h, uint8_t *dst, uint8_t *dst16, uin
       *reinterpret_cast<__nv_bfloat16 *>(dst + o) = hi;
       *reinterpret_cast<__half *>(dst16 + o) = __float2half_rn(fminf(fmaxf(v, -65504.f), 65504.f));
       if (l > 0) *reinterpret_cast<__nv_bfloat16 *>(dst_lo + (o - off1)) = __float2bfloat16_rn(v - __bfloat162float(hi));
+      if (l == 0) {  // chunk-major copy: chunk s = kk / CHK is one contiguous W x CHK slice
+        const int chk = 2 * h.L * h.F, s = kk / chk, c = kk % chk;
+        const size_t oc = (size_t)s * h.width * chk * 2 + ((size_t)(nn / 8) * (chk / 8) + c / 8) * 128 + (nn % 8) * 16 +
+                          (c % 8) * 2;
+        *reinterpret_cast<__half *>(dst_w0c + oc) = __float2half_rn(fminf(fmaxf(v, -65504.f), 65504.f));
+      }
     }
     const float *b = p + (size_t)Nr * K;
     float *bd = reinterpret_cast<float *>(dst + h.umma_bias_off) + (size_t)l * h.width;
@@ -990,7 +996,7 @@ __global__ void build_plain_out_kernel(DevObject h, float *dst) {
 
 cudaError_t launch_build_umma(const DevObject &h, cudaStream_t st) {
   build_umma_kernel<<<152, 256, 0, st>>>(h, const_cast<uint8_t *>(h.umma), const_cast<uint8_t *>(h.umma_h),
-                                         const_cast<uint8_t *>(h.umma_lo));
+                                         const_cast<uint8_t *>(h.umma_lo), const_cast<uint8_t *>(h.w0_16c));
   build_plain_out_kernel<<<16, 256, 0, st>>>(h, const_cast<float *>(h.plain_out));
   return cudaGetLastError();
 }

@@ -199,12 +199,17 @@ int lsnif::run_query(lsnif_ctx *ctx, Workspace *ws, const lsnif_rays *r, lsnif_h
       return fail(LSNIF_ERR_UNSUPPORTED, "query: the fused FP8 path needs F in {2,4}, width 64/128, L <= 16, "
                                          "L*F a multiple of 16 and one shape for all objects");
   }
+  bool streamed = false;  // FP16 with the weights streamed (networks too large for shared memory)
   if (fused16_precision(precision)) {
     rep.umma_bytes = sh.umma_max;
     rep.umma_lo_bytes = sh.umma_lo_max;
-    if (sh.mixed_fused || !fused_supported(rep) || fused_smem_bytes(rep, sh.H, precision == LSNIF_FP16_FUSED) > 232448)
-      return fail(LSNIF_ERR_UNSUPPORTED, "query: the fused BF16/FP16 path needs F in {2,4}, width 64/128, L <= 16, "
-                                         "one shape for all objects and weights that fit shared memory");
+    if (sh.mixed_fused || !fused_supported(rep) || fused_smem_bytes(rep, sh.H, precision == LSNIF_FP16_FUSED) > 232448) {
+      streamed = precision == LSNIF_FP16_FUSED && !sh.mixed_fused && fused16s_supported(rep) &&
+                 fused16s_smem_bytes(rep, sh.H) <= 232448;
+      if (!streamed)
+        return fail(LSNIF_ERR_UNSUPPORTED, "query: the fused BF16/FP16 path needs F in {2,4}, width 64/128, L <= 16 "
+                                           "and one shape for all objects; BF16 also weights that fit shared memory");
+    }
   }
   const int n_in = precision == LSNIF_FP32_PLAIN ? sh.n_in : 0;
   if ((rc = ensure_workspace(ctx, ws, r->n, sh.H, sh.n_slots, n_in))) return rc;
@@ -230,6 +235,7 @@ int lsnif::run_query(lsnif_ctx *ctx, Workspace *ws, const lsnif_rays *r, lsnif_h
   if (e == cudaSuccess) {
     if (precision == LSNIF_FP32_PLAIN) e = launch_plain_tail(q, ws->cap_nin, kChunkTiles, &launches);
     else if (precision == LSNIF_FP8_FUSED) e = launch_fused8(q, rep, ctx->fp8_variant, &launches);
+    else if (streamed) e = launch_fused16s(q, rep, &launches);
     else e = launch_fused(q, rep, ctx->fused_variant, precision == LSNIF_FP16_FUSED, &launches);
   }
   // rays on mesh objects were answered as misses by the traversal (no

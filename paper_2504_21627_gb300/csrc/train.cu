@@ -2,7 +2,9 @@
 // labels by ray casting, and one optimisation step of the whole object --
 // forward with saved activations, the multi-head loss, backward through the
 // network, scatter of the feature gradients into the hash tables, Adam.
-// Everything here is FP32 (the paper accumulates gradients in FP32).
+// Gradients are accumulated in FP32 (as in the paper). The network's dense
+// products run on the tensor cores (train_gemm.cu: two-term BF16 operands,
+// FP32 accumulation), or, for reference, as the FP32 SIMT GEMM below.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -205,57 +207,71 @@ __global__ void label_kernel(const DevObject *dobj, RaysArg r, lsnif_labels L) {
 }
 
 // ---------------------------------------------------------------------------
-// forward features of the batch (FP32 tables); rows of rays that meet no
-// occupied voxel stay zero
+// forward features of the batch (FP32 tables), one thread per (ray, point,
+// level): consecutive threads write consecutive levels of a point, and the
+// corner loads of all levels are in flight together. Rows of rays that meet
+// no occupied voxel stay zero.
 // ---------------------------------------------------------------------------
+template <int F>
+__device__ __forceinline__ void feature_level(const DevObject &ob, int l, const float3 &p, float *xo) {
+  const float *tl = ob.tab32 + (size_t)l * (ob.mask + 1) * F;
+  float f[F];
+  encode_level<float, F>(tl, ob.mask, p, (float)ob.res[l], f);
+#pragma unroll
+  for (int j = 0; j < F; ++j) xo[j] = f[j];
+}
+
 __global__ void train_features_kernel(const DevObject *dobj, int64_t B, const int32_t *k, const float *pts,
                                       float *X) {
   const DevObject &ob = *dobj;
-  const int H = ob.H, LF = ob.L * ob.F;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < B * H; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = e / H;
-    const int h = (int)(e % H);
-    float *xo = X + i * ob.n_in + (size_t)h * LF;
+  const int H = ob.H, L = ob.L, F = ob.F;
+  const int64_t tot = B * H * L;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int l = (int)(e % L);
+    const int64_t ih = e / L;
+    const int h = (int)(ih % H);
+    const int64_t i = ih / H;
+    float *xo = X + i * ob.n_in + ((size_t)h * L + l) * F;
     if (h >= 2 * k[i]) {
-      for (int j = 0; j < LF; ++j) xo[j] = 0.f;
+      for (int j = 0; j < F; ++j) xo[j] = 0.f;
       continue;
     }
-    const float3 p = make_float3(pts[(i * H + h) * 3], pts[(i * H + h) * 3 + 1], pts[(i * H + h) * 3 + 2]);
-    for (int l = 0; l < ob.L; ++l) {
-      const float *tl = ob.tab32 + (size_t)l * (ob.mask + 1) * ob.F;
-      const float N = (float)ob.res[l];
-      if (ob.F == 2) {
-        float f[2];
-        encode_level<float, 2>(tl, ob.mask, p, N, f);
-        xo[l * 2] = f[0]; xo[l * 2 + 1] = f[1];
-      } else if (ob.F == 4) {
-        float f[4];
-        encode_level<float, 4>(tl, ob.mask, p, N, f);
-        for (int j = 0; j < 4; ++j) xo[l * 4 + j] = f[j];
-      } else {
-        float f[1];
-        encode_level<float, 1>(tl, ob.mask, p, N, f);
-        xo[l] = f[0];
-      }
-    }
+    const float *pp = pts + (i * H + h) * 3;
+    const float3 p = make_float3(pp[0], pp[1], pp[2]);
+    if (F == 2) feature_level<2>(ob, l, p, xo);
+    else if (F == 4) feature_level<4>(ob, l, p, xo);
+    else feature_level<1>(ob, l, p, xo);
   }
 }
 
-// scatter dX (B x n_in) into the table gradients, live points only
+// Scatter dX (B x n_in) into the table gradients, live points only. An entry
+// point bit-identical to the previous segment's exit point (consecutive
+// occupied voxels share a face) has the same corners and weights: its
+// gradient is added to the exit point's before one set of reductions.
 __global__ void train_scatter_kernel(const DevObject *dobj, int64_t B, const int32_t *k, const float *pts,
                                      const float *dX, float *gtab) {
   const DevObject &ob = *dobj;
-  const int H = ob.H;
-  const int64_t tot = B * H * ob.L;
+  const int H = ob.H, L = ob.L, F = ob.F;
+  const int64_t tot = B * H * L;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
-    const int l = (int)(e % ob.L);
-    const int64_t ih = e / ob.L;
+    const int l = (int)(e % L);
+    const int64_t ih = e / L;
     const int h = (int)(ih % H);
     const int64_t i = ih / H;
-    if (h >= 2 * k[i]) continue;
-    const float3 p = make_float3(pts[(i * H + h) * 3], pts[(i * H + h) * 3 + 1], pts[(i * H + h) * 3 + 2]);
-    const float *g = dX + i * ob.n_in + ((size_t)h * ob.L + l) * ob.F;
-    encode_level_backward(gtab + (size_t)l * (ob.mask + 1) * ob.F, ob.mask, p, (float)ob.res[l], g, ob.F);
+    const int n_pts = 2 * k[i];
+    if (h >= n_pts) continue;
+    const float *pp = pts + (i * H + h) * 3;
+    const float3 p = make_float3(pp[0], pp[1], pp[2]);
+    // an entry point (even h > 0) equal to the exit point before it is scattered by that point's thread
+    if (h > 0 && (h & 1) == 0 && pp[-3] == p.x && pp[-2] == p.y && pp[-1] == p.z) continue;
+    const float *g = dX + i * ob.n_in + ((size_t)h * L + l) * F;
+    float gs[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int f = 0; f < F; ++f) gs[f] = g[f];
+    if ((h & 1) == 1 && h + 1 < n_pts && pp[3] == p.x && pp[4] == p.y && pp[5] == p.z) {
+      const float *g2 = g + (size_t)L * F;  // the next point's features, same level
+      for (int f = 0; f < F; ++f) gs[f] += g2[f];
+    }
+    encode_level_backward(gtab + (size_t)l * (ob.mask + 1) * F, ob.mask, p, (float)ob.res[l], gs, F);
   }
 }
 
@@ -457,7 +473,20 @@ cudaError_t launch_label_rays(const DevObject *dobj, const DevObject &h, const R
 
 cudaError_t launch_train_step(const DevObject *dobj, const DevObject &h, const RaysArg &rays, const lsnif_labels &lab,
                               const lsnif_train_opts &opts, int64_t step, TrainBuffers &tb, int64_t n_params_mlp,
-                              cudaStream_t st) {
+                              int *err, cudaStream_t st) {
+  const bool tc = opts.products == LSNIF_TRAIN_TENSOR_CORES;
+  cudaError_t ge = cudaSuccess;  // first failed product launch
+  auto mm = [&](int M, int N, int K, const float *A, int lda, int tA, const float *Bm, int ldb, int tB, float *C,
+                int ldc, int mode, const float *bias = nullptr, float *post = nullptr, const float *aux = nullptr,
+                int act = 0, int k_split = 1) {
+    if (tc) {
+      const cudaError_t e2 = launch_tc_gemm(st, M, N, K, A, lda, tA, Bm, ldb, tB, C, ldc, mode, bias, post, aux, act,
+                                            k_split, err);
+      if (ge == cudaSuccess) ge = e2;
+    } else {
+      gemm(st, M, N, K, A, lda, tA, Bm, ldb, tB, C, ldc, mode, bias, post, aux, act, k_split);
+    }
+  };
   const int64_t B = rays.n;
   const int W = h.width, NI = h.n_in, NO = h.n_out, NH = h.n_hidden;
   const size_t ntab = ((size_t)h.L << h.log2T) * h.F;
@@ -468,7 +497,7 @@ cudaError_t launch_train_step(const DevObject *dobj, const DevObject &h, const R
   cudaError_t e = launch_trace_only(dobj, rays, tb.k, tb.t01, tb.pts, nullptr, nullptr, st);
   if (e != cudaSuccess) return e;
   count_live_kernel<<<grid_for(B, 256, 152 * 4), 256, 0, st>>>(tb.k, B, tb.loss + 6);
-  train_features_kernel<<<grid_for(B * h.H, 256, 152 * 32), 256, 0, st>>>(dobj, B, tb.k, tb.pts, tb.feats);
+  train_features_kernel<<<grid_for(B * h.H * h.L, 256, 152 * 32), 256, 0, st>>>(dobj, B, tb.k, tb.pts, tb.feats);
   // forward: pre[l], acts[l] (B x W each), logits Z
   const float *p = h.mlp32;
   const float *Wl[LSNIF_MAX_HIDDEN + 1], *bl[LSNIF_MAX_HIDDEN + 1];
@@ -484,11 +513,11 @@ cudaError_t launch_train_step(const DevObject *dobj, const DevObject &h, const R
   int K = NI;
   for (int l = 0; l < NH; ++l) {
     float *pre = tb.pre + (size_t)l * B * W, *post = tb.acts + (size_t)l * B * W;
-    gemm(st, (int)B, W, K, in, K, 0, Wl[l], K, 1, pre, W, 2, bl[l], post, nullptr, h.act);
+    mm((int)B, W, K, in, K, 0, Wl[l], K, 1, pre, W, 2, bl[l], post, nullptr, h.act);
     in = post;
     K = W;
   }
-  gemm(st, (int)B, NO, W, in, W, 0, Wl[NH], W, 1, tb.Z, NO, 3, bl[NH]);
+  mm((int)B, NO, W, in, W, 0, Wl[NH], W, 1, tb.Z, NO, 3, bl[NH]);
   loss_kernel<<<grid_for(B, 256, 152 * 8), 256, 0, st>>>(dobj, B, tb.k, tb.Z, lab, tb.dZ, tb.loss, tb.loss + 6);
   // backward through the network; gradient layout mirrors the packed weights
   float *gW[LSNIF_MAX_HIDDEN + 1], *gb[LSNIF_MAX_HIDDEN + 1];
@@ -510,7 +539,7 @@ cudaError_t launch_train_step(const DevObject *dobj, const DevObject &h, const R
     const int fi = l == 0 ? NI : W;
     const float *hin = l == 0 ? tb.feats : tb.acts + (size_t)(l - 1) * B * W;
     // dW = d^T . hin  (dcols x fi), split over the batch
-    gemm(st, dcols, fi, (int)B, d, dcols, 1, hin, fi, 0, gW[l], fi, 1, nullptr, nullptr, nullptr, 0, ks);
+    mm(dcols, fi, (int)B, d, dcols, 1, hin, fi, 0, gW[l], fi, 1, nullptr, nullptr, nullptr, 0, ks);
     {
       const int threads = dcols * std::max(1, 256 / dcols);
       colsum_kernel<<<152 * 8, threads, threads * sizeof(float), st>>>(d, B, dcols, gb[l]);
@@ -519,10 +548,10 @@ cudaError_t launch_train_step(const DevObject *dobj, const DevObject &h, const R
     // multiply by act'(pre of layer l-1)
     float *dn = (l % 2 == 0) ? tb.dA : tb.dB;
     if (l > 0)
-      gemm(st, (int)B, fi, dcols, d, dcols, 0, Wl[l], fi, 0, dn, fi, 4, nullptr, nullptr,
-           tb.pre + (size_t)(l - 1) * B * W, h.act);
+      mm((int)B, fi, dcols, d, dcols, 0, Wl[l], fi, 0, dn, fi, 4, nullptr, nullptr, tb.pre + (size_t)(l - 1) * B * W,
+         h.act);
     else
-      gemm(st, (int)B, fi, dcols, d, dcols, 0, Wl[l], fi, 0, dn, fi, 0);
+      mm((int)B, fi, dcols, d, dcols, 0, Wl[l], fi, 0, dn, fi, 0);
     d = dn;
     dcols = fi;
   }
@@ -540,6 +569,7 @@ cudaError_t launch_train_step(const DevObject *dobj, const DevObject &h, const R
                                                                          opts.beta1, opts.beta2, opts.eps, (float)c1,
                                                                          (float)c2);
   }
+  if (ge != cudaSuccess) return ge;
   return cudaGetLastError();
 }
 

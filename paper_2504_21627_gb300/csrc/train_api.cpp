@@ -149,7 +149,10 @@ extern "C" int lsnif_train_step(lsnif_ctx *ctx, const lsnif_rays *rays, const ls
   RaysArg ra{rays->ox, rays->oy, rays->oz, rays->dx, rays->dy, rays->dz, rays->tmin, rays->tmax, nullptr, o->handle,
              rays->n};
   const int64_t step = opts->apply_update ? o->step + 1 : o->step;
-  cudaError_t e = launch_train_step(ctx->d_objs + o->slot, o->d, ra, *labels, *opts, step, o->tb, o->n_params_mlp, st);
+  if (opts->products != LSNIF_TRAIN_TENSOR_CORES && opts->products != LSNIF_TRAIN_FP32_SIMT)
+    return fail(LSNIF_ERR_INVALID_ARG, "lsnif_train_step: unknown products %d", opts->products);
+  cudaError_t e = launch_train_step(ctx->d_objs + o->slot, o->d, ra, *labels, *opts, step, o->tb, o->n_params_mlp,
+                                    ctx->d_err, st);
   if (e != cudaSuccess) return cuda_fail(e, "lsnif_train_step");
   if (opts->apply_update) {
     o->step = step;

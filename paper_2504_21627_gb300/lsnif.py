@@ -25,6 +25,7 @@ ERR = {-1: "INVALID_ARG", -2: "BAD_HANDLE", -3: "OUT_OF_MEMORY", -4: "OVER_BUDGE
 FP32_PLAIN, BF16_FUSED, FP8_FUSED, FP16_FUSED = 0, 1, 2, 3
 PARAM_OCCUPANCY, PARAM_TABLES, PARAM_MLP, PARAM_GRAD_TABLES, PARAM_GRAD_MLP = 0, 1, 2, 3, 4
 TRAIN_UNIFORMS = 40
+TRAIN_TENSOR_CORES, TRAIN_FP32_SIMT = 0, 1
 MAX_LEVELS = 32
 
 
@@ -98,7 +99,7 @@ class Labels(C.Structure):
 
 class TrainOpts(C.Structure):
     _fields_ = [("lr", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float),
-                ("apply_update", C.c_int32)]
+                ("apply_update", C.c_int32), ("products", C.c_int32)]
 
 
 class TrainStats(C.Structure):
@@ -603,10 +604,11 @@ class Context:
         return Labels(*[_ptr(lab.get(k)) for k in ("occ", "t_local", "normal", "albedo", "mat", "t_hit", "tri", "k")])
 
     def train_step(self, rays, lab: dict, obj: int, lr: float = 0.01, apply_update: bool = True,
-                   stats: bool = True, stream=None) -> TrainStats | None:
+                   stats: bool = True, stream=None, products: int = 0) -> TrainStats | None:
+        """products: TRAIN_TENSOR_CORES (0) or TRAIN_FP32_SIMT (1)."""
         rs = rays_struct(rays, None, obj)
         ls = self.labels_struct(lab)
-        opts = TrainOpts(lr, 0.9, 0.999, 1e-8, 1 if apply_update else 0)
+        opts = TrainOpts(lr, 0.9, 0.999, 1e-8, 1 if apply_update else 0, products)
         st = TrainStats()
         _check(self.lib.lsnif_train_step(self.h, C.byref(rs), C.byref(ls), C.byref(opts),
                                          C.byref(st) if stats else None, _stream(stream)))

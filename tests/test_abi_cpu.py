@@ -41,7 +41,7 @@ def test_library_exports_every_declared_symbol(lib):
 def test_binding_covers_every_declared_symbol(lib):
     from paper_2504_21627_gb300 import lsnif
     assert sorted(lsnif.SIGNATURES) == _declared()
-    assert lsnif.load_library().lsnif_version() == 1
+    assert lsnif.load_library().lsnif_version() == 2
 
 
 def test_library_exports_nothing_else(lib):

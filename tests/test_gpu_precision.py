@@ -2,8 +2,11 @@
 networks (Sec. 5: inference in half precision). Random-weight networks put
 many decisions at the boundary, so the bounds are stated on networks trained
 by the library's own training step: the icosphere object of the training
-tests and a noise torus at the full benchmark configuration (V 128, 16
-levels, 2^19 entries, 4 x 64). Every output is compared with the oracle's
+tests, a noise torus at the full benchmark configuration (V 128, 16
+levels, 2^19 entries, 4 x 64) and an object of the path-tracing stress
+configuration's network shape (16 levels x 4 features, 4 x 128; 2^19
+entries per level instead of 2^21, to bound the oracle's FP64 copy), which
+runs on the streamed FP16 kernel. Every output is compared with the oracle's
 FP64 query on the same FP32 master parameters:
 
   visibility mismatch <= 0.1% of the rays, hit distance within 1e-3 of the
@@ -68,6 +71,11 @@ def trained(ctx):
     rays = np.concatenate([I.rays_sphere_to_box(6000, 2.5, lo, hi, seed=78),
                            I.rays_pinhole(I.seeded_camera(2, width=96, height=96))], axis=1)
     out["torus"] = (h, mesh, cfg, np.ascontiguousarray(rays))
+    cfg = I.cfg_stress_object(log2_T=19)
+    mesh = I.noise_torus_tris(8, 50000, amplitude=0.05, n_mat=4)
+    h = _train(ctx, mesh, cfg, 1500, 1 << 16, 1 << 20, 7)
+    lo, hi = O.bbox(mesh.verts)
+    out["stress"] = (h, mesh, cfg, I.rays_sphere_to_box(8000, 2.5, lo, hi, seed=79))
     return out
 
 
@@ -107,8 +115,10 @@ def _show(name, label, e):
           f"{e['near']} near-face left out)")
 
 
-@pytest.mark.parametrize("name", ["icosphere", "torus"])
-@pytest.mark.parametrize("prec,label", [(lsnif.BF16_FUSED, "BF16"), (lsnif.FP16_FUSED, "FP16")])
+@pytest.mark.parametrize("name,prec,label", [
+    ("icosphere", lsnif.BF16_FUSED, "BF16"), ("icosphere", lsnif.FP16_FUSED, "FP16"),
+    ("torus", lsnif.BF16_FUSED, "BF16"), ("torus", lsnif.FP16_FUSED, "FP16"),
+    ("stress", lsnif.FP16_FUSED, "FP16 (streamed weights)")])
 def test_half_precision_meets_the_bounds_against_the_fp64_oracle(ctx, trained, name, prec, label):
     e = _errors(ctx, trained, name, prec)
     _show(name, label, e)
@@ -118,7 +128,7 @@ def test_half_precision_meets_the_bounds_against_the_fp64_oracle(ctx, trained, n
     assert e["mat"] >= MAT_MIN, e
 
 
-@pytest.mark.parametrize("name", ["icosphere", "torus"])
+@pytest.mark.parametrize("name", ["icosphere", "torus", "stress"])
 def test_fp32_and_fp8_against_the_fp64_oracle(ctx, trained, name):
     e32 = _errors(ctx, trained, name, lsnif.FP32_PLAIN)
     _show(name, "FP32", e32)
