@@ -465,8 +465,11 @@ def bench_train(args):
     from paper_2504_21627_gb300 import lsnif
     out = {"workload": "train", "metric": "training steps/s at batch 2^18 (forward, loss, backward, Adam); "
                                           "network products on the tensor cores and, for reference, FP32 SIMT"}
-    for name, cfg, mesh in (("icosphere", I.cfg_icosphere_small(), I.icosphere(3)),
-                            ("torus", I.cfg_torus_4m(), I.noise_torus(seed=2))):
+    objects = (("icosphere", I.cfg_icosphere_small(), I.icosphere(3)),
+               ("torus", I.cfg_torus_4m(), I.noise_torus(seed=2)))
+    if args.profile_step:   # profiling captures: the torus only, one step in a profiler range
+        objects = objects[1:]
+    for name, cfg, mesh in objects:
         ctx = lsnif.Context(0)
         h = ctx.load_object(mesh, cfg, keep_mesh=True)
         n_pool, B = 1 << 22, 1 << 18
@@ -485,6 +488,17 @@ def bench_train(args):
             idx = torch.randint(0, pool.shape[1], (B,), device="cuda", generator=gen)
             batches.append((pool[:, idx].contiguous(), {k: v[idx].contiguous() for k, v in lab.items()}))
         first = ctx.train_step(*batches[0], h).total
+        if args.profile_step:
+            for s in range(3):
+                ctx.train_step(*batches[s % 8], h, stats=False)
+            torch.cuda.synchronize()
+            torch.cuda.cudart().cudaProfilerStart()
+            ctx.train_step(*batches[3], h, stats=False)
+            torch.cuda.synchronize()
+            torch.cuda.cudart().cudaProfilerStop()
+            print(json.dumps({"profile_step": "torus training step", "batch": B}))
+            ctx.close()
+            return
         out[name] = {"data_generation_s": t_data, "pool_rays": int(pool.shape[1]), "loss_first": first}
         steps = max(20, args.steps)
         for label, products in (("tensor_cores", lsnif.TRAIN_TENSOR_CORES), ("fp32_simt", lsnif.TRAIN_FP32_SIMT)):
@@ -577,9 +591,9 @@ def bench_sweep(args):
 
 def bench_stress1(args):
     """One object of the stress scene's network shape (L 16, F 4, T 2^21,
-    1152-128x4-12) on the torus workload's mesh and camera: FP8 fused and
-    FP32 plain queries of side x side primary rays, with the FP8 kernel's
-    stage times. A single-object case of the stress network, small enough
+    1152-128x4-12) on the torus workload's mesh and camera: FP16 fused
+    (streamed weights), FP8 fused and FP32 plain queries of side x side
+    primary rays, with their stage times. A single-object case of the stress network, small enough
     for full profiler captures at side 1024."""
     import torch
     from paper_2504_21627_gb300 import lsnif
@@ -598,7 +612,8 @@ def bench_stress1(args):
     stream = torch.cuda.current_stream()
     out = {"workload": "stress1", "network": "L=16 F=4 T=2^21, 1152-128x4-12", "rays": n,
            "group_mode": ctx.tuning()[2]}
-    for name, prec, steps in (("fp8", lsnif.FP8_FUSED, args.steps), ("fp32", lsnif.FP32_PLAIN, 3)):
+    for name, prec, steps in (("fp16", lsnif.FP16_FUSED, args.steps), ("fp8", lsnif.FP8_FUSED, args.steps),
+                              ("fp32", lsnif.FP32_PLAIN, 3)):
         res = ctx.query_rays(rays, obj=obj, precision=prec)
         for _ in range(args.warmup):
             ctx.query_rays(rays, obj=obj, precision=prec, out=res)
@@ -743,8 +758,10 @@ def bench_scene(args):
     one lsnif_query_scene (broad phase over the instances' boxes, pairs
     grouped by object, nearest hit) and one lsnif_bounce_rays. Mrays/s
     counts every submitted ray (dead rays included), as the query's own
-    metric does. The F 4, 4 x 128 network runs on the FP8 tensor-core path
-    (its BF16 first layer does not fit shared memory) and on the FP32 path."""
+    metric does. The F 4, 4 x 128 network runs on the FP16 path (the
+    streamed-weights kernel: its weights do not fit shared memory; the
+    accepted half-precision path of this shape), the FP8 path and the FP32
+    path."""
     import torch
     from paper_2504_21627_gb300 import lsnif
     stress = args.scene_net == "stress"
@@ -787,7 +804,8 @@ def bench_scene(args):
            "instances": len(insts), "unique_objects": len(spec), "rays_per_bounce": n,
            "mesh_objects": int(sum(ctx.object_info(h).kind == 1 for h in handles)),
            "network": "L=16 F=4 T=2^21, 1152-128x4-12" if stress else "L=16 F=2 T=2^21, 576-64x4-12"}
-    fast = (("fp8", lsnif.FP8_FUSED, max(3, args.steps // 4)),) if stress else \
+    fast = (("fp16", lsnif.FP16_FUSED, max(3, args.steps // 4)), ("fp8", lsnif.FP8_FUSED, max(3, args.steps // 4))) \
+        if stress else \
         (("bf16", lsnif.BF16_FUSED, max(3, args.steps // 4)), ("fp8", lsnif.FP8_FUSED, max(3, args.steps // 4)))
     for name, prec, steps in fast + (("fp32", lsnif.FP32_PLAIN, 2),):
         stats = []
