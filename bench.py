@@ -987,18 +987,30 @@ def main():
     meanh, _, vh = replicas.aggregate(float(msh.mean()), n)
 
     # ---- end to end through the host-buffer C-ABI call ----
+    # page-locked host buffers; the kernels read the rays and write the results
+    # there directly (lsnif_set_host_mode DIRECT), and, for reference, the
+    # staged copies of the default mode
     host_rays = torch.from_numpy(rays_np).pin_memory()
     hres = ctx._alloc_hits(n, 0, False, device=False)
-    for _ in range(3):
-        ctx.query_rays_host(host_rays, obj=obj, precision=lsnif.BF16_FUSED, out=hres)
-    e2e_t = []
-    barrier()
-    for _ in range(max(3, args.steps // 2)):
-        t0 = time.perf_counter()
-        ctx.query_rays_host(host_rays, obj=obj, precision=lsnif.BF16_FUSED, out=hres)
-        e2e_t.append(time.perf_counter() - t0)
-    barrier()
-    e2e_ms = reduce_max(float(np.mean(e2e_t)) * 1e3)
+
+    def e2e_time(mode):
+        ctx.set_host_mode(mode)
+        for _ in range(3):
+            ctx.query_rays_host(host_rays, obj=obj, precision=lsnif.BF16_FUSED, out=hres)
+        ts = []
+        barrier()
+        for _ in range(max(3, args.steps // 2)):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ctx.query_rays_host(host_rays, obj=obj, precision=lsnif.BF16_FUSED, out=hres)
+            ts.append(time.perf_counter() - t0)
+        barrier()
+        return reduce_max(float(np.mean(ts)) * 1e3)
+
+    e2e_staged_ms = e2e_time(lsnif.HOST_STAGED)
+    e2e_ms = e2e_time(lsnif.HOST_DIRECT)
+    ctx.set_host_mode(lsnif.HOST_STAGED)
     h2d = n * 8 * 4
     d2h = n * (1 + 4 + 12 + 4 + 12)
 
@@ -1069,7 +1081,9 @@ def main():
                      # 32 B of ray in and 33 B of results per submitted ray
                      "memory_ceiling_mrays_s": peak * 1e9 / ((alg_bytes - live * 54) / n + 65) / 1e6},
         "e2e": {"value": world * n / (e2e_ms / 1e3) / 1e6, "unit": "Mrays/s", "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
+                "host_mode": "direct: the kernels read the page-locked rays and write the page-locked results",
+                "staged": {"value": world * n / (e2e_staged_ms / 1e3) / 1e6, "ms_per_step": e2e_staged_ms}},
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
         "wall_s": {"bf16_timed": wall16, "fp32_timed": wall32, "fp8_timed": wall8},

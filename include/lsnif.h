@@ -272,6 +272,18 @@ LSNIF_API int lsnif_query_rays(lsnif_ctx *ctx, const lsnif_rays *rays, lsnif_hit
 LSNIF_API int lsnif_query_rays_host(lsnif_ctx *ctx, const lsnif_rays *rays, lsnif_hits *hits, int precision,
                           void *stream);
 
+/* How lsnif_query_rays_host moves data (an integration choice; the paper has
+ * no counterpart). STAGED (default): copies through device buffers in
+ * chunks that overlap the queries; any host memory. DIRECT: when every
+ * buffer given is page-locked host memory (cudaHostAlloc, cudaHostRegister,
+ * PyTorch pinned tensors), the kernels read the rays and write the results
+ * there through its mapped address, with no staging copies or staging
+ * memory -- on GB300 host memory is reached over the coherent NVLink-C2C
+ * link; otherwise the call stages as in STAGED. Results are the same bit for
+ * bit. Errors: INVALID_ARG. */
+enum lsnif_host_mode { LSNIF_HOST_STAGED = 0, LSNIF_HOST_DIRECT = 1 };
+LSNIF_API int lsnif_set_host_mode(lsnif_ctx *ctx, int mode);
+
 /* lsnif_query_rays for callers that cannot allocate device memory while they
  * run -- for example a renderer whose frame loop forbids cudaMalloc/cudaFree
  * because they can synchronise the whole device, or a plug-in inside a host

@@ -330,6 +330,53 @@ extern "C" int lsnif_set_graph_mode(lsnif_ctx *ctx, int on) {
 // the copies of neighbouring chunks overlap the query of chunk c (the two
 // copy directions also overlap each other). Synchronous: returns once every
 // result is in host memory.
+extern "C" int lsnif_set_host_mode(lsnif_ctx *ctx, int mode) {
+  if (!ctx) return fail(LSNIF_ERR_INVALID_ARG, "lsnif_set_host_mode: ctx is NULL");
+  if (mode != LSNIF_HOST_STAGED && mode != LSNIF_HOST_DIRECT)
+    return fail(LSNIF_ERR_INVALID_ARG, "lsnif_set_host_mode: unknown mode %d", mode);
+  ctx->host_mode = mode;
+  return LSNIF_OK;
+}
+
+// The device address of a page-locked, mapped host buffer (the same address
+// under unified addressing), or NULL when p is not one (pageable memory,
+// device memory) or is NULL.
+static void *mapped_host(const void *p) {
+  if (!p) return nullptr;
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
+// Direct host-buffer query: every given buffer is page-locked host memory
+// that the kernels read and write through its mapped address (on GB300 the
+// host memory is reached over the coherent NVLink-C2C link), so nothing is
+// staged or copied. Returns 1 (not done) when some buffer is not
+// page-locked; the caller then stages.
+static int query_host_direct(lsnif_ctx *ctx, const lsnif_rays *rays, lsnif_hits *hits, int precision,
+                             cudaStream_t st, int *rc) {
+  lsnif_rays dr = *rays;
+  lsnif_hits dh = *hits;
+  const float **rin[8] = {&dr.ox, &dr.oy, &dr.oz, &dr.dx, &dr.dy, &dr.dz, &dr.tmin, &dr.tmax};
+  for (auto pp : rin)
+    if (!(*pp = static_cast<const float *>(mapped_host(*pp)))) return 1;
+  if (rays->obj && !(dr.obj = static_cast<const uint32_t *>(mapped_host(rays->obj)))) return 1;
+  float **fout[8] = {&dh.t, &dh.nx, &dh.ny, &dh.nz, &dh.ar, &dh.ag, &dh.ab, &dh.logits};
+  for (auto pp : fout)
+    if (*pp && !(*pp = static_cast<float *>(mapped_host(*pp)))) return 1;
+  if (hits->hit && !(dh.hit = static_cast<uint8_t *>(mapped_host(hits->hit)))) return 1;
+  if (hits->mat && !(dh.mat = static_cast<int32_t *>(mapped_host(hits->mat)))) return 1;
+  *rc = run_query(ctx, &ctx->ws, &dr, &dh, precision, st, ctx->profiling);
+  if (*rc == LSNIF_OK) {
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) *rc = cuda_fail(e, "lsnif_query_rays_host");
+  }
+  return 0;
+}
+
 extern "C" int lsnif_query_rays_host(lsnif_ctx *ctx, const lsnif_rays *rays, lsnif_hits *hits, int precision,
                                      void *stream) {
   if (!ctx) return fail(LSNIF_ERR_INVALID_ARG, "lsnif_query_rays_host: ctx is NULL");
@@ -338,6 +385,9 @@ extern "C" int lsnif_query_rays_host(lsnif_ctx *ctx, const lsnif_rays *rays, lsn
   if (rays->n == 0) return LSNIF_OK;
   cudaSetDevice(ctx->device);
   cudaStream_t st = (cudaStream_t)stream;
+  if (hits->logits && rays->obj)
+    return fail(LSNIF_ERR_INVALID_ARG, "lsnif_query_rays_host: logits need a single object");
+  if (ctx->host_mode == LSNIF_HOST_DIRECT && query_host_direct(ctx, rays, hits, precision, st, &rc) == 0) return rc;
   Shape sh;
   if ((rc = shape_of(ctx, rays, &sh))) return rc;
   const int64_t n = rays->n;

@@ -69,6 +69,7 @@ struct lsnif_ctx {
   int fp8_variant = 0;    // FP8 fused-kernel shape (lsnif_set_variant8)
   int trace_mode = 1;     // traversal kernel (see lsnif_autotune)
   int group_mode = 0;     // grouping of live rays (see lsnif_set_group_mode)
+  int host_mode = 0;      // host-buffer queries: 0 staged copies, 1 direct access (lsnif_set_host_mode)
   // CUDA-graph cache of queries (see lsnif_set_graph_mode)
   bool graph_mode = false;
   std::map<std::vector<uint64_t>, cudaGraphExec_t> graphs;

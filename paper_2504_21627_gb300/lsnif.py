@@ -26,6 +26,7 @@ FP32_PLAIN, BF16_FUSED, FP8_FUSED, FP16_FUSED = 0, 1, 2, 3
 PARAM_OCCUPANCY, PARAM_TABLES, PARAM_MLP, PARAM_GRAD_TABLES, PARAM_GRAD_MLP = 0, 1, 2, 3, 4
 TRAIN_UNIFORMS = 40
 TRAIN_TENSOR_CORES, TRAIN_FP32_SIMT = 0, 1
+HOST_STAGED, HOST_DIRECT = 0, 1
 MAX_LEVELS = 32
 
 
@@ -165,6 +166,7 @@ SIGNATURES = {
     "lsnif_set_profiling": (_I, [_P, _I]),
     "lsnif_last_profile": (_I, [_P, C.POINTER(Profile)]),
     "lsnif_gather_rate": (_I, [_P, _U32, _I64, _P, C.POINTER(C.c_double)]),
+    "lsnif_set_host_mode": (_I, [_P, _I]),
     "lsnif_device_bytes": (_SZ, [_P]),
     "lsnif_debug_fail_alloc_after": (_I, [_P, _I64]),
 }
@@ -644,6 +646,10 @@ class Context:
         p = Profile()
         _check(self.lib.lsnif_last_profile(self.h, C.byref(p)))
         return p
+
+    def set_host_mode(self, mode: int):
+        """HOST_STAGED (0) or HOST_DIRECT (1) for query_rays_host (see lsnif_set_host_mode)."""
+        _check(self.lib.lsnif_set_host_mode(self.h, mode))
 
     def gather_rate(self, obj: int, loads: int = 0, stream=None) -> float:
         """Random 8-byte loads per second over the object's FP16 tables (the

@@ -373,14 +373,26 @@ def test_full_size_torus_4m_rays(ctx, torus, prec):
     assert np.all((np.abs(ln - 1) < 1e-4) | (ln == 0))
 
 
-def test_host_buffer_query_equals_device_query(ctx, sphere):
+@pytest.mark.parametrize("mode", [lsnif.HOST_STAGED, lsnif.HOST_DIRECT])
+def test_host_buffer_query_equals_device_query(ctx, sphere, mode):
+    """Staged copies or direct access of page-locked host buffers: the same
+    results as the device query, bit for bit. In direct mode a pageable
+    buffer makes the call stage instead."""
     rays = I.rays_sphere_to_box(3000, 3.0, sphere["orc"].bmin, sphere["orc"].bmax, seed=41)
-    for prec in (lsnif.FP32_PLAIN, lsnif.BF16_FUSED, lsnif.FP16_FUSED):
-        dev = ctx.query_rays(_cuda(rays), obj=sphere["h"], precision=prec)
-        torch.cuda.synchronize()
-        host = ctx.query_rays_host(torch.from_numpy(rays).pin_memory(), obj=sphere["h"], precision=prec)
-        for a, b in ((dev.hit, host.hit), (dev.t, host.t), (dev.mat, host.mat), (dev.normal, host.normal)):
-            assert torch.equal(a.cpu(), b.cpu())
+    ctx.set_host_mode(mode)
+    try:
+        for prec in (lsnif.FP32_PLAIN, lsnif.BF16_FUSED, lsnif.FP16_FUSED):
+            dev = ctx.query_rays(_cuda(rays), obj=sphere["h"], precision=prec)
+            torch.cuda.synchronize()
+            host = ctx.query_rays_host(torch.from_numpy(rays).pin_memory(), obj=sphere["h"], precision=prec)
+            for a, b in ((dev.hit, host.hit), (dev.t, host.t), (dev.mat, host.mat), (dev.normal, host.normal)):
+                assert torch.equal(a.cpu(), b.cpu())
+            # pageable rays: staged whatever the mode
+            out = ctx._alloc_hits(rays.shape[1], 0, False, device=False)
+            host2 = ctx.query_rays_host(torch.from_numpy(rays.copy()), obj=sphere["h"], precision=prec, out=out)
+            assert torch.equal(dev.t.cpu(), host2.t.cpu()) and torch.equal(dev.hit.cpu(), host2.hit.cpu())
+    finally:
+        ctx.set_host_mode(lsnif.HOST_STAGED)
 
 
 def test_chunked_host_buffer_query_equals_device_query(ctx, torus):
@@ -394,11 +406,14 @@ def test_chunked_host_buffer_query_equals_device_query(ctx, torus):
     dev = ctx.query_rays(_cuda(rays), obj=torus["h"], precision=lsnif.BF16_FUSED, logits=True)
     torch.cuda.synchronize()
     host_rays = torch.from_numpy(rays).pin_memory()
-    out = ctx._alloc_hits(n, 8 + torus["cfg"].n_mat, True, device=False)
-    host = ctx.query_rays_host(host_rays, obj=torus["h"], precision=lsnif.BF16_FUSED, out=out)
-    for a, b in ((dev.hit, host.hit), (dev.t, host.t), (dev.mat, host.mat), (dev.normal, host.normal),
-                 (dev.logits, host.logits)):
-        assert torch.equal(torch.nan_to_num(a.cpu(), nan=-1e30), torch.nan_to_num(b.cpu(), nan=-1e30))
+    for mode in (lsnif.HOST_STAGED, lsnif.HOST_DIRECT):
+        ctx.set_host_mode(mode)
+        out = ctx._alloc_hits(n, 8 + torus["cfg"].n_mat, True, device=False)
+        host = ctx.query_rays_host(host_rays, obj=torus["h"], precision=lsnif.BF16_FUSED, out=out)
+        for a, b in ((dev.hit, host.hit), (dev.t, host.t), (dev.mat, host.mat), (dev.normal, host.normal),
+                     (dev.logits, host.logits)):
+            assert torch.equal(torch.nan_to_num(a.cpu(), nan=-1e30), torch.nan_to_num(b.cpu(), nan=-1e30))
+    ctx.set_host_mode(lsnif.HOST_STAGED)
     assert dev.hit.sum().item() > 100000
 
 
