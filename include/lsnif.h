@@ -610,8 +610,11 @@ LSNIF_API int lsnif_submit(lsnif_ctx *ctx, const lsnif_rays *rays, lsnif_hits *h
  * handle) is reported as DEVICE_CHECK on that request's ticket only: each of
  * the context's serving streams has its own device error word, copied to
  * host memory behind the request's kernels, so no read blocks and other
- * requests are not charged. The queue advances only inside lsnif_submit and
- * lsnif_poll. */
+ * requests are not charged. Each of the context's serving streams takes up
+ * to two requests, the second in stream order behind the first when the
+ * stream's scratch already fits it: an admitted request starts on the device
+ * when its predecessor ends, without a host call. Requests still waiting in
+ * the queue are admitted inside lsnif_submit and lsnif_poll. */
 LSNIF_API int lsnif_poll(lsnif_ctx *ctx, uint64_t ticket, int64_t timeout_us, lsnif_req_stats *st);
 
 /* Number of submitted requests not yet reported done by lsnif_poll. */

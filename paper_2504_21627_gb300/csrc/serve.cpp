@@ -1,8 +1,10 @@
 // Serving loop: continuous batching of query requests over a pool of CUDA
-// streams. A request waits in a FIFO queue until a stream is idle and its
-// scratch fits the context's memory budget; it is then launched on that
+// streams. A request waits in a FIFO queue until a stream can take it and
+// its scratch fits the context's memory budget; it is then launched on that
 // stream, so requests admitted later overlap on the device with those
-// already running. Completion is observed through CUDA events; lsnif_poll
+// already running. A stream takes up to kDepth requests: one behind another
+// in stream order when the stream's scratch already fits it, so that the
+// device moves from one to the next without a host call in between. Completion is observed through CUDA events; lsnif_poll
 // never blocks past its timeout. Each stream has its own device error word:
 // a failed device-side check (an unknown object handle, a bounded wait that
 // gave up) is copied to page-locked host memory behind the request's kernels
@@ -19,6 +21,7 @@ using namespace lsnif;
 namespace lsnif {
 
 constexpr int kStreams = 4;
+constexpr int kDepth = 2;  // requests in flight per stream
 constexpr size_t kMaxQueued = 4096;
 
 enum ReqState { kQueued, kRunning, kDone };
@@ -35,14 +38,16 @@ struct Request {
   cudaEvent_t ev_ready = nullptr;  // the caller's stream reached submit: inputs are ready
   cudaEvent_t ev_start = nullptr, ev_done = nullptr;
   float gpu_ms = 0.f;
+  int err_idx = -1;  // which of its stream's host error words receives its device errors
 };
 
 struct StreamSlot {
   cudaStream_t s = nullptr;
   Workspace ws;
-  Request *cur = nullptr;
-  int *d_err = nullptr;           // this stream's device error word (kept at 0 between requests)
-  volatile int *h_err = nullptr;  // page-locked copy of it, written behind each request's kernels
+  std::deque<Request *> inflight;  // launched, in stream order
+  int *d_err = nullptr;            // this stream's device error word (kept at 0 between requests)
+  volatile int *h_err = nullptr;   // kDepth page-locked words, one per request in flight (round robin)
+  uint64_t launched = 0;
 };
 
 struct Server {
@@ -90,12 +95,12 @@ static int server_get(lsnif_ctx *ctx, Server **out) {
       } else if ((rc = dev_alloc(ctx, sizeof(int), &d, "serving error word")) == LSNIF_OK) {
         sl.d_err = static_cast<int *>(d);
         if (cudaMemset(sl.d_err, 0, sizeof(int)) != cudaSuccess ||
-            cudaHostAlloc(&h, sizeof(int), cudaHostAllocDefault) != cudaSuccess) {
+            cudaHostAlloc(&h, kDepth * sizeof(int), cudaHostAllocDefault) != cudaSuccess) {
           cudaGetLastError();
           rc = fail(LSNIF_ERR_CUDA, "serving: cannot set up the error words");
         } else {
           sl.h_err = static_cast<volatile int *>(h);
-          *sl.h_err = 0;
+          for (int k = 0; k < kDepth; ++k) sl.h_err[k] = 0;
         }
       }
       if (rc != LSNIF_OK) {
@@ -110,42 +115,34 @@ static int server_get(lsnif_ctx *ctx, Server **out) {
   return LSNIF_OK;
 }
 
-// Observe finished requests, then admit queued ones in FIFO order while a
-// stream is idle and memory allows.
+// Observe finished requests (in stream order), then admit queued ones in
+// FIFO order while a stream can take them and memory allows.
 static void advance(lsnif_ctx *ctx, Server *sv) {
   for (auto &sl : sv->slots) {
-    Request *r = sl.cur;
-    if (!r) continue;
-    cudaError_t q = cudaEventQuery(r->ev_done);
-    if (q == cudaErrorNotReady) continue;
-    if (q != cudaSuccess) {
-      cudaGetLastError();
-      r->rc = fail(LSNIF_ERR_CUDA, "serving: request %llu failed on the device", (unsigned long long)r->ticket);
-    } else {
-      cudaEventElapsedTime(&r->gpu_ms, r->ev_start, r->ev_done);
-      // the stream's error word, copied behind the request's kernels (ev_done follows the copy)
-      const int h = *sl.h_err;
-      if (h) {
-        *sl.h_err = 0;
-        r->rc = fail(LSNIF_ERR_DEVICE_CHECK, "serving: request %llu: a kernel reported a failed check (0x%x)",
-                     (unsigned long long)r->ticket, h);
+    while (!sl.inflight.empty()) {
+      Request *r = sl.inflight.front();
+      cudaError_t q = cudaEventQuery(r->ev_done);
+      if (q == cudaErrorNotReady) break;
+      if (q != cudaSuccess) {
+        cudaGetLastError();
+        r->rc = fail(LSNIF_ERR_CUDA, "serving: request %llu failed on the device", (unsigned long long)r->ticket);
+      } else {
+        cudaEventElapsedTime(&r->gpu_ms, r->ev_start, r->ev_done);
+        // the stream's error word, copied behind the request's kernels (ev_done follows the copy)
+        const int h = sl.h_err[r->err_idx];
+        if (h) {
+          sl.h_err[r->err_idx] = 0;
+          r->rc = fail(LSNIF_ERR_DEVICE_CHECK, "serving: request %llu: a kernel reported a failed check (0x%x)",
+                       (unsigned long long)r->ticket, h);
+        }
       }
+      r->state = kDone;
+      r->done_us = now_us();
+      sl.inflight.pop_front();
     }
-    r->state = kDone;
-    r->done_us = now_us();
-    sl.cur = nullptr;
   }
   while (!sv->queue.empty()) {
-    int idle = -1;
-    for (int i = 0; i < kStreams; ++i)
-      if (!sv->slots[i].cur) { idle = i; break; }
-    if (idle < 0) return;
     Request *r = sv->queue.front();
-    StreamSlot &sl = sv->slots[idle];
-    int running = 0;
-    for (auto &s2 : sv->slots) running += s2.cur != nullptr;
-    // memory admission: the request's scratch must fit the budget; idle
-    // streams give their scratch back before a request is refused
     int H = 0, n_in = 0, n_slots = std::max(ctx->n_slots_used, 1);
     for (int s = 0; s < ctx->n_slots_used; ++s)
       if (ctx->slots[s]) {
@@ -153,16 +150,31 @@ static void advance(lsnif_ctx *ctx, Server *sv) {
         n_in = std::max(n_in, ctx->slots[s]->d.n_in);
       }
     const int nin_q = r->precision == LSNIF_FP32_PLAIN ? n_in : 0;
+    auto fits = [&](const StreamSlot &sl) {
+      return sl.ws.base && r->rays.n <= sl.ws.cap_rays && H <= sl.ws.cap_H && n_slots <= sl.ws.cap_slots &&
+             nin_q <= sl.ws.cap_nin;
+    };
+    // an idle stream first (its scratch may be regrown); else a stream with
+    // room in its depth whose scratch already fits (no regrowth while busy)
+    int pick = -1;
+    for (int i = 0; i < kStreams && pick < 0; ++i)
+      if (sv->slots[i].inflight.empty()) pick = i;
+    for (int i = 0; i < kStreams && pick < 0; ++i)
+      if ((int)sv->slots[i].inflight.size() < kDepth && fits(sv->slots[i])) pick = i;
+    if (pick < 0) return;
+    StreamSlot &sl = sv->slots[pick];
+    int running = 0;
+    for (auto &s2 : sv->slots) running += (int)s2.inflight.size();
+    // memory admission: the request's scratch must fit the budget; idle
+    // streams give their scratch back before a request is refused
     int rc = LSNIF_OK;
-    bool fits = sl.ws.base && r->rays.n <= sl.ws.cap_rays && H <= sl.ws.cap_H && n_slots <= sl.ws.cap_slots &&
-                nin_q <= sl.ws.cap_nin;
-    if (!fits) {
+    if (!fits(sl)) {
       cudaStreamSynchronize(sl.s);
       free_workspace(ctx, &sl.ws);
       size_t need = workspace_bytes(r->rays.n, H, n_slots, nin_q);
       if (ctx->budget && ctx->used + need > ctx->budget) {
         for (auto &s2 : sv->slots)
-          if (!s2.cur && s2.ws.base) free_workspace(ctx, &s2.ws);
+          if (s2.inflight.empty() && s2.ws.base) free_workspace(ctx, &s2.ws);
       }
       if (ctx->budget && ctx->used + need > ctx->budget) {
         if (running) return;  // wait for memory to free up
@@ -176,12 +188,14 @@ static void advance(lsnif_ctx *ctx, Server *sv) {
     sv->queue.pop_front();
     r->start_us = now_us();
     if (rc == LSNIF_OK) {
+      r->err_idx = (int)(sl.launched++ % kDepth);
       cudaStreamWaitEvent(sl.s, r->ev_ready, 0);   // after the caller's writes to the buffers
       cudaEventRecord(r->ev_start, sl.s);
       rc = run_query(ctx, &sl.ws, &r->rays, &r->hits, r->precision, sl.s, false, sl.d_err);
       if (rc == LSNIF_OK) {
         // hand the error word to the host and clear it for the stream's next request
-        cudaError_t e = cudaMemcpyAsync((void *)sl.h_err, sl.d_err, sizeof(int), cudaMemcpyDeviceToHost, sl.s);
+        cudaError_t e = cudaMemcpyAsync((void *)(sl.h_err + r->err_idx), sl.d_err, sizeof(int),
+                                        cudaMemcpyDeviceToHost, sl.s);
         if (e == cudaSuccess) e = cudaMemsetAsync(sl.d_err, 0, sizeof(int), sl.s);
         if (e != cudaSuccess) rc = cuda_fail(e, "serving: error word");
       }
@@ -194,8 +208,8 @@ static void advance(lsnif_ctx *ctx, Server *sv) {
       continue;
     }
     r->state = kRunning;
-    r->stream = idle;
-    sl.cur = r;
+    r->stream = pick;
+    sl.inflight.push_back(r);
   }
 }
 
