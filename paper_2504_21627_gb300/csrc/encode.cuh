@@ -393,6 +393,9 @@ __device__ __forceinline__ void encode_levels_h2_pairs(const __half *__restrict_
     const float w0y = 1.f - wy[u], w0z = 1.f - wz[u];
     const float wq[4] = {w0y * w0z, wy[u] * w0z, w0y * wz[u], wy[u] * wz[u]};
     const __half2 wx2 = __float2half2_rn(wx[u]);
+    // the four row weights rounded to FP16 two at a time, then broadcast
+    const __half2 w01 = __floats2half2_rn(wq[0], wq[1]), w23 = __floats2half2_rn(wq[2], wq[3]);
+    const __half2 wqh[4] = {__low2half2(w01), __high2half2(w01), __low2half2(w23), __high2half2(w23)};
     __half2 acc = __float2half2_rn(0.f);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -404,7 +407,7 @@ __device__ __forceinline__ void encode_levels_h2_pairs(const __half *__restrict_
       const __half2 v0 = *reinterpret_cast<const __half2 *>(&w0);
       const __half2 v1 = *reinterpret_cast<const __half2 *>(&w1);
       const __half2 lerp = __hfma2(wx2, __hsub2(v1, v0), v0);
-      acc = __hfma2(__float2half2_rn(wq[q]), lerp, acc);
+      acc = __hfma2(wqh[q], lerp, acc);
     }
     out[u] = acc;
   }

@@ -181,20 +181,20 @@ __device__ __noinline__ void mma_role(const FusedArgs *ap, uint8_t *base, uint32
     const uint32_t idesc0 = idesc_f16(W, H16);
     for (int i = 0;; ++i) {
       const int tb = i & 1;
-      if (!mbar_wait(su32(&b_ready[tb]), (uint32_t)((i >> 1) & 1), abort_flag)) break;
+      if (!mbar_wait_sleep(su32(&b_ready[tb]), (uint32_t)((i >> 1) & 1), abort_flag)) break;
       const TileInfo ti = s_info[tb];
       if (ti.stop) break;
       const DevObject &ob = objs[ti.slot];
       const int CHK = 2 * ob.L * F;
       const uint32_t a_sbo = (uint32_t)(CHK / 8) * 128u, w0_sbo = (uint32_t)(ob.n_in / 8) * 128u;
-      if (i >= 2 && !mbar_wait(su32(&b_acce[tb]), (uint32_t)(((i - 2) >> 1) & 1), abort_flag)) break;
+      if (i >= 2 && !mbar_wait_sleep(su32(&b_acce[tb]), (uint32_t)(((i - 2) >> 1) & 1), abort_flag)) break;
       tc_after();
       const uint32_t dacc = tmem + (uint32_t)(tb * W);
       bool ok = true;
       for (int s = 0; s < ti.kmax; ++s) {
         const int c = chunk_ctr + s;
         const int buf = c % nbuf;
-        if (!mbar_wait(su32(&b_full[buf]), (uint32_t)((c / nbuf) & 1), abort_flag)) {
+        if (!mbar_wait_sleep(su32(&b_full[buf]), (uint32_t)((c / nbuf) & 1), abort_flag)) {
           ok = false;
           break;
         }
@@ -405,7 +405,7 @@ __device__ __noinline__ void epilogue_role(const FusedArgs *ap, uint8_t *base, u
       if (last) stop_at = i + 1;
 
       // ---- layers after the first, decode ----
-      if (etid == 0) s_misc[2] = mbar_wait(su32(&b_accf[tb]), (uint32_t)((i >> 1) & 1), abort_flag) ? 0 : 1;
+      if (etid == 0) s_misc[2] = mbar_wait_sleep(su32(&b_accf[tb]), (uint32_t)((i >> 1) & 1), abort_flag) ? 0 : 1;
       named_sync(2, kEpiThreads);
       if (!s_misc[2]) {
         tc_after();
@@ -472,7 +472,7 @@ __device__ __noinline__ void epilogue_role(const FusedArgs *ap, uint8_t *base, u
                 }
               }
               mma_commit(su32(b_layer));
-              mbar_wait(su32(b_layer), (uint32_t)(layer_ctr & 1), abort_flag);
+              mbar_wait_sleep(su32(b_layer), (uint32_t)(layer_ctr & 1), abort_flag);
             }
             ++layer_ctr;
             named_sync(2, kEpiThreads);
@@ -586,7 +586,7 @@ __global__ void __launch_bounds__((NG + 1 + kEpiWarps) * 32, 1) fused_kernel(con
     for (int i = 0;; ++i) {
       const int tb = i & 1;
       // the epilogue warps set the tile up: rows, work lists, weights
-      if (!mbar_wait(su32(&b_ready[tb]), (uint32_t)((i >> 1) & 1), abort_flag)) break;
+      if (!mbar_wait_sleep(su32(&b_ready[tb]), (uint32_t)((i >> 1) & 1), abort_flag)) break;
       const TileInfo ti = s_info[tb];
       if (ti.stop) break;
       const int kmax = ti.kmax;
@@ -606,6 +606,19 @@ __global__ void __launch_bounds__((NG + 1 + kEpiWarps) * 32, 1) fused_kernel(con
       const int CHK = 2 * L * F;  // columns per chunk
       const uint32_t a_sbo = (uint32_t)(CHK / 8) * 128u;
       const size_t lstride = (size_t)(mask + 1) * F;
+      // The boundary point of a thread's next gather item is loaded while
+      // the current item's corner loads are in flight (across the chunks of
+      // a tile too), so that the point's memory latency is not added to
+      // every item's. pn_chunk: the chunk whose first item pn already holds.
+      float3 pn = make_float3(0.f, 0.f, 0.f);
+      int pn_chunk = -1;
+      auto load_point = [&](int s2, int it2, int ngt2, float inv2) {
+        const int g2 = __float2int_rz(((float)it2 + 0.5f) * inv2);
+        const int e2 = s_lst[s2 * kListStride + (it2 - g2 * ngt2)];
+        const int ray2 = s_ray[tb * kTileM + (e2 & 127)];
+        const float *P = q.s.pts + ((size_t)ray2 * Hs + 2 * s2 + (e2 >> 7)) * 3;
+        return make_float3(P[0], P[1], P[2]);
+      };
       for (int s = 0; s < kmax; ++s) {
         const int c = chunk_ctr + s;
         const int buf = c % nbuf, use = c / nbuf;
@@ -621,33 +634,51 @@ __global__ void __launch_bounds__((NG + 1 + kEpiWarps) * 32, 1) fused_kernel(con
         // copies of chunk c - nbuf + 1 (which read it) are written. Every
         // thread waits, with or without items: an arrival on the full barrier
         // must not land in the phase of chunk c - nbuf.
-        if (use > 0) mbar_wait(su32(&b_empty[buf]), (uint32_t)((use - 1) & 1), abort_flag);
+        if (use > 0) mbar_wait_sleep(su32(&b_empty[buf]), (uint32_t)((use - 1) & 1), abort_flag);
         {
           const int cp = c - nbuf + 1;
-          if (cp >= 0 && cp < c) mbar_wait(su32(&b_full[cp % nbuf]), (uint32_t)((cp / nbuf) & 1), abort_flag);
+          if (cp >= 0 && cp < c) mbar_wait_sleep(su32(&b_full[cp % nbuf]), (uint32_t)((cp / nbuf) & 1), abort_flag);
         }
         // gathers: the lanes of a warp take consecutive entries (neighbouring
         // rays) at the same column group, so at coarse levels they share
         // corners and cache sectors
         const float inv_g = 1.f / (float)max(ngt, 1);
+        if (!XROWS && pn_chunk != s && first_g < nb_g && first_g * 32 + lane < n_gi)
+          pn = load_point(s, first_g * 32 + lane, ngt, inv_g);
         for (int b = first_g; b < nb_g; b += NG) {
           const int it = b * 32 + lane;
+          const float3 p = pn;
+          if (!XROWS) {
+            const int bn = b + NG;
+            if (bn < nb_g) {
+              if (bn * 32 + lane < n_gi) pn = load_point(s, bn * 32 + lane, ngt, inv_g);
+            } else if (s + 1 < kmax) {
+              // this thread's first item of the next chunk
+              uint32_t all2 = 0;
+#pragma unroll
+              for (int w = 0; w < 4; ++w) all2 += s_ws[(s + 1) * 4 + w];
+              const int ngt2 = (int)(all2 & 1023u), n_gi2 = ngt2 * G;
+              const int first2 = (warp - (rot_g + nb_g) % NG + NG) % NG;
+              if (first2 * 32 + lane < n_gi2) {
+                pn = load_point(s + 1, first2 * 32 + lane, ngt2, 1.f / (float)max(ngt2, 1));
+                pn_chunk = s + 1;
+              }
+            }
+          }
           if (it < n_gi) {
             const int g = __float2int_rz(((float)it + 0.5f) * inv_g);
             const int t = it - g * ngt;
             const int e = s_lst[s * kListStride + t];
             const int r = e & 127, j = e >> 7;
-            const int ray = s_ray[tb * kTileM + r];
             uint4 outv;
             if (XROWS) {
+              const int ray = s_ray[tb * kTileM + r];
               const float *xr = a.X + (int64_t)ray * n_in + (size_t)(2 * s + j) * L * F + g * 8;
               const float4 x0 = *reinterpret_cast<const float4 *>(xr);
               const float4 x1 = *reinterpret_cast<const float4 *>(xr + 4);
               outv = make_uint4(pack_op(x0.x, x0.y, H16), pack_op(x0.z, x0.w, H16), pack_op(x1.x, x1.y, H16),
                                 pack_op(x1.z, x1.w, H16));
             } else {
-              const float *P = q.s.pts + ((size_t)ray * Hs + 2 * s + j) * 3;
-              const float3 p = make_float3(P[0], P[1], P[2]);
               constexpr int LPG = 8 / F;  // levels per 16-byte group
               // the group's 8 features as operand words: F = 2 gathers give
               // one half2 per level, F = 4 gathers FP32 values
@@ -696,7 +727,7 @@ __global__ void __launch_bounds__((NG + 1 + kEpiWarps) * 32, 1) fused_kernel(con
         const int n_o = kListStride - ngt;
         if (nct > 0 && first_o < nb_o) {  // copies read the previous chunk: it must be complete
           const int cq = c - 1;
-          mbar_wait(su32(&b_full[cq % nbuf]), (uint32_t)((cq / nbuf) & 1), abort_flag);
+          mbar_wait_sleep(su32(&b_full[cq % nbuf]), (uint32_t)((cq / nbuf) & 1), abort_flag);
         }
         const float inv_o = 1.f / (float)max(n_o, 1);
         for (int b = first_o; b < nb_o; b += NG) {
@@ -761,14 +792,15 @@ size_t fused_smem_bytes(const DevObject &h, int H_max, bool fp16) {
 // the 228 KiB one, which leaves L1 28 KiB instead of 60 KiB; the gather's
 // coarse levels live in L1, and on the torus workload that alone took the
 // fused kernel from 2.79 to 3.93 ms. A ring of 3 buffers ran as fast as 4,
-// one of 2 about 13% slower. So: the largest ring of at least 3 buffers that
-// stays within the 196 KiB configuration, else the largest that fits at all.
+// one of 2 about 13% slower; the FP16 kernel (no lo weights) with 3 buffers
+// fits the 164 KiB configuration, whose 92 KiB of L1 made it 3% faster than
+// with 4. So: 3 buffers when they stay within the 196 KiB configuration,
+// else the largest ring that fits at all.
 constexpr uint32_t kSmemL1Friendly = 195u * 1024u;
 
 static int pick_nbuf(const DevObject &h, int list_chunks, bool fp16) {
   auto total = [&](int nb) { return make_layout(blob_bytes(h), lo_bytes(h, fp16), h.F, h.width, nb, list_chunks).total; };
-  for (int nb = kNBufMax; nb >= 3; --nb)
-    if (total(nb) <= kSmemL1Friendly) return nb;
+  if (total(3) <= kSmemL1Friendly) return 3;
   for (int nb = kNBufMax; nb >= 2; --nb)
     if (total(nb) <= 232448) return nb;
   return 0;

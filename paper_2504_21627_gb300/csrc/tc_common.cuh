@@ -66,6 +66,25 @@ __device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity, volati
   }
 }
 
+// The same with a sleep between tests (32 ns doubling to 512 ns), for
+// kernels whose waiting warps share the SM's issue slots with busy ones: a
+// waiting warp then issues fewer instructions. In the fused query kernel
+// this was 1% faster than waking on every completed test.
+__device__ __forceinline__ bool mbar_wait_sleep(uint32_t addr, uint32_t parity, volatile int *abort_flag) {
+  const long long t0 = clock64();
+  unsigned ns = 32u;
+  while (true) {
+    if (mbar_try(addr, parity)) return true;
+    __nanosleep(ns);
+    ns = ns < 512u ? 2u * ns : 512u;
+    if (*abort_flag) return false;
+    if (clock64() - t0 > kWaitCycles) {
+      *abort_flag = 1;
+      return false;
+    }
+  }
+}
+
 // Bounded wait that ignores the abort flag (teardown: in-flight MMAs).
 __device__ __forceinline__ bool mbar_wait_teardown(uint32_t addr, uint32_t parity) {
   const long long t0 = clock64();
