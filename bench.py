@@ -923,7 +923,7 @@ def main():
         variant = ctx.autotune(rays, obj=obj, reps=3)
     if args.variant is not None:   # fixed shape (profiling runs, whose timings differ)
         variant = args.variant
-    ctx.set_variant(variant)
+        ctx.set_variant(variant)   # for BF16 and FP16 (else FP16 keeps its own autotuned shape)
     vshape = lsnif.Context.variants()[variant]
     stream = torch.cuda.current_stream()
     if args.profile_step:

@@ -468,7 +468,7 @@ LSNIF_API int lsnif_variant_count(void);
  * flight per gather item. Errors: INVALID_ARG for v out of range. */
 LSNIF_API int lsnif_variant_shape(int v, int *threads, int *levels);
 
-/* Use variant v for every later BF16 query of the context. */
+/* Use variant v for every later BF16 and FP16 fused query of the context. */
 LSNIF_API int lsnif_set_variant(lsnif_ctx *ctx, int v);
 
 /* The FP8 fused kernel's shapes (LSNIF_FP8_FUSED with F = 4; F = 2 always
@@ -492,9 +492,11 @@ LSNIF_API int lsnif_set_trace_mode(lsnif_ctx *ctx, int mode);
 /* Time every fused-kernel variant on `rays` (DEVICE buffers, `reps` BF16
  * queries each after one warm-up, CUDA events on `stream`, synchronous), keep
  * the fastest, then the other traversal kernel and (single-object rays) the
- * other grouping, keeping each if faster; *chosen (may be NULL) receives the
- * variant index. Results of the queries are discarded; all choices compute
- * identical results. */
+ * other grouping, keeping each if faster; then time every variant again with
+ * FP16 queries and keep the fastest for LSNIF_FP16_FUSED (the FP16 kernel
+ * holds no lo weights, so its shared memory and L1 differ). *chosen (may be
+ * NULL) receives the BF16 variant index. Results of the queries are
+ * discarded; all choices compute identical results. */
 LSNIF_API int lsnif_autotune(lsnif_ctx *ctx, const lsnif_rays *rays, int reps, void *stream, int *chosen);
 
 /* How live rays are grouped into 128-ray tiles: 0 = by object, then by
@@ -506,8 +508,8 @@ LSNIF_API int lsnif_autotune(lsnif_ctx *ctx, const lsnif_rays *rays, int reps, v
  * compute identical results. */
 LSNIF_API int lsnif_set_group_mode(lsnif_ctx *ctx, int mode);
 
-/* The context's current fused-kernel variant, traversal kernel and
- * grouping (lsnif_autotune sets all three). */
+/* The context's current fused-kernel variant of BF16 queries, traversal
+ * kernel and grouping (lsnif_autotune sets all three). */
 LSNIF_API int lsnif_get_tuning(lsnif_ctx *ctx, int *variant, int *trace_mode, int *group_mode);
 
 /* ---- training (Sec. 5.2, 5.3) ------------------------------------------ */

@@ -610,6 +610,10 @@ __global__ void __launch_bounds__((NG + 1 + kEpiWarps) * 32, 1) fused_kernel(con
       // the current item's corner loads are in flight (across the chunks of
       // a tile too), so that the point's memory latency is not added to
       // every item's. pn_chunk: the chunk whose first item pn already holds.
+      // Only for the 8-byte pair gather at 512 threads (128 registers): the
+      // other variants have no registers to spare for it (it made them
+      // spill and run slower).
+      constexpr bool kPrefetch = !XROWS && GS == 2 && NG + 1 + kEpiWarps <= 16;
       float3 pn = make_float3(0.f, 0.f, 0.f);
       int pn_chunk = -1;
       auto load_point = [&](int s2, int it2, int ngt2, float inv2) {
@@ -643,12 +647,12 @@ __global__ void __launch_bounds__((NG + 1 + kEpiWarps) * 32, 1) fused_kernel(con
         // rays) at the same column group, so at coarse levels they share
         // corners and cache sectors
         const float inv_g = 1.f / (float)max(ngt, 1);
-        if (!XROWS && pn_chunk != s && first_g < nb_g && first_g * 32 + lane < n_gi)
+        if (kPrefetch && pn_chunk != s && first_g < nb_g && first_g * 32 + lane < n_gi)
           pn = load_point(s, first_g * 32 + lane, ngt, inv_g);
         for (int b = first_g; b < nb_g; b += NG) {
           const int it = b * 32 + lane;
-          const float3 p = pn;
-          if (!XROWS) {
+          float3 p = pn;
+          if constexpr (kPrefetch) {
             const int bn = b + NG;
             if (bn < nb_g) {
               if (bn * 32 + lane < n_gi) pn = load_point(s, bn * 32 + lane, ngt, inv_g);
@@ -679,6 +683,7 @@ __global__ void __launch_bounds__((NG + 1 + kEpiWarps) * 32, 1) fused_kernel(con
               outv = make_uint4(pack_op(x0.x, x0.y, H16), pack_op(x0.z, x0.w, H16), pack_op(x1.x, x1.y, H16),
                                 pack_op(x1.z, x1.w, H16));
             } else {
+              if constexpr (!kPrefetch) p = load_point(s, it, ngt, inv_g);
               constexpr int LPG = 8 / F;  // levels per 16-byte group
               // the group's 8 features as operand words: F = 2 gathers give
               // one half2 per level, F = 4 gathers FP32 values

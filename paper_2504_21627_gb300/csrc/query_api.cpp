@@ -236,7 +236,9 @@ int lsnif::run_query(lsnif_ctx *ctx, Workspace *ws, const lsnif_rays *r, lsnif_h
     if (precision == LSNIF_FP32_PLAIN) e = launch_plain_tail(q, ws->cap_nin, kChunkTiles, &launches);
     else if (precision == LSNIF_FP8_FUSED) e = launch_fused8(q, rep, ctx->fp8_variant, &launches);
     else if (streamed) e = launch_fused16s(q, rep, &launches);
-    else e = launch_fused(q, rep, ctx->fused_variant, precision == LSNIF_FP16_FUSED, &launches);
+    else
+      e = launch_fused(q, rep, precision == LSNIF_FP16_FUSED ? ctx->fused_variant16 : ctx->fused_variant,
+                       precision == LSNIF_FP16_FUSED, &launches);
   }
   // rays on mesh objects were answered as misses by the traversal (no
   // voxels); their BVH query overwrites them
@@ -275,7 +277,9 @@ static int query_graph(lsnif_ctx *ctx, const lsnif_rays *r, lsnif_hits *h, int p
   if ((rc = ensure_workspace(ctx, &ctx->ws, r->n, sh.H, sh.n_slots, n_in))) return rc;
   if (ctx->graphs_ws != ctx->ws.base) clear_graphs(ctx);
   std::vector<uint64_t> key = {(uint64_t)r->n, (uint64_t)precision,
-                               (uint64_t)(precision == LSNIF_FP8_FUSED ? 1000 + ctx->fp8_variant : ctx->fused_variant),
+                               (uint64_t)(precision == LSNIF_FP8_FUSED    ? 1000 + ctx->fp8_variant
+                                          : precision == LSNIF_FP16_FUSED ? 2000 + ctx->fused_variant16
+                                                                          : ctx->fused_variant),
                                (uint64_t)ctx->trace_mode, (uint64_t)ctx->group_mode, (uint64_t)sh.n_slots,
                                (uint64_t)r->single_obj};
   for (const void *p : {(const void *)r->ox, (const void *)r->oy, (const void *)r->oz, (const void *)r->dx,
@@ -597,6 +601,7 @@ extern "C" int lsnif_set_variant(lsnif_ctx *ctx, int v) {
   if (!ctx || v < 0 || v >= fused_variant_count())
     return fail(LSNIF_ERR_INVALID_ARG, "lsnif_set_variant: bad variant %d", v);
   ctx->fused_variant = v;
+  ctx->fused_variant16 = v;
   return LSNIF_OK;
 }
 
@@ -624,12 +629,13 @@ extern "C" int lsnif_autotune(lsnif_ctx *ctx, const lsnif_rays *rays, int reps, 
   cudaEvent_t a, b;
   cudaEventCreate(&a);
   cudaEventCreate(&b);
-  const int keep_v = ctx->fused_variant, keep_t = ctx->trace_mode, keep_g = ctx->group_mode;
-  auto time_it = [&](float *ms) -> int {
-    int rc = run_query(ctx, &ctx->ws, rays, &none, LSNIF_BF16_FUSED, st, false);
+  const int keep_v = ctx->fused_variant, keep_v16 = ctx->fused_variant16, keep_t = ctx->trace_mode,
+            keep_g = ctx->group_mode;
+  auto time_it = [&](float *ms, int precision = LSNIF_BF16_FUSED) -> int {
+    int rc = run_query(ctx, &ctx->ws, rays, &none, precision, st, false);
     if (rc) return rc;
     cudaEventRecord(a, st);
-    for (int r = 0; r < reps && rc == LSNIF_OK; ++r) rc = run_query(ctx, &ctx->ws, rays, &none, LSNIF_BF16_FUSED, st, false);
+    for (int r = 0; r < reps && rc == LSNIF_OK; ++r) rc = run_query(ctx, &ctx->ws, rays, &none, precision, st, false);
     cudaEventRecord(b, st);
     if (rc) return rc;
     if ((rc = check_device(ctx, st))) return rc;
@@ -668,15 +674,30 @@ extern "C" int lsnif_autotune(lsnif_ctx *ctx, const lsnif_rays *rays, int reps, 
       }
     }
   }
+  // the FP16 kernel's shape on its own (its shared memory, so its L1, differs)
+  int best16 = -1;
+  if (rc == LSNIF_OK) {
+    ctx->trace_mode = best_t;
+    ctx->group_mode = best_g;
+    float best16_ms = 0.f;
+    for (int v = 0; v < fused_variant_count() && rc == LSNIF_OK; ++v) {
+      ctx->fused_variant16 = v;
+      float ms = 0.f;
+      if ((rc = time_it(&ms, LSNIF_FP16_FUSED))) break;
+      if (best16 < 0 || ms < best16_ms) { best16 = v; best16_ms = ms; }
+    }
+  }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   if (rc) {
     ctx->fused_variant = keep_v;
+    ctx->fused_variant16 = keep_v16;
     ctx->trace_mode = keep_t;
     ctx->group_mode = keep_g;
     return rc;
   }
   ctx->fused_variant = best;
+  ctx->fused_variant16 = best16;
   ctx->trace_mode = best_t;
   ctx->group_mode = best_g;
   if (chosen) *chosen = best;

@@ -65,7 +65,8 @@ struct lsnif_ctx {
   int *d_err = nullptr;
   int32_t *d_prof_meta = nullptr;
   lsnif::Workspace ws;
-  int fused_variant = 0;  // fused-kernel shape (see lsnif_autotune)
+  int fused_variant = 0;    // fused-kernel shape of BF16 queries (see lsnif_autotune)
+  int fused_variant16 = 0;  // and of FP16 queries
   int fp8_variant = 0;    // FP8 fused-kernel shape (lsnif_set_variant8)
   int trace_mode = 1;     // traversal kernel (see lsnif_autotune)
   int group_mode = 0;     // grouping of live rays (see lsnif_set_group_mode)
