@@ -22,9 +22,10 @@
 // lo.lo product, about 2^-16 of the rest, is left out), so the gradients keep
 // FP32-level accuracy and the FP32 exponent range (no loss scaling). Two
 // shared-memory stages: a stage is refilled once the MMAs that read it have
-// completed.
+// completed; the loads of the next chunk go to registers before the current
+// chunk's MMAs are issued, so their latency overlaps them.
 //
-// Tiles: 128 rows (the tcgen05 M; rows past M are zero), N_CH <= 192 columns
+// Tiles: 128 rows (the tcgen05 M; rows past M are zero), N_CH <= 96 columns
 // (the grid's y dimension walks larger N), K in chunks of 64; the grid's z
 // dimension splits K (the batch, for weight gradients) into ranges whose
 // partial products are added atomically.
@@ -42,7 +43,6 @@ namespace {
 constexpr int kGM = 128;        // tile rows (tcgen05 M)
 constexpr int kGK = 64;         // K chunk per stage
 constexpr int kGThreads = 256;  // eight warps; warps w and w + 4 share TMEM lane quarter w
-constexpr int kGMaxN = 192;     // columns per CTA at most (shared memory and TMEM sizes)
 
 // kind::f16 instruction descriptor, BF16 A and B (K-major), FP32 D, M = 128
 __device__ __forceinline__ uint32_t idesc_bf16(int N) {
@@ -89,7 +89,7 @@ struct GemmArgs {
   float *post;
   const float *aux;
   int act;
-  int n_ch;      // columns per CTA (multiple of 16, <= kGMaxN)
+  int n_ch;      // columns per CTA (multiple of 16, <= 96)
   int k_per_z;   // K range per grid z (a multiple of kGK)
   int nst;       // shared-memory stages (1 when a CTA's K range is one chunk)
   int *err;      // device error word (bounded waits that give up)
@@ -100,9 +100,12 @@ struct GemmArgs {
 // must stay 0), rows past the operand's end are not written (they only feed
 // rows or columns of the product that are not stored). kc: X(row, k) =
 // P[row ld + k] (contiguous along k); else X(row, k) = P[k ld + row]
-// (contiguous along rows: the transposed read of dY^T, X^T and W^T). Each
-// thread issues a batch of up to kBatch 16-byte loads before it converts and
-// stores any, so that the loads of a stage are in flight together.
+// (contiguous along rows: the transposed read of dY^T, X^T and W^T). A chunk
+// of one operand is at most 128 rows x 64 = 2048 items of 4 elements, so each
+// of the 256 threads holds at most kBatch of them. Staging is split in two:
+// stage_load issues a thread's 16-byte loads into registers, stage_store
+// converts and writes them, so that the loads of chunk c + 1 are in flight
+// while chunk c is multiplied.
 constexpr int kBatch = 8;
 
 __device__ __forceinline__ void put4_k(uint8_t *hi, uint8_t *lo, int row, int k, const float (&v)[4]) {
@@ -124,6 +127,69 @@ __device__ __forceinline__ void put4_rows(uint8_t *hi, uint8_t *lo, int row, int
   }
 }
 
+// item it of a chunk: (row, k) of its first element
+__device__ __forceinline__ void item_pos(bool kc, int it, int rows4, int &row, int &k) {
+  if (kc) { row = it >> 4; k = (it & 15) * 4; }
+  else { k = it / rows4; row = (it - k * rows4) * 4; }
+}
+
+__device__ __forceinline__ void stage_load(float (&v)[kBatch][4], const float *P, int ld, bool kc, int r0,
+                                           int tile_rows, int nrows, int k0, int kend, int tid) {
+  const int rows = min(nrows - r0, tile_rows);
+  const bool vec = ((ld & 3) == 0) && ((reinterpret_cast<uintptr_t>(P) & 15) == 0);
+  const int rows4 = (rows + 3) >> 2;
+  const int items = kc ? rows * (kGK / 4) : rows4 * kGK;
+#pragma unroll
+  for (int b = 0; b < kBatch; ++b) {
+    const int it = tid + b * kGThreads;
+    v[b][0] = v[b][1] = v[b][2] = v[b][3] = 0.f;
+    if (it >= items) continue;
+    int row, k;
+    item_pos(kc, it, rows4, row, k);
+    const int gk = k0 + k;
+    if (kc) {
+      const float *src = P + (int64_t)(r0 + row) * ld + gk;
+      if (vec && gk + 3 < kend) {
+        const float4 f = __ldg(reinterpret_cast<const float4 *>(src));
+        v[b][0] = f.x; v[b][1] = f.y; v[b][2] = f.z; v[b][3] = f.w;
+      } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (gk + j < kend) v[b][j] = __ldg(src + j);
+      }
+    } else if (gk < kend) {
+      const float *src = P + (int64_t)gk * ld + r0 + row;
+      if (vec && row + 3 < rows) {
+        const float4 f = __ldg(reinterpret_cast<const float4 *>(src));
+        v[b][0] = f.x; v[b][1] = f.y; v[b][2] = f.z; v[b][3] = f.w;
+      } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (row + j < rows) v[b][j] = __ldg(src + j);
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void stage_store(uint8_t *hi, uint8_t *lo, const float (&v)[kBatch][4], bool kc, int r0,
+                                            int tile_rows, int nrows, int tid) {
+  const int rows = min(nrows - r0, tile_rows);
+  const int rows4 = (rows + 3) >> 2;
+  const int items = kc ? rows * (kGK / 4) : rows4 * kGK;
+#pragma unroll
+  for (int b = 0; b < kBatch; ++b) {
+    const int it = tid + b * kGThreads;
+    if (it >= items) break;
+    int row, k;
+    item_pos(kc, it, rows4, row, k);
+    if (kc) put4_k(hi, lo, row, k, v[b]);
+    else put4_rows(hi, lo, row, k, v[b]);
+  }
+}
+
+// Both operands of a chunk staged one after the other, each thread issuing
+// its (at most kBatch) loads of an operand before it converts any: the
+// short products' form, which holds one operand's registers at a time.
 __device__ __forceinline__ void stage(uint8_t *hi, uint8_t *lo, const float *P, int ld, bool kc, int r0,
                                       int tile_rows, int nrows, int k0, int kend, int tid) {
   const int rows = min(nrows - r0, tile_rows);
@@ -178,6 +244,10 @@ __device__ __forceinline__ void stage(uint8_t *hi, uint8_t *lo, const float *P, 
 
 // One CTA: rows [blockIdx.x 128, +128) x columns [blockIdx.y n_ch, +n_ch) of
 // C, K range [blockIdx.z k_per_z, +k_per_z).
+// PIPE: the next chunk's loads are issued before this chunk's MMAs (CTAs
+// with more than one chunk); otherwise one operand's registers at a time, so
+// that short products keep more CTAs per SM.
+template <bool PIPE>
 __global__ void __launch_bounds__(kGThreads) tc_gemm_kernel(const __grid_constant__ GemmArgs g) {
   extern __shared__ __align__(1024) uint8_t gsm_raw[];
   uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(gsm_raw) + 1023) & ~uintptr_t(1023));
@@ -213,6 +283,11 @@ __global__ void __launch_bounds__(kGThreads) tc_gemm_kernel(const __grid_constan
   const uint32_t tmem = *s_tmem;
   const uint32_t idesc = idesc_bf16(n_ch);
 
+  float va[kBatch][4], vb[kBatch][4];  // PIPE only
+  if (PIPE && nchunks > 0) {
+    stage_load(va, g.A, g.lda, a_kc, m0, kGM, g.M, kb, ke, tid);
+    stage_load(vb, g.B, g.ldb, b_kc, n0, n_ch, g.N, kb, ke, tid);
+  }
   for (int c = 0; c < nchunks; ++c) {
     const int buf = c % g.nst, use = c / g.nst;
     uint8_t *st = base + buf * stage_bytes;
@@ -221,9 +296,19 @@ __global__ void __launch_bounds__(kGThreads) tc_gemm_kernel(const __grid_constan
       __syncthreads();
       if (*abort_flag) break;
     }
-    const int k0 = kb + c * kGK;
-    stage(st, st + a_bytes, g.A, g.lda, a_kc, m0, kGM, g.M, k0, ke, tid);
-    stage(st + 2 * a_bytes, st + 2 * a_bytes + b_bytes, g.B, g.ldb, b_kc, n0, n_ch, g.N, k0, ke, tid);
+    if constexpr (PIPE) {
+      stage_store(st, st + a_bytes, va, a_kc, m0, kGM, g.M, tid);
+      stage_store(st + 2 * a_bytes, st + 2 * a_bytes + b_bytes, vb, b_kc, n0, n_ch, g.N, tid);
+      if (c + 1 < nchunks) {  // the next chunk's loads fly during this chunk's sync and MMAs
+        const int k1 = kb + (c + 1) * kGK;
+        stage_load(va, g.A, g.lda, a_kc, m0, kGM, g.M, k1, ke, tid);
+        stage_load(vb, g.B, g.ldb, b_kc, n0, n_ch, g.N, k1, ke, tid);
+      }
+    } else {
+      const int k0 = kb + c * kGK;
+      stage(st, st + a_bytes, g.A, g.lda, a_kc, m0, kGM, g.M, k0, ke, tid);
+      stage(st + 2 * a_bytes, st + 2 * a_bytes + b_bytes, g.B, g.ldb, b_kc, n0, n_ch, g.N, k0, ke, tid);
+    }
     fence_async_smem();
     tc_before();
     __syncthreads();
@@ -323,12 +408,15 @@ cudaError_t launch_tc_gemm(cudaStream_t st, int M, int N, int K, const float *A,
   const size_t smem = g.nst * stage + 64 + 1024;
   static int attr = 0;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
+    cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(tc_gemm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
     if (e != cudaSuccess) return e;
     attr = 1;
   }
   dim3 grid((M + kGM - 1) / kGM, (N + g.n_ch - 1) / g.n_ch, nz);
-  tc_gemm_kernel<<<grid, kGThreads, smem, st>>>(g);
+  if (g.nst > 1) tc_gemm_kernel<true><<<grid, kGThreads, smem, st>>>(g);
+  else tc_gemm_kernel<false><<<grid, kGThreads, smem, st>>>(g);
   return cudaGetLastError();
 }
 
