@@ -221,16 +221,33 @@ __device__ __forceinline__ void feature_level(const DevObject &ob, int l, const 
   for (int j = 0; j < F; ++j) xo[j] = f[j];
 }
 
+// (ray i, point h, level l) of work item e = (i H + h) L + l, with 32-bit
+// divisions when every item index fits 32 bits (a 64-bit integer division
+// costs several times the instructions of a 32-bit one)
+__device__ __forceinline__ void split_item(int64_t e, bool narrow, int H, int L, int64_t &i, int &h, int &l) {
+  if (narrow) {
+    const uint32_t u = (uint32_t)e, ih = u / (uint32_t)L, i32 = ih / (uint32_t)H;
+    l = (int)(u - ih * (uint32_t)L);
+    h = (int)(ih - i32 * (uint32_t)H);
+    i = i32;
+  } else {
+    const int64_t ih = e / L;
+    l = (int)(e - ih * L);
+    i = ih / H;
+    h = (int)(ih - i * H);
+  }
+}
+
 __global__ void train_features_kernel(const DevObject *dobj, int64_t B, const int32_t *k, const float *pts,
                                       float *X) {
   const DevObject &ob = *dobj;
   const int H = ob.H, L = ob.L, F = ob.F;
   const int64_t tot = B * H * L;
+  const bool narrow = tot + (int64_t)gridDim.x * blockDim.x < (int64_t(1) << 32);
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
-    const int l = (int)(e % L);
-    const int64_t ih = e / L;
-    const int h = (int)(ih % H);
-    const int64_t i = ih / H;
+    int64_t i;
+    int h, l;
+    split_item(e, narrow, H, L, i, h, l);
     float *xo = X + i * ob.n_in + ((size_t)h * L + l) * F;
     if (h >= 2 * k[i]) {
       for (int j = 0; j < F; ++j) xo[j] = 0.f;
@@ -253,11 +270,11 @@ __global__ void train_scatter_kernel(const DevObject *dobj, int64_t B, const int
   const DevObject &ob = *dobj;
   const int H = ob.H, L = ob.L, F = ob.F;
   const int64_t tot = B * H * L;
+  const bool narrow = tot + (int64_t)gridDim.x * blockDim.x < (int64_t(1) << 32);
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
-    const int l = (int)(e % L);
-    const int64_t ih = e / L;
-    const int h = (int)(ih % H);
-    const int64_t i = ih / H;
+    int64_t i;
+    int h, l;
+    split_item(e, narrow, H, L, i, h, l);
     const int n_pts = 2 * k[i];
     if (h >= n_pts) continue;
     const float *pp = pts + (i * H + h) * 3;
