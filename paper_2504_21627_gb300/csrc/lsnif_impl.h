@@ -205,6 +205,14 @@ struct TrainBuffers {
   float *pts;       // B x H x 3
   float *t01;       // B x 2
   int32_t *k;       // B
+  // the query traversal's own outputs for the batch: one-byte point counts
+  // (widened into k), shared-point bits, object slots, its histogram
+  // (kMaxSlots x kBuckets) and counters
+  uint8_t *k8;
+  uint32_t *dup;
+  int16_t *slot;
+  int32_t *counts;
+  int32_t *meta;
   float *loss;      // 8 accumulators
   float *grad_mlp;  // n_params_mlp
   float *grad_tab;  // L x T x F
@@ -216,9 +224,11 @@ cudaError_t launch_make_training_rays(const DevObject *dobj, const DevObject &h,
                                       cudaStream_t st);
 cudaError_t launch_label_rays(const DevObject *dobj, const DevObject &h, const RaysArg &rays,
                               const lsnif_labels &out, cudaStream_t st);
-cudaError_t launch_train_step(const DevObject *dobj, const DevObject &h, const RaysArg &rays,
-                              const lsnif_labels &lab, const lsnif_train_opts &opts, int64_t step,
-                              TrainBuffers &tb, int64_t n_params_mlp, int *err, cudaStream_t st);
+// objs, n_slots: the context's object array up to this object's slot (the
+// traversal resolves the rays' handle in it)
+cudaError_t launch_train_step(const DevObject *objs, int n_slots, const DevObject *dobj, const DevObject &h,
+                              const RaysArg &rays, const lsnif_labels &lab, const lsnif_train_opts &opts,
+                              int64_t step, TrainBuffers &tb, int64_t n_params_mlp, int *err, cudaStream_t st);
 // C[M x N] = op(A) . op(B) on the tensor cores (two-term BF16, FP32
 // accumulation), op(A)[m][k] = tA ? A[k lda + m] : A[m lda + k], op(B)[k][n] =
 // tB ? B[n ldb + k] : B[k ldb + n]; mode 0 store, 1 atomic add (k_split > 1

@@ -452,10 +452,14 @@ __global__ void loss_kernel(const DevObject *dobj, int64_t B, const int32_t *k, 
   }
 }
 
-__global__ void count_live_kernel(const int32_t *k, int64_t B, float *count) {
+// k = k8 (the traversal's one-byte point counts), and the live-ray count
+__global__ void widen_count_kernel(const uint8_t *k8, int64_t B, int32_t *k, float *count) {
   float c = 0.f;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < B; i += (int64_t)gridDim.x * blockDim.x)
-    c += k[i] > 0 ? 1.f : 0.f;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < B; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t ki = k8[i];
+    k[i] = ki;
+    c += ki > 0 ? 1.f : 0.f;
+  }
   for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
   if ((threadIdx.x & 31) == 0) atomicAdd(count, c);
 }
@@ -488,9 +492,9 @@ cudaError_t launch_label_rays(const DevObject *dobj, const DevObject &h, const R
   return cudaGetLastError();
 }
 
-cudaError_t launch_train_step(const DevObject *dobj, const DevObject &h, const RaysArg &rays, const lsnif_labels &lab,
-                              const lsnif_train_opts &opts, int64_t step, TrainBuffers &tb, int64_t n_params_mlp,
-                              int *err, cudaStream_t st) {
+cudaError_t launch_train_step(const DevObject *objs, int n_slots, const DevObject *dobj, const DevObject &h,
+                              const RaysArg &rays, const lsnif_labels &lab, const lsnif_train_opts &opts,
+                              int64_t step, TrainBuffers &tb, int64_t n_params_mlp, int *err, cudaStream_t st) {
   const bool tc = opts.products == LSNIF_TRAIN_TENSOR_CORES;
   cudaError_t ge = cudaSuccess;  // first failed product launch
   auto mm = [&](int M, int N, int K, const float *A, int lda, int tA, const float *Bm, int ldb, int tB, float *C,
@@ -510,10 +514,28 @@ cudaError_t launch_train_step(const DevObject *dobj, const DevObject &h, const R
   cudaMemsetAsync(tb.loss, 0, 8 * sizeof(float), st);
   cudaMemsetAsync(tb.grad_mlp, 0, sizeof(float) * n_params_mlp, st);
   cudaMemsetAsync(tb.grad_tab, 0, sizeof(float) * ntab, st);
-  // a1-a5 for the batch
-  cudaError_t e = launch_trace_only(dobj, rays, tb.k, tb.t01, tb.pts, nullptr, nullptr, st);
+  // a1-a5 for the batch: the query's persistent-lane traversal with empty
+  // cube skipping (the voxels and boundary points of the voxel-by-voxel
+  // walk, bit for bit), no results written
+  QueryLaunch q{};
+  q.objs = objs;
+  q.n_slots = n_slots;
+  q.H_max = h.H;
+  q.rays = rays;
+  q.s.pts = tb.pts;
+  q.s.t01 = tb.t01;
+  q.s.k = tb.k8;
+  q.s.dup = tb.dup;
+  q.s.slot = tb.slot;
+  q.s.counts = tb.counts;
+  q.s.meta = tb.meta;
+  q.err = err;
+  q.stream = st;
+  q.trace_mode = 1;
+  int launches = 0;
+  cudaError_t e = launch_trace(q, &launches);
   if (e != cudaSuccess) return e;
-  count_live_kernel<<<grid_for(B, 256, 152 * 4), 256, 0, st>>>(tb.k, B, tb.loss + 6);
+  widen_count_kernel<<<grid_for(B, 256, 152 * 4), 256, 0, st>>>(tb.k8, B, tb.k, tb.loss + 6);
   train_features_kernel<<<grid_for(B * h.H * h.L, 256, 152 * 32), 256, 0, st>>>(dobj, B, tb.k, tb.pts, tb.feats);
   // forward: pre[l], acts[l] (B x W each), logits Z
   const float *p = h.mlp32;

@@ -69,6 +69,11 @@ static int ensure_train(lsnif_ctx *ctx, Object *o, int64_t B) {
   TALLOC(pts, float *, 12 * (size_t)B * c.H);
   TALLOC(t01, float *, 8 * (size_t)B);
   TALLOC(k, int32_t *, 4 * (size_t)B);
+  TALLOC(k8, uint8_t *, (size_t)B);
+  TALLOC(dup, uint32_t *, 4 * (size_t)B);
+  TALLOC(slot, int16_t *, 2 * (size_t)B);
+  TALLOC(counts, int32_t *, 4 * (size_t)kMaxSlots * kBuckets);
+  TALLOC(meta, int32_t *, 64);
   if (!keep.loss) {
     TALLOC(loss, float *, 64);
     TALLOC(grad_mlp, float *, 4 * (size_t)o->n_params_mlp);
@@ -151,8 +156,8 @@ extern "C" int lsnif_train_step(lsnif_ctx *ctx, const lsnif_rays *rays, const ls
   const int64_t step = opts->apply_update ? o->step + 1 : o->step;
   if (opts->products != LSNIF_TRAIN_TENSOR_CORES && opts->products != LSNIF_TRAIN_FP32_SIMT)
     return fail(LSNIF_ERR_INVALID_ARG, "lsnif_train_step: unknown products %d", opts->products);
-  cudaError_t e = launch_train_step(ctx->d_objs + o->slot, o->d, ra, *labels, *opts, step, o->tb, o->n_params_mlp,
-                                    ctx->d_err, st);
+  cudaError_t e = launch_train_step(ctx->d_objs, o->slot + 1, ctx->d_objs + o->slot, o->d, ra, *labels, *opts, step,
+                                    o->tb, o->n_params_mlp, ctx->d_err, st);
   if (e != cudaSuccess) return cuda_fail(e, "lsnif_train_step");
   if (opts->apply_update) {
     o->step = step;

@@ -586,6 +586,34 @@ def test_tuning_choices_give_identical_results(ctx, torus):
     ctx.set_group_mode(keep[2])
 
 
+def test_autotune_picks_valid_choices_and_keeps_results(ctx, torus):
+    """lsnif_autotune times the fused-kernel variants on BF16 queries, the
+    traversal kernels and groupings, then the variants again on FP16 queries
+    (a choice of its own). Every choice computes the same bits, so BF16 and
+    FP16 queries after tuning equal those before."""
+    cam = I.seeded_camera(2)
+    rays = _cuda(np.ascontiguousarray(I.rays_pinhole(cam, px0=600, py0=600, w=384, h=256)))
+    keep = ctx.tuning()
+    ctx.set_variant(0)
+    before = {}
+    for prec in (lsnif.BF16_FUSED, lsnif.FP16_FUSED):
+        out = ctx.query_rays(rays, obj=torus["h"], precision=prec, logits=True)
+        before[prec] = (out.hit.clone(), out.t.clone(), out.logits.clone())
+    v = ctx.autotune(rays, obj=torus["h"], reps=1)
+    ctx.check()
+    assert 0 <= v < len(lsnif.Context.variants())
+    tv, tm, gm = ctx.tuning()
+    assert tv == v and tm in (0, 1) and gm in (0, 1)
+    for prec in (lsnif.BF16_FUSED, lsnif.FP16_FUSED):
+        out = ctx.query_rays(rays, obj=torus["h"], precision=prec, logits=True)
+        ctx.check()
+        for a, b in zip(before[prec], (out.hit, out.t, out.logits)):
+            assert torch.equal(torch.nan_to_num(a, nan=-1e30), torch.nan_to_num(b, nan=-1e30)), prec
+    ctx.set_variant(keep[0])
+    ctx.set_trace_mode(keep[1])
+    ctx.set_group_mode(keep[2])
+
+
 def _tie_rays(orc, n_random, seed):
     """Rays that meet many lattice planes at the same parameter: along the
     axes on lattice-aligned lines, along the diagonals through lattice points,
