@@ -359,7 +359,12 @@ __device__ __forceinline__ void encode_levels_h2_pairs(const __half *__restrict_
                                                        __half2 (&out)[NL]) {
   const uint8_t *base = reinterpret_cast<const uint8_t *>(tab0);
   float wx[NL], wy[NL], wz[NL];
-  uint32_t lo[NL];  // bit q: corner x0 of row q is the odd word of its pair
+  // Corner x0 of row q is the odd word of its pair when bit 0 of its index
+  // is set. The y and z multipliers are odd, so stepping y or z by one flips
+  // bit 0 of the hash: bit 0 of row q's index is h0 ^ dy ^ dz, with h0 that
+  // of row 0 (the table mask keeps bit 0).
+  static_assert((kPi2 & 1u) && (kPi3 & 1u), "the row parity below needs odd y and z multipliers");
+  bool h0[NL];
   bool odd[NL];
   uint2 ga[NL][4];
   uint32_t gb[NL][4];
@@ -373,19 +378,17 @@ __device__ __forceinline__ void encode_levels_h2_pairs(const __half *__restrict_
     const uint32_t hz0 = c.cz * kPi3, hz1 = hz0 + kPi3;
     const uint8_t *tl = base + (size_t)u * level_stride;
     odd[u] = (c.cx & 1u) && c.wx != 0.f;
+    h0[u] = ((c.cx ^ hy0 ^ hz0) & 1u) != 0u;
     const void *pb[4];
-    uint32_t bits = 0;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int dy = q & 1, dz = q >> 1;
       const uint32_t b = (dy ? hy1 : hy0) ^ (dz ? hz1 : hz0);
       const uint32_t ia = (c.cx ^ b) & mask;
       const uint32_t ib = ((c.cx + 1u) ^ b) & mask;
-      bits |= (ia & 1u) << q;
       ga[u][q] = __ldg(reinterpret_cast<const uint2 *>(tl + (size_t)(ia & ~1u) * 4));
       pb[q] = tl + (size_t)ib * 4;
     }
-    lo[u] = bits;
     ldg4x4_if(gb[u], pb[0], pb[1], pb[2], pb[3], odd[u]);
   }
 #pragma unroll
@@ -399,7 +402,7 @@ __device__ __forceinline__ void encode_levels_h2_pairs(const __half *__restrict_
     __half2 acc = __float2half2_rn(0.f);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const bool hi = (lo[u] >> q) & 1u;
+      const bool hi = (q == 0 || q == 3) ? h0[u] : !h0[u];
       const uint32_t w0 = hi ? ga[u][q].y : ga[u][q].x;
       // x1: the other word of the pair (even cx), its own load (odd cx), or,
       // with wx = 0, a word of weight exactly 0
