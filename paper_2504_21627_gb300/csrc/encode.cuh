@@ -246,21 +246,49 @@ __device__ __forceinline__ void encode_levels_f16(const __half *__restrict__ tab
   for (int u = 0; u < NL; ++u) {
 #pragma unroll
     for (int f = 0; f < F; ++f) out[u][f] = 0.f;
+    if constexpr (F == 4) {
+      // 8-byte entries, two per group. Which half of its group corner x0 of
+      // row q takes is bit 0 of its index: that of row 0 flipped by dy and
+      // by dz (the y and z multipliers are odd). Corner x1 shares the group
+      // when cx ^ (cx + 1), masked, is below 2 -- the same for every row.
+      // The words of each corner are selected first and converted once.
+      static_assert((kPi2 & 1u) && (kPi3 & 1u), "the row parity needs odd y and z multipliers");
+      const bool j0 = (ia[u][0] & 1u) != 0u;
+      const bool same = (ia[u][0] ^ ib[u][0]) < (uint32_t)G;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int dy = q & 1, dz = q >> 1;
-      // all three sources of the x1 corner are formed, then selected
-      float v0[F], vg[F], vb[F], v1[F];
-      unpack_entry<__half, F>(ga[u][q], ia[u][q] & (G - 1), v0);
-      unpack_entry<__half, F>(ga[u][q], ib[u][q] & (G - 1), vg);
-      const uint4 t = make_uint4(gb[u][q][0], EB == 8 ? gb[u][q][EB / 4 - 1] : 0u, 0u, 0u);
-      unpack_entry<__half, F>(t, 0, vb);
-      const bool same = (ia[u][q] ^ ib[u][q]) < (uint32_t)G;
+      for (int q = 0; q < 4; ++q) {
+        const int dy = q & 1, dz = q >> 1;
+        const bool ja = (dy ^ dz) ? !j0 : j0;
+        const uint32_t a0 = ja ? ga[u][q].z : ga[u][q].x, a1 = ja ? ga[u][q].w : ga[u][q].y;
+        const uint32_t o0 = ja ? ga[u][q].x : ga[u][q].z, o1 = ja ? ga[u][q].y : ga[u][q].w;
+        const uint32_t b0 = pb[u][q] ? gb[u][q][0] : (same ? o0 : a0);
+        const uint32_t b1 = pb[u][q] ? gb[u][q][1] : (same ? o1 : a1);
+        const float2 x00 = __half22float2(*reinterpret_cast<const __half2 *>(&a0));
+        const float2 x01 = __half22float2(*reinterpret_cast<const __half2 *>(&a1));
+        const float2 x10 = __half22float2(*reinterpret_cast<const __half2 *>(&b0));
+        const float2 x11 = __half22float2(*reinterpret_cast<const __half2 *>(&b1));
+        const float v0[4] = {x00.x, x00.y, x01.x, x01.y}, v1[4] = {x10.x, x10.y, x11.x, x11.y};
+        const float wyz = (dy ? wy[u] : 1.f - wy[u]) * (dz ? wz[u] : 1.f - wz[u]);
 #pragma unroll
-      for (int f = 0; f < F; ++f) v1[f] = pb[u][q] ? vb[f] : (same ? vg[f] : v0[f]);
-      const float wyz = (dy ? wy[u] : 1.f - wy[u]) * (dz ? wz[u] : 1.f - wz[u]);
+        for (int f = 0; f < F; ++f) out[u][f] = fmaf(wyz, fmaf(wx[u], v1[f] - v0[f], v0[f]), out[u][f]);
+      }
+    } else {
 #pragma unroll
-      for (int f = 0; f < F; ++f) out[u][f] = fmaf(wyz, fmaf(wx[u], v1[f] - v0[f], v0[f]), out[u][f]);
+      for (int q = 0; q < 4; ++q) {
+        const int dy = q & 1, dz = q >> 1;
+        // all three sources of the x1 corner are formed, then selected
+        float v0[F], vg[F], vb[F], v1[F];
+        unpack_entry<__half, F>(ga[u][q], ia[u][q] & (G - 1), v0);
+        unpack_entry<__half, F>(ga[u][q], ib[u][q] & (G - 1), vg);
+        const uint4 t = make_uint4(gb[u][q][0], EB == 8 ? gb[u][q][EB / 4 - 1] : 0u, 0u, 0u);
+        unpack_entry<__half, F>(t, 0, vb);
+        const bool same = (ia[u][q] ^ ib[u][q]) < (uint32_t)G;
+#pragma unroll
+        for (int f = 0; f < F; ++f) v1[f] = pb[u][q] ? vb[f] : (same ? vg[f] : v0[f]);
+        const float wyz = (dy ? wy[u] : 1.f - wy[u]) * (dz ? wz[u] : 1.f - wz[u]);
+#pragma unroll
+        for (int f = 0; f < F; ++f) out[u][f] = fmaf(wyz, fmaf(wx[u], v1[f] - v0[f], v0[f]), out[u][f]);
+      }
     }
   }
 }
