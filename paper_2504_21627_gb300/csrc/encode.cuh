@@ -444,6 +444,48 @@ __device__ __forceinline__ void encode_levels_h2_pairs(const __half *__restrict_
   }
 }
 
+// encode_level<float, 2> without branches between the loads: every row's
+// 16-byte group of corner x0 (skipped for zero-weight rows) and, where x1
+// lies in another group, x1's entry are loaded together, then selected by
+// word. The half of its group x0 takes is known from row 0's (the y and z
+// multipliers are odd), and x1 shares the group when cx ^ (cx + 1), masked,
+// is below 2. The same values as encode_level: x1 reads 0 where wx = 0.
+__device__ __forceinline__ void encode_level_f32x2(const float *__restrict__ tab, uint32_t mask, const float3 &p,
+                                                   float N, float (&out)[2]) {
+  static_assert((kPi2 & 1u) && (kPi3 & 1u), "the row parity needs odd y and z multipliers");
+  const Cell c = lattice_cell(p, N);
+  const bool nx = c.wx != 0.f, ny = c.wy != 0.f, nz = c.wz != 0.f;
+  const uint32_t hy0 = c.cy * kPi2, hy1 = (c.cy + 1u) * kPi2;
+  const uint32_t hz0 = c.cz * kPi3, hz1 = (c.cz + 1u) * kPi3;
+  const bool j0 = ((c.cx ^ hy0 ^ hz0) & 1u) != 0u;
+  const bool same = ((c.cx ^ (c.cx + 1u)) & mask) < 2u;
+  const uint8_t *base = reinterpret_cast<const uint8_t *>(tab);
+  uint4 ga[4];
+  uint2 gb[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int dy = q & 1, dz = q >> 1;
+    const bool pa = (dy == 0 || ny) && (dz == 0 || nz);
+    const uint32_t b = (dy ? hy1 : hy0) ^ (dz ? hz1 : hz0);
+    const uint32_t ia = (c.cx ^ b) & mask, ib = ((c.cx + 1u) ^ b) & mask;
+    ga[q] = ldg16_if(base + (size_t)(ia & ~1u) * 8, pa);
+    gb[q] = ldg8_if(base + (size_t)ib * 8, pa && nx && !same);
+  }
+  out[0] = out[1] = 0.f;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int dy = q & 1, dz = q >> 1;
+    const bool ja = (dy ^ dz) ? !j0 : j0;
+    const float a0 = __uint_as_float(ja ? ga[q].z : ga[q].x), a1 = __uint_as_float(ja ? ga[q].w : ga[q].y);
+    const float o0 = __uint_as_float(ja ? ga[q].x : ga[q].z), o1 = __uint_as_float(ja ? ga[q].y : ga[q].w);
+    const float b0 = nx ? (same ? o0 : __uint_as_float(gb[q].x)) : 0.f;
+    const float b1 = nx ? (same ? o1 : __uint_as_float(gb[q].y)) : 0.f;
+    const float wyz = (dy ? c.wy : 1.f - c.wy) * (dz ? c.wz : 1.f - c.wz);
+    out[0] = fmaf(wyz, fmaf(c.wx, b0 - a0, a0), out[0]);
+    out[1] = fmaf(wyz, fmaf(c.wx, b1 - a1, a1), out[1]);
+  }
+}
+
 // The same gather split into issue and interpolation, so that the loads of
 // the next level are in flight while the current level is interpolated
 // (a two-stage software pipeline over the levels of a column group).

@@ -216,7 +216,8 @@ template <int F>
 __device__ __forceinline__ void feature_level(const DevObject &ob, int l, const float3 &p, float *xo) {
   const float *tl = ob.tab32 + (size_t)l * (ob.mask + 1) * F;
   float f[F];
-  encode_level<float, F>(tl, ob.mask, p, (float)ob.res[l], f);
+  if constexpr (F == 2) encode_level_f32x2(tl, ob.mask, p, (float)ob.res[l], f);
+  else encode_level<float, F>(tl, ob.mask, p, (float)ob.res[l], f);
 #pragma unroll
   for (int j = 0; j < F; ++j) xo[j] = f[j];
 }
