@@ -36,6 +36,26 @@ def test_hash_structure_against_published_multipliers():
             assert h == O.hash_index(x, 0, 0, log2T) ^ O.hash_index(0, y, 0, log2T) ^ O.hash_index(0, 0, z, log2T)
 
 
+def test_hash_low_bits_the_gather_relies_on():
+    """Index facts the GPU gathers use to skip per-corner work, checked on
+    the oracle's hash: a step in y or in z flips bit 0 of the index (the y
+    and z multipliers are odd), so one row's parity gives every row's; and
+    the x neighbours' indices differ by (cx ^ (cx + 1)) & mask whatever y
+    and z are, so whether they share an aligned pair is one test per cell."""
+    pr = _primes()
+    assert pr["pi2"] % 2 == 1 and pr["pi3"] % 2 == 1
+    g = np.random.default_rng(11)
+    for log2T in (2, 14, 19):
+        mask = (1 << log2T) - 1
+        for x, y, z in g.integers(0, 4096, size=(200, 3)):
+            x, y, z = int(x), int(y), int(z)
+            h = O.hash_index(x, y, z, log2T)
+            assert (O.hash_index(x, y + 1, z, log2T) ^ h) & 1 == 1
+            assert (O.hash_index(x, y, z + 1, log2T) ^ h) & 1 == 1
+            assert (O.hash_index(x, y + 1, z + 1, log2T) ^ h) & 1 == 0
+            assert O.hash_index(x + 1, y, z, log2T) ^ h == (x ^ (x + 1)) & mask
+
+
 def test_weights_sum_to_one():
     g = np.random.default_rng(0)
     pts = g.random((500, 3))
