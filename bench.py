@@ -49,8 +49,8 @@ def fused_source_hash() -> str:
 
 def recorded_profile(key: str):
     """A figure of the committed ncu summary of the fused kernel (DRAM bytes
-    per launch, L2 sectors per gathered point), or None when the kernel
-    sources changed after the capture."""
+    per launch, L2 sectors per gathered point, tensor-pipe activity), or None
+    when the kernel sources changed after the capture."""
     if not os.path.exists(PROFILE_MD):
         return None
     txt = open(PROFILE_MD).read()
@@ -1072,6 +1072,9 @@ def main():
                      "peak_source": "measured in this run: lsnif_gather_rate, random 8-byte loads over the "
                                     "object's FP16 tables (L2-resident), 32 B sectors",
                      "l2_sectors_per_launch": l2_sectors, "gathered_points": gathered_points,
+                     # ncu sm__pipe_tensor_cycles_active of the same kernel sources (1024^2
+                     # capture): the MLP on tcgen05 is not what bounds the kernel
+                     "tensor_pipe_active_pct": recorded_profile("tensor_pipe_active_pct"),
                      "l2_peak_requests_per_s": gather_rate, "corner_loads_per_launch": loads,
                      "corner_loads_per_s": loads / (fused_ms / 1e3),
                      "hbm": {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
