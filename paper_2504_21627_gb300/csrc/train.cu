@@ -446,10 +446,22 @@ __global__ void loss_kernel(const DevObject *dobj, int64_t B, const int32_t *k, 
     s[5] += y * l_m;
   }
   s[0] = s[1] + s[2] + s[3] + s[4] + s[5];
+  // warp sums, then block sums, then one atomic per block and term (six
+  // addresses take every block's atomic, so fewer of them contend less)
+  __shared__ float part[6][32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int j = 0; j < 6; ++j) {
     float v = s[j];
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0) atomicAdd(acc + j, v * inv_live);
+    if (lane == 0) part[j][warp] = v;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    for (int j = 0; j < 6; ++j) {
+      float v = lane < nw ? part[j][lane] : 0.f;
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+      if (lane == 0) atomicAdd(acc + j, v * inv_live);
+    }
   }
 }
 
