@@ -444,6 +444,43 @@ __global__ void __launch_bounds__(256) scatter_kernel(QueryLaunch q) {
   }
 }
 
+// The same with each block's counts summed in shared memory first: one
+// global atomic per block and bucket instead of one per warp and bucket (a
+// query's few buckets otherwise take every warp's atomics). One ray per
+// thread; nb = n_slots x kBuckets counts and as many block bases in shared
+// memory.
+__global__ void __launch_bounds__(1024) scatter_block_kernel(QueryLaunch q, int nb) {
+  extern __shared__ int sh_scatter[];
+  int *s_cnt = sh_scatter, *s_base = sh_scatter + nb;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) s_cnt[b] = 0;
+  __syncthreads();
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  int bucket = -1;
+  if (i < q.rays.n) {
+    const int k = q.s.k[i];
+    const int s = q.s.slot[i];
+    if (k > 0 && s >= 0) bucket = s * kBuckets + (q.group_mode == 2 ? 1 : k);
+  }
+  const unsigned active = __ballot_sync(0xffffffffu, bucket >= 0);
+  int rank = 0;
+  if (bucket >= 0) {
+    const unsigned peers = __match_any_sync(active, bucket);
+    const int leader = __ffs(peers) - 1;
+    int wbase = 0;
+    if (lane == leader) wbase = atomicAdd(&s_cnt[bucket], __popc(peers));
+    wbase = __shfl_sync(peers, wbase, leader);
+    rank = wbase + __popc(peers & ((1u << lane) - 1u));
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+    const int c = s_cnt[b];
+    s_base[b] = c ? atomicAdd(&q.s.cursor[b], c) : 0;
+  }
+  __syncthreads();
+  if (bucket >= 0) q.s.order[q.s.offsets[bucket] + s_base[bucket] + rank] = (int32_t)i;
+}
+
 // ---------------------------------------------------------------------------
 // Order-keeping grouping for single-object queries: live rays are compacted
 // in their original order, so a 128-ray tile holds neighbouring rays (for
@@ -797,8 +834,14 @@ cudaError_t launch_group(const QueryLaunch &q, int *launches) {
     return cudaGetLastError();
   }
   scan_kernel<<<1, 1024, 0, q.stream>>>(q);
-  const int grid = grid_for(q.rays.n, 256, 152 * 16);
-  scatter_kernel<<<grid, 256, 0, q.stream>>>(q);
+  const int nb = q.n_slots * kBuckets;
+  if (nb <= 4096) {
+    const int64_t blocks = (q.rays.n + 1023) / 1024;
+    scatter_block_kernel<<<(unsigned)std::max<int64_t>(blocks, 1), 1024, 2 * nb * sizeof(int), q.stream>>>(q, nb);
+  } else {
+    const int grid = grid_for(q.rays.n, 256, 152 * 16);
+    scatter_kernel<<<grid, 256, 0, q.stream>>>(q);
+  }
   *launches += 2;
   return cudaGetLastError();
 }
