@@ -586,6 +586,29 @@ def test_tuning_choices_give_identical_results(ctx, torus):
     ctx.set_group_mode(keep[2])
 
 
+def test_grouping_with_many_objects_matches_oracle():
+    """The grouping sums each block's rays per bucket in shared memory while
+    the buckets (object slots x 33 point counts) fit it, and falls back to
+    per-warp global atomics beyond 124 slots. A context holding 126 objects
+    takes that path; the query of one of them must still match the oracle."""
+    c = lsnif.Context(0)
+    try:
+        cfg = I.cfg_icosphere_small()
+        tri = I.single_triangle((-0.8, -0.5, 0.2), (0.9, -0.2, 0.3), (0.1, 0.8, -0.2))
+        small = I.Config(V=8, H=18, L=4, F=2, log2_T=8, N_min=4, N_max=16, n_hidden=1, width=64, n_mat=1)
+        for j in range(125):
+            p = I.random_params(small, 100 + j)
+            c.load_object(tri, small, tables=p.tables, mlp=p.packed_mlp())
+        mesh = I.icosphere(3)
+        h, orc, p = _make(c, mesh, cfg, seed=3)
+        o = dict(h=h, orc=orc, p=p, mesh=mesh, cfg=cfg)
+        rays = I.rays_sphere_to_box(3000, 3.0, orc.bmin, orc.bmax, seed=21)
+        _query_compare(c, o, rays, lsnif.FP32_PLAIN, fp32_tol(cfg))
+        _query_compare(c, o, rays, lsnif.FP16_FUSED, FP16_TOL + fp32_tol(cfg))
+    finally:
+        c.close()
+
+
 def test_autotune_picks_valid_choices_and_keeps_results(ctx, torus):
     """lsnif_autotune times the fused-kernel variants on BF16 queries, the
     traversal kernels and groupings, then the variants again on FP16 queries
