@@ -25,3 +25,15 @@ def test_reference_arm_prints_the_contract_line():
     e2e = line["e2e"]
     assert e2e["value"] == line["value"] and e2e["unit"] == line["unit"]
     assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
+
+
+def test_committed_fused_profile_matches_the_kernel_sources():
+    """The roofline's DRAM traffic, L2 sectors per gathered point and tensor
+    activity come from the committed ncu summary of the fused kernel, tied to
+    a hash of its sources; a change to those sources must come with a new
+    capture (the bench reports null for them otherwise)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    for key in ("dram_bytes_per_launch", "l2_sectors_per_gathered_point", "tensor_pipe_active_pct"):
+        v = bench.recorded_profile(key)
+        assert v is not None and v > 0, key
