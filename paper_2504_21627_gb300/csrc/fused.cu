@@ -177,7 +177,7 @@ __device__ __noinline__ void mma_role(const FusedArgs *ap, uint8_t *base, uint32
   const uint32_t ring_stride = lay.ring_stride;
   {
     // =================== MMA warp ===================
-    int chunk_ctr = 0;
+    int rbuf = 0, ruse = 0;  // ring slot and pass of the next chunk
     const uint32_t idesc0 = idesc_f16(W, H16);
     for (int i = 0;; ++i) {
       const int tb = i & 1;
@@ -192,9 +192,15 @@ __device__ __noinline__ void mma_role(const FusedArgs *ap, uint8_t *base, uint32
       const uint32_t dacc = tmem + (uint32_t)(tb * W);
       bool ok = true;
       for (int s = 0; s < ti.kmax; ++s) {
-        const int c = chunk_ctr + s;
-        const int buf = c % nbuf;
-        if (!mbar_wait_sleep(su32(&b_full[buf]), (uint32_t)((c / nbuf) & 1), abort_flag)) {
+        // ring position of the next chunk, kept as counters (no division by
+        // the run-time ring size)
+        const int buf = rbuf;
+        const uint32_t phase = (uint32_t)(ruse & 1);
+        if (++rbuf == nbuf) {
+          rbuf = 0;
+          ++ruse;
+        }
+        if (!mbar_wait_sleep(su32(&b_full[buf]), phase, abort_flag)) {
           ok = false;
           break;
         }
@@ -211,7 +217,6 @@ __device__ __noinline__ void mma_role(const FusedArgs *ap, uint8_t *base, uint32
         __syncwarp();
       }
       if (!ok) break;
-      chunk_ctr += ti.kmax;
       if (lane == 0) mma_commit(su32(&b_accf[tb]));
       __syncwarp();
     }
@@ -581,7 +586,7 @@ __global__ void __launch_bounds__((NG + 1 + kEpiWarps) * 32, 1) fused_kernel(con
     int L = 0, n_in = 0;
     uint32_t mask = 0;
     const uint16_t *tab = nullptr;
-    int chunk_ctr = 0;
+    int rbuf = 0, ruse = 0;    // ring slot and pass of the next chunk
     int rot_g = 0, rot_o = 0;  // round-robin origin of the gather / other blocks
     for (int i = 0;; ++i) {
       const int tb = i & 1;
@@ -624,8 +629,18 @@ __global__ void __launch_bounds__((NG + 1 + kEpiWarps) * 32, 1) fused_kernel(con
         return make_float3(P[0], P[1], P[2]);
       };
       for (int s = 0; s < kmax; ++s) {
-        const int c = chunk_ctr + s;
-        const int buf = c % nbuf, use = c / nbuf;
+        // ring slot and pass of this warp's c-th chunk (c = use nbuf + buf),
+        // kept as counters: no division by the run-time ring size
+        const int buf = rbuf, use = ruse;
+        if (++rbuf == nbuf) {
+          rbuf = 0;
+          ++ruse;
+        }
+        // chunk c - 1 (whose exit points the copies read) and chunk
+        // c - nbuf + 1 (which read this slot's previous chunk)
+        const int pbuf = buf > 0 ? buf - 1 : nbuf - 1, puse = buf > 0 ? use : use - 1;
+        const bool wrap = buf + 1 == nbuf;
+        const int nbuf1 = wrap ? 0 : buf + 1, nuse1 = wrap ? use : use - 1;
         uint8_t *A = s_ring + buf * ring_stride;
         uint32_t all = 0;
 #pragma unroll
@@ -639,10 +654,7 @@ __global__ void __launch_bounds__((NG + 1 + kEpiWarps) * 32, 1) fused_kernel(con
         // thread waits, with or without items: an arrival on the full barrier
         // must not land in the phase of chunk c - nbuf.
         if (use > 0) mbar_wait_sleep(su32(&b_empty[buf]), (uint32_t)((use - 1) & 1), abort_flag);
-        {
-          const int cp = c - nbuf + 1;
-          if (cp >= 0 && cp < c) mbar_wait_sleep(su32(&b_full[cp % nbuf]), (uint32_t)((cp / nbuf) & 1), abort_flag);
-        }
+        if (nbuf > 1 && nuse1 >= 0) mbar_wait_sleep(su32(&b_full[nbuf1]), (uint32_t)(nuse1 & 1), abort_flag);
         // gathers: the lanes of a warp take consecutive entries (neighbouring
         // rays) at the same column group, so at coarse levels they share
         // corners and cache sectors
@@ -730,10 +742,8 @@ __global__ void __launch_bounds__((NG + 1 + kEpiWarps) * 32, 1) fused_kernel(con
         }
         // copies (entry point = previous chunk's exit point) and zero fills
         const int n_o = kListStride - ngt;
-        if (nct > 0 && first_o < nb_o) {  // copies read the previous chunk: it must be complete
-          const int cq = c - 1;
-          mbar_wait_sleep(su32(&b_full[cq % nbuf]), (uint32_t)((cq / nbuf) & 1), abort_flag);
-        }
+        if (nct > 0 && first_o < nb_o)  // copies read the previous chunk: it must be complete
+          mbar_wait_sleep(su32(&b_full[pbuf]), (uint32_t)(puse & 1), abort_flag);
         const float inv_o = 1.f / (float)max(n_o, 1);
         for (int b = first_o; b < nb_o; b += NG) {
           const int it = b * 32 + lane;
@@ -744,7 +754,7 @@ __global__ void __launch_bounds__((NG + 1 + kEpiWarps) * 32, 1) fused_kernel(con
             const int r = e & 127, j = e >> 7;
             uint4 outv = make_uint4(0u, 0u, 0u, 0u);
             if (t < nct) {
-              const uint8_t *Ap = s_ring + ((c - 1) % nbuf) * ring_stride;
+              const uint8_t *Ap = s_ring + pbuf * ring_stride;
               outv = *reinterpret_cast<const uint4 *>(Ap + core_off(r, G + g, a_sbo));
             }
             *reinterpret_cast<uint4 *>(A + core_off(r, j * G + g, a_sbo)) = outv;
@@ -755,7 +765,6 @@ __global__ void __launch_bounds__((NG + 1 + kEpiWarps) * 32, 1) fused_kernel(con
         fence_async_smem();
         mbar_arrive(su32(&b_full[buf]));
       }
-      chunk_ctr += kmax;
     }
   } else if (warp == kMmaWarp) {
     mma_role<F, W, XROWS, NG, H16>(&a, base, tmem);
