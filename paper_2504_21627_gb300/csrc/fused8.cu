@@ -178,37 +178,42 @@ __device__ __noinline__ void mma8_role(const Fused8Args *ap, uint8_t *base, uint
   const DevObject *objs = a.q.objs;
   const int nbuf = a.nbuf;
   const Smem8 S = carve8<F, W>(a, base);
-  int chunk_ctr = 0;
+  int rbuf = 0, ruse = 0;  // ring slot and pass of the next chunk
   const uint32_t idesc0 = idesc_e4m3(W);
   for (int i = 0;; ++i) {
     const int tb = i & 1;
-    if (!mbar_wait(su32(&S.ready[tb]), (uint32_t)((i >> 1) & 1), S.abort_flag)) break;
+    if (!mbar_wait_sleep(su32(&S.ready[tb]), (uint32_t)((i >> 1) & 1), S.abort_flag)) break;
     const TileInfo ti = S.info[tb];
     if (ti.stop) break;
     const DevObject &ob = objs[ti.slot];
     const int CHK = 2 * ob.L * F;  // bytes = elements
     const uint32_t sbo = (uint32_t)(CHK / 16) * 128u;
     const uint32_t slice = (uint32_t)W * CHK;
-    if (i >= 2 && !mbar_wait(su32(&S.acce[tb]), (uint32_t)(((i - 2) >> 1) & 1), S.abort_flag)) break;
+    if (i >= 2 && !mbar_wait_sleep(su32(&S.acce[tb]), (uint32_t)(((i - 2) >> 1) & 1), S.abort_flag)) break;
     tc_after();
     const uint32_t dacc = tmem + (uint32_t)(tb * W);
     bool ok = true;
     for (int s = 0; s < ti.kmax; ++s) {
-      const int c = chunk_ctr + s;
-      const int buf = c % nbuf, use = c / nbuf;
+      // ring slot and pass of the next chunk, kept as counters (no division
+      // by the run-time ring size)
+      const int buf = rbuf, use = ruse;
+      if (++rbuf == nbuf) {
+        rbuf = 0;
+        ++ruse;
+      }
       uint8_t *slot = S.ring + buf * S.ring_stride;
       // the slot's previous MMAs must be done before its weights are replaced
-      if (use > 0 && !mbar_wait(su32(&S.empty[buf]), (uint32_t)((use - 1) & 1), S.abort_flag)) {
+      if (use > 0 && !mbar_wait_sleep(su32(&S.empty[buf]), (uint32_t)((use - 1) & 1), S.abort_flag)) {
         ok = false;
         break;
       }
       // the weight slice travels by bulk copy while the gather warps fill
       // the A tile of the same slot
       if (lane == 0) bulk_g2s(su32(slot + S.slot_w), ob.w0_8 + (size_t)s * slice, slice, su32(&S.wfull[buf]));
-      const bool got_a = mbar_wait(su32(&S.full[buf]), (uint32_t)(use & 1), S.abort_flag);
+      const bool got_a = mbar_wait_sleep(su32(&S.full[buf]), (uint32_t)(use & 1), S.abort_flag);
       // the copy is waited for even after an abort: it must land before the
       // shared memory is released
-      const bool got_w = got_a ? mbar_wait(su32(&S.wfull[buf]), (uint32_t)(use & 1), S.abort_flag)
+      const bool got_w = got_a ? mbar_wait_sleep(su32(&S.wfull[buf]), (uint32_t)(use & 1), S.abort_flag)
                                : mbar_wait_teardown(su32(&S.wfull[buf]), (uint32_t)(use & 1));
       if (!got_a || !got_w) {
         if (!got_w) *S.abort_flag = 1;
@@ -228,7 +233,6 @@ __device__ __noinline__ void mma8_role(const Fused8Args *ap, uint8_t *base, uint
       __syncwarp();
     }
     if (!ok) break;
-    chunk_ctr += ti.kmax;
     if (lane == 0) mma_commit(su32(&S.accf[tb]));
     __syncwarp();
   }
@@ -376,7 +380,7 @@ __device__ __noinline__ void epilogue8_role(const Fused8Args *ap, uint8_t *base,
     if (!deferred) setup(i + 1, tn);
     if (last) stop_at = i + 1;
 
-    if (etid == 0) S.misc[2] = mbar_wait(su32(&S.accf[tb]), (uint32_t)((i >> 1) & 1), S.abort_flag) ? 0 : 1;
+    if (etid == 0) S.misc[2] = mbar_wait_sleep(su32(&S.accf[tb]), (uint32_t)((i >> 1) & 1), S.abort_flag) ? 0 : 1;
     named_sync(2, kEpiThreads);
     if (!S.misc[2]) {
       tc_after();
@@ -420,7 +424,7 @@ __device__ __noinline__ void epilogue8_role(const Fused8Args *ap, uint8_t *base,
               mma_e4m3(dacc, ad, bd, idesc, ks > 0 ? 1u : 0u);
             }
             mma_commit(su32(S.layer));
-            mbar_wait(su32(S.layer), (uint32_t)(layer_ctr & 1), S.abort_flag);
+            mbar_wait_sleep(su32(S.layer), (uint32_t)(layer_ctr & 1), S.abort_flag);
           }
           ++layer_ctr;
           named_sync(2, kEpiThreads);
@@ -509,11 +513,11 @@ __global__ void __launch_bounds__((NG + 1 + kEpiWarps) * 32, 1) fused8_kernel(co
     uint32_t mask = 0;
     const uint16_t *tab = nullptr;
     float s0 = 1.f;  // scale of the network input
-    int chunk_ctr = 0;
+    int rbuf = 0, ruse = 0;  // ring slot and pass of the next chunk
     int rot_g = 0, rot_o = 0;
     for (int i = 0;; ++i) {
       const int tb = i & 1;
-      if (!mbar_wait(su32(&S.ready[tb]), (uint32_t)((i >> 1) & 1), S.abort_flag)) break;
+      if (!mbar_wait_sleep(su32(&S.ready[tb]), (uint32_t)((i >> 1) & 1), S.abort_flag)) break;
       const TileInfo ti = S.info[tb];
       if (ti.stop) break;
       const int kmax = ti.kmax;
@@ -532,8 +536,18 @@ __global__ void __launch_bounds__((NG + 1 + kEpiWarps) * 32, 1) fused8_kernel(co
       const uint32_t a_sbo = (uint32_t)(CHK / 16) * 128u;
       const size_t lstride = (size_t)(mask + 1) * F;
       for (int s = 0; s < kmax; ++s) {
-        const int c = chunk_ctr + s;
-        const int buf = c % nbuf, use = c / nbuf;
+        // ring slot and pass of this warp's c-th chunk (c = use nbuf + buf),
+        // kept as counters: no division by the run-time ring size
+        const int buf = rbuf, use = ruse;
+        if (++rbuf == nbuf) {
+          rbuf = 0;
+          ++ruse;
+        }
+        // chunk c - 1 (whose exit points the copies read) and chunk
+        // c - nbuf + 1 (which read this slot's previous chunk)
+        const int pbuf = buf > 0 ? buf - 1 : nbuf - 1, puse = buf > 0 ? use : use - 1;
+        const bool wrap = buf + 1 == nbuf;
+        const int nbuf1 = wrap ? 0 : buf + 1, nuse1 = wrap ? use : use - 1;
         uint8_t *A = S.ring + buf * S.ring_stride;
         uint32_t all = 0;
 #pragma unroll
@@ -542,11 +556,8 @@ __global__ void __launch_bounds__((NG + 1 + kEpiWarps) * 32, 1) fused8_kernel(co
         const int n_gi = ngt * G, n_oi = (kListStride - ngt) * G;
         const int nb_g = (n_gi + 31) >> 5, nb_o = (n_oi + 31) >> 5;
         const int first_g = (warp - rot_g + NG) % NG, first_o = (warp - rot_o + NG) % NG;
-        if (use > 0) mbar_wait(su32(&S.empty[buf]), (uint32_t)((use - 1) & 1), S.abort_flag);
-        {
-          const int cp = c - nbuf + 1;
-          if (cp >= 0 && cp < c) mbar_wait(su32(&S.full[cp % nbuf]), (uint32_t)((cp / nbuf) & 1), S.abort_flag);
-        }
+        if (use > 0) mbar_wait_sleep(su32(&S.empty[buf]), (uint32_t)((use - 1) & 1), S.abort_flag);
+        if (nbuf > 1 && nuse1 >= 0) mbar_wait_sleep(su32(&S.full[nbuf1]), (uint32_t)(nuse1 & 1), S.abort_flag);
         const float inv_g = 1.f / (float)max(ngt, 1);
         for (int b = first_g; b < nb_g; b += NG) {
           const int it = b * 32 + lane;
@@ -583,10 +594,7 @@ __global__ void __launch_bounds__((NG + 1 + kEpiWarps) * 32, 1) fused8_kernel(co
           }
         }
         const int n_o = kListStride - ngt;
-        if (nct > 0 && first_o < nb_o) {
-          const int cq = c - 1;
-          mbar_wait(su32(&S.full[cq % nbuf]), (uint32_t)((cq / nbuf) & 1), S.abort_flag);
-        }
+        if (nct > 0 && first_o < nb_o) mbar_wait_sleep(su32(&S.full[pbuf]), (uint32_t)(puse & 1), S.abort_flag);
         const float inv_o = 1.f / (float)max(n_o, 1);
         for (int b = first_o; b < nb_o; b += NG) {
           const int it = b * 32 + lane;
@@ -597,7 +605,7 @@ __global__ void __launch_bounds__((NG + 1 + kEpiWarps) * 32, 1) fused8_kernel(co
             const int r = e & 127, j = e >> 7;
             uint4 outv = make_uint4(0u, 0u, 0u, 0u);
             if (t < nct) {
-              const uint8_t *Ap = S.ring + ((c - 1) % nbuf) * S.ring_stride;
+              const uint8_t *Ap = S.ring + pbuf * S.ring_stride;
               outv = *reinterpret_cast<const uint4 *>(Ap + core_off(r, G + g, a_sbo));
             }
             *reinterpret_cast<uint4 *>(A + core_off(r, j * G + g, a_sbo)) = outv;
@@ -608,7 +616,6 @@ __global__ void __launch_bounds__((NG + 1 + kEpiWarps) * 32, 1) fused8_kernel(co
         fence_async_smem();
         mbar_arrive(su32(&S.full[buf]));
       }
-      chunk_ctr += kmax;
     }
   } else if (warp == kMmaWarp) {
     mma8_role<F, W, NG>(&a, base, tmem);
