@@ -337,7 +337,8 @@ def batched_run(steps: int, warmup: int, total_rays: int):
         "value_fp32": n / (ms32.mean() / 1e3) / 1e6, "ms_bf16": float(ms16.mean()), "ms_fp32": float(ms32.mean()),
         "p50_ms_bf16": float(np.percentile(ms16, 50)), "p99_ms_bf16": float(np.percentile(ms16, 99)),
         "live_frac": prof.n_live / n, "mean_points_per_live_ray": prof.n_points / max(prof.n_live, 1),
-        "fused_variant": lsnif.Context.variants()[variant], "device_gb": ctx.device_bytes() / 1e9,
+        "fused_variant": lsnif.Context.variants()[variant], "group_mode": ctx.tuning()[2],
+        "device_gb": ctx.device_bytes() / 1e9,
         "l2": "flushed before every timed step", "graph": True, "setup_s": t_setup}
     ctx.close()
     return out
@@ -857,7 +858,8 @@ def main():
     ap.add_argument("--scene-net", default="stress", choices=["stress", "small"])
     ap.add_argument("--variant8", type=int, default=None, help="FP8 fused-kernel variant for --workload scene")
     ap.add_argument("--group-mode", type=int, default=None,
-                    help="stress1 / scene: live rays grouped by (object, point count) (0) or kept in ray order (1)")
+                    help="stress1 / scene: live rays grouped by (object, point count) (0), kept in ray order (1) "
+                         "or sorted by the cell of their first point (2)")
     ap.add_argument("--scene-objects", type=int, default=8, help="unique objects (below 8 only for profiling)")
     ap.add_argument("--scene-instances", type=int, default=32)
     ap.add_argument("--scene-spp", type=int, default=4)

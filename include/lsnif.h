@@ -491,8 +491,8 @@ LSNIF_API int lsnif_set_trace_mode(lsnif_ctx *ctx, int mode);
 
 /* Time every fused-kernel variant on `rays` (DEVICE buffers, `reps` BF16
  * queries each after one warm-up, CUDA events on `stream`, synchronous), keep
- * the fastest, then the other traversal kernel and (single-object rays) the
- * other grouping, keeping each if faster; then time every variant again with
+ * the fastest, then the other traversal kernel and the other groupings,
+ * keeping each if faster; then time every variant again with
  * FP16 queries and keep the fastest for LSNIF_FP16_FUSED (the FP16 kernel
  * holds no lo weights, so its shared memory and L1 differ). *chosen (may be
  * NULL) receives the BF16 variant index. Results of the queries are
@@ -504,8 +504,13 @@ LSNIF_API int lsnif_autotune(lsnif_ctx *ctx, const lsnif_rays *rays, int reps, v
  * each object: single-object queries keep the original order exactly,
  * multi-object queries (and instanced scenes) group by object only and keep
  * each warp's run of consecutive rays together (neighbouring primary rays
- * share voxels and lattice cells, which the gather's caches exploit). Both
- * compute identical results. */
+ * share voxels and lattice cells, which the gather's caches exploit);
+ * 2 = by object, then by the Morton code of the cell (64 per axis of the
+ * object's box, fewer when more than 8 objects are loaded: at most 2^21
+ * object-cell pairs) that holds the ray's first boundary point, so that
+ * tiles hold nearby points whatever order the rays come in (secondary rays,
+ * rays shuffled across objects). All compute identical results;
+ * LSNIF_ERR_INVALID_ARG for any other mode. */
 LSNIF_API int lsnif_set_group_mode(lsnif_ctx *ctx, int mode);
 
 /* The context's current fused-kernel variant of BF16 queries, traversal

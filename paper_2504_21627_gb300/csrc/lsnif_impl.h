@@ -128,6 +128,8 @@ struct QueryScratch {
   int32_t *meta;     // [0] n_live, [1] n_tiles, [2] n_points, [3] tile cursor
   float *X;          // FP32 path: chunk of tiles x kTileM rows x ldx features
   int32_t *blk;      // coherent grouping: live rays and points per block of kGroupBlock rays, then offsets
+  int32_t *bins;     // spatial grouping: live rays per (object, cell) bin, then each bin's first position
+  int32_t *bin_sums; // spatial grouping: block sums of the bins' scan (kSpatialBins / 1024 + 2)
   int32_t max_tiles; // upper bound on tiles (n / kTileM + n_slots)
   int32_t wmax;      // FP32 path: widest layer (hidden width or padded output)
 };
@@ -143,16 +145,30 @@ struct QueryLaunch {
   cudaStream_t stream;
   int trace_mode;         // traversal kernel: 0 one ray per thread, 1 persistent lanes
   int group_mode;         // 0: live rays grouped by (object, k desc); 1: one object, original order kept;
-                          // 2: grouped by object only, warps of consecutive rays kept together
+                          // 2: grouped by object only, warps of consecutive rays kept together;
+                          // 3: by object, then by the Morton cell of the first boundary point
   int single_slot;        // object slot of a single-object query (group_mode 1)
 };
 
 constexpr int kGroupBlock = 4096;  // rays per block of the order-keeping grouping
+constexpr int64_t kSpatialBins = int64_t(1) << 21;  // spatial grouping: (object, cell) bins at most
+
+// Spatial grouping: bits of a cell's Morton code, 3 m for 2^m cells per axis
+// of the unit cube -- m = 6 (64 per axis) where the objects' bins fit
+// kSpatialBins, fewer for many objects.
+inline int spatial_cell_bits(int n_slots) {
+  int m = 6;
+  while (m > 1 && ((int64_t)n_slots << (3 * m)) > kSpatialBins) --m;
+  return 3 * m;
+}
 
 // ---- launchers (query.cu) ----
 // Traversal + histogram; returns kernels launched (adds to *launches).
 cudaError_t launch_trace(const QueryLaunch &q, int *launches);
 cudaError_t launch_group(const QueryLaunch &q, int *launches);
+// exclusive scan of v[0..n) in place; sums needs (n + 1023) / 1024 + 1
+// entries and receives the total at sums[(n + 1023) / 1024]
+cudaError_t launch_exclusive_scan(int32_t *v, int64_t n, int32_t *sums, cudaStream_t st);
 cudaError_t launch_plain_tail(const QueryLaunch &q, int ldx, int chunk_tiles, int *launches);
 cudaError_t launch_trace_only(const DevObject *dobj, const RaysArg &rays, int32_t *k, float *t01,
                               float *pts, int32_t *vox, int *err, cudaStream_t st);

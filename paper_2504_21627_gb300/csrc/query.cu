@@ -372,8 +372,8 @@ __global__ void __launch_bounds__(1024) scan_kernel(QueryLaunch q) {
       int start = run;
       for (int k = kMaxCap; k >= 1; --k) {
         int c = q.s.counts[s * kBuckets + k];
-        // group mode 2: one bucket per object (bucket k = 1 takes all)
-        q.s.offsets[s * kBuckets + k] = q.group_mode == 2 ? start : run;
+        // group modes 2 and 3: one bucket per object (bucket k = 1 takes all)
+        q.s.offsets[s * kBuckets + k] = q.group_mode >= 2 ? start : run;
         q.s.cursor[s * kBuckets + k] = 0;
         run += c;
         pts += 2 * k * c;
@@ -584,6 +584,137 @@ __global__ void __launch_bounds__(1024) group_scatter_kernel(QueryLaunch q) {
     if (live) q.s.order[base + s_warp[warp] + __popc(m & ((1u << lane) - 1u))] = (int32_t)i;
     base += s_total;
     __syncthreads();
+  }
+}
+
+// exclusive scan of n int32 in place, in blocks of 1024; block totals to sums
+__global__ void __launch_bounds__(1024) scan_block_kernel(int32_t *v, int64_t n, int32_t *sums) {
+  __shared__ int32_t ws[32];
+  const int64_t i = (int64_t)blockIdx.x * 1024 + threadIdx.x;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int32_t x = i < n ? v[i] : 0;
+  int32_t inc = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += y;
+  }
+  if (lane == 31) ws[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    int32_t s = ws[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int32_t y = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += y;
+    }
+    ws[lane] = s;
+  }
+  __syncthreads();
+  const int32_t before = (w > 0 ? ws[w - 1] : 0) + inc - x;
+  if (i < n) v[i] = before;
+  if (threadIdx.x == 1023) sums[blockIdx.x] = ws[31];
+}
+
+// single block: exclusive scan of the block sums (any count), total at sums[nb]
+__global__ void __launch_bounds__(1024) scan_sums_kernel(int32_t *sums, int nb) {
+  __shared__ int32_t carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __shared__ int32_t ws[32];
+  for (int base = 0; base < nb; base += 1024) {
+    const int i = base + threadIdx.x;
+    const int32_t x = i < nb ? sums[i] : 0;
+    int32_t inc = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += y;
+    }
+    if (lane == 31) ws[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+      int32_t s = ws[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int32_t y = __shfl_up_sync(0xffffffffu, s, o);
+        if (lane >= o) s += y;
+      }
+      ws[lane] = s;
+    }
+    __syncthreads();
+    const int32_t before = carry + (w > 0 ? ws[w - 1] : 0) + inc - x;
+    if (i < nb) sums[i] = before;
+    __syncthreads();
+    if (threadIdx.x == 0) carry += ws[31];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) sums[nb] = carry;
+}
+
+__global__ void scan_add_kernel(int32_t *v, int64_t n, const int32_t *sums) {
+  const int64_t i = (int64_t)blockIdx.x * 1024 + threadIdx.x;
+  if (i < n) v[i] += sums[blockIdx.x];
+}
+
+// ---------------------------------------------------------------------------
+// Spatial grouping (group mode 3): live rays sorted by object, then by the
+// Morton code of the cell (2^m per axis of the object's unit cube) that
+// holds their first boundary point -- a counting sort over (object, cell)
+// bins: count, exclusive scan, scatter. A 128-ray tile then holds rays whose
+// points lie close together whatever order the rays came in (secondary
+// rays, rays shuffled across objects), so the gathers' corner loads share
+// L1 and L2 lines. Objects stay in ascending slot order, so the object
+// ranges and tiles of scan_kernel (one bucket per object) hold as they are.
+// Rays of one bin land in any order; no result depends on it.
+// ---------------------------------------------------------------------------
+// bits 0..7 of v moved to bits 0, 3, 6, ..., 21
+__device__ __forceinline__ uint32_t spread_bits3(uint32_t v) {
+  v &= 0xffu;
+  v = (v | (v << 8)) & 0x0300f00fu;
+  v = (v | (v << 4)) & 0x030c30c3u;
+  v = (v | (v << 2)) & 0x09249249u;
+  return v;
+}
+
+// (object slot, Morton cell) bin of ray i, or -1 when it is not live
+__device__ __forceinline__ int spatial_bin(const QueryLaunch &q, int64_t i, int cell_bits) {
+  if (q.s.k[i] == 0) return -1;
+  const int s = q.s.slot[i];
+  if (s < 0) return -1;
+  const float *P = q.s.pts + (size_t)i * q.H_max * 3;
+  const int side = 1 << (cell_bits / 3);
+  const float scale = (float)side;
+  uint32_t c[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) c[a] = (uint32_t)min(max((int)(P[a] * scale), 0), side - 1);
+  return (s << cell_bits) | (int)(spread_bits3(c[0]) | (spread_bits3(c[1]) << 1) | (spread_bits3(c[2]) << 2));
+}
+
+__global__ void __launch_bounds__(256) spatial_count_kernel(QueryLaunch q, int cell_bits) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int bin = i < q.rays.n ? spatial_bin(q, i, cell_bits) : -1;
+  const unsigned active = __ballot_sync(0xffffffffu, bin >= 0);
+  if (bin >= 0) {
+    const unsigned peers = __match_any_sync(active, bin);
+    if ((int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&q.s.bins[bin], __popc(peers));
+  }
+}
+
+// bins hold the bins' first positions; each warp takes its rays' ranks
+__global__ void __launch_bounds__(256) spatial_scatter_kernel(QueryLaunch q, int cell_bits) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int bin = i < q.rays.n ? spatial_bin(q, i, cell_bits) : -1;
+  const unsigned active = __ballot_sync(0xffffffffu, bin >= 0);
+  if (bin >= 0) {
+    const unsigned peers = __match_any_sync(active, bin);
+    const int leader = __ffs(peers) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(&q.s.bins[bin], __popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    q.s.order[base + __popc(peers & ((1u << lane) - 1u))] = (int32_t)i;
   }
 }
 
@@ -833,6 +964,20 @@ cudaError_t launch_group(const QueryLaunch &q, int *launches) {
     *launches += 3;
     return cudaGetLastError();
   }
+  if (q.group_mode == 3) {
+    const int bits = spatial_cell_bits(q.n_slots);
+    const int64_t nbins = (int64_t)q.n_slots << bits;
+    const unsigned blocks = (unsigned)std::max<int64_t>((q.rays.n + 255) / 256, 1);
+    scan_kernel<<<1, 1024, 0, q.stream>>>(q);
+    cudaError_t e = cudaMemsetAsync(q.s.bins, 0, (size_t)nbins * 4, q.stream);
+    if (e != cudaSuccess) return e;
+    spatial_count_kernel<<<blocks, 256, 0, q.stream>>>(q, bits);
+    e = launch_exclusive_scan(q.s.bins, nbins, q.s.bin_sums, q.stream);
+    if (e != cudaSuccess) return e;
+    spatial_scatter_kernel<<<blocks, 256, 0, q.stream>>>(q, bits);
+    *launches += 6;
+    return cudaGetLastError();
+  }
   scan_kernel<<<1, 1024, 0, q.stream>>>(q);
   const int nb = q.n_slots * kBuckets;
   if (nb <= 4096) {
@@ -843,6 +988,15 @@ cudaError_t launch_group(const QueryLaunch &q, int *launches) {
     scatter_kernel<<<grid, 256, 0, q.stream>>>(q);
   }
   *launches += 2;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_exclusive_scan(int32_t *v, int64_t n, int32_t *sums, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const int64_t nb = (n + 1023) / 1024;
+  scan_block_kernel<<<(unsigned)nb, 1024, 0, st>>>(v, n, sums);
+  scan_sums_kernel<<<1, 1024, 0, st>>>(sums, (int)nb);
+  scan_add_kernel<<<(unsigned)nb, 1024, 0, st>>>(v, n, sums);
   return cudaGetLastError();
 }
 

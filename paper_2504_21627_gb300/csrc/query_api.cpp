@@ -36,7 +36,8 @@ size_t lsnif::workspace_bytes(int64_t n, int H, int n_slots, int n_in) {
   size_t b = al((size_t)n * H * 12) + al((size_t)n * 8) + al((size_t)n) + al((size_t)n * 4) + al((size_t)n * 2) +
              al((size_t)n * 4) +
              3 * al((size_t)n_slots * kBuckets * 4) + al((size_t)mt * 12) + al(64 * 4) +
-             al((size_t)(n / kGroupBlock + 2) * 8);
+             al((size_t)(n / kGroupBlock + 2) * 8) + al((size_t)kSpatialBins * 4) +
+             al((size_t)(kSpatialBins / 1024 + 2) * 4);
   if (n_in > 0) b += al((size_t)std::min(mt, kChunkTiles) * kTileM * n_in * 4);
   return b;
 }
@@ -93,6 +94,8 @@ static QueryScratch carve(Workspace *ws, int64_t n, int H, int n_slots, int n_in
   s.tiles = c.take<int32_t>((size_t)mt * 12);
   s.meta = c.take<int32_t>(64 * 4);
   s.blk = c.take<int32_t>((size_t)(N / kGroupBlock + 2) * 8);
+  s.bins = c.take<int32_t>((size_t)kSpatialBins * 4);
+  s.bin_sums = c.take<int32_t>((size_t)(kSpatialBins / 1024 + 2) * 4);
   s.X = ws->cap_nin > 0 ? c.take<float>((size_t)std::min(mt, kChunkTiles) * kTileM * ws->cap_nin * 4) : nullptr;
   s.max_tiles = max_tiles_for(n, n_slots);
   return s;
@@ -224,7 +227,7 @@ int lsnif::run_query(lsnif_ctx *ctx, Workspace *ws, const lsnif_rays *r, lsnif_h
   q.err = err;
   q.stream = st;
   q.trace_mode = ctx->trace_mode;
-  q.group_mode = ctx->group_mode == 1 ? (r->obj ? 2 : 1) : 0;
+  q.group_mode = ctx->group_mode == 2 ? 3 : ctx->group_mode == 1 ? (r->obj ? 2 : 1) : 0;
   q.single_slot = r->obj ? 0 : sh.rep->slot;
   int launches = 0;
   if (profile) cudaEventRecord(ctx->ev[0], st);
@@ -662,10 +665,10 @@ extern "C" int lsnif_autotune(lsnif_ctx *ctx, const lsnif_rays *rays, int reps, 
       if (ms < best_ms) { best_t = t; best_ms = ms; }
     }
     ctx->trace_mode = best_t;
-    // grouping: by (object, point count), or rays kept in order within
-    // their object
+    // grouping: by (object, point count), rays kept in order within their
+    // object, or sorted by the cell of their first point
     if (rc == LSNIF_OK) {
-      for (int g = 0; g < 2 && rc == LSNIF_OK; ++g) {
+      for (int g = 0; g < 3 && rc == LSNIF_OK; ++g) {
         if (g == best_g) continue;
         ctx->group_mode = g;
         float ms = 0.f;
@@ -713,7 +716,7 @@ extern "C" int lsnif_get_tuning(lsnif_ctx *ctx, int *variant, int *trace_mode, i
 }
 
 extern "C" int lsnif_set_group_mode(lsnif_ctx *ctx, int mode) {
-  if (!ctx || (mode != 0 && mode != 1)) return fail(LSNIF_ERR_INVALID_ARG, "lsnif_set_group_mode: bad mode %d", mode);
+  if (!ctx || mode < 0 || mode > 2) return fail(LSNIF_ERR_INVALID_ARG, "lsnif_set_group_mode: bad mode %d", mode);
   ctx->group_mode = mode;
   return LSNIF_OK;
 }

@@ -59,77 +59,6 @@ __global__ void scene_count_kernel(RaysArg r, const DevInstance *inst, int n_ins
   count[i] = c;
 }
 
-// exclusive scan of n int32 in place, in blocks of 1024; block totals to sums
-__global__ void __launch_bounds__(1024) scan_block_kernel(int32_t *v, int64_t n, int32_t *sums) {
-  __shared__ int32_t ws[32];
-  const int64_t i = (int64_t)blockIdx.x * 1024 + threadIdx.x;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int32_t x = i < n ? v[i] : 0;
-  int32_t inc = x;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-    if (lane >= o) inc += y;
-  }
-  if (lane == 31) ws[w] = inc;
-  __syncthreads();
-  if (w == 0) {
-    int32_t s = ws[lane];
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int32_t y = __shfl_up_sync(0xffffffffu, s, o);
-      if (lane >= o) s += y;
-    }
-    ws[lane] = s;
-  }
-  __syncthreads();
-  const int32_t before = (w > 0 ? ws[w - 1] : 0) + inc - x;
-  if (i < n) v[i] = before;
-  if (threadIdx.x == 1023) sums[blockIdx.x] = ws[31];
-}
-
-// single block: exclusive scan of the block sums (any count), total at sums[nb]
-__global__ void __launch_bounds__(1024) scan_sums_kernel(int32_t *sums, int nb) {
-  __shared__ int32_t carry;
-  if (threadIdx.x == 0) carry = 0;
-  __syncthreads();
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  __shared__ int32_t ws[32];
-  for (int base = 0; base < nb; base += 1024) {
-    const int i = base + threadIdx.x;
-    const int32_t x = i < nb ? sums[i] : 0;
-    int32_t inc = x;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-      if (lane >= o) inc += y;
-    }
-    if (lane == 31) ws[w] = inc;
-    __syncthreads();
-    if (w == 0) {
-      int32_t s = ws[lane];
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int32_t y = __shfl_up_sync(0xffffffffu, s, o);
-        if (lane >= o) s += y;
-      }
-      ws[lane] = s;
-    }
-    __syncthreads();
-    const int32_t before = carry + (w > 0 ? ws[w - 1] : 0) + inc - x;
-    if (i < nb) sums[i] = before;
-    __syncthreads();
-    if (threadIdx.x == 0) carry += ws[31];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) sums[nb] = carry;
-}
-
-__global__ void scan_add_kernel(int32_t *v, int64_t n, const int32_t *sums) {
-  const int64_t i = (int64_t)blockIdx.x * 1024 + threadIdx.x;
-  if (i < n) v[i] += sums[blockIdx.x];
-}
-
 struct PairOut {
   float *ox, *oy, *oz, *dx, *dy, *dz, *tmin, *tmax;
   uint32_t *obj;
@@ -313,10 +242,7 @@ extern "C" int lsnif_query_scene(lsnif_ctx *ctx, const lsnif_rays *rays, const l
     e = cudaMemcpyAsync(offset, count, (size_t)n * 4, cudaMemcpyDeviceToDevice, st);
   }
   if (e == cudaSuccess) {
-    scan_block_kernel<<<(unsigned)nb, 1024, 0, st>>>(offset, n, sums);
-    scan_sums_kernel<<<1, 1024, 0, st>>>(sums, (int)nb);
-    scan_add_kernel<<<(unsigned)nb, 1024, 0, st>>>(offset, n, sums);
-    e = cudaGetLastError();
+    e = launch_exclusive_scan(offset, n, sums, st);
   }
   int32_t total = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&total, sums + nb, 4, cudaMemcpyDeviceToHost, st);

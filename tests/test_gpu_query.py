@@ -426,16 +426,20 @@ def test_multi_object_batch_equals_single_object_queries(ctx, sphere, torus):
     perm = np.random.default_rng(5).permutation(both.shape[1])
     both = np.ascontiguousarray(both[:, perm])
     handles = np.ascontiguousarray(handles[perm])
-    for prec in (lsnif.FP32_PLAIN, lsnif.BF16_FUSED):
-        mixed = ctx.query_rays(_cuda(both), obj_per_ray=_cuda(handles.view(np.int32)), precision=prec)
-        a = ctx.query_rays(_cuda(ra), obj=sphere["h"], precision=prec)
-        b = ctx.query_rays(_cuda(rb), obj=torus["h"], precision=prec)
-        ctx.check()
-        inv = np.argsort(perm)
-        for f in ("hit", "t", "mat"):
-            m = getattr(mixed, f).cpu().numpy()[inv]
-            single = np.concatenate([getattr(a, f).cpu().numpy(), getattr(b, f).cpu().numpy()])
-            assert np.array_equal(m, single), f
+    keep = ctx.tuning()
+    for gm in (0, 1, 2):
+        ctx.set_group_mode(gm)
+        for prec in (lsnif.FP32_PLAIN, lsnif.BF16_FUSED):
+            mixed = ctx.query_rays(_cuda(both), obj_per_ray=_cuda(handles.view(np.int32)), precision=prec)
+            a = ctx.query_rays(_cuda(ra), obj=sphere["h"], precision=prec)
+            b = ctx.query_rays(_cuda(rb), obj=torus["h"], precision=prec)
+            ctx.check()
+            inv = np.argsort(perm)
+            for f in ("hit", "t", "mat"):
+                m = getattr(mixed, f).cpu().numpy()[inv]
+                single = np.concatenate([getattr(a, f).cpu().numpy(), getattr(b, f).cpu().numpy()])
+                assert np.array_equal(m, single), (gm, prec, f)
+    ctx.set_group_mode(keep[2])
 
 
 def test_unknown_handle_is_reported_not_run(ctx, sphere):
@@ -567,7 +571,7 @@ def test_tuning_choices_give_identical_results(ctx, torus):
     keep = ctx.tuning()
     for prec in (lsnif.FP32_PLAIN, lsnif.BF16_FUSED, lsnif.FP16_FUSED):
         for tm in (0, 1):
-            for gm in (0, 1):
+            for gm in (0, 1, 2):
                 for v in (range(len(lsnif.Context.variants())) if prec != lsnif.FP32_PLAIN else [0]):
                     ctx.set_trace_mode(tm)
                     ctx.set_group_mode(gm)
@@ -583,6 +587,32 @@ def test_tuning_choices_give_identical_results(ctx, torus):
                             (prec, tm, gm, v)
     ctx.set_variant(keep[0])
     ctx.set_trace_mode(keep[1])
+    ctx.set_group_mode(keep[2])
+
+
+def test_spatial_grouping_is_independent_of_the_ray_order(ctx, torus):
+    """Group mode 2 sorts live rays by the cell of their first boundary
+    point, so tiles are built from the same neighbourhoods whatever order
+    the rays arrive in. Shuffled rays must give, ray for ray, the bits that
+    the ordered rays give under every grouping."""
+    cam = I.seeded_camera(2)
+    base = np.ascontiguousarray(I.rays_pinhole(cam, px0=400, py0=600, w=512, h=384))
+    perm = np.random.default_rng(17).permutation(base.shape[1])
+    inv = torch.from_numpy(np.argsort(perm))
+    shuffled = _cuda(np.ascontiguousarray(base[:, perm]))
+    keep = ctx.tuning()
+    for prec in (lsnif.FP32_PLAIN, lsnif.BF16_FUSED, lsnif.FP16_FUSED):
+        ctx.set_group_mode(1)
+        ref = ctx.query_rays(_cuda(base), obj=torus["h"], precision=prec, logits=True)
+        ref = (ref.hit.cpu(), ref.t.cpu(), ref.mat.cpu(), ref.logits.cpu())
+        assert ref[0].sum() > 10000
+        for gm in (0, 1, 2):
+            ctx.set_group_mode(gm)
+            out = ctx.query_rays(shuffled, obj=torus["h"], precision=prec, logits=True)
+            ctx.check()
+            got = (out.hit.cpu()[inv], out.t.cpu()[inv], out.mat.cpu()[inv], out.logits.cpu()[inv])
+            for a, b in zip(ref, got):
+                assert torch.equal(torch.nan_to_num(a, nan=-1e30), torch.nan_to_num(b, nan=-1e30)), (prec, gm)
     ctx.set_group_mode(keep[2])
 
 
@@ -603,8 +633,10 @@ def test_grouping_with_many_objects_matches_oracle():
         h, orc, p = _make(c, mesh, cfg, seed=3)
         o = dict(h=h, orc=orc, p=p, mesh=mesh, cfg=cfg)
         rays = I.rays_sphere_to_box(3000, 3.0, orc.bmin, orc.bmax, seed=21)
-        _query_compare(c, o, rays, lsnif.FP32_PLAIN, fp32_tol(cfg))
-        _query_compare(c, o, rays, lsnif.FP16_FUSED, FP16_TOL + fp32_tol(cfg))
+        for gm in (0, 2):   # 2: 126 objects take 4096 cells each
+            c.set_group_mode(gm)
+            _query_compare(c, o, rays, lsnif.FP32_PLAIN, fp32_tol(cfg))
+            _query_compare(c, o, rays, lsnif.FP16_FUSED, FP16_TOL + fp32_tol(cfg))
     finally:
         c.close()
 
@@ -626,7 +658,7 @@ def test_autotune_picks_valid_choices_and_keeps_results(ctx, torus):
     ctx.check()
     assert 0 <= v < len(lsnif.Context.variants())
     tv, tm, gm = ctx.tuning()
-    assert tv == v and tm in (0, 1) and gm in (0, 1)
+    assert tv == v and tm in (0, 1) and gm in (0, 1, 2)
     for prec in (lsnif.BF16_FUSED, lsnif.FP16_FUSED):
         out = ctx.query_rays(rays, obj=torus["h"], precision=prec, logits=True)
         ctx.check()
