@@ -337,7 +337,8 @@ def batched_run(steps: int, warmup: int, total_rays: int):
         "value_fp32": n / (ms32.mean() / 1e3) / 1e6, "ms_bf16": float(ms16.mean()), "ms_fp32": float(ms32.mean()),
         "p50_ms_bf16": float(np.percentile(ms16, 50)), "p99_ms_bf16": float(np.percentile(ms16, 99)),
         "live_frac": prof.n_live / n, "mean_points_per_live_ray": prof.n_points / max(prof.n_live, 1),
-        "fused_variant": lsnif.Context.variants()[variant], "group_mode": ctx.tuning()[2],
+        "fused_variant": lsnif.Context.variants()[variant], "trace_mode": ctx.tuning()[1],
+        "group_mode": ctx.tuning()[2],
         "device_gb": ctx.device_bytes() / 1e9,
         "l2": "flushed before every timed step", "graph": True, "setup_s": t_setup}
     ctx.close()
@@ -609,10 +610,12 @@ def bench_stress1(args):
         ctx.set_variant8(args.variant8)
     if args.group_mode is not None:
         ctx.set_group_mode(args.group_mode)
+    if args.trace_mode is not None:
+        ctx.set_trace_mode(args.trace_mode)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
     out = {"workload": "stress1", "network": "L=16 F=4 T=2^21, 1152-128x4-12", "rays": n,
-           "group_mode": ctx.tuning()[2]}
+           "trace_mode": ctx.tuning()[1], "group_mode": ctx.tuning()[2]}
     for name, prec, steps in (("fp16", lsnif.FP16_FUSED, args.steps), ("fp8", lsnif.FP8_FUSED, args.steps),
                               ("fp32", lsnif.FP32_PLAIN, 3)):
         res = ctx.query_rays(rays, obj=obj, precision=prec)
@@ -777,8 +780,11 @@ def bench_scene(args):
                                        keep_mesh=args.primary == "raster", bvh_below_faces=args.bvh_below_faces))
     if args.variant8 is not None:
         ctx.set_variant8(args.variant8)
-    if args.group_mode is not None:
-        ctx.set_group_mode(args.group_mode)
+    # bounce rays arrive in no spatial order and pairs mix 8 objects: the
+    # presorted traversal and the spatial grouping (62.5 against 74 ms per
+    # FP16 frame with the in-order kernels)
+    ctx.set_group_mode(2 if args.group_mode is None else args.group_mode)
+    ctx.set_trace_mode(2 if args.trace_mode is None else args.trace_mode)
     insts = [(handles[o], A, b) for o, A, b in I.seeded_instances(args.scene_instances, len(spec), seed=9,
                                                                    spread=10.0)]
     if args.primary == "raster":
@@ -804,6 +810,7 @@ def bench_scene(args):
     out = {"workload": "scene", "metric": "Mrays/s over 3 bounces of an instanced scene (misses included)",
            "instances": len(insts), "unique_objects": len(spec), "rays_per_bounce": n,
            "mesh_objects": int(sum(ctx.object_info(h).kind == 1 for h in handles)),
+           "trace_mode": ctx.tuning()[1], "group_mode": ctx.tuning()[2],
            "network": "L=16 F=4 T=2^21, 1152-128x4-12" if stress else "L=16 F=2 T=2^21, 576-64x4-12"}
     fast = (("fp16", lsnif.FP16_FUSED, max(3, args.steps // 4)), ("fp8", lsnif.FP8_FUSED, max(3, args.steps // 4))) \
         if stress else \
@@ -859,7 +866,10 @@ def main():
     ap.add_argument("--variant8", type=int, default=None, help="FP8 fused-kernel variant for --workload scene")
     ap.add_argument("--group-mode", type=int, default=None,
                     help="stress1 / scene: live rays grouped by (object, point count) (0), kept in ray order (1) "
-                         "or sorted by the cell of their first point (2)")
+                         "or sorted by the cell of their first point (2; the scene's default)")
+    ap.add_argument("--trace-mode", type=int, default=None,
+                    help="stress1 / scene: traversal in ray order (1) or over rays presorted by entry cell (2; the scene's "
+                         "default)")
     ap.add_argument("--scene-objects", type=int, default=8, help="unique objects (below 8 only for profiling)")
     ap.add_argument("--scene-instances", type=int, default=32)
     ap.add_argument("--scene-spp", type=int, default=4)

@@ -485,13 +485,17 @@ LSNIF_API int lsnif_set_variant8(lsnif_ctx *ctx, int v);
 
 /* Traversal kernel for later queries: 0 = one ray per thread, voxel by
  * voxel; 1 = persistent lanes (a lane whose ray finished takes the next ray
- * from a global counter) that cross bricks without occupied voxels in one
- * step. Both compute identical results. */
+ * from a global counter) that cross empty cubes of voxels in one step;
+ * 2 = the same lanes, handed the rays in the order of a counting sort by
+ * (object, Morton cell of the point where the ray enters the object's box,
+ * direction octant), so that shuffled rays (secondary rays, rays mixed
+ * across objects) walk neighbouring voxels together. All compute identical
+ * results; LSNIF_ERR_INVALID_ARG for any other mode. */
 LSNIF_API int lsnif_set_trace_mode(lsnif_ctx *ctx, int mode);
 
 /* Time every fused-kernel variant on `rays` (DEVICE buffers, `reps` BF16
  * queries each after one warm-up, CUDA events on `stream`, synchronous), keep
- * the fastest, then the other traversal kernel and the other groupings,
+ * the fastest, then the other traversal kernels and the other groupings,
  * keeping each if faster; then time every variant again with
  * FP16 queries and keep the fastest for LSNIF_FP16_FUSED (the FP16 kernel
  * holds no lo weights, so its shared memory and L1 differ). *chosen (may be

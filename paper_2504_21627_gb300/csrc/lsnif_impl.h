@@ -128,8 +128,8 @@ struct QueryScratch {
   int32_t *meta;     // [0] n_live, [1] n_tiles, [2] n_points, [3] tile cursor
   float *X;          // FP32 path: chunk of tiles x kTileM rows x ldx features
   int32_t *blk;      // coherent grouping: live rays and points per block of kGroupBlock rays, then offsets
-  int32_t *bins;     // spatial grouping: live rays per (object, cell) bin, then each bin's first position
-  int32_t *bin_sums; // spatial grouping: block sums of the bins' scan (kSpatialBins / 1024 + 2)
+  int32_t *bins;     // counting sorts: rays per bin, then each bin's first position (kBinsAlloc)
+  int32_t *bin_sums; // counting sorts: block sums of the bins' scan (kBinSumsAlloc)
   int32_t max_tiles; // upper bound on tiles (n / kTileM + n_slots)
   int32_t wmax;      // FP32 path: widest layer (hidden width or padded output)
 };
@@ -143,7 +143,8 @@ struct QueryLaunch {
   QueryScratch s;
   int *err;               // device error word
   cudaStream_t stream;
-  int trace_mode;         // traversal kernel: 0 one ray per thread, 1 persistent lanes
+  int trace_mode;         // traversal kernel: 0 one ray per thread, 1 persistent lanes, 2 persistent lanes
+                          // over rays presorted by (object, entry cell, direction octant)
   int group_mode;         // 0: live rays grouped by (object, k desc); 1: one object, original order kept;
                           // 2: grouped by object only, warps of consecutive rays kept together;
                           // 3: by object, then by the Morton cell of the first boundary point
@@ -152,6 +153,10 @@ struct QueryLaunch {
 
 constexpr int kGroupBlock = 4096;  // rays per block of the order-keeping grouping
 constexpr int64_t kSpatialBins = int64_t(1) << 21;  // spatial grouping: (object, cell) bins at most
+// bins and block sums the scratch holds for either counting sort (the
+// presorted traversal adds one bin for the rays that miss)
+constexpr int64_t kBinsAlloc = kSpatialBins + 1;
+constexpr int64_t kBinSumsAlloc = (kBinsAlloc + 1023) / 1024 + 1;
 
 // Spatial grouping: bits of a cell's Morton code, 3 m for 2^m cells per axis
 // of the unit cube -- m = 6 (64 per axis) where the objects' bins fit

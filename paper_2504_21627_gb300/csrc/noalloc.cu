@@ -103,13 +103,14 @@ extern "C" int lsnif_query_rays_noalloc(lsnif_ctx *ctx, const lsnif_rays *r, lsn
 
   // carve the static scratch; reject what does not fit
   const int64_t n = r->n;
-  const bool spatial = ctx->group_mode == 2;  // its bins take 8 MiB of the scratch
+  // the counting sorts' bins take 8 MiB of the scratch
+  const bool spatial = ctx->group_mode == 2 || ctx->trace_mode == 2;
   const int max_tiles = (int)(n / kTileM + n_slots + 1);
   const size_t need = al256((size_t)n * H * 12) + al256((size_t)n * 8) + al256((size_t)n) + al256((size_t)n * 4) +
                       al256((size_t)n * 2) +
                       al256((size_t)n * 4) + 3 * al256((size_t)n_slots * kBuckets * 4) +
                       al256((size_t)max_tiles * 12) + al256(64 * 4) + al256((size_t)(n / kGroupBlock + 2) * 8) +
-                      (spatial ? al256((size_t)kSpatialBins * 4) + al256((size_t)(kSpatialBins / 1024 + 2) * 4) : 0);
+                      (spatial ? al256((size_t)kBinsAlloc * 4) + al256((size_t)kBinSumsAlloc * 4) : 0);
   if (need > kNoAllocBytes)
     return fail(LSNIF_ERR_INVALID_ARG,
                 "lsnif_query_rays_noalloc: %lld rays need %zu bytes of scratch but the static scratch holds %zu "
@@ -138,8 +139,8 @@ extern "C" int lsnif_query_rays_noalloc(lsnif_ctx *ctx, const lsnif_rays *r, lsn
   s.meta = reinterpret_cast<int32_t *>(take(64 * 4));
   s.blk = reinterpret_cast<int32_t *>(take((size_t)(n / kGroupBlock + 2) * 8));
   if (spatial) {
-    s.bins = reinterpret_cast<int32_t *>(take((size_t)kSpatialBins * 4));
-    s.bin_sums = reinterpret_cast<int32_t *>(take((size_t)(kSpatialBins / 1024 + 2) * 4));
+    s.bins = reinterpret_cast<int32_t *>(take((size_t)kBinsAlloc * 4));
+    s.bin_sums = reinterpret_cast<int32_t *>(take((size_t)kBinSumsAlloc * 4));
   }
   s.X = nullptr;
   s.max_tiles = max_tiles;
@@ -155,7 +156,7 @@ extern "C" int lsnif_query_rays_noalloc(lsnif_ctx *ctx, const lsnif_rays *r, lsn
   q.err = ctx->d_err;
   q.stream = (cudaStream_t)stream;
   q.trace_mode = ctx->trace_mode;
-  q.group_mode = spatial ? 3 : ctx->group_mode == 1 ? (r->obj ? 2 : 1) : 0;
+  q.group_mode = ctx->group_mode == 2 ? 3 : ctx->group_mode == 1 ? (r->obj ? 2 : 1) : 0;
   q.single_slot = r->obj ? 0 : rep->slot;
   // The bucket counts must start at zero: launch_trace clears them on the
   // stream; the grouping kernel resets the cursors and the tile counter.

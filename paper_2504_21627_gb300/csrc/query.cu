@@ -90,6 +90,80 @@ __global__ void __launch_bounds__(256) trace_kernel(QueryLaunch q, int smem_hist
   }
 }
 
+// bits 0..7 of v moved to bits 0, 3, 6, ..., 21
+__device__ __forceinline__ uint32_t spread_bits3(uint32_t v) {
+  v &= 0xffu;
+  v = (v | (v << 8)) & 0x0300f00fu;
+  v = (v | (v << 4)) & 0x030c30c3u;
+  v = (v | (v << 2)) & 0x09249249u;
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// Presorted traversal (trace mode 2): before the persistent-lane kernel, a
+// counting sort hands it the rays in the order (object, Morton cell of the
+// point where the ray enters the object's unit cube, direction octant), so
+// the lanes of a warp walk neighbouring voxels in similar directions even
+// when the rays arrive shuffled (secondary rays, rays mixed across objects):
+// their distance-field and occupancy loads share cache lines and their step
+// counts are alike. Rays that miss their box or name an unknown object go to
+// one last bin; the traversal answers them as before. The key of each ray
+// is kept in q.s.dup (the traversal overwrites it later) and the order in
+// q.s.order (the grouping overwrites it later).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t presort_key(const QueryLaunch &q, int64_t i, int key_bits, uint32_t last) {
+  const uint32_t h = q.rays.obj ? q.rays.obj[i] : q.rays.single_handle;
+  const int s = slot_of(q.objs, q.n_slots, h);
+  if (s < 0) return last;
+  const DevObject &ob = q.objs[s];
+  float3 o, d;
+  float t0, t1;
+  int ea;
+  if (!(ob.kind == 0 && to_unit(ob, q.rays.ox[i], q.rays.oy[i], q.rays.oz[i], q.rays.dx[i], q.rays.dy[i],
+                                q.rays.dz[i], o, d) &&
+        unit_slab(o, d, q.rays.tmin[i], t0, t1, ea)))
+    return last;
+  const int m = key_bits / 3 - 1;  // cell bits per axis; 3 bits go to the octant
+  const float scale = (float)(1 << m);
+  const float e[3] = {fmaf(t0, d.x, o.x), fmaf(t0, d.y, o.y), fmaf(t0, d.z, o.z)};
+  uint32_t cell = 0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const uint32_t c = (uint32_t)min(max((int)(e[a] * scale), 0), (1 << m) - 1);
+    cell |= spread_bits3(c) << a;
+  }
+  const uint32_t oct = (d.x < 0.f ? 1u : 0u) | (d.y < 0.f ? 2u : 0u) | (d.z < 0.f ? 4u : 0u);
+  return ((uint32_t)s << key_bits) | (cell << 3) | oct;
+}
+
+__global__ void __launch_bounds__(256) presort_count_kernel(QueryLaunch q, int key_bits, uint32_t last) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool in = i < q.rays.n;
+  const uint32_t key = in ? presort_key(q, i, key_bits, last) : 0u;
+  if (in) q.s.dup[i] = key;
+  const unsigned active = __ballot_sync(0xffffffffu, in);
+  if (in) {
+    const unsigned peers = __match_any_sync(active, key);
+    if ((int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&q.s.bins[key], __popc(peers));
+  }
+}
+
+__global__ void __launch_bounds__(256) presort_scatter_kernel(QueryLaunch q) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const bool in = i < q.rays.n;
+  const uint32_t key = in ? q.s.dup[i] : 0u;
+  const unsigned active = __ballot_sync(0xffffffffu, in);
+  if (in) {
+    const unsigned peers = __match_any_sync(active, key);
+    const int leader = __ffs(peers) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(&q.s.bins[key], __popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    q.s.order[base + __popc(peers & ((1u << lane) - 1u))] = (int32_t)i;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Persistent-lane traversal: after each round of cells a warp hands a new
 // ray to every lane whose ray finished (global ray counter, warp-aggregated).
@@ -161,7 +235,8 @@ __device__ __forceinline__ int voxel_distance(const DevObject &ob, int x, int y,
   return __ldg(ob.dist + ((uint32_t)z * ob.V + (uint32_t)y) * ob.V + (uint32_t)x);
 }
 
-__global__ void __launch_bounds__(256) trace_pool_kernel(QueryLaunch q, int smem_hist, int steps_per_round) {
+__global__ void __launch_bounds__(256) trace_pool_kernel(QueryLaunch q, int smem_hist, int steps_per_round,
+                                                          const int32_t *__restrict__ perm) {
   extern __shared__ int sh_hist[];
   const int nb = q.n_slots * kBuckets;
   if (smem_hist) {
@@ -202,11 +277,12 @@ __global__ void __launch_bounds__(256) trace_pool_kernel(QueryLaunch q, int smem
       if (lane == leader) base = atomicAdd(counter, __popc(m));
       base = __shfl_sync(FULL, base, leader);
       if (need) {
-        const int64_t my = (int64_t)base + __popc(m & ((1u << lane) - 1u));
-        if (my >= n) {
+        const int64_t pos = (int64_t)base + __popc(m & ((1u << lane) - 1u));
+        if (pos >= n) {
           exhausted = true;
         } else {
-          // start ray `my`
+          // start ray `my` (the pos-th ray of the presorted order, if any)
+          const int64_t my = perm ? (int64_t)__ldg(perm + pos) : pos;
           R.i = my;
           const uint32_t h = q.rays.obj ? q.rays.obj[my] : q.rays.single_handle;
           R.s = slot_of(q.objs, q.n_slots, h);
@@ -669,15 +745,6 @@ __global__ void scan_add_kernel(int32_t *v, int64_t n, const int32_t *sums) {
 // ranges and tiles of scan_kernel (one bucket per object) hold as they are.
 // Rays of one bin land in any order; no result depends on it.
 // ---------------------------------------------------------------------------
-// bits 0..7 of v moved to bits 0, 3, 6, ..., 21
-__device__ __forceinline__ uint32_t spread_bits3(uint32_t v) {
-  v &= 0xffu;
-  v = (v | (v << 8)) & 0x0300f00fu;
-  v = (v | (v << 4)) & 0x030c30c3u;
-  v = (v | (v << 2)) & 0x09249249u;
-  return v;
-}
-
 // (object slot, Morton cell) bin of ray i, or -1 when it is not live
 __device__ __forceinline__ int spatial_bin(const QueryLaunch &q, int64_t i, int cell_bits) {
   if (q.s.k[i] == 0) return -1;
@@ -945,8 +1012,28 @@ cudaError_t launch_trace(const QueryLaunch &q, int *launches) {
     // ray -- unit-cube transform, slab test, first cell -- is the costly,
     // divergent part); 8, 32 and 64 cells per round took 0.76, 0.66 and
     // 0.61 ms on the 4M-ray torus query
-    trace_pool_kernel<<<grid, 256, smem, q.stream>>>(q, smem_hist, 64);
+    trace_pool_kernel<<<grid, 256, smem, q.stream>>>(q, smem_hist, 64, nullptr);
     *launches += 1;
+    return cudaGetLastError();
+  }
+  if (q.trace_mode == 2) {
+    const int key_bits = spatial_cell_bits(q.n_slots);
+    const uint32_t last = (uint32_t)q.n_slots << key_bits;  // rays the traversal answers as misses
+    const int64_t nbins = (int64_t)last + 1;
+    const unsigned blocks = (unsigned)std::max<int64_t>((q.rays.n + 255) / 256, 1);
+    cudaMemsetAsync(q.s.meta + 4, 0, sizeof(int32_t), q.stream);
+    cudaError_t e = cudaMemsetAsync(q.s.bins, 0, (size_t)nbins * 4, q.stream);
+    if (e != cudaSuccess) return e;
+    presort_count_kernel<<<blocks, 256, 0, q.stream>>>(q, key_bits, last);
+    e = launch_exclusive_scan(q.s.bins, nbins, q.s.bin_sums, q.stream);
+    if (e != cudaSuccess) return e;
+    presort_scatter_kernel<<<blocks, 256, 0, q.stream>>>(q);
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = (int)std::min<int64_t>((q.rays.n + 255) / 256, (int64_t)sms * 8);
+    trace_pool_kernel<<<grid, 256, smem, q.stream>>>(q, smem_hist, 64, q.s.order);
+    *launches += 6;
     return cudaGetLastError();
   }
   const int grid = grid_for(q.rays.n, 256, 152 * 16);

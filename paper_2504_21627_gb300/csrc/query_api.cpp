@@ -36,8 +36,8 @@ size_t lsnif::workspace_bytes(int64_t n, int H, int n_slots, int n_in) {
   size_t b = al((size_t)n * H * 12) + al((size_t)n * 8) + al((size_t)n) + al((size_t)n * 4) + al((size_t)n * 2) +
              al((size_t)n * 4) +
              3 * al((size_t)n_slots * kBuckets * 4) + al((size_t)mt * 12) + al(64 * 4) +
-             al((size_t)(n / kGroupBlock + 2) * 8) + al((size_t)kSpatialBins * 4) +
-             al((size_t)(kSpatialBins / 1024 + 2) * 4);
+             al((size_t)(n / kGroupBlock + 2) * 8) + al((size_t)kBinsAlloc * 4) +
+             al((size_t)kBinSumsAlloc * 4);
   if (n_in > 0) b += al((size_t)std::min(mt, kChunkTiles) * kTileM * n_in * 4);
   return b;
 }
@@ -94,8 +94,8 @@ static QueryScratch carve(Workspace *ws, int64_t n, int H, int n_slots, int n_in
   s.tiles = c.take<int32_t>((size_t)mt * 12);
   s.meta = c.take<int32_t>(64 * 4);
   s.blk = c.take<int32_t>((size_t)(N / kGroupBlock + 2) * 8);
-  s.bins = c.take<int32_t>((size_t)kSpatialBins * 4);
-  s.bin_sums = c.take<int32_t>((size_t)(kSpatialBins / 1024 + 2) * 4);
+  s.bins = c.take<int32_t>((size_t)kBinsAlloc * 4);
+  s.bin_sums = c.take<int32_t>((size_t)kBinSumsAlloc * 4);
   s.X = ws->cap_nin > 0 ? c.take<float>((size_t)std::min(mt, kChunkTiles) * kTileM * ws->cap_nin * 4) : nullptr;
   s.max_tiles = max_tiles_for(n, n_slots);
   return s;
@@ -657,7 +657,7 @@ extern "C" int lsnif_autotune(lsnif_ctx *ctx, const lsnif_rays *rays, int reps, 
   int best_t = ctx->trace_mode, best_g = ctx->group_mode;
   if (rc == LSNIF_OK) {
     ctx->fused_variant = best;
-    for (int t = 0; t < 2 && rc == LSNIF_OK; ++t) {
+    for (int t = 0; t < 3 && rc == LSNIF_OK; ++t) {
       if (t == best_t) continue;
       ctx->trace_mode = t;
       float ms = 0.f;
@@ -722,7 +722,7 @@ extern "C" int lsnif_set_group_mode(lsnif_ctx *ctx, int mode) {
 }
 
 extern "C" int lsnif_set_trace_mode(lsnif_ctx *ctx, int mode) {
-  if (!ctx || (mode != 0 && mode != 1)) return fail(LSNIF_ERR_INVALID_ARG, "lsnif_set_trace_mode: bad mode %d", mode);
+  if (!ctx || mode < 0 || mode > 2) return fail(LSNIF_ERR_INVALID_ARG, "lsnif_set_trace_mode: bad mode %d", mode);
   ctx->trace_mode = mode;
   return LSNIF_OK;
 }

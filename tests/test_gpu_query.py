@@ -427,7 +427,8 @@ def test_multi_object_batch_equals_single_object_queries(ctx, sphere, torus):
     both = np.ascontiguousarray(both[:, perm])
     handles = np.ascontiguousarray(handles[perm])
     keep = ctx.tuning()
-    for gm in (0, 1, 2):
+    for tm, gm in ((1, 0), (1, 1), (2, 2)):
+        ctx.set_trace_mode(tm)
         ctx.set_group_mode(gm)
         for prec in (lsnif.FP32_PLAIN, lsnif.BF16_FUSED):
             mixed = ctx.query_rays(_cuda(both), obj_per_ray=_cuda(handles.view(np.int32)), precision=prec)
@@ -438,7 +439,8 @@ def test_multi_object_batch_equals_single_object_queries(ctx, sphere, torus):
             for f in ("hit", "t", "mat"):
                 m = getattr(mixed, f).cpu().numpy()[inv]
                 single = np.concatenate([getattr(a, f).cpu().numpy(), getattr(b, f).cpu().numpy()])
-                assert np.array_equal(m, single), (gm, prec, f)
+                assert np.array_equal(m, single), (tm, gm, prec, f)
+    ctx.set_trace_mode(keep[1])
     ctx.set_group_mode(keep[2])
 
 
@@ -570,7 +572,7 @@ def test_tuning_choices_give_identical_results(ctx, torus):
     ref = {}
     keep = ctx.tuning()
     for prec in (lsnif.FP32_PLAIN, lsnif.BF16_FUSED, lsnif.FP16_FUSED):
-        for tm in (0, 1):
+        for tm in (0, 1, 2):
             for gm in (0, 1, 2):
                 for v in (range(len(lsnif.Context.variants())) if prec != lsnif.FP32_PLAIN else [0]):
                     ctx.set_trace_mode(tm)
@@ -592,9 +594,11 @@ def test_tuning_choices_give_identical_results(ctx, torus):
 
 def test_spatial_grouping_is_independent_of_the_ray_order(ctx, torus):
     """Group mode 2 sorts live rays by the cell of their first boundary
-    point, so tiles are built from the same neighbourhoods whatever order
-    the rays arrive in. Shuffled rays must give, ray for ray, the bits that
-    the ordered rays give under every grouping."""
+    point, and trace mode 2 sorts all rays by their box entry cell and
+    direction before the traversal, so the kernels see the same
+    neighbourhoods whatever order the rays arrive in. Shuffled rays must
+    give, ray for ray, the bits that the ordered rays give under every
+    traversal and grouping."""
     cam = I.seeded_camera(2)
     base = np.ascontiguousarray(I.rays_pinhole(cam, px0=400, py0=600, w=512, h=384))
     perm = np.random.default_rng(17).permutation(base.shape[1])
@@ -606,13 +610,15 @@ def test_spatial_grouping_is_independent_of_the_ray_order(ctx, torus):
         ref = ctx.query_rays(_cuda(base), obj=torus["h"], precision=prec, logits=True)
         ref = (ref.hit.cpu(), ref.t.cpu(), ref.mat.cpu(), ref.logits.cpu())
         assert ref[0].sum() > 10000
-        for gm in (0, 1, 2):
+        for tm, gm in ((1, 0), (1, 1), (1, 2), (2, 1), (2, 2), (0, 2)):
+            ctx.set_trace_mode(tm)
             ctx.set_group_mode(gm)
             out = ctx.query_rays(shuffled, obj=torus["h"], precision=prec, logits=True)
             ctx.check()
             got = (out.hit.cpu()[inv], out.t.cpu()[inv], out.mat.cpu()[inv], out.logits.cpu()[inv])
             for a, b in zip(ref, got):
-                assert torch.equal(torch.nan_to_num(a, nan=-1e30), torch.nan_to_num(b, nan=-1e30)), (prec, gm)
+                assert torch.equal(torch.nan_to_num(a, nan=-1e30), torch.nan_to_num(b, nan=-1e30)), (prec, tm, gm)
+    ctx.set_trace_mode(keep[1])
     ctx.set_group_mode(keep[2])
 
 
@@ -633,7 +639,8 @@ def test_grouping_with_many_objects_matches_oracle():
         h, orc, p = _make(c, mesh, cfg, seed=3)
         o = dict(h=h, orc=orc, p=p, mesh=mesh, cfg=cfg)
         rays = I.rays_sphere_to_box(3000, 3.0, orc.bmin, orc.bmax, seed=21)
-        for gm in (0, 2):   # 2: 126 objects take 4096 cells each
+        for tm, gm in ((1, 0), (2, 2)):   # 126 objects: 4096 cells each
+            c.set_trace_mode(tm)
             c.set_group_mode(gm)
             _query_compare(c, o, rays, lsnif.FP32_PLAIN, fp32_tol(cfg))
             _query_compare(c, o, rays, lsnif.FP16_FUSED, FP16_TOL + fp32_tol(cfg))
@@ -658,7 +665,7 @@ def test_autotune_picks_valid_choices_and_keeps_results(ctx, torus):
     ctx.check()
     assert 0 <= v < len(lsnif.Context.variants())
     tv, tm, gm = ctx.tuning()
-    assert tv == v and tm in (0, 1) and gm in (0, 1, 2)
+    assert tv == v and tm in (0, 1, 2) and gm in (0, 1, 2)
     for prec in (lsnif.BF16_FUSED, lsnif.FP16_FUSED):
         out = ctx.query_rays(rays, obj=torus["h"], precision=prec, logits=True)
         ctx.check()

@@ -31,7 +31,7 @@ def test_noalloc_query_matches_the_regular_query_twice_in_a_row():
         obj = ctx.load_object(mesh, cfg, tables=params.tables, mlp=params.packed_mlp())
         cam = I.seeded_camera(2, width=256, height=256)
         rays = torch.from_numpy(I.rays_pinhole(cam)).cuda()            # 65536 rays
-        for trace_mode, group_mode in ((1, 0), (0, 1), (1, 2)):
+        for trace_mode, group_mode in ((1, 0), (0, 1), (1, 2), (2, 1)):
             ctx.set_trace_mode(trace_mode)
             ctx.set_group_mode(group_mode)
             ref = ctx.query_rays(rays, obj=obj, precision=lsnif.BF16_FUSED)
@@ -66,7 +66,8 @@ def test_noalloc_query_with_an_object_per_ray():
         lo, hi = np.full(3, -1.1, np.float32), np.full(3, 1.1, np.float32)
         rays = torch.from_numpy(I.rays_sphere_to_box(20000, 3.0, lo, hi, seed=41)).cuda()
         per_ray = torch.from_numpy(np.asarray(objs, np.uint32)[np.arange(20000) % 2]).cuda()
-        for group_mode in (1, 2):
+        for trace_mode, group_mode in ((1, 1), (2, 2)):
+            ctx.set_trace_mode(trace_mode)
             ctx.set_group_mode(group_mode)
             ref = ctx.query_rays(rays, obj_per_ray=per_ray, precision=lsnif.BF16_FUSED)
             ctx.check()
