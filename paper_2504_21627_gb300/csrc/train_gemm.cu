@@ -66,11 +66,6 @@ __device__ __forceinline__ void split2(float a, float b, uint32_t &hi, uint32_t 
   lo = *reinterpret_cast<const uint32_t *>(&l);
 }
 
-__device__ __forceinline__ uint16_t bf16_bits(float x) {
-  const __nv_bfloat16 h = __float2bfloat16_rn(x);
-  return *reinterpret_cast<const uint16_t *>(&h);
-}
-
 // byte offset of element (row, k) in a K = 64 core-matrix tile
 __device__ __forceinline__ uint32_t tile_off(int row, int k) {
   return (uint32_t)(row >> 3) * 1024u + (uint32_t)(k >> 3) * 128u + (uint32_t)(row & 7) * 16u +
@@ -100,146 +95,106 @@ struct GemmArgs {
 // must stay 0), rows past the operand's end are not written (they only feed
 // rows or columns of the product that are not stored). kc: X(row, k) =
 // P[row ld + k] (contiguous along k); else X(row, k) = P[k ld + row]
-// (contiguous along rows: the transposed read of dY^T, X^T and W^T). A chunk
-// of one operand is at most 128 rows x 64 = 2048 items of 4 elements, so each
-// of the 256 threads holds at most kBatch of them. Staging is split in two:
-// stage_load issues a thread's 16-byte loads into registers, stage_store
-// converts and writes them, so that the loads of chunk c + 1 are in flight
-// while chunk c is multiplied.
-constexpr int kBatch = 8;
+// (contiguous along rows: the transposed read of dY^T, X^T and W^T).
+//
+// An item is one row's 8 consecutive k -- the 16 bytes that row holds in one
+// core matrix -- so a thread converts it to two 16-byte words (hi, lo) and
+// stores each with one instruction. Items are laid out over a warp so that
+// each quarter-warp stores one whole 128-byte core matrix (8 consecutive
+// rows, the same k), which touches every shared-memory bank once:
+//   kc:   a warp's 32 items are 8 rows x 4 groups of k; a thread reads its
+//         row's 8 values as two 16-byte loads;
+//   else: a warp's 32 items are 32 consecutive rows at one group of k; a
+//         thread reads its 8 values one k at a time, and each of those loads
+//         reads 128 consecutive bytes across the warp.
+// (Storing 2 or 4 bytes per element along the other axis of a core matrix
+// put 8 lanes of a warp on one bank.) A chunk of one operand is at most 128
+// rows x 8 groups = 1024 items, kItems per thread. Staging is split in two:
+// stage_load issues a thread's loads into registers, stage_store converts and
+// writes them, so that the loads of chunk c + 1 are in flight while chunk c
+// is multiplied.
+constexpr int kItems = 4;
 
-__device__ __forceinline__ void put4_k(uint8_t *hi, uint8_t *lo, int row, int k, const float (&v)[4]) {
-  uint32_t h0, l0, h1, l1;
-  split2(v[0], v[1], h0, l0);
-  split2(v[2], v[3], h1, l1);
-  const uint32_t o = tile_off(row, k);
-  *reinterpret_cast<uint2 *>(hi + o) = make_uint2(h0, h1);
-  *reinterpret_cast<uint2 *>(lo + o) = make_uint2(l0, l1);
-}
-
-__device__ __forceinline__ void put4_rows(uint8_t *hi, uint8_t *lo, int row, int k, const float (&v)[4]) {
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const uint16_t h = bf16_bits(v[j]);
-    const uint32_t o = tile_off(row + j, k);
-    *reinterpret_cast<uint16_t *>(hi + o) = h;
-    *reinterpret_cast<uint16_t *>(lo + o) = bf16_bits(v[j] - __uint_as_float((uint32_t)h << 16));
+__device__ __forceinline__ void item_rk(bool kc, int it, int &row, int &k) {
+  if (kc) {
+    row = (it & 7) + ((it >> 6) << 3);
+    k = ((it >> 3) & 7) * 8;
+  } else {
+    row = (it & 31) + ((it >> 8) << 5);
+    k = ((it >> 5) & 7) * 8;
   }
 }
 
-// item it of a chunk: (row, k) of its first element
-__device__ __forceinline__ void item_pos(bool kc, int it, int rows4, int &row, int &k) {
-  if (kc) { row = it >> 4; k = (it & 15) * 4; }
-  else { k = it / rows4; row = (it - k * rows4) * 4; }
+__device__ __forceinline__ int chunk_items(bool kc, int rows) {
+  return kc ? ((rows + 7) & ~7) * 8 : ((rows + 31) & ~31) * 8;
 }
 
-__device__ __forceinline__ void stage_load(float (&v)[kBatch][4], const float *P, int ld, bool kc, int r0,
+__device__ __forceinline__ void stage_load(float (&v)[kItems][8], const float *P, int ld, bool kc, int r0,
                                            int tile_rows, int nrows, int k0, int kend, int tid) {
   const int rows = min(nrows - r0, tile_rows);
+  const int items = chunk_items(kc, rows);
   const bool vec = ((ld & 3) == 0) && ((reinterpret_cast<uintptr_t>(P) & 15) == 0);
-  const int rows4 = (rows + 3) >> 2;
-  const int items = kc ? rows * (kGK / 4) : rows4 * kGK;
 #pragma unroll
-  for (int b = 0; b < kBatch; ++b) {
+  for (int b = 0; b < kItems; ++b) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[b][j] = 0.f;
     const int it = tid + b * kGThreads;
-    v[b][0] = v[b][1] = v[b][2] = v[b][3] = 0.f;
     if (it >= items) continue;
     int row, k;
-    item_pos(kc, it, rows4, row, k);
+    item_rk(kc, it, row, k);
+    if (row >= rows) continue;
     const int gk = k0 + k;
     if (kc) {
       const float *src = P + (int64_t)(r0 + row) * ld + gk;
-      if (vec && gk + 3 < kend) {
-        const float4 f = __ldg(reinterpret_cast<const float4 *>(src));
-        v[b][0] = f.x; v[b][1] = f.y; v[b][2] = f.z; v[b][3] = f.w;
-      } else {
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
-          if (gk + j < kend) v[b][j] = __ldg(src + j);
+      for (int h = 0; h < 2; ++h) {
+        if (vec && gk + 4 * h + 3 < kend) {
+          const float4 f = __ldg(reinterpret_cast<const float4 *>(src + 4 * h));
+          v[b][4 * h + 0] = f.x; v[b][4 * h + 1] = f.y; v[b][4 * h + 2] = f.z; v[b][4 * h + 3] = f.w;
+        } else {
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            if (gk + 4 * h + j < kend) v[b][4 * h + j] = __ldg(src + 4 * h + j);
+        }
       }
-    } else if (gk < kend) {
+    } else {
       const float *src = P + (int64_t)gk * ld + r0 + row;
-      if (vec && row + 3 < rows) {
-        const float4 f = __ldg(reinterpret_cast<const float4 *>(src));
-        v[b][0] = f.x; v[b][1] = f.y; v[b][2] = f.z; v[b][3] = f.w;
-      } else {
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
-          if (row + j < rows) v[b][j] = __ldg(src + j);
-      }
+      for (int j = 0; j < 8; ++j)
+        if (gk + j < kend) v[b][j] = __ldg(src + (int64_t)j * ld);
     }
   }
 }
 
-__device__ __forceinline__ void stage_store(uint8_t *hi, uint8_t *lo, const float (&v)[kBatch][4], bool kc, int r0,
+__device__ __forceinline__ void stage_store(uint8_t *hi, uint8_t *lo, const float (&v)[kItems][8], bool kc, int r0,
                                             int tile_rows, int nrows, int tid) {
   const int rows = min(nrows - r0, tile_rows);
-  const int rows4 = (rows + 3) >> 2;
-  const int items = kc ? rows * (kGK / 4) : rows4 * kGK;
+  const int items = chunk_items(kc, rows);
 #pragma unroll
-  for (int b = 0; b < kBatch; ++b) {
+  for (int b = 0; b < kItems; ++b) {
     const int it = tid + b * kGThreads;
     if (it >= items) break;
     int row, k;
-    item_pos(kc, it, rows4, row, k);
-    if (kc) put4_k(hi, lo, row, k, v[b]);
-    else put4_rows(hi, lo, row, k, v[b]);
+    item_rk(kc, it, row, k);
+    if (row >= rows) continue;
+    uint4 h, l;
+    split2(v[b][0], v[b][1], h.x, l.x);
+    split2(v[b][2], v[b][3], h.y, l.y);
+    split2(v[b][4], v[b][5], h.z, l.z);
+    split2(v[b][6], v[b][7], h.w, l.w);
+    const uint32_t o = tile_off(row, k);  // k is a multiple of 8: 16-byte aligned
+    *reinterpret_cast<uint4 *>(hi + o) = h;
+    *reinterpret_cast<uint4 *>(lo + o) = l;
   }
 }
 
-// Both operands of a chunk staged one after the other, each thread issuing
-// its (at most kBatch) loads of an operand before it converts any: the
-// short products' form, which holds one operand's registers at a time.
+// One operand of a chunk loaded and stored before the other: the short
+// products' form, which holds one operand's registers at a time.
 __device__ __forceinline__ void stage(uint8_t *hi, uint8_t *lo, const float *P, int ld, bool kc, int r0,
                                       int tile_rows, int nrows, int k0, int kend, int tid) {
-  const int rows = min(nrows - r0, tile_rows);
-  const bool vec = ((ld & 3) == 0) && ((reinterpret_cast<uintptr_t>(P) & 15) == 0);
-  // items of 4 elements: along k (kc) or along rows (otherwise)
-  const int rows4 = (rows + 3) >> 2;
-  const int items = kc ? rows * (kGK / 4) : rows4 * kGK;
-  for (int i0 = tid; i0 < items; i0 += kGThreads * kBatch) {
-    float v[kBatch][4];
-    int rr[kBatch], kk[kBatch];
-#pragma unroll
-    for (int b = 0; b < kBatch; ++b) {
-      const int it = i0 + b * kGThreads;
-      int row, k;
-      if (kc) { row = it >> 4; k = (it & 15) * 4; }
-      else { k = it / rows4; row = (it - k * rows4) * 4; }
-      rr[b] = row;
-      kk[b] = k;
-      v[b][0] = v[b][1] = v[b][2] = v[b][3] = 0.f;
-      if (it >= items) continue;
-      const int gk = k0 + k;
-      if (kc) {
-        const float *src = P + (int64_t)(r0 + row) * ld + gk;
-        if (vec && gk + 3 < kend) {
-          const float4 f = __ldg(reinterpret_cast<const float4 *>(src));
-          v[b][0] = f.x; v[b][1] = f.y; v[b][2] = f.z; v[b][3] = f.w;
-        } else {
-#pragma unroll
-          for (int j = 0; j < 4; ++j)
-            if (gk + j < kend) v[b][j] = __ldg(src + j);
-        }
-      } else if (gk < kend) {
-        const float *src = P + (int64_t)gk * ld + r0 + row;
-        if (vec && row + 3 < rows) {
-          const float4 f = __ldg(reinterpret_cast<const float4 *>(src));
-          v[b][0] = f.x; v[b][1] = f.y; v[b][2] = f.z; v[b][3] = f.w;
-        } else {
-#pragma unroll
-          for (int j = 0; j < 4; ++j)
-            if (row + j < rows) v[b][j] = __ldg(src + j);
-        }
-      }
-    }
-#pragma unroll
-    for (int b = 0; b < kBatch; ++b) {
-      if (i0 + b * kGThreads >= items) break;
-      if (kc) put4_k(hi, lo, rr[b], kk[b], v[b]);
-      else put4_rows(hi, lo, rr[b], kk[b], v[b]);
-    }
-  }
+  float v[kItems][8];
+  stage_load(v, P, ld, kc, r0, tile_rows, nrows, k0, kend, tid);
+  stage_store(hi, lo, v, kc, r0, tile_rows, nrows, tid);
 }
 
 // One CTA: rows [blockIdx.x 128, +128) x columns [blockIdx.y n_ch, +n_ch) of
@@ -283,7 +238,7 @@ __global__ void __launch_bounds__(kGThreads) tc_gemm_kernel(const __grid_constan
   const uint32_t tmem = *s_tmem;
   const uint32_t idesc = idesc_bf16(n_ch);
 
-  float va[kBatch][4], vb[kBatch][4];  // PIPE only
+  float va[kItems][8], vb[kItems][8];  // PIPE only
   if (PIPE && nchunks > 0) {
     stage_load(va, g.A, g.lda, a_kc, m0, kGM, g.M, kb, ke, tid);
     stage_load(vb, g.B, g.ldb, b_kc, n0, n_ch, g.N, kb, ke, tid);
