@@ -303,8 +303,10 @@ LSNIF_API int lsnif_set_host_mode(lsnif_ctx *ctx, int mode);
  * previous call's contents, so calls that overlap on the GPU (other
  * streams, other threads, other contexts of the process) race: serialise
  * them. A batch whose scratch does not fit (about 230 bytes per ray for H =
- * 18, i.e. some 140k rays) is rejected with LSNIF_ERR_INVALID_ARG and a
- * message giving the sizes. Errors otherwise as lsnif_query_rays. */
+ * 18, i.e. some 140k rays; when trace mode 2 or group mode 2 is chosen their
+ * counting sort takes 8 MiB of the array first, leaving room for about
+ * 100k) is rejected with LSNIF_ERR_INVALID_ARG and a message giving the
+ * sizes. Errors otherwise as lsnif_query_rays. */
 LSNIF_API int lsnif_query_rays_noalloc(lsnif_ctx *ctx, const lsnif_rays *rays, lsnif_hits *hits, void *stream);
 
 /* ---- instanced scenes (Sec. 4 wavefront integration, Sec. 6 instancing) -- */
